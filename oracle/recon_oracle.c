@@ -1,0 +1,771 @@
+/*
+ * recon_oracle.c -- plain CPU FP64 oracle of the displacement-potential solve
+ * of "Nonlinear reconstruction" (Zhu et al. 2016, arXiv:1611.09638).
+ *
+ * TEST INFRASTRUCTURE ONLY: the slow, obviously-correct reference the CUDA
+ * library is checked against.  Single-threaded, FP64, plain loops in
+ * ascending index order, no blocking, no fusion.  Only tests, the smoke check
+ * and the benchmark's CPU-baseline leg may load it.  It shares no code with
+ * the CUDA library.
+ *
+ * The method, step by step (Sec. II moving-mesh iteration; App. A):
+ *   init  rho_bar = mean(rho); tracer c has mass w_c = rho_c / rho_bar at
+ *         curvilinear coordinate xi_c = c (its grid node); phi = 0.
+ *   step  1. m = CIC deposit of the tracers (mass per curvilinear cell, the
+ *            paper's rho sqrt(g); Sec. IV "displace ... then assign to a
+ *            uniform grid").
+ *         2. triad e = I + Hess(phi), sqrt_g = det e, lambda0 = min eig e
+ *            (Eq. mapping; App. A).
+ *         3. Sigma = 1 - m, limiters C(lambda0) and E(sqrt_g, Sigma), source
+ *            s = S(Sigma + C + E) - mean (App. A, Eq. elliptic).
+ *         4. R = rms(s); stop if R <= tol_out ("until the mass per volume
+ *            element is approximately constant").
+ *         5. with x ~ xi the operator is div(m grad .); a = max(m, a_min);
+ *            solve L(a) phidot = s by multigrid V-cycles (App. A).
+ *         6. dphi = S phidot (App. A, Delta phi = S phidot), mean removed.
+ *         7. step limiter: largest alpha = 2^-k keeping I + Hess(phi + alpha
+ *            dphi) positive definite and the move below d_max cells (Sec. II:
+ *            positive definiteness via smoothing and grid limiters).
+ *         8. phi += alpha dphi (phi = sum of the increments, Sec. II / App. A);
+ *            the mesh moves by grad dphi in Eulerian space, so every tracer
+ *            moves in xi by -alpha e^-1 grad dphi (Sec. IV "displace the
+ *            particles by the negative displacement", with the triad e of
+ *            the current map so that tracers stay on the mesh phi defines).
+ *   out   delta_r = -Laplacian phi (Sec. II, Eq. rec); x = xi + grad phi.
+ */
+#include "recon_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_E_INVALID (-1)
+#define ORC_E_NOMEM (-2)
+#define ORC_E_LIMITER (-5)
+
+/* ------------------------------------------------------------------ grid */
+
+static long wrapi(long i, long n) {
+    long r = i % n;
+    return r < 0 ? r + n : r;
+}
+
+static size_t at(const int n[3], long i, long j, long k) {
+    return ((size_t)wrapi(i, n[0]) * (size_t)n[1] + (size_t)wrapi(j, n[1])) * (size_t)n[2] +
+           (size_t)wrapi(k, n[2]);
+}
+
+static size_t ncells(const int n[3]) { return (size_t)n[0] * (size_t)n[1] * (size_t)n[2]; }
+
+static int is_pow2_ge(int v, int lo) { return v >= lo && (v & (v - 1)) == 0; }
+
+static int dims_ok(const int n[3], int lo) {
+    return is_pow2_ge(n[0], lo) && is_pow2_ge(n[1], lo) && is_pow2_ge(n[2], lo);
+}
+
+/* ------------------------------------------------------------ CIC deposit */
+
+/* Cloud-in-cell weights of a coordinate along one axis: node index i0 with
+ * weight 1-f and node i0+1 with weight f, after periodic wrapping. */
+static void cic_axis(double x, int n, long* i0, double* f) {
+    double u = x - (double)n * floor(x / (double)n); /* into [0, n] */
+    double fl = floor(u);
+    *f = u - fl;
+    long i = (long)fl;
+    if (i >= n) i -= n;
+    *i0 = i;
+}
+
+int orc_cic_deposit(const int n[3], const double* x, const double* w, int64_t np,
+                    double* out) {
+    if (!n || !dims_ok(n, 1) || (!x && np > 0) || !out || np < 0) return ORC_E_INVALID;
+    memset(out, 0, ncells(n) * sizeof(double));
+    for (int64_t p = 0; p < np; ++p) {
+        long i0[3];
+        double f[3];
+        for (int a = 0; a < 3; ++a) cic_axis(x[3 * p + a], n[a], &i0[a], &f[a]);
+        double wp = w ? w[p] : 1.0;
+        for (int di = 0; di < 2; ++di)
+            for (int dj = 0; dj < 2; ++dj)
+                for (int dk = 0; dk < 2; ++dk) {
+                    double wx = di ? f[0] : 1.0 - f[0];
+                    double wy = dj ? f[1] : 1.0 - f[1];
+                    double wz = dk ? f[2] : 1.0 - f[2];
+                    out[at(n, i0[0] + di, i0[1] + dj, i0[2] + dk)] += wp * (wx * wy * wz);
+                }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------ operators */
+
+int orc_apply_L(const int n[3], const double h[3], const double* a, const double* u,
+                double* out) {
+    if (!n || !h || !a || !u || !out) return ORC_E_INVALID;
+    for (long i = 0; i < n[0]; ++i)
+        for (long j = 0; j < n[1]; ++j)
+            for (long k = 0; k < n[2]; ++k) {
+                size_t c = at(n, i, j, k);
+                double acc = 0.0;
+                for (int ax = 0; ax < 3; ++ax) {
+                    long di = ax == 0, dj = ax == 1, dk = ax == 2;
+                    size_t pl = at(n, i + di, j + dj, k + dk);
+                    size_t mi = at(n, i - di, j - dj, k - dk);
+                    double ap = 0.5 * (a[c] + a[pl]);
+                    double am = 0.5 * (a[c] + a[mi]);
+                    acc += (ap * (u[pl] - u[c]) - am * (u[c] - u[mi])) / (h[ax] * h[ax]);
+                }
+                out[c] = acc;
+            }
+    return 0;
+}
+
+int orc_rbgs_sweep(const int n[3], const double h[3], const double* a, const double* f,
+                   double* u) {
+    if (!n || !h || !a || !f || !u) return ORC_E_INVALID;
+    for (int colour = 0; colour < 2; ++colour)
+        for (long i = 0; i < n[0]; ++i)
+            for (long j = 0; j < n[1]; ++j)
+                for (long k = 0; k < n[2]; ++k) {
+                    if ((i + j + k) % 2 != colour) continue;
+                    size_t c = at(n, i, j, k);
+                    double diag = 0.0, off = 0.0;
+                    for (int ax = 0; ax < 3; ++ax) {
+                        long di = ax == 0, dj = ax == 1, dk = ax == 2;
+                        size_t pl = at(n, i + di, j + dj, k + dk);
+                        size_t mi = at(n, i - di, j - dj, k - dk);
+                        double ap = 0.5 * (a[c] + a[pl]) / (h[ax] * h[ax]);
+                        double am = 0.5 * (a[c] + a[mi]) / (h[ax] * h[ax]);
+                        diag += ap + am;
+                        off += ap * u[pl] + am * u[mi];
+                    }
+                    /* L u = off - diag u = f at this node */
+                    u[c] = (off - f[c]) / diag;
+                }
+    return 0;
+}
+
+static void coarse_dims(const int n[3], int nc[3]) {
+    for (int a = 0; a < 3; ++a) nc[a] = n[a] > 4 ? n[a] / 2 : n[a];
+}
+
+int orc_restrict(const int n[3], const double* fine, double* coarse) {
+    if (!n || !fine || !coarse) return ORC_E_INVALID;
+    int nc[3];
+    coarse_dims(n, nc);
+    int cz[3] = {n[0] > 4, n[1] > 4, n[2] > 4};
+    for (long I = 0; I < nc[0]; ++I)
+        for (long J = 0; J < nc[1]; ++J)
+            for (long K = 0; K < nc[2]; ++K) {
+                double acc = 0.0;
+                for (int oi = -cz[0]; oi <= cz[0]; ++oi)
+                    for (int oj = -cz[1]; oj <= cz[1]; ++oj)
+                        for (int ok = -cz[2]; ok <= cz[2]; ++ok) {
+                            /* weights 1/4, 1/2, 1/4 along coarsened axes, 1 otherwise */
+                            double wi = cz[0] ? (oi == 0 ? 0.5 : 0.25) : 1.0;
+                            double wj = cz[1] ? (oj == 0 ? 0.5 : 0.25) : 1.0;
+                            double wk = cz[2] ? (ok == 0 ? 0.5 : 0.25) : 1.0;
+                            long fi = (cz[0] ? 2 * I : I) + oi;
+                            long fj = (cz[1] ? 2 * J : J) + oj;
+                            long fk = (cz[2] ? 2 * K : K) + ok;
+                            acc += wi * wj * wk * fine[at(n, fi, fj, fk)];
+                        }
+                coarse[at(nc, I, J, K)] = acc;
+            }
+    return 0;
+}
+
+/* Linear interpolation stencil of fine index i along one axis: up to two
+ * coarse indices with weights. */
+static int prolong_axis(long i, int coarsened, long idx[2], double wt[2]) {
+    if (!coarsened) {
+        idx[0] = i;
+        wt[0] = 1.0;
+        return 1;
+    }
+    if (i % 2 == 0) {
+        idx[0] = i / 2;
+        wt[0] = 1.0;
+        return 1;
+    }
+    idx[0] = (i - 1) / 2;
+    idx[1] = (i + 1) / 2;
+    wt[0] = wt[1] = 0.5;
+    return 2;
+}
+
+int orc_prolong_add(const int n[3], const double* coarse, double* fine) {
+    if (!n || !coarse || !fine) return ORC_E_INVALID;
+    int nc[3];
+    coarse_dims(n, nc);
+    for (long i = 0; i < n[0]; ++i)
+        for (long j = 0; j < n[1]; ++j)
+            for (long k = 0; k < n[2]; ++k) {
+                long ii[2], jj[2], kk[2];
+                double wi[2], wj[2], wk[2];
+                int ni = prolong_axis(i, n[0] > 4, ii, wi);
+                int nj = prolong_axis(j, n[1] > 4, jj, wj);
+                int nk = prolong_axis(k, n[2] > 4, kk, wk);
+                double acc = 0.0;
+                for (int p = 0; p < ni; ++p)
+                    for (int q = 0; q < nj; ++q)
+                        for (int r = 0; r < nk; ++r)
+                            acc += wi[p] * wj[q] * wk[r] * coarse[at(nc, ii[p], jj[q], kk[r])];
+                fine[at(n, i, j, k)] += acc;
+            }
+    return 0;
+}
+
+int orc_apply_S(const int n[3], double s_side, const double* u, double* out) {
+    if (!n || !u || !out || u == out) return ORC_E_INVALID;
+    /* weights (s_side, 1 - 2 s_side, s_side) along every axis: a weighted mean
+     * over the 3x3x3 block of nearest neighbours */
+    double w[3] = {s_side, 1.0 - 2.0 * s_side, s_side};
+    for (long i = 0; i < n[0]; ++i)
+        for (long j = 0; j < n[1]; ++j)
+            for (long k = 0; k < n[2]; ++k) {
+                double acc = 0.0;
+                for (int oi = -1; oi <= 1; ++oi)
+                    for (int oj = -1; oj <= 1; ++oj)
+                        for (int ok = -1; ok <= 1; ++ok)
+                            acc += w[oi + 1] * w[oj + 1] * w[ok + 1] * u[at(n, i + oi, j + oj, k + ok)];
+                out[at(n, i, j, k)] = acc;
+            }
+    return 0;
+}
+
+/* -------------------------------------------------------------- multigrid */
+
+#define ORC_MAX_LEVELS 32
+
+typedef struct {
+    int nlev;
+    int n[ORC_MAX_LEVELS][3];
+    double h[ORC_MAX_LEVELS][3];
+    double* a[ORC_MAX_LEVELS]; /* coefficient per level, a[0] borrowed */
+} orc_hier;
+
+static double norm2(const double* v, size_t len) {
+    double s = 0.0;
+    for (size_t i = 0; i < len; ++i) s += v[i] * v[i];
+    return sqrt(s);
+}
+
+static double mean(const double* v, size_t len) {
+    double s = 0.0;
+    for (size_t i = 0; i < len; ++i) s += v[i];
+    return s / (double)len;
+}
+
+/* Levels: each axis longer than 4 is halved (spacing doubled) until every
+ * axis is 4; the coefficient is carried down by full weighting. */
+static int hier_build(const int n[3], const double* a0, orc_hier* H) {
+    memset(H, 0, sizeof(*H));
+    int l = 0;
+    for (int ax = 0; ax < 3; ++ax) {
+        H->n[0][ax] = n[ax];
+        H->h[0][ax] = 1.0;
+    }
+    H->a[0] = (double*)a0;
+    while (H->n[l][0] > 4 || H->n[l][1] > 4 || H->n[l][2] > 4) {
+        if (l + 1 >= ORC_MAX_LEVELS) return ORC_E_INVALID;
+        for (int ax = 0; ax < 3; ++ax) {
+            int c = H->n[l][ax] > 4;
+            H->n[l + 1][ax] = c ? H->n[l][ax] / 2 : H->n[l][ax];
+            H->h[l + 1][ax] = c ? 2.0 * H->h[l][ax] : H->h[l][ax];
+        }
+        H->a[l + 1] = (double*)malloc(ncells(H->n[l + 1]) * sizeof(double));
+        if (!H->a[l + 1]) return ORC_E_NOMEM;
+        orc_restrict(H->n[l], H->a[l], H->a[l + 1]);
+        ++l;
+    }
+    H->nlev = l + 1;
+    return 0;
+}
+
+static void hier_free(orc_hier* H) {
+    for (int l = 1; l < H->nlev; ++l) free(H->a[l]);
+    /* partially built levels */
+    for (int l = H->nlev > 0 ? H->nlev : 1; l < ORC_MAX_LEVELS; ++l)
+        if (H->a[l]) free(H->a[l]);
+}
+
+/* Coarsest level: dense solve of [L 1; 1^T 0][u; mu] = [f; 0] by Gaussian
+ * elimination with partial pivoting (u has mean zero, L u = f - mean f). */
+static int coarse_solve(const int n[3], const double h[3], const double* a, const double* f,
+                        double* u) {
+    size_t nc = ncells(n), m = nc + 1;
+    double* M = (double*)calloc(m * m, sizeof(double));
+    double* rhs = (double*)calloc(m, sizeof(double));
+    double* e = (double*)calloc(nc, sizeof(double));
+    double* col = (double*)calloc(nc, sizeof(double));
+    if (!M || !rhs || !e || !col) {
+        free(M), free(rhs), free(e), free(col);
+        return ORC_E_NOMEM;
+    }
+    for (size_t c = 0; c < nc; ++c) {
+        memset(e, 0, nc * sizeof(double));
+        e[c] = 1.0;
+        orc_apply_L(n, h, a, e, col);
+        for (size_t r = 0; r < nc; ++r) M[r * m + c] = col[r];
+    }
+    for (size_t r = 0; r < nc; ++r) {
+        M[r * m + nc] = 1.0;
+        M[nc * m + r] = 1.0;
+        rhs[r] = f[r];
+    }
+    for (size_t p = 0; p < m; ++p) {
+        size_t piv = p;
+        for (size_t r = p + 1; r < m; ++r)
+            if (fabs(M[r * m + p]) > fabs(M[piv * m + p])) piv = r;
+        if (piv != p) {
+            for (size_t c = 0; c < m; ++c) {
+                double t = M[p * m + c];
+                M[p * m + c] = M[piv * m + c];
+                M[piv * m + c] = t;
+            }
+            double t = rhs[p];
+            rhs[p] = rhs[piv];
+            rhs[piv] = t;
+        }
+        for (size_t r = p + 1; r < m; ++r) {
+            double fct = M[r * m + p] / M[p * m + p];
+            if (fct == 0.0) continue;
+            for (size_t c = p; c < m; ++c) M[r * m + c] -= fct * M[p * m + c];
+            rhs[r] -= fct * rhs[p];
+        }
+    }
+    for (size_t p = m; p-- > 0;) {
+        double s = rhs[p];
+        for (size_t c = p + 1; c < m; ++c) s -= M[p * m + c] * rhs[c];
+        rhs[p] = s / M[p * m + p];
+    }
+    for (size_t r = 0; r < nc; ++r) u[r] = rhs[r];
+    free(M), free(rhs), free(e), free(col);
+    return 0;
+}
+
+static int vcycle_level(const orc_params* p, const orc_hier* H, int l, const double* f,
+                        double* u) {
+    const int* n = H->n[l];
+    const double* h = H->h[l];
+    if (l == H->nlev - 1) return coarse_solve(n, h, H->a[l], f, u);
+    size_t len = ncells(n);
+    for (int s = 0; s < p->nu1; ++s) orc_rbgs_sweep(n, h, H->a[l], f, u);
+    double* r = (double*)malloc(len * sizeof(double));
+    size_t clen = ncells(H->n[l + 1]);
+    double* fc = (double*)malloc(clen * sizeof(double));
+    double* uc = (double*)calloc(clen, sizeof(double));
+    if (!r || !fc || !uc) {
+        free(r), free(fc), free(uc);
+        return ORC_E_NOMEM;
+    }
+    orc_apply_L(n, h, H->a[l], u, r);
+    for (size_t i = 0; i < len; ++i) r[i] = f[i] - r[i];
+    orc_restrict(n, r, fc);
+    int rc = vcycle_level(p, H, l + 1, fc, uc);
+    if (rc == 0) {
+        orc_prolong_add(n, uc, u);
+        for (int s = 0; s < p->nu2; ++s) orc_rbgs_sweep(n, h, H->a[l], f, u);
+    }
+    free(r), free(fc), free(uc);
+    return rc;
+}
+
+int orc_vcycle(const orc_params* p, const double* a, const double* f, double* u) {
+    if (!p || !a || !f || !u || !dims_ok(p->n, 4)) return ORC_E_INVALID;
+    orc_hier H;
+    int rc = hier_build(p->n, a, &H);
+    if (rc == 0) rc = vcycle_level(p, &H, 0, f, u);
+    hier_free(&H);
+    return rc;
+}
+
+int orc_mg_solve(const orc_params* p, const double* a, const double* s, double* u,
+                 int* ncycles, double* relres) {
+    if (!p || !a || !s || !u || !dims_ok(p->n, 4)) return ORC_E_INVALID;
+    size_t len = ncells(p->n);
+    memset(u, 0, len * sizeof(double));
+    double snorm = norm2(s, len);
+    int cyc = 0;
+    double rel = 0.0;
+    if (snorm > 0.0) {
+        orc_hier H;
+        int rc = hier_build(p->n, a, &H);
+        double* r = (double*)malloc(len * sizeof(double));
+        if (rc != 0 || !r) {
+            hier_free(&H);
+            free(r);
+            return rc ? rc : ORC_E_NOMEM;
+        }
+        const double h1[3] = {1.0, 1.0, 1.0};
+        rel = 1.0;
+        while (cyc < p->max_vcycles) {
+            rc = vcycle_level(p, &H, 0, s, u);
+            if (rc) break;
+            ++cyc;
+            orc_apply_L(p->n, h1, a, u, r);
+            for (size_t i = 0; i < len; ++i) r[i] = s[i] - r[i];
+            rel = norm2(r, len) / snorm;
+            if (rel <= p->tol_in) break;
+        }
+        hier_free(&H);
+        free(r);
+        if (rc) return rc;
+    }
+    if (ncycles) *ncycles = cyc;
+    if (relres) *relres = rel;
+    return 0;
+}
+
+/* --------------------------------------------------------------- geometry */
+
+/* Hessian of phi at node (i,j,k): 3-point second differences on the
+ * diagonal, 4-point centred cross differences off it. */
+static void hessian(const int n[3], const double* f, long i, long j, long k, double H[3][3]) {
+    long o[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    double c = f[at(n, i, j, k)];
+    for (int a = 0; a < 3; ++a) {
+        H[a][a] = f[at(n, i + o[a][0], j + o[a][1], k + o[a][2])] - 2.0 * c +
+                  f[at(n, i - o[a][0], j - o[a][1], k - o[a][2])];
+        for (int b = a + 1; b < 3; ++b) {
+            long pi = o[a][0] + o[b][0], pj = o[a][1] + o[b][1], pk = o[a][2] + o[b][2];
+            long qi = o[a][0] - o[b][0], qj = o[a][1] - o[b][1], qk = o[a][2] - o[b][2];
+            double v = f[at(n, i + pi, j + pj, k + pk)] - f[at(n, i + qi, j + qj, k + qk)] -
+                       f[at(n, i - qi, j - qj, k - qk)] + f[at(n, i - pi, j - pj, k - pk)];
+            H[a][b] = H[b][a] = 0.25 * v;
+        }
+    }
+}
+
+static double det3(const double e[3][3]) {
+    return e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) -
+           e[0][1] * (e[1][0] * e[2][2] - e[1][2] * e[2][0]) +
+           e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]);
+}
+
+double orc_min_eig_sym3(const double A[3][3]) {
+    double m[3][3];
+    memcpy(m, A, sizeof(m));
+    for (int sweep = 0; sweep < 64; ++sweep) {
+        double off = m[0][1] * m[0][1] + m[0][2] * m[0][2] + m[1][2] * m[1][2];
+        if (off == 0.0) break;
+        for (int p = 0; p < 2; ++p)
+            for (int q = p + 1; q < 3; ++q) {
+                if (m[p][q] == 0.0) continue;
+                /* rotation angle zeroing m[p][q] */
+                double theta = (m[q][q] - m[p][p]) / (2.0 * m[p][q]);
+                double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                for (int r = 0; r < 3; ++r) { /* columns p, q */
+                    double mrp = m[r][p], mrq = m[r][q];
+                    m[r][p] = c * mrp - s * mrq;
+                    m[r][q] = s * mrp + c * mrq;
+                }
+                for (int r = 0; r < 3; ++r) { /* rows p, q */
+                    double mpr = m[p][r], mqr = m[q][r];
+                    m[p][r] = c * mpr - s * mqr;
+                    m[q][r] = s * mpr + c * mqr;
+                }
+                m[p][q] = m[q][p] = 0.0;
+            }
+    }
+    double l = m[0][0];
+    if (m[1][1] < l) l = m[1][1];
+    if (m[2][2] < l) l = m[2][2];
+    return l;
+}
+
+int orc_geometry(const int n[3], const double* phi, double* sqrt_g, double* lambda0) {
+    if (!n || !phi || !dims_ok(n, 1)) return ORC_E_INVALID;
+    for (long i = 0; i < n[0]; ++i)
+        for (long j = 0; j < n[1]; ++j)
+            for (long k = 0; k < n[2]; ++k) {
+                double H[3][3], e[3][3];
+                hessian(n, phi, i, j, k, H);
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b) e[a][b] = (a == b ? 1.0 : 0.0) + H[a][b];
+                size_t c = at(n, i, j, k);
+                if (sqrt_g) sqrt_g[c] = det3(e);
+                if (lambda0) lambda0[c] = orc_min_eig_sym3(e);
+            }
+    return 0;
+}
+
+static double heaviside(double x) { return x > 0.0 ? 1.0 : 0.0; }
+
+/* Compression limiter C(lambda0) of App. A under the chosen reading. */
+static double climit(int reading, double xi_m, double lambda0) {
+    double lam = lambda0 > 1e-12 ? lambda0 : 1e-12;
+    double q = xi_m / lam;
+    double v;
+    switch (reading) {
+        case ORC_CLIM_LITERAL: v = q - heaviside(q - 1.0); break;
+        case ORC_CLIM_STEP: v = q * heaviside(q - 1.0); break;
+        default: v = q - 1.0 > 0.0 ? q - 1.0 : 0.0; break;
+    }
+    return 4.0 * v * v;
+}
+
+int orc_source(const orc_params* p, const double* phi, const double* m, double* s,
+               double* t_out) {
+    if (!p || !phi || !m || !s || !dims_ok(p->n, 1)) return ORC_E_INVALID;
+    const int* n = p->n;
+    size_t len = ncells(n);
+    double* g = (double*)malloc(len * sizeof(double));
+    double* lam = (double*)malloc(len * sizeof(double));
+    double* t = (double*)malloc(len * sizeof(double));
+    if (!g || !lam || !t) {
+        free(g), free(lam), free(t);
+        return ORC_E_NOMEM;
+    }
+    orc_geometry(n, phi, g, lam);
+    for (size_t c = 0; c < len; ++c) {
+        double Sigma = 1.0 - m[c];                          /* deviation density */
+        double C = climit(p->climiter, p->xi_m, lam[c]);    /* compression limiter */
+        double E = -2.0 * heaviside(g[c] - p->v_m) * fabs(Sigma); /* expansion limiter */
+        t[c] = Sigma + C + E;
+    }
+    orc_apply_S(n, p->s_side, t, s);
+    double mu = mean(s, len);
+    for (size_t c = 0; c < len; ++c) s[c] -= mu;
+    if (t_out) memcpy(t_out, t, len * sizeof(double));
+    free(g), free(lam), free(t);
+    return 0;
+}
+
+/* ------------------------------------------------------------ limiter */
+
+/* lambda_min(M) > floor  <=>  M - floor I positive definite (Sylvester's
+ * criterion: all leading principal minors positive). */
+static int pd_sylvester(const double M0[3][3], double floor) {
+    double M[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) M[a][b] = M0[a][b] - (a == b ? floor : 0.0);
+    double m1 = M[0][0];
+    double m2 = M[0][0] * M[1][1] - M[0][1] * M[1][0];
+    double m3 = det3(M);
+    return m1 > 0.0 && m2 > 0.0 && m3 > 0.0;
+}
+
+/* central-difference gradient component ax of f at a node */
+static double cgrad(const int n[3], const double* f, long i, long j, long k, int ax) {
+    long di = ax == 0, dj = ax == 1, dk = ax == 2;
+    return 0.5 * (f[at(n, i + di, j + dj, k + dk)] - f[at(n, i - di, j - dj, k - dk)]);
+}
+
+int orc_step_limiter(const orc_params* p, const double* phi, const double* dphi,
+                     double* alpha) {
+    if (!p || !phi || !dphi || !alpha || !dims_ok(p->n, 1)) return ORC_E_INVALID;
+    const int* n = p->n;
+    double gmax = 0.0;
+    for (long i = 0; i < n[0]; ++i)
+        for (long j = 0; j < n[1]; ++j)
+            for (long k = 0; k < n[2]; ++k)
+                for (int ax = 0; ax < 3; ++ax) {
+                    double g = fabs(cgrad(n, dphi, i, j, k, ax));
+                    if (g > gmax) gmax = g;
+                }
+    for (double al = 1.0; al >= p->alpha_min; al *= 0.5) {
+        int ok = al * gmax <= p->d_max;
+        for (long i = 0; ok && i < n[0]; ++i)
+            for (long j = 0; ok && j < n[1]; ++j)
+                for (long k = 0; ok && k < n[2]; ++k) {
+                    double H0[3][3], H1[3][3], M[3][3];
+                    hessian(n, phi, i, j, k, H0);
+                    hessian(n, dphi, i, j, k, H1);
+                    for (int a = 0; a < 3; ++a)
+                        for (int b = 0; b < 3; ++b)
+                            M[a][b] = (a == b ? 1.0 : 0.0) + H0[a][b] + al * H1[a][b];
+                    ok = pd_sylvester(M, p->lambda_floor);
+                }
+        if (ok) {
+            *alpha = al;
+            return 0;
+        }
+    }
+    return ORC_E_LIMITER;
+}
+
+/* -------------------------------------------------------------- advance */
+
+int orc_advance(const int n[3], double alpha, const double* dphi, double* phi, double* xi,
+                int64_t np) {
+    if (!n || !dphi || !phi || (!xi && np > 0) || !dims_ok(n, 1)) return ORC_E_INVALID;
+    size_t len = ncells(n);
+    /* Node velocity of a tracer's curvilinear coordinate: the mesh point xi
+     * moves by grad dphi in Eulerian space (Eq. mapping), so a tracer at rest
+     * in x moves in xi by -e^-1 grad dphi, e = I + Hess(phi) the current
+     * triad (App. A).  V = e^-1 G at every node, G the central-difference
+     * gradient of dphi; phi is read before its own update. */
+    double* V = (double*)malloc(3 * len * sizeof(double));
+    if (!V) return ORC_E_NOMEM;
+    for (long i = 0; i < n[0]; ++i)
+        for (long j = 0; j < n[1]; ++j)
+            for (long k = 0; k < n[2]; ++k) {
+                double H[3][3], e[3][3], G[3];
+                hessian(n, phi, i, j, k, H);
+                for (int a = 0; a < 3; ++a) {
+                    for (int b = 0; b < 3; ++b) e[a][b] = (a == b ? 1.0 : 0.0) + H[a][b];
+                    G[a] = cgrad(n, dphi, i, j, k, a);
+                }
+                /* e^-1 G by Cramer's rule (e symmetric positive definite) */
+                double d = det3(e);
+                size_t c = at(n, i, j, k);
+                for (int a = 0; a < 3; ++a) {
+                    double ea[3][3];
+                    memcpy(ea, e, sizeof(ea));
+                    for (int r = 0; r < 3; ++r) ea[r][a] = G[r];
+                    V[3 * c + a] = det3(ea) / d;
+                }
+            }
+    for (size_t c = 0; c < len; ++c) phi[c] += alpha * dphi[c];
+    for (int64_t t = 0; t < np; ++t) {
+        long i0[3];
+        double f[3], v[3] = {0.0, 0.0, 0.0};
+        for (int a = 0; a < 3; ++a) cic_axis(xi[3 * t + a], n[a], &i0[a], &f[a]);
+        for (int di = 0; di < 2; ++di)
+            for (int dj = 0; dj < 2; ++dj)
+                for (int dk = 0; dk < 2; ++dk) {
+                    double w = (di ? f[0] : 1.0 - f[0]) * (dj ? f[1] : 1.0 - f[1]) *
+                               (dk ? f[2] : 1.0 - f[2]);
+                    size_t c = at(n, i0[0] + di, i0[1] + dj, i0[2] + dk);
+                    for (int a = 0; a < 3; ++a) v[a] += w * V[3 * c + a];
+                }
+        for (int a = 0; a < 3; ++a) xi[3 * t + a] -= alpha * v[a];
+    }
+    free(V);
+    return 0;
+}
+
+/* ---------------------------------------------------------------- outputs */
+
+int orc_delta_r(const int n[3], const double* phi, double* out) {
+    if (!n || !phi || !out || !dims_ok(n, 1)) return ORC_E_INVALID;
+    for (long i = 0; i < n[0]; ++i)
+        for (long j = 0; j < n[1]; ++j)
+            for (long k = 0; k < n[2]; ++k) {
+                double H[3][3];
+                hessian(n, phi, i, j, k, H);
+                out[at(n, i, j, k)] = -(H[0][0] + H[1][1] + H[2][2]);
+            }
+    return 0;
+}
+
+int orc_mesh_x(const int n[3], const double* phi, double* out) {
+    if (!n || !phi || !out || !dims_ok(n, 1)) return ORC_E_INVALID;
+    for (long i = 0; i < n[0]; ++i)
+        for (long j = 0; j < n[1]; ++j)
+            for (long k = 0; k < n[2]; ++k) {
+                size_t c = at(n, i, j, k);
+                out[3 * c + 0] = (double)i + cgrad(n, phi, i, j, k, 0);
+                out[3 * c + 1] = (double)j + cgrad(n, phi, i, j, k, 1);
+                out[3 * c + 2] = (double)k + cgrad(n, phi, i, j, k, 2);
+            }
+    return 0;
+}
+
+/* ------------------------------------------------------------ whole solve */
+
+static int params_ok(const orc_params* p) {
+    return p && dims_ok(p->n, 8) && p->xi_m > 0.0 && p->xi_m < 1.0 && p->v_m > 1.0 &&
+           p->a_min > 0.0 && p->s_side >= 0.0 && p->s_side <= 0.25 && p->nu1 >= 0 && p->nu2 >= 0 && p->nu1 + p->nu2 > 0 &&
+           p->tol_in > 0.0 && p->max_vcycles > 0 && p->tol_out >= 0.0 && p->k_max >= 0 &&
+           p->d_max > 0.0 && p->alpha_min > 0.0 && p->alpha_min <= 1.0 &&
+           p->lambda_floor >= 0.0 && p->lambda_floor < 1.0;
+}
+
+int orc_solve(const orc_params* p, const double* rho, const double* replay_alpha,
+              double* phi, double* xi_out, double* m_out, int* steps, orc_trace* tr) {
+    if (!params_ok(p) || !rho || !phi) return ORC_E_INVALID;
+    const int* n = p->n;
+    size_t len = ncells(n);
+    double rho_sum = 0.0;
+    for (size_t c = 0; c < len; ++c) {
+        if (!(rho[c] >= 0.0) || !isfinite(rho[c])) return ORC_E_INVALID;
+        rho_sum += rho[c];
+    }
+    if (!(rho_sum > 0.0)) return ORC_E_INVALID;
+    double rho_bar = rho_sum / (double)len;
+
+    double* w = (double*)malloc(len * sizeof(double));
+    double* xi = (double*)malloc(3 * len * sizeof(double));
+    double* m = (double*)malloc(len * sizeof(double));
+    double* s = (double*)malloc(len * sizeof(double));
+    double* a = (double*)malloc(len * sizeof(double));
+    double* phidot = (double*)malloc(len * sizeof(double));
+    double* dphi = (double*)malloc(len * sizeof(double));
+    double* g = (double*)malloc(len * sizeof(double));
+    double* lam = (double*)malloc(len * sizeof(double));
+    int rc = 0, k = 0, done = 0;
+    if (!w || !xi || !m || !s || !a || !phidot || !dphi || !g || !lam) {
+        rc = ORC_E_NOMEM;
+        goto out;
+    }
+    /* init: tracer c = node c with mass rho_c / rho_bar; phi = 0 */
+    for (long i = 0; i < n[0]; ++i)
+        for (long j = 0; j < n[1]; ++j)
+            for (long kk = 0; kk < n[2]; ++kk) {
+                size_t c = at(n, i, j, kk);
+                w[c] = rho[c] / rho_bar;
+                xi[3 * c + 0] = (double)i;
+                xi[3 * c + 1] = (double)j;
+                xi[3 * c + 2] = (double)kk;
+            }
+    memset(phi, 0, len * sizeof(double));
+
+    for (k = 0; k < p->k_max; ++k) {
+        orc_cic_deposit(n, xi, w, (int64_t)len, m);              /* 1 */
+        rc = orc_source(p, phi, m, s, NULL);                      /* 2, 3 */
+        if (rc) goto out;
+        double R = 0.0;
+        for (size_t c = 0; c < len; ++c) R += s[c] * s[c];
+        R = sqrt(R / (double)len);                                /* 4 */
+        if (tr) {
+            orc_geometry(n, phi, g, lam);
+            double md = g[0], ml = lam[0], ms = 0.0;
+            for (size_t c = 0; c < len; ++c) {
+                if (g[c] < md) md = g[c];
+                if (lam[c] < ml) ml = lam[c];
+                ms += m[c];
+            }
+            if (tr->R) tr->R[k] = R;
+            if (tr->min_det) tr->min_det[k] = md;
+            if (tr->min_lam) tr->min_lam[k] = ml;
+            if (tr->mass) tr->mass[k] = ms;
+        }
+        if (R <= p->tol_out) {
+            done = 1;
+            break;
+        }
+        for (size_t c = 0; c < len; ++c) a[c] = m[c] > p->a_min ? m[c] : p->a_min; /* 5 */
+        int ncyc = 0;
+        double rel = 0.0;
+        rc = orc_mg_solve(p, a, s, phidot, &ncyc, &rel);
+        if (rc) goto out;
+        orc_apply_S(n, p->s_side, phidot, dphi);     /* 6 */
+        double mu = mean(dphi, len);
+        for (size_t c = 0; c < len; ++c) dphi[c] -= mu;
+        double alpha;                                             /* 7 */
+        if (replay_alpha) {
+            alpha = replay_alpha[k];
+        } else {
+            rc = orc_step_limiter(p, phi, dphi, &alpha);
+            if (rc) goto out;
+        }
+        rc = orc_advance(n, alpha, dphi, phi, xi, (int64_t)len); /* 8 */
+        if (rc) goto out;
+        if (tr) {
+            if (tr->alpha) tr->alpha[k] = alpha;
+            if (tr->ncycles) tr->ncycles[k] = ncyc;
+            if (tr->relres) tr->relres[k] = rel;
+        }
+    }
+    if (m_out) orc_cic_deposit(n, xi, w, (int64_t)len, m_out);
+    if (xi_out) memcpy(xi_out, xi, 3 * len * sizeof(double));
+out:
+    if (steps) *steps = k;
+    free(w), free(xi), free(m), free(s), free(a), free(phidot), free(dphi), free(g), free(lam);
+    if (rc) return rc;
+    return done ? 0 : 1;
+}
