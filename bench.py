@@ -1,0 +1,364 @@
+"""Benchmark of the reconstruction solve on GB300.
+
+One step = one whole recon_solve (every step of the moving-mesh iteration,
+Sec. II / App. A of Zhu et al. 2016) on the 256^3 / 400 Mpc/h 2LPT workload
+(BBKS, Gamma 0.2, n_s 1, sigma_8 0.8, seed 1001), from phi = 0 on the
+density already resident in HBM, in mixed precision; the plain FP64 form of
+the same solve is timed beside it.  Metric: Mcells/s per full reconstruction
+solve at fixed residual = ncells / solve time / 1e6 (whole job: summed over
+ranks, which solve independent copies of the workload).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload lpt256]
+    python bench.py --impl reference ...   # the CPU FP64 oracle, bounded sample
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mcells/s per full reconstruction solve at fixed residual, mixed vs FP64 GPU"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="lpt256")
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            pk = json.load(fh)
+        for key in ("hbm_gbs", "hbm_GBps", "hbm"):
+            if key in pk:
+                v = pk[key]
+                if isinstance(v, dict):
+                    v = v.get("value", v.get("burst"))
+                return float(v), "measured"
+    except Exception:
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def _traffic(kernel_tag):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+        src = os.path.join(ROOT, "paper_1611_09638_gb300", "csrc", rec["source"])
+        with open(src, "rb") as fh:
+            digest = hashlib.sha256(fh.read()).hexdigest()
+        if rec.get("kernel") == kernel_tag and rec.get("sha256") == digest:
+            return float(rec["bytes_per_sweep_full_size"])
+    except Exception:
+        pass
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for ln in (self.out or "").splitlines():
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) >= 7:
+                try:
+                    rows.append((float(parts[0]), float(parts[1]), parts[3:7]))
+                except ValueError:
+                    pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, fl in rows for i, f in enumerate(fl)
+                          if f.lower() in ("active", "1", "yes")})
+        return {"sm_mhz": float(np.median([r[0] for r in rows])),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def _workload(name):
+    from paper_1611_09638_gb300.inputs import WORKLOADS
+
+    return WORKLOADS[name]
+
+
+def run_gb300(a):
+    import torch
+
+    from paper_1611_09638_gb300 import Recon
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    W = _workload(a.workload)
+    n = W.n
+    cells = n ** 3
+    pos_host, _ = W.particles()
+    pos_dev = torch.from_numpy(pos_host).cuda()
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(precision, steps, warmup, profile=False):
+        R = Recon((n, n, n), box=W.box, precision=precision, profile=int(profile))
+        R.deposit_particles(pos_dev)
+        for _ in range(warmup):
+            R.solve(record=False)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stats = []
+        with Clocks(local) as clk:
+            e0.record(stream)
+            for _ in range(steps):
+                stats.append(R.solve(record=True))
+            e1.record(stream)
+            barrier()
+        ms = e0.elapsed_time(e1) / steps
+        R.close()
+        return ms, stats, clk.summary()
+
+    ms_mixed, st_mixed, clocks = timed("mixed", a.steps, a.warmup, profile=True)
+    ms_fp64, st_fp64, _ = timed("fp64", max(a.fp64_steps, 1), 1)
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        import torch.distributed as dist
+
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    ms_mixed = max_over_ranks(ms_mixed)
+    ms_fp64 = max_over_ranks(ms_fp64)
+    value = world * cells / (ms_mixed * 1e-3) / 1e6
+    value_fp64 = world * cells / (ms_fp64 * 1e-3) / 1e6
+
+    # roofline of the dominant kernel: the finest-level FP32 red-black sweep
+    sm_ms = sum(s.smooth_ms for s in st_mixed)
+    sweeps = sum(s.smooth_sweeps for s in st_mixed)
+    sweep_bytes = st_mixed[0].smooth_bytes
+    peak, peak_kind = _peak_hbm()
+    achieved = sweep_bytes / (sm_ms * 1e-3 / sweeps) / 1e9 if sweeps else None
+    roof = {"bound": "hbm", "kernel": "rbgs_f32 finest-level sweep (red + black)",
+            "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak if achieved else None, "peak_source": peak_kind,
+            "traffic": _traffic("rbgs_f32"), "algorithmic_bytes_per_sweep": sweep_bytes,
+            "sweeps_timed": sweeps, "share_of_solve": sm_ms / (ms_mixed * a.steps)}
+
+    e2e = None
+    if not a.no_e2e:
+        R = Recon((n, n, n), box=W.box, precision="mixed")
+        pin_pos = torch.from_numpy(pos_host).pin_memory()
+        out = torch.empty((n, n, n), dtype=torch.float64).pin_memory()
+        for _ in range(1):
+            R.deposit_particles(pin_pos)
+            R.solve(record=False)
+            R.field("delta_r", out=out)
+        barrier()
+        t0 = time.perf_counter()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        k2 = max(1, min(a.steps, 3))
+        for _ in range(k2):
+            R.deposit_particles(pin_pos)
+            R.solve(record=False)
+            R.field("delta_r", out=out)
+        e1.record(stream)
+        barrier()
+        e2e_ms = max_over_ranks(e0.elapsed_time(e1) / k2)
+        wall_ms = (time.perf_counter() - t0) * 1e3 / k2
+        R.close()
+        e2e = {"value": world * cells / (e2e_ms * 1e-3) / 1e6, "unit": "Mcells/s",
+               "h2d_bytes_per_step": int(pos_host.nbytes), "d2h_bytes_per_step": int(out.numel() * 8),
+               "ms_per_step": e2e_ms, "host_wall_ms_per_step": wall_ms,
+               "path": "recon_deposit(host pinned particles) + recon_solve + recon_field(delta_r -> host pinned)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cpu = cpu_baseline(W, st_mixed[0])
+
+    s0 = st_mixed[0]
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mcells/s", "n_gpus": world,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_mixed, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": W.name, "grid": [n, n, n], "box_mpc_h": W.box,
+                   "displacement": "2LPT" if W.order == 2 else "ZA", "seed": W.seed,
+                   "precision": "mixed", "k_max": 40, "tol_in": 1e-8, "tol_out": 1e-3,
+                   "steps_per_solve": s0.steps, "vcycles_per_solve": s0.vcycles,
+                   "l2": "inputs larger than L2 (working set ~1.7 GB per solve)",
+                   "parallelism": f"replicas x{world}"},
+        "fp64_gpu": {"value": value_fp64, "unit": "Mcells/s", "ms_per_step": ms_fp64,
+                     "steps": max(a.fp64_steps, 1), "vcycles_per_solve": st_fp64[0].vcycles,
+                     "mixed_over_fp64": value / value_fp64},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(sum(s.launches for s in st_mixed)),
+        "clocks": clocks,
+    }
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def cpu_baseline(W, st):
+    """The CPU oracle as it stands (single thread) on a bounded sample of the
+    same workload: one V-cycle and one each of the per-step passes on the full
+    grid, scaled by the GPU solve's own step and V-cycle counts to one solve."""
+    import oracle as O
+
+    n = W.n
+    pos, _ = W.particles()
+    x = pos / W.cell
+    rho = O.cic_deposit((n, n, n), x)
+    m = rho / rho.mean()
+    p = O.OracleParams(n=(n, n, n))
+    t = {}
+    t0 = time.perf_counter()
+    O.cic_deposit((n, n, n), x, m.ravel())
+    t["deposit"] = time.perf_counter() - t0
+    phi = np.zeros((n, n, n))
+    t0 = time.perf_counter()
+    s, _ = O.source(p, phi, m)
+    t["source"] = time.perf_counter() - t0
+    a_ = np.maximum(m, p.a_min)
+    t0 = time.perf_counter()
+    u = O.vcycle(p, a_, s, np.zeros_like(s))
+    t["vcycle"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    d = O.apply_S(u)
+    t["smooth"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    O.step_limiter(p, phi, d * 1e-3)
+    t["limiter"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    O.advance(1.0, d * 1e-3, phi, x)
+    t["advance"] = time.perf_counter() - t0
+    per_step = t["deposit"] + t["source"] + t["smooth"] + t["limiter"] + t["advance"]
+    solve_s = st.steps * per_step + st.vcycles * t["vcycle"] + t["deposit"]
+    return {"value": n ** 3 / solve_s / 1e6, "unit": "Mcells/s", "cores": 1, "kind": "oracle",
+            "sample": (f"{n}^3 grid: one oracle V-cycle ({t['vcycle']:.1f} s) and one of each "
+                       f"per-step pass ({per_step:.1f} s), scaled to the GPU solve's "
+                       f"{st.steps} steps and {st.vcycles} V-cycles"),
+            "sample_seconds": sum(t.values()), "est_solve_seconds": solve_s}
+
+
+def run_reference(a):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    import oracle as O
+
+    W = _workload(a.workload)
+    n = W.n
+    pos, _ = W.particles()
+    x = pos / W.cell
+    rho = O.cic_deposit((n, n, n), x)
+    m = rho / rho.mean()
+    p = O.OracleParams(n=(n, n, n))
+    s, _ = O.source(p, np.zeros((n, n, n)), m)
+    a_ = np.maximum(m, p.a_min)
+    # one step of this arm = one oracle V-cycle on the full grid; the solve
+    # time is that times the V-cycles of a solve plus the per-step passes
+    # measured once
+    t0 = time.perf_counter()
+    O.cic_deposit((n, n, n), x, m.ravel())
+    O.source(p, np.zeros((n, n, n)), m)
+    per_step_fixed = time.perf_counter() - t0
+    steps_per_solve, vc_per_solve = 40, 40 * 17
+    for _ in range(a.warmup):
+        O.vcycle(p, a_, s, np.zeros_like(s))
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        O.vcycle(p, a_, s, np.zeros_like(s))
+    tv = (time.perf_counter() - t0) / a.steps
+    solve_s = steps_per_solve * per_step_fixed + vc_per_solve * tv
+    value = n ** 3 / solve_s / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mcells/s",
+            "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": tv * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": W.name, "grid": [n, n, n], "box_mpc_h": W.box,
+                       "precision": "fp64 (CPU oracle)"},
+            "cpu_baseline": {"value": value, "unit": "Mcells/s", "cores": 1, "kind": "oracle",
+                             "sample": (f"each step one oracle V-cycle on the {n}^3 grid; solve "
+                                        f"time = {vc_per_solve} V-cycles + {steps_per_solve} x "
+                                        f"deposit and source passes")},
+            "e2e": {"value": value, "unit": "Mcells/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gb300(args)

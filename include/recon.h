@@ -1,0 +1,165 @@
+/*
+ * recon.h -- C ABI of the GB300 (sm_103a) nonlinear-reconstruction solver.
+ *
+ * The library solves for the displacement potential phi(xi) of "Nonlinear
+ * reconstruction" (Zhu, Yu, Pen, Chen & Yu 2016, arXiv:1611.09638): the
+ * pure-gradient coordinate map x = xi + grad phi (Sec. II, Eq. mapping) that
+ * stays positive definite and carries an observed density to constant mass per
+ * curvilinear cell.  It is found by the moving-mesh iteration of Sec. II and
+ * App. A: each step deposits the density on the deformed mesh by CIC, builds
+ * the limited, smoothed source S(Sigma + C + E) of App. A Eq. (elliptic),
+ * solves the linearised elliptic equation with variable-coefficient multigrid
+ * V-cycles, limits the step so the map stays positive definite, and advances
+ * the mesh.  The output is the reconstructed density delta_r = -lap phi
+ * (Sec. II, Eq. rec).
+ *
+ * Conventions
+ *   - Periodic vertex grid of n[0] x n[1] x n[2] nodes (each a power of two,
+ *     >= 8), C order with the last axis fastest: idx = (i*n1 + j)*n2 + k.
+ *   - Cells are cubes of side h = box[a] / n[a] (all three equal).  With
+ *     box = {0,0,0} the grid unit is used (h = 1).
+ *   - Every array argument is a plain pointer to host OR device memory (the
+ *     library tells them apart through unified addressing); device pointers
+ *     must be on the device that was current at recon_create.  Inputs are
+ *     borrowed for the duration of the call only; the handle owns all of its
+ *     device state.
+ *   - Every call returns a status (RECON_OK = 0, errors < 0, RECON_NOT_CONVERGED
+ *     = 1 is a warning with valid results) and never traps or aborts; the
+ *     thread-local text of the last error is returned by recon_last_error().
+ *   - All work runs on the CUDA stream given at create.  recon_solve and
+ *     recon_field return after the stream has finished their work.
+ */
+#ifndef RECON_H
+#define RECON_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RECON_OK 0
+#define RECON_NOT_CONVERGED 1 /* k_max steps done before rms(s) <= tol_out */
+#define RECON_E_INVALID (-1)  /* bad argument / parameter                  */
+#define RECON_E_OOM (-2)      /* device allocation failed                 */
+#define RECON_E_CUDA (-3)     /* a CUDA runtime call failed               */
+#define RECON_E_NONFINITE (-4) /* NaN/Inf or negative input               */
+#define RECON_E_LIMITER (-5)  /* step limiter found no alpha >= alpha_min  */
+#define RECON_E_TIMEOUT (-6)  /* a bounded device wait expired             */
+#define RECON_E_STATE (-7)    /* call out of order (e.g. solve before deposit) */
+#define RECON_E_UNSUPPORTED (-8) /* feature not available in this build    */
+
+/* arithmetic of the solve */
+#define RECON_FP64 0  /* every step in FP64                                   */
+#define RECON_MIXED 1 /* FP32 smoothing / restriction / prolongation inside an
+                         FP64 defect correction; residual, phi, mesh, limiter FP64 */
+
+/* readings of the printed compression limiter C(phi) of App. A */
+#define RECON_CLIM_SOFT 0    /* C = 4 max(0, xi_m/lambda0 - 1)^2            */
+#define RECON_CLIM_LITERAL 1 /* C = 4 [xi_m/lambda0 - H(xi_m/lambda0 - 1)]^2 */
+#define RECON_CLIM_STEP 2    /* C = 4 [(xi_m/lambda0) H(xi_m/lambda0 - 1)]^2 */
+
+/* recon_deposit modes */
+#define RECON_PARTICLES 0 /* data: np x 3 positions (box units), mass: np or NULL */
+#define RECON_GRID 1      /* data: n[0]*n[1]*n[2] density values, mass: NULL      */
+
+/* recon_field selectors (all FP64) */
+#define RECON_FIELD_PHI 0      /* phi, in box units squared (h^2 x grid units)   */
+#define RECON_FIELD_DELTA_R 1  /* delta_r = -7-point Laplacian of phi (Eq. rec)   */
+#define RECON_FIELD_MESH_X 2   /* ncells x 3: x = xi + central grad phi, box units */
+#define RECON_FIELD_MASS 3     /* m: mass per curvilinear cell / mean, last deposit */
+#define RECON_FIELD_DET 4      /* sqrt(g) = det(I + Hess phi)                      */
+#define RECON_FIELD_LAMBDA0 5  /* minimum eigenvalue of I + Hess phi               */
+#define RECON_FIELD_DENSITY 6  /* the deposited input density rho (as given/gridded) */
+
+typedef struct {
+    int n[3];            /* grid nodes per axis                                */
+    double box[3];       /* box side per axis in physical units, or all 0      */
+    int precision;       /* RECON_FP64 or RECON_MIXED                          */
+    double xi_m;         /* maximal compression factor, 1/10 (App. A)          */
+    double v_m;          /* expansion volume limit, 10 (App. A)                */
+    double a_min;        /* floor of the operator coefficient in voids, 0.01   */
+    int climiter;        /* RECON_CLIM_*                                       */
+    double s_side;       /* smoothing S: per-axis side weight of the 3x3x3 mean, 1/4 */
+    int nu1, nu2;        /* pre / post red-black Gauss-Seidel sweeps, 2 / 2    */
+    double tol_in;       /* stop the linear solve at ||s - L phidot|| <= tol_in ||s|| */
+    int max_vcycles;     /* V-cycle cap per step                               */
+    double tol_out;      /* stop the iteration when rms(s) <= tol_out          */
+    int k_max;           /* step cap                                           */
+    double d_max;        /* step limiter: max |alpha grad dphi| in cells       */
+    double alpha_min;    /* step limiter: smallest admissible alpha            */
+    double lambda_floor; /* step limiter: lambda_min(I + Hess phi) must exceed it */
+    const double* replay_alpha; /* optional host array[k_max]: force alpha_k   */
+    int profile;         /* nonzero: time the finest-level smoothing sweeps with
+                            CUDA events (reported in recon_stats.smooth_ms)    */
+} recon_params;
+
+/* Per-solve record.  The per-step arrays are optional caller-owned host
+ * buffers of length k_max (NULL to skip). */
+typedef struct {
+    int status;          /* same value recon_solve returned                    */
+    int steps;           /* mesh advances done                                 */
+    int vcycles;         /* V-cycles over all steps                            */
+    double R0, R;        /* rms(s) at the first and at the last step start     */
+    double min_det;      /* min det(I + Hess phi) at the end                   */
+    double min_lambda0;  /* min lambda0 at the end                             */
+    double max_delta_r;  /* max delta_r at the end                             */
+    double mass_error;   /* |sum m - ncells| / ncells at the last deposit      */
+    double ms;           /* wall time of the solve (CUDA events), milliseconds */
+    double* alpha;       /* [k_max] accepted alpha per step                    */
+    double* Rk;          /* [k_max] rms(s) at step start                       */
+    int* ncycles;        /* [k_max] V-cycles per step                          */
+    double* relres;      /* [k_max] final relative residual per step           */
+    long long launches;  /* kernels this solve launched                        */
+    double smooth_ms;    /* with params.profile: time in finest-level sweeps   */
+    int smooth_sweeps;   /* with params.profile: number of those sweeps        */
+    double smooth_bytes; /* algorithmic bytes of one such sweep (read u, a, f;
+                            write u), for the roofline                          */
+} recon_stats;
+
+/* Fill *p with the defaults above for an n0 x n1 x n2 grid (grid units,
+ * FP64).  Always succeeds for a non-NULL p. */
+int recon_default_params(recon_params* p, int n0, int n1, int n2);
+
+/* Create a solver (Sec. II, App. A): validates p (dims powers of two >= 8,
+ * cubic cells, 0 < xi_m < 1, v_m > 1, ...), allocates every device buffer of
+ * the grid and its multigrid hierarchy on the current device, and binds the
+ * handle to cuda_stream (a cudaStream_t; NULL = the legacy default stream).
+ * On error *out is NULL. */
+int recon_create(void** out, const recon_params* p, void* cuda_stream);
+
+/* Grid the observed density (Sec. III, "generate the density field on a
+ * grid").  RECON_PARTICLES: data holds np x 3 positions in box units (any real
+ * value; wrapped periodically), mass holds np masses or is NULL for unit mass;
+ * the CIC deposit accumulates in 64-bit fixed point, so the result does not
+ * depend on the order of the particles.  RECON_GRID: data holds the density on
+ * the grid (np must equal the cell count), mass must be NULL.  Rejects
+ * NaN/Inf, negative masses or densities, and zero total mass. */
+int recon_deposit(void* h, int mode, const double* data, const double* mass, int64_t np);
+
+/* Run the whole moving-mesh solve from phi = 0 on the deposited density
+ * (Sec. II; App. A).  Returns RECON_OK when rms(s) <= tol_out,
+ * RECON_NOT_CONVERGED after k_max steps (results valid), or an error.
+ * stats may be NULL. */
+int recon_solve(void* h, recon_stats* stats);
+
+/* Copy one output field (RECON_FIELD_*) of the last solve to dst (host or
+ * device), dst_bytes >= its size (ncells x 8, MESH_X ncells x 24). */
+int recon_field(void* h, int which, void* dst, size_t dst_bytes);
+
+/* Vector-Jacobian product of the last solve, from dL/d(delta_r) to
+ * dL/d(rho) (the differentiable map rho -> delta_r).  Not available in this
+ * build: returns RECON_E_UNSUPPORTED. */
+int recon_adjoint(void* h, const double* grad_delta_r, double* grad_rho);
+
+/* Release every device buffer of the handle (after finishing its stream). */
+void recon_destroy(void* h);
+
+/* Text of the last error on this thread ("" if none). */
+const char* recon_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

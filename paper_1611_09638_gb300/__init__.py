@@ -1,0 +1,161 @@
+"""GB300 (sm_103a) nonlinear reconstruction: the displacement-potential solve of
+Zhu, Yu, Pen, Chen & Yu 2016 (arXiv:1611.09638) behind the C ABI of
+include/recon.h.
+
+``Recon`` is a thin wrapper: it marshals torch tensors (device memory, the
+current CUDA stream) into librecon.so calls; every step of the solve runs in
+the library's CUDA kernels.  There is no CPU path: without the compiled library
+or a CUDA device the calls raise.
+"""
+import ctypes as C
+from dataclasses import dataclass, field
+from typing import Optional
+
+import numpy as np
+
+from . import _abi
+from ._abi import (RECON_FP64, RECON_MIXED, RECON_OK, RECON_NOT_CONVERGED, ReconError,  # noqa: F401
+                   FIELDS)
+
+__all__ = ["Recon", "SolveStats", "default_params", "RECON_FP64", "RECON_MIXED", "ReconError"]
+
+
+def default_params(n, box=None, precision="fp64", **overrides):
+    """recon_params filled by recon_default_params, then overridden."""
+    lib = _abi.load()
+    p = _abi.recon_params()
+    _abi.check(lib.recon_default_params(C.byref(p), int(n[0]), int(n[1]), int(n[2])),
+               "recon_default_params")
+    if box is not None:
+        b = [float(box)] * 3 if np.isscalar(box) else [float(v) for v in box]
+        p.box[:] = b
+    p.precision = {"fp64": RECON_FP64, "mixed": RECON_MIXED}[precision]
+    for k, v in overrides.items():
+        if k == "replay_alpha":
+            continue
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+@dataclass
+class SolveStats:
+    status: int
+    steps: int
+    vcycles: int
+    R0: float
+    R: float
+    min_det: float
+    min_lambda0: float
+    max_delta_r: float
+    mass_error: float
+    ms: float
+    alpha: np.ndarray = field(default=None)
+    Rk: np.ndarray = field(default=None)
+    ncycles: np.ndarray = field(default=None)
+    relres: np.ndarray = field(default=None)
+
+
+def _ptr(x):
+    """Raw pointer of a torch tensor or numpy array (C-contiguous float64)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        assert x.is_contiguous() and str(x.dtype) == "torch.float64", "need contiguous float64"
+        return C.c_void_p(x.data_ptr())
+    assert x.dtype == np.float64 and x.flags.c_contiguous, "need contiguous float64"
+    return C.c_void_p(x.ctypes.data)
+
+
+class Recon:
+    """One solver handle for an n[0] x n[1] x n[2] periodic grid of side box."""
+
+    def __init__(self, n, box=None, precision="fp64", stream=None, replay_alpha=None, **params):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("paper_1611_09638_gb300 needs a CUDA device (no CPU path)")
+        self._lib = _abi.load()
+        self.n = tuple(int(v) for v in n)
+        self.cells = int(np.prod(self.n))
+        self.params = default_params(self.n, box, precision, **params)
+        self._replay = None
+        if replay_alpha is not None:
+            ra = np.zeros(self.params.k_max)
+            ra[:len(replay_alpha)] = replay_alpha
+            self._replay = np.ascontiguousarray(ra, dtype=np.float64)
+            self.params.replay_alpha = self._replay.ctypes.data_as(C.POINTER(C.c_double))
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        _abi.check(self._lib.recon_create(C.byref(h), C.byref(self.params),
+                                          C.c_void_p(self.stream.cuda_stream)), "recon_create")
+        self._h = h
+
+    # -- inputs ------------------------------------------------------------
+    def deposit_particles(self, pos, mass=None):
+        """Grid particles (np x 3 positions in box units; host or device)."""
+        n_p = int(pos.shape[0])
+        return _abi.check(self._lib.recon_deposit(self._h, _abi.RECON_PARTICLES, _ptr(pos),
+                                                  _ptr(mass), n_p), "recon_deposit")
+
+    def deposit_grid(self, rho):
+        """Take a density grid (host or device, n cells, float64)."""
+        return _abi.check(self._lib.recon_deposit(self._h, _abi.RECON_GRID, _ptr(rho), None,
+                                                  int(np.prod(rho.shape))), "recon_deposit")
+
+    # -- solve -------------------------------------------------------------
+    def solve(self, record=True) -> SolveStats:
+        st = _abi.recon_stats()
+        K = max(int(self.params.k_max), 1)
+        arrs = {}
+        if record:
+            for k in ("alpha", "Rk", "relres"):
+                arrs[k] = np.zeros(K)
+                setattr(st, k, arrs[k].ctypes.data_as(C.POINTER(C.c_double)))
+            arrs["ncycles"] = np.zeros(K, dtype=np.int32)
+            st.ncycles = arrs["ncycles"].ctypes.data_as(C.POINTER(C.c_int))
+        rc = self._lib.recon_solve(self._h, C.byref(st))
+        _abi.check(rc, "recon_solve")
+        k = st.steps
+        out = SolveStats(rc, k, st.vcycles, st.R0, st.R, st.min_det, st.min_lambda0,
+                         st.max_delta_r, st.mass_error, st.ms)
+        if record:
+            out.alpha, out.ncycles, out.relres = arrs["alpha"][:k], arrs["ncycles"][:k], arrs["relres"][:k]
+            out.Rk = arrs["Rk"][:min(k + 1, K)] if rc == RECON_OK else arrs["Rk"][:k]
+        return out
+
+    # -- outputs -----------------------------------------------------------
+    def field(self, which, out=None):
+        """Copy an output field into ``out`` (a float64 tensor or array, host or
+        device) or into a new device tensor."""
+        import torch
+
+        code = FIELDS[which]
+        shape = self.n + (3,) if which == "mesh_x" else self.n
+        if out is None:
+            out = torch.empty(shape, dtype=torch.float64, device="cuda")
+        nbytes = int(np.prod(shape)) * 8
+        _abi.check(self._lib.recon_field(self._h, code, _ptr(out), nbytes), "recon_field")
+        return out
+
+    def adjoint(self, grad_delta_r, grad_rho):
+        return _abi.check(self._lib.recon_adjoint(self._h, _ptr(grad_delta_r), _ptr(grad_rho)),
+                          "recon_adjoint")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.recon_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

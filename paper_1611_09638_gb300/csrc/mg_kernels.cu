@@ -1,0 +1,297 @@
+// mg_kernels.cu -- variable-coefficient multigrid kernels for the linearised
+// elliptic equation of App. A (Eq. elliptic with x ~ xi):
+//     L u = sum_a h_a^-2 [A+ (u+ - u) - A- (u - u-)],  A+- = (a + a+-) / 2,
+// red-black Gauss-Seidel smoothing (red = (i+j+k) even first), residual,
+// full-weighting restriction, trilinear prolongation, and a dense solve of the
+// 4^3 coarsest level with the mean constraint.  Templated on float (mixed mode)
+// and double.
+#include "recon_internal.cuh"
+#include "reduce.cuh"
+
+namespace recon {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int nblocks(long long work) { return (int)((work + kThreads - 1) / kThreads); }
+
+// Seven-point operator pieces at node c of level L: diagonal D and
+// off-diagonal sum O, so that (L u)_c = O - D u_c.
+template <typename T>
+struct Stencil7 {
+    T diag, off;
+};
+
+template <typename T>
+__device__ inline Stencil7<T> stencil7(const Dims& d, T hx, T hy, T hz, int i, int j, int k, int c,
+                                       const T* __restrict__ u, const T* __restrict__ a) {
+    const int xp = cell_index(d, i + 1, j, k), xm = cell_index(d, i - 1, j, k);
+    const int yp = cell_index(d, i, j + 1, k), ym = cell_index(d, i, j - 1, k);
+    const int zp = cell_index(d, i, j, k + 1), zm = cell_index(d, i, j, k - 1);
+    const T ac = a[c];
+    const T h = T(0.5);
+    T apx = h * (ac + a[xp]) * hx, amx = h * (ac + a[xm]) * hx;
+    T apy = h * (ac + a[yp]) * hy, amy = h * (ac + a[ym]) * hy;
+    T apz = h * (ac + a[zp]) * hz, amz = h * (ac + a[zm]) * hz;
+    Stencil7<T> s;
+    s.diag = (apx + amx) + (apy + amy) + (apz + amz);
+    s.off = (apx * u[xp] + amx * u[xm]) + (apy * u[yp] + amy * u[ym]) + (apz * u[zp] + amz * u[zm]);
+    return s;
+}
+
+// One colour of a red-black Gauss-Seidel sweep; thread t owns the t-th node
+// of that colour (nodes of a colour alternate along the fastest axis).
+template <typename T>
+__global__ void k_rbgs_colour(Dims d, T hx, T hy, T hz, int colour, T* __restrict__ u,
+                              const T* __restrict__ f, const T* __restrict__ a) {
+    const int half = d.cells >> 1;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= half) return;
+    const int hs2 = d.s2 - 1;
+    const int kk = t & ((1 << hs2) - 1);
+    const int j = (t >> hs2) & (d.n1 - 1);
+    const int i = t >> (d.s1 + hs2);
+    const int k = 2 * kk + ((i + j + colour) & 1);
+    const int c = cell_index(d, i, j, k);
+    Stencil7<T> s = stencil7<T>(d, hx, hy, hz, i, j, k, c, u, a);
+    u[c] = (s.off - f[c]) / s.diag;
+}
+
+template <typename T>
+__global__ void k_residual(Dims d, T hx, T hy, T hz, const T* __restrict__ u,
+                           const T* __restrict__ f, const T* __restrict__ a, T* __restrict__ r) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= d.cells) return;
+    int i, j, k;
+    cell_coords(d, c, i, j, k);
+    Stencil7<T> s = stencil7<T>(d, hx, hy, hz, i, j, k, c, u, a);
+    r[c] = f[c] - (s.off - s.diag * u[c]);
+}
+
+__global__ void k_residual64_to32(Dims d, double hx, double hy, double hz,
+                                  const double* __restrict__ u, const double* __restrict__ f,
+                                  const double* __restrict__ a, float* __restrict__ r32,
+                                  double* __restrict__ partials) {
+    double acc = 0.0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < d.cells; c += gridDim.x * blockDim.x) {
+        int i, j, k;
+        cell_coords(d, c, i, j, k);
+        Stencil7<double> s = stencil7<double>(d, hx, hy, hz, i, j, k, c, u, a);
+        double r = f[c] - (s.off - s.diag * u[c]);
+        if (r32) r32[c] = (float)r;
+        acc += r * r;
+    }
+    acc = block_reduce<OpSum>(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+// Full weighting: weights (1/4, 1/2, 1/4) along every coarsened axis.
+template <typename T>
+__global__ void k_restrict(Dims df, Dims dc, int cx, int cy, int cz, const T* __restrict__ in,
+                           T* __restrict__ out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= dc.cells) return;
+    int I, J, K;
+    cell_coords(dc, c, I, J, K);
+    const int fi = cx ? 2 * I : I, fj = cy ? 2 * J : J, fk = cz ? 2 * K : K;
+    T acc = T(0);
+    for (int oi = -cx; oi <= cx; ++oi) {
+        const T wi = cx ? (oi == 0 ? T(0.5) : T(0.25)) : T(1);
+        for (int oj = -cy; oj <= cy; ++oj) {
+            const T wj = cy ? (oj == 0 ? T(0.5) : T(0.25)) : T(1);
+            for (int ok = -cz; ok <= cz; ++ok) {
+                const T wk = cz ? (ok == 0 ? T(0.5) : T(0.25)) : T(1);
+                acc += wi * wj * wk * in[cell_index(df, fi + oi, fj + oj, fk + ok)];
+            }
+        }
+    }
+    out[c] = acc;
+}
+
+// Trilinear prolongation of the coarse correction, added to the fine field.
+template <typename T>
+__global__ void k_prolong_add(Dims df, Dims dc, int cx, int cy, int cz, const T* __restrict__ uc,
+                              T* __restrict__ u) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= df.cells) return;
+    int i, j, k;
+    cell_coords(df, c, i, j, k);
+    int ii[2], jj[2], kk[2];
+    T wi[2], wj[2], wk[2];
+    int ni, nj, nk;
+    if (!cx) { ii[0] = i; wi[0] = T(1); ni = 1; }
+    else if (!(i & 1)) { ii[0] = i >> 1; wi[0] = T(1); ni = 1; }
+    else { ii[0] = i >> 1; ii[1] = (i >> 1) + 1; wi[0] = wi[1] = T(0.5); ni = 2; }
+    if (!cy) { jj[0] = j; wj[0] = T(1); nj = 1; }
+    else if (!(j & 1)) { jj[0] = j >> 1; wj[0] = T(1); nj = 1; }
+    else { jj[0] = j >> 1; jj[1] = (j >> 1) + 1; wj[0] = wj[1] = T(0.5); nj = 2; }
+    if (!cz) { kk[0] = k; wk[0] = T(1); nk = 1; }
+    else if (!(k & 1)) { kk[0] = k >> 1; wk[0] = T(1); nk = 1; }
+    else { kk[0] = k >> 1; kk[1] = (k >> 1) + 1; wk[0] = wk[1] = T(0.5); nk = 2; }
+    T acc = T(0);
+    for (int p = 0; p < ni; ++p)
+        for (int q = 0; q < nj; ++q)
+            for (int r = 0; r < nk; ++r)
+                acc += wi[p] * wj[q] * wk[r] * uc[cell_index(dc, ii[p], jj[q], kk[r])];
+    u[c] += acc;
+}
+
+// Coarsest level (64 nodes): Gauss-Jordan inversion with partial pivoting of
+// the bordered system [L 1; 1^T 0] (65 x 65), in FP64, by one block working
+// on the augmented matrix [M | I] held in global memory (65 x 130).
+constexpr int kNc = 64, kNb = 65, kW = 130;
+
+template <typename T>
+__global__ void k_coarse_invert(Dims d, double hx, double hy, double hz, const T* __restrict__ a,
+                                double* __restrict__ aug) {
+    __shared__ double fac[kNb];
+    __shared__ int piv_row;
+    for (int e = threadIdx.x; e < kNb * kW; e += blockDim.x) aug[e] = 0.0;
+    __syncthreads();
+    if (threadIdx.x < kNc) {
+        const int c = threadIdx.x;
+        int i, j, k;
+        cell_coords(d, c, i, j, k);
+        const int nb[6] = {cell_index(d, i + 1, j, k), cell_index(d, i - 1, j, k),
+                           cell_index(d, i, j + 1, k), cell_index(d, i, j - 1, k),
+                           cell_index(d, i, j, k + 1), cell_index(d, i, j, k - 1)};
+        const double hh[3] = {hx, hy, hz};
+        double diag = 0.0;
+        for (int q = 0; q < 6; ++q) {
+            double w = 0.5 * ((double)a[c] + (double)a[nb[q]]) * hh[q >> 1];
+            diag += w;
+            aug[c * kW + nb[q]] += w;  // row c of L; distinct neighbours on 4^3
+        }
+        aug[c * kW + c] -= diag;
+        aug[c * kW + kNc] = 1.0;
+        aug[kNc * kW + c] = 1.0;
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < kNb; r += blockDim.x) aug[r * kW + kNb + r] = 1.0;
+    __syncthreads();
+    for (int p = 0; p < kNb; ++p) {
+        if (threadIdx.x == 0) {
+            int best = p;
+            double bv = fabs(aug[p * kW + p]);
+            for (int r = p + 1; r < kNb; ++r) {
+                double v = fabs(aug[r * kW + p]);
+                if (v > bv) { bv = v; best = r; }
+            }
+            piv_row = best;
+        }
+        __syncthreads();
+        const int pr = piv_row;
+        if (pr != p)
+            for (int cc = threadIdx.x; cc < kW; cc += blockDim.x) {
+                double t = aug[p * kW + cc];
+                aug[p * kW + cc] = aug[pr * kW + cc];
+                aug[pr * kW + cc] = t;
+            }
+        __syncthreads();
+        const double pv = aug[p * kW + p];
+        __syncthreads();
+        for (int cc = threadIdx.x; cc < kW; cc += blockDim.x) aug[p * kW + cc] /= pv;
+        __syncthreads();
+        for (int r = threadIdx.x; r < kNb; r += blockDim.x) fac[r] = aug[r * kW + p];
+        __syncthreads();
+        for (int e = threadIdx.x; e < kNb * kW; e += blockDim.x) {
+            const int r = e / kW, cc = e - r * kW;
+            if (r != p) aug[e] -= fac[r] * aug[p * kW + cc];
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__global__ void k_coarse_solve(const double* __restrict__ aug, const T* __restrict__ f,
+                               T* __restrict__ u) {
+    const int r = threadIdx.x;
+    if (r >= kNc) return;
+    double acc = 0.0;
+    for (int c = 0; c < kNc; ++c) acc += aug[r * kW + kNb + c] * (double)f[c];
+    u[r] = (T)acc;
+}
+
+__global__ void k_correct(int cells, double* __restrict__ u, const float* __restrict__ e) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < cells) u[c] += (double)e[c];
+}
+
+}  // namespace
+
+template <typename T>
+void launch_rbgs_sweep(const Level& L, T* u, const T* f, const T* a, cudaStream_t st) {
+    const int half = L.d.cells >> 1;
+    launch_counter() += 2;
+    for (int colour = 0; colour < 2; ++colour)
+        k_rbgs_colour<T><<<nblocks(half), kThreads, 0, st>>>(L.d, (T)L.h2i[0], (T)L.h2i[1],
+                                                             (T)L.h2i[2], colour, u, f, a);
+}
+
+template <typename T>
+void launch_residual(const Level& L, const T* u, const T* f, const T* a, T* r, cudaStream_t st) {
+    launch_counter()++;
+    k_residual<T><<<nblocks(L.d.cells), kThreads, 0, st>>>(L.d, (T)L.h2i[0], (T)L.h2i[1],
+                                                           (T)L.h2i[2], u, f, a, r);
+}
+
+template <typename T>
+void launch_restrict(const Level& fine, const Level& coarse, const T* in, T* out, cudaStream_t st) {
+    launch_counter()++;
+    k_restrict<T><<<nblocks(coarse.d.cells), kThreads, 0, st>>>(
+        fine.d, coarse.d, fine.coarsen[0], fine.coarsen[1], fine.coarsen[2], in, out);
+}
+
+template <typename T>
+void launch_prolong_add(const Level& fine, const Level& coarse, const T* uc, T* u, cudaStream_t st) {
+    launch_counter()++;
+    k_prolong_add<T><<<nblocks(fine.d.cells), kThreads, 0, st>>>(
+        fine.d, coarse.d, fine.coarsen[0], fine.coarsen[1], fine.coarsen[2], uc, u);
+}
+
+template <typename T>
+void launch_coarse_invert(const Level& L, const T* a, double* minv, cudaStream_t st) {
+    launch_counter()++;
+    k_coarse_invert<T><<<1, 256, 0, st>>>(L.d, L.h2i[0], L.h2i[1], L.h2i[2], a, minv);
+}
+
+template <typename T>
+void launch_coarse_solve(const double* minv, const T* f, T* u, cudaStream_t st) {
+    launch_counter()++;
+    k_coarse_solve<T><<<1, kNc, 0, st>>>(minv, f, u);
+}
+
+void launch_residual64_to32(const Level& L, const double* u, const double* f, const double* a,
+                            float* r32, double* partials, cudaStream_t st) {
+    launch_counter()++;
+    k_residual64_to32<<<kRedBlocks, kRedThreads, 0, st>>>(L.d, L.h2i[0], L.h2i[1], L.h2i[2], u, f,
+                                                          a, r32, partials);
+}
+
+void launch_residual_norm64(const Level& L, const double* u, const double* f, const double* a,
+                            double* partials, cudaStream_t st) {
+    launch_counter()++;
+    k_residual64_to32<<<kRedBlocks, kRedThreads, 0, st>>>(L.d, L.h2i[0], L.h2i[1], L.h2i[2], u, f,
+                                                          a, nullptr, partials);
+}
+
+void launch_correct(int cells, double* u, const float* e, cudaStream_t st) {
+    launch_counter()++;
+    k_correct<<<nblocks(cells), kThreads, 0, st>>>(cells, u, e);
+}
+
+#define RECON_INSTANTIATE(T)                                                                    \
+    template void launch_rbgs_sweep<T>(const Level&, T*, const T*, const T*, cudaStream_t);   \
+    template void launch_residual<T>(const Level&, const T*, const T*, const T*, T*,           \
+                                     cudaStream_t);                                           \
+    template void launch_restrict<T>(const Level&, const Level&, const T*, T*, cudaStream_t);  \
+    template void launch_prolong_add<T>(const Level&, const Level&, const T*, T*,              \
+                                        cudaStream_t);                                        \
+    template void launch_coarse_invert<T>(const Level&, const T*, double*, cudaStream_t);      \
+    template void launch_coarse_solve<T>(const double*, const T*, T*, cudaStream_t);
+RECON_INSTANTIATE(float)
+RECON_INSTANTIATE(double)
+#undef RECON_INSTANTIATE
+
+}  // namespace recon

@@ -1,0 +1,644 @@
+// recon_api.cu -- the C ABI (include/recon.h) and the host orchestration of
+// the moving-mesh solve (Sec. II, App. A of Zhu et al. 2016): per step the
+// deposit on the deformed mesh, the limited smoothed source, the multigrid
+// solve of the linearised equation (FP64, or FP32 V-cycles inside an FP64
+// defect correction), the smoothed increment, the step limiter and the advance.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/recon.h"
+#include "recon_internal.cuh"
+
+using namespace recon;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(RECON_E_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                                  \
+    } while (0)
+
+struct Handle {
+    recon_params p{};
+    std::vector<double> replay;
+    cudaStream_t st = nullptr;
+    int device = 0;
+    Dims d{};
+    int cells = 0;
+    double h = 1.0;
+    std::vector<Level> lv;
+    bool mixed = false;
+
+    // FP64 state (device)
+    double *rho = nullptr, *w = nullptr, *ox = nullptr, *oy = nullptr, *oz = nullptr;
+    double *phi = nullptr, *m = nullptr, *a64 = nullptr, *t = nullptr, *s = nullptr;
+    double *phidot = nullptr, *dphi = nullptr, *v3 = nullptr;  // v3: 3 x cells
+    unsigned long long* mfix = nullptr;
+    // multigrid per level: FP64 (FP64 mode) or FP32 (mixed mode)
+    std::vector<double*> u64, f64, c64, r64;
+    std::vector<float*> u32, f32, c32, r32;
+    double* minv = nullptr;
+    double* part[4] = {nullptr, nullptr, nullptr, nullptr};
+    double* scal = nullptr;   // device scalars
+    double* hscal = nullptr;  // pinned host copy
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::vector<void*> allocs;
+    // params.profile: event pairs around the finest-level smoothing sweeps
+    std::vector<cudaEvent_t> prof_ev;
+    size_t prof_used = 0;
+    int prof_sweeps = 0;
+
+    bool have_density = false, solved = false;
+    double rho_sum = 0.0;
+    double last_mass = 0.0;
+};
+
+template <typename T>
+int dalloc(Handle* H, T** p, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(RECON_E_OOM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T),
+                    cudaGetErrorString(e));
+    }
+    H->allocs.push_back(q);
+    *p = (T*)q;
+    return RECON_OK;
+}
+
+void free_all(Handle* H) {
+    for (void* q : H->allocs) cudaFree(q);
+    H->allocs.clear();
+    if (H->hscal) cudaFreeHost(H->hscal);
+    if (H->ev0) cudaEventDestroy(H->ev0);
+    if (H->ev1) cudaEventDestroy(H->ev1);
+    H->hscal = nullptr, H->ev0 = H->ev1 = nullptr;
+    for (cudaEvent_t e : H->prof_ev) cudaEventDestroy(e);
+    H->prof_ev.clear();
+}
+
+// Record one profiling event on the handle's stream (events are pooled).
+void prof_mark(Handle* H) {
+    if (H->prof_used == H->prof_ev.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        H->prof_ev.push_back(e);
+    }
+    cudaEventRecord(H->prof_ev[H->prof_used++], H->st);
+}
+
+template <typename T>
+void smooth_sweeps(Handle* H, int l, int nu, T* u, const T* f, const T* c) {
+    const bool prof = H->p.profile && l == 0 && nu > 0;
+    if (prof) prof_mark(H);
+    for (int s = 0; s < nu; ++s) launch_rbgs_sweep<T>(H->lv[l], u, f, c, H->st);
+    if (prof) {
+        prof_mark(H);
+        H->prof_sweeps += nu;
+    }
+}
+
+bool pow2_ge(int v, int lo) { return v >= lo && (v & (v - 1)) == 0; }
+
+int check_params(const recon_params* p) {
+    if (!p) return fail(RECON_E_INVALID, "params is NULL");
+    for (int a = 0; a < 3; ++a)
+        if (!pow2_ge(p->n[a], 8) || p->n[a] > 4096)
+            return fail(RECON_E_INVALID, "n[%d] = %d must be a power of two in [8, 4096]", a, p->n[a]);
+    if ((long long)p->n[0] * p->n[1] * p->n[2] > (1ll << 30))
+        return fail(RECON_E_INVALID, "grid larger than 2^30 cells");
+    bool zero_box = p->box[0] == 0.0 && p->box[1] == 0.0 && p->box[2] == 0.0;
+    if (!zero_box) {
+        for (int a = 0; a < 3; ++a)
+            if (!(p->box[a] > 0.0) || !std::isfinite(p->box[a]))
+                return fail(RECON_E_INVALID, "box[%d] must be positive", a);
+        double h0 = p->box[0] / p->n[0];
+        for (int a = 1; a < 3; ++a)
+            if (std::fabs(p->box[a] / p->n[a] - h0) > 1e-12 * h0)
+                return fail(RECON_E_INVALID, "cells must be cubic (box[a]/n[a] equal)");
+    }
+    if (p->precision != RECON_FP64 && p->precision != RECON_MIXED)
+        return fail(RECON_E_INVALID, "precision must be RECON_FP64 or RECON_MIXED");
+    if (!(p->xi_m > 0.0 && p->xi_m < 1.0)) return fail(RECON_E_INVALID, "need 0 < xi_m < 1");
+    if (!(p->v_m > 1.0)) return fail(RECON_E_INVALID, "need v_m > 1");
+    if (!(p->a_min > 0.0)) return fail(RECON_E_INVALID, "need a_min > 0");
+    if (p->climiter < 0 || p->climiter > 2) return fail(RECON_E_INVALID, "bad climiter");
+    if (!(p->s_side >= 0.0 && p->s_side <= 0.25)) return fail(RECON_E_INVALID, "need 0 <= s_side <= 1/4");
+    if (p->nu1 < 0 || p->nu2 < 0 || p->nu1 + p->nu2 == 0 || p->nu1 > 16 || p->nu2 > 16)
+        return fail(RECON_E_INVALID, "bad nu1/nu2");
+    if (!(p->tol_in > 0.0) || p->max_vcycles < 1) return fail(RECON_E_INVALID, "bad tol_in/max_vcycles");
+    if (!(p->tol_out >= 0.0) || p->k_max < 0) return fail(RECON_E_INVALID, "bad tol_out/k_max");
+    if (!(p->d_max > 0.0)) return fail(RECON_E_INVALID, "need d_max > 0");
+    if (!(p->alpha_min > 0.0 && p->alpha_min <= 1.0)) return fail(RECON_E_INVALID, "need 0 < alpha_min <= 1");
+    if (!(p->lambda_floor >= 0.0 && p->lambda_floor < 1.0)) return fail(RECON_E_INVALID, "need 0 <= lambda_floor < 1");
+    return RECON_OK;
+}
+
+// 2^F with F chosen so that any partial sum of terms totalling <= total stays
+// below 2^61 in the signed 64-bit accumulator.
+double fixed_scale(double total) {
+    int e = 0;
+    std::frexp(total > 1.0 ? total : 1.0, &e);  // total < 2^e
+    return std::ldexp(1.0, 61 - e);
+}
+
+int sync_scalars(Handle* H) {
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(H->hscal, H->scal, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, H->st));
+    CK(cudaStreamSynchronize(H->st));
+    return RECON_OK;
+}
+
+// ------------------------------------------------------------ V-cycles
+
+template <typename T>
+struct MG {
+    std::vector<T*>& u;
+    std::vector<T*>& f;
+    std::vector<T*>& c;
+    std::vector<T*>& r;
+};
+
+template <typename T>
+void vcycle(Handle* H, MG<T>& g, int l, T* u, const T* f) {
+    const int last = (int)H->lv.size() - 1;
+    const Level& L = H->lv[l];
+    if (l == last) {
+        launch_coarse_solve<T>(H->minv, f, u, H->st);
+        return;
+    }
+    smooth_sweeps<T>(H, l, H->p.nu1, u, f, g.c[l]);
+    launch_residual<T>(L, u, f, g.c[l], g.r[l], H->st);
+    launch_restrict<T>(L, H->lv[l + 1], g.r[l], g.f[l + 1], H->st);
+    cudaMemsetAsync(g.u[l + 1], 0, sizeof(T) * H->lv[l + 1].d.cells, H->st);
+    vcycle<T>(H, g, l + 1, g.u[l + 1], g.f[l + 1]);
+    launch_prolong_add<T>(L, H->lv[l + 1], g.u[l + 1], u, H->st);
+    smooth_sweeps<T>(H, l, H->p.nu2, u, f, g.c[l]);
+}
+
+template <typename T>
+void build_hierarchy(Handle* H, std::vector<T*>& c) {
+    for (size_t l = 0; l + 1 < H->lv.size(); ++l)
+        launch_restrict<T>(H->lv[l], H->lv[l + 1], c[l], c[l + 1], H->st);
+    launch_coarse_invert<T>(H->lv.back(), c.back(), H->minv, H->st);
+}
+
+// Solve L(a) phidot = s to ||s - L phidot|| <= tol_in ||s||.
+int mg_solve(Handle* H, double snorm2, int* ncyc, double* relres) {
+    *ncyc = 0;
+    *relres = 0.0;
+    CK(cudaMemsetAsync(H->phidot, 0, sizeof(double) * H->cells, H->st));
+    if (!(snorm2 > 0.0)) return RECON_OK;
+    const Level& L0 = H->lv[0];
+    if (!H->mixed) {
+        MG<double> g{H->u64, H->f64, H->c64, H->r64};
+        for (int cyc = 1; cyc <= H->p.max_vcycles; ++cyc) {
+            vcycle<double>(H, g, 0, H->phidot, H->s);
+            launch_residual_norm64(L0, H->phidot, H->s, H->a64, H->part[0], H->st);
+            finish_reduce(H->part[0], 0, H->scal, SC_RES2, H->st);
+            int rc = sync_scalars(H);
+            if (rc) return rc;
+            *ncyc = cyc;
+            *relres = std::sqrt(H->hscal[SC_RES2] / snorm2);
+            if (*relres <= H->p.tol_in) break;
+        }
+    } else {
+        MG<float> g{H->u32, H->f32, H->c32, H->r32};
+        for (int cyc = 0;; ++cyc) {
+            // FP64 defect: r = s - L phidot, handed to the FP32 V-cycle as its RHS
+            launch_residual64_to32(L0, H->phidot, H->s, H->a64, H->f32[0], H->part[0], H->st);
+            finish_reduce(H->part[0], 0, H->scal, SC_RES2, H->st);
+            int rc = sync_scalars(H);
+            if (rc) return rc;
+            *ncyc = cyc;
+            *relres = std::sqrt(H->hscal[SC_RES2] / snorm2);
+            if (*relres <= H->p.tol_in || cyc == H->p.max_vcycles) break;
+            CK(cudaMemsetAsync(H->u32[0], 0, sizeof(float) * H->cells, H->st));
+            vcycle<float>(H, g, 0, H->u32[0], H->f32[0]);
+            launch_correct(H->cells, H->phidot, H->u32[0], H->st);
+        }
+    }
+    return RECON_OK;
+}
+
+int deposit_step(Handle* H) {
+    const double scale = fixed_scale((double)H->cells);
+    launch_deposit_tracers(H->d, H->ox, H->oy, H->oz, H->w, scale, H->mfix, H->st);
+    launch_mass_coef(H->cells, H->mfix, 1.0 / scale, H->p.a_min, H->m, H->a64,
+                     H->mixed ? H->c32[0] : nullptr, H->part[0], H->st);
+    finish_reduce(H->part[0], 0, H->scal, SC_SUM_M, H->st);
+    return RECON_OK;
+}
+
+int solve(Handle* H, recon_stats* stats) {
+    const recon_params& p = H->p;
+    const int n = H->cells;
+    const long long launches0 = launch_counter().load();
+    H->prof_used = 0;
+    H->prof_sweeps = 0;
+    CK(cudaEventRecord(H->ev0, H->st));
+    // init: tracer c = node c with mass rho_c / rho_bar, phi = 0
+    const double rho_bar = H->rho_sum / (double)n;
+    launch_init_tracers(n, H->rho, 1.0 / rho_bar, H->w, H->ox, H->oy, H->oz, H->phi, H->st);
+
+    SourceParams sp{p.xi_m, p.v_m, p.climiter};
+    int kmax = 0;
+    while (kmax < 1100 && std::ldexp(1.0, -(kmax + 1)) >= p.alpha_min) ++kmax;
+    LimiterParams lp{p.lambda_floor, kmax};
+
+    int status = RECON_NOT_CONVERGED, k = 0, vtot = 0;
+    double R0 = 0.0, R = 0.0;
+    bool need_final_deposit = true;
+    for (k = 0; k < p.k_max; ++k) {
+        deposit_step(H);
+        launch_geometry_source(H->d, sp, H->phi, H->m, H->t, H->part[0], H->part[1], H->st);
+        finish_reduce(H->part[0], 0, H->scal, SC_SUM_T, H->st);
+        finish_reduce(H->part[1], 1, H->scal, SC_MIN_DET, H->st);
+        launch_smooth_S(H->d, p.s_side, H->t, H->scal + SC_SUM_T, H->s, nullptr, H->part[2], H->st);
+        finish_reduce(H->part[2], 0, H->scal, SC_SUM_S2, H->st);
+        int rc = sync_scalars(H);
+        if (rc) return rc;
+        const double s2 = H->hscal[SC_SUM_S2];
+        R = std::sqrt(s2 / (double)n);
+        if (k == 0) R0 = R;
+        H->last_mass = H->hscal[SC_SUM_M];
+        if (stats && stats->Rk) stats->Rk[k] = R;
+        if (R <= p.tol_out) {
+            status = RECON_OK;
+            need_final_deposit = false;
+            break;
+        }
+        if (H->mixed) build_hierarchy<float>(H, H->c32);
+        else build_hierarchy<double>(H, H->c64);
+        int ncyc = 0;
+        double rel = 0.0;
+        rc = mg_solve(H, s2, &ncyc, &rel);
+        if (rc) return rc;
+        vtot += ncyc;
+        // dphi = S phidot (its mean is removed in the advance)
+        launch_smooth_S(H->d, p.s_side, H->phidot, nullptr, H->dphi, H->part[0], nullptr, H->st);
+        finish_reduce(H->part[0], 0, H->scal, SC_SUM_DPHI, H->st);
+        double alpha;
+        if (!H->replay.empty()) {
+            alpha = H->replay[k];
+        } else {
+            launch_limiter(H->d, lp, H->phi, H->dphi, H->part[1], H->part[2], H->st);
+            finish_reduce(H->part[1], 2, H->scal, SC_MAX_K, H->st);
+            finish_reduce(H->part[2], 2, H->scal, SC_MAX_G, H->st);
+            rc = sync_scalars(H);
+            if (rc) return rc;
+            const int kpd = (int)H->hscal[SC_MAX_K];
+            const double gmax = H->hscal[SC_MAX_G];
+            if (kpd > kmax)
+                return fail(RECON_E_LIMITER, "step %d: no alpha >= alpha_min keeps the map positive definite", k);
+            alpha = std::ldexp(1.0, -kpd);
+            while (alpha * gmax > p.d_max && alpha >= p.alpha_min) alpha *= 0.5;
+            if (alpha < p.alpha_min)
+                return fail(RECON_E_LIMITER, "step %d: move limit needs alpha < alpha_min", k);
+        }
+        launch_node_velocity(H->d, H->phi, H->dphi, H->v3, H->v3 + n, H->v3 + 2 * (size_t)n, H->st);
+        launch_advance(H->d, H->v3, H->v3 + n, H->v3 + 2 * (size_t)n, alpha, H->dphi,
+                       H->scal + SC_SUM_DPHI, H->ox, H->oy, H->oz, H->phi, H->st);
+        if (stats) {
+            if (stats->alpha) stats->alpha[k] = alpha;
+            if (stats->ncycles) stats->ncycles[k] = ncyc;
+            if (stats->relres) stats->relres[k] = rel;
+        }
+    }
+    if (need_final_deposit) {
+        deposit_step(H);
+        int rc = sync_scalars(H);
+        if (rc) return rc;
+        H->last_mass = H->hscal[SC_SUM_M];
+    }
+    CK(cudaEventRecord(H->ev1, H->st));
+    CK(cudaEventSynchronize(H->ev1));
+    H->solved = true;
+    if (stats) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, H->ev0, H->ev1);
+        stats->status = status;
+        stats->steps = k;
+        stats->vcycles = vtot;
+        stats->R0 = R0;
+        stats->R = R;
+        stats->ms = ms;
+        stats->mass_error = std::fabs(H->last_mass - (double)n) / (double)n;
+        stats->launches = launch_counter().load() - launches0;
+        double sm = 0.0;
+        for (size_t q = 0; q + 1 < H->prof_used; q += 2) {
+            float e = 0.f;
+            if (cudaEventElapsedTime(&e, H->prof_ev[q], H->prof_ev[q + 1]) == cudaSuccess) sm += e;
+        }
+        cudaGetLastError();
+        stats->smooth_ms = sm;
+        stats->smooth_sweeps = H->prof_sweeps;
+        // one sweep reads u, a, f and writes u at the finest level
+        stats->smooth_bytes = 4.0 * (H->mixed ? sizeof(float) : sizeof(double)) * (double)n;
+        launch_geometry_out(H->d, H->phi, nullptr, nullptr, H->part[0], H->part[1], H->st);
+        finish_reduce(H->part[0], 1, H->scal, SC_MIN_DET, H->st);
+        finish_reduce(H->part[1], 1, H->scal, SC_MIN_LAM, H->st);
+        launch_delta_r(H->d, H->phi, H->t, H->part[2], H->st);
+        finish_reduce(H->part[2], 2, H->scal, SC_MAX_DR, H->st);
+        int rc = sync_scalars(H);
+        if (rc) return rc;
+        stats->min_det = H->hscal[SC_MIN_DET];
+        stats->min_lambda0 = H->hscal[SC_MIN_LAM];
+        stats->max_delta_r = H->hscal[SC_MAX_DR];
+    }
+    return status;
+}
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" {
+
+int recon_default_params(recon_params* p, int n0, int n1, int n2) {
+    if (!p) return fail(RECON_E_INVALID, "params is NULL");
+    std::memset(p, 0, sizeof(*p));
+    p->n[0] = n0, p->n[1] = n1, p->n[2] = n2;
+    p->precision = RECON_FP64;
+    p->xi_m = 0.1;
+    p->v_m = 10.0;
+    p->a_min = 0.01;
+    p->climiter = RECON_CLIM_SOFT;
+    p->s_side = 0.25;
+    p->nu1 = 2, p->nu2 = 2;
+    p->tol_in = 1e-8;
+    p->max_vcycles = 50;
+    p->tol_out = 1e-3;
+    p->k_max = 40;
+    p->d_max = 0.5;
+    p->alpha_min = std::ldexp(1.0, -20);
+    p->lambda_floor = 0.02;
+    p->replay_alpha = nullptr;
+    return RECON_OK;
+}
+
+int recon_create(void** out, const recon_params* p, void* cuda_stream) {
+    g_err[0] = 0;
+    if (!out) return fail(RECON_E_INVALID, "out is NULL");
+    *out = nullptr;
+    int rc = check_params(p);
+    if (rc) return rc;
+    Handle* H = new Handle();
+    H->p = *p;
+    if (p->replay_alpha) H->replay.assign(p->replay_alpha, p->replay_alpha + p->k_max);
+    H->p.replay_alpha = nullptr;
+    H->st = (cudaStream_t)cuda_stream;
+    H->mixed = p->precision == RECON_MIXED;
+    cudaGetDevice(&H->device);
+    H->d = make_dims(p->n[0], p->n[1], p->n[2]);
+    H->cells = H->d.cells;
+    H->h = (p->box[0] > 0.0) ? p->box[0] / p->n[0] : 1.0;
+    // levels: halve every axis longer than 4 until all are 4
+    {
+        Level L{};
+        L.d = H->d;
+        for (int a = 0; a < 3; ++a) L.h2i[a] = 1.0;
+        while (true) {
+            int nn[3] = {L.d.n0, L.d.n1, L.d.n2};
+            for (int a = 0; a < 3; ++a) L.coarsen[a] = nn[a] > 4;
+            H->lv.push_back(L);
+            if (!L.coarsen[0] && !L.coarsen[1] && !L.coarsen[2]) break;
+            Level C{};
+            int cn[3];
+            for (int a = 0; a < 3; ++a) {
+                cn[a] = L.coarsen[a] ? nn[a] / 2 : nn[a];
+                C.h2i[a] = L.coarsen[a] ? L.h2i[a] * 0.25 : L.h2i[a];
+            }
+            C.d = make_dims(cn[0], cn[1], cn[2]);
+            L = C;
+        }
+    }
+    const size_t n = H->cells;
+    const int nl = (int)H->lv.size();
+#define AL(ptr, cnt)                          \
+    do {                                      \
+        if ((rc = dalloc(H, &(ptr), (cnt)))) { \
+            free_all(H);                      \
+            delete H;                         \
+            return rc;                        \
+        }                                     \
+    } while (0)
+    AL(H->rho, n); AL(H->w, n); AL(H->ox, n); AL(H->oy, n); AL(H->oz, n);
+    AL(H->phi, n); AL(H->m, n); AL(H->a64, n); AL(H->t, n); AL(H->s, n);
+    AL(H->phidot, n); AL(H->dphi, n); AL(H->v3, 3 * n); AL(H->mfix, n);
+    AL(H->minv, 65 * 130); AL(H->scal, SC_COUNT);
+    for (int q = 0; q < 4; ++q) AL(H->part[q], kRedBlocks);
+    if (!H->mixed) {
+        H->u64.assign(nl, nullptr), H->f64.assign(nl, nullptr), H->c64.assign(nl, nullptr),
+            H->r64.assign(nl, nullptr);
+        H->u64[0] = H->phidot, H->f64[0] = H->s, H->c64[0] = H->a64;
+        AL(H->r64[0], n);
+        for (int l = 1; l < nl; ++l) {
+            size_t cl = H->lv[l].d.cells;
+            AL(H->u64[l], cl); AL(H->f64[l], cl); AL(H->c64[l], cl); AL(H->r64[l], cl);
+        }
+    } else {
+        H->u32.assign(nl, nullptr), H->f32.assign(nl, nullptr), H->c32.assign(nl, nullptr),
+            H->r32.assign(nl, nullptr);
+        for (int l = 0; l < nl; ++l) {
+            size_t cl = H->lv[l].d.cells;
+            AL(H->u32[l], cl); AL(H->f32[l], cl); AL(H->c32[l], cl); AL(H->r32[l], cl);
+        }
+    }
+#undef AL
+    if (cudaMallocHost((void**)&H->hscal, SC_COUNT * sizeof(double)) != cudaSuccess ||
+        cudaEventCreate(&H->ev0) != cudaSuccess || cudaEventCreate(&H->ev1) != cudaSuccess) {
+        cudaGetLastError();
+        free_all(H);
+        delete H;
+        return fail(RECON_E_OOM, "pinned host buffer or event creation failed");
+    }
+    cudaError_t e = cudaMemsetAsync(H->mfix, 0, n * sizeof(unsigned long long), H->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(H->st);
+    if (e != cudaSuccess) {
+        free_all(H);
+        delete H;
+        return fail(RECON_E_CUDA, "initialisation failed: %s", cudaGetErrorString(e));
+    }
+    *out = H;
+    return RECON_OK;
+}
+
+int recon_deposit(void* hp, int mode, const double* data, const double* mass, int64_t np) {
+    g_err[0] = 0;
+    Handle* H = (Handle*)hp;
+    if (!H || !data) return fail(RECON_E_INVALID, "handle or data is NULL");
+    const int n = H->cells;
+    H->have_density = false;
+    H->solved = false;
+    if (mode == RECON_GRID) {
+        if (mass) return fail(RECON_E_INVALID, "RECON_GRID takes no mass array");
+        if (np != n) return fail(RECON_E_INVALID, "RECON_GRID needs np == cell count (%d)", n);
+        CK(cudaMemcpyAsync(H->rho, data, sizeof(double) * n, cudaMemcpyDefault, H->st));
+        launch_validate_grid(n, H->rho, H->part[0], H->part[1], H->st);
+    } else if (mode == RECON_PARTICLES) {
+        if (np <= 0) return fail(RECON_E_INVALID, "no particles");
+        // host inputs are staged through a temporary device buffer
+        const double* dpos = data;
+        const double* dmass = mass;
+        void* stage = nullptr;
+        bool host_pos = !is_device_ptr(data), host_mass = mass && !is_device_ptr(mass);
+        size_t bytes = (host_pos ? 3 * sizeof(double) * np : 0) + (host_mass ? sizeof(double) * np : 0);
+        if (bytes) {
+            cudaError_t e = cudaMallocAsync(&stage, bytes, H->st);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return fail(RECON_E_OOM, "staging buffer of %zu bytes failed", bytes);
+            }
+            char* q = (char*)stage;
+            if (host_pos) {
+                CK(cudaMemcpyAsync(q, data, 3 * sizeof(double) * np, cudaMemcpyHostToDevice, H->st));
+                dpos = (const double*)q;
+                q += 3 * sizeof(double) * np;
+            }
+            if (host_mass) {
+                CK(cudaMemcpyAsync(q, mass, sizeof(double) * np, cudaMemcpyHostToDevice, H->st));
+                dmass = (const double*)q;
+            }
+        }
+        launch_validate_particles(np, dpos, dmass, H->part[0], H->part[1], H->st);
+        finish_reduce(H->part[0], 0, H->scal, SC_SUM_RHO, H->st);
+        finish_reduce(H->part[1], 2, H->scal, SC_BAD, H->st);
+        int rc = sync_scalars(H);
+        if (rc == RECON_OK && H->hscal[SC_BAD] != 0.0)
+            rc = fail(RECON_E_NONFINITE, "particle positions or masses are not finite / negative");
+        if (rc == RECON_OK && !(H->hscal[SC_SUM_RHO] > 0.0))
+            rc = fail(RECON_E_INVALID, "total particle mass is zero");
+        if (rc == RECON_OK) {
+            const double scale = fixed_scale(H->hscal[SC_SUM_RHO]);
+            launch_deposit_particles(H->d, np, dpos, dmass, 1.0 / H->h, scale, H->mfix, H->st);
+            launch_fix_to_double(n, H->mfix, 1.0 / scale, H->rho, H->st);
+            launch_validate_grid(n, H->rho, H->part[0], H->part[1], H->st);
+        }
+        if (stage) cudaFreeAsync(stage, H->st);
+        if (rc) {
+            cudaStreamSynchronize(H->st);
+            return rc;
+        }
+    } else {
+        return fail(RECON_E_INVALID, "unknown deposit mode %d", mode);
+    }
+    finish_reduce(H->part[0], 0, H->scal, SC_SUM_RHO, H->st);
+    finish_reduce(H->part[1], 2, H->scal, SC_BAD, H->st);
+    int rc = sync_scalars(H);
+    if (rc) return rc;
+    if (H->hscal[SC_BAD] != 0.0) return fail(RECON_E_NONFINITE, "density has NaN/Inf or negative values");
+    if (!(H->hscal[SC_SUM_RHO] > 0.0)) return fail(RECON_E_INVALID, "total density is zero");
+    H->rho_sum = H->hscal[SC_SUM_RHO];
+    H->have_density = true;
+    return RECON_OK;
+}
+
+int recon_solve(void* hp, recon_stats* stats) {
+    g_err[0] = 0;
+    Handle* H = (Handle*)hp;
+    if (!H) return fail(RECON_E_INVALID, "handle is NULL");
+    if (!H->have_density) return fail(RECON_E_STATE, "recon_deposit must succeed before recon_solve");
+    int rc = solve(H, stats);
+    if (rc < 0) {
+        cudaStreamSynchronize(H->st);
+        H->solved = false;
+        if (stats) stats->status = rc;
+    }
+    return rc;
+}
+
+int recon_field(void* hp, int which, void* dst, size_t dst_bytes) {
+    g_err[0] = 0;
+    Handle* H = (Handle*)hp;
+    if (!H || !dst) return fail(RECON_E_INVALID, "handle or dst is NULL");
+    const size_t n = H->cells;
+    const size_t need = (which == RECON_FIELD_MESH_X ? 3 : 1) * n * sizeof(double);
+    if (dst_bytes < need) return fail(RECON_E_INVALID, "dst holds %zu bytes, need %zu", dst_bytes, need);
+    if (which == RECON_FIELD_DENSITY) {
+        if (!H->have_density) return fail(RECON_E_STATE, "no density deposited");
+        CK(cudaMemcpyAsync(dst, H->rho, need, cudaMemcpyDefault, H->st));
+        CK(cudaStreamSynchronize(H->st));
+        return RECON_OK;
+    }
+    if (!H->solved) return fail(RECON_E_STATE, "no completed solve");
+    const double* src = nullptr;
+    switch (which) {
+        case RECON_FIELD_PHI:
+            launch_scale(H->cells, H->phi, H->h * H->h, H->t, H->st);
+            src = H->t;
+            break;
+        case RECON_FIELD_DELTA_R:
+            launch_delta_r(H->d, H->phi, H->t, H->part[0], H->st);
+            src = H->t;
+            break;
+        case RECON_FIELD_MESH_X:
+            launch_mesh_x(H->d, H->phi, H->h, H->v3, H->st);
+            src = H->v3;
+            break;
+        case RECON_FIELD_MASS:
+            src = H->m;
+            break;
+        case RECON_FIELD_DET:
+            launch_geometry_out(H->d, H->phi, H->t, nullptr, H->part[0], H->part[1], H->st);
+            src = H->t;
+            break;
+        case RECON_FIELD_LAMBDA0:
+            launch_geometry_out(H->d, H->phi, nullptr, H->t, H->part[0], H->part[1], H->st);
+            src = H->t;
+            break;
+        default:
+            return fail(RECON_E_INVALID, "unknown field %d", which);
+    }
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(dst, src, need, cudaMemcpyDefault, H->st));
+    CK(cudaStreamSynchronize(H->st));
+    return RECON_OK;
+}
+
+int recon_adjoint(void* hp, const double* grad_delta_r, double* grad_rho) {
+    (void)hp, (void)grad_delta_r, (void)grad_rho;
+    return fail(RECON_E_UNSUPPORTED, "recon_adjoint is not available in this build");
+}
+
+void recon_destroy(void* hp) {
+    Handle* H = (Handle*)hp;
+    if (!H) return;
+    cudaStreamSynchronize(H->st);
+    free_all(H);
+    delete H;
+}
+
+const char* recon_last_error(void) { return g_err; }
+
+}  // extern "C"

@@ -1,0 +1,153 @@
+// recon_internal.cuh -- shared declarations of the CUDA kernels' launch
+// wrappers and the grid helpers (internal to librecon.so).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+
+namespace recon {
+
+// Kernels launched by this library (for the launch count a solve reports).
+inline std::atomic<long long>& launch_counter() {
+    static std::atomic<long long> c{0};
+    return c;
+}
+
+// Periodic power-of-two grid: n0 x n1 x n2 nodes, last axis fastest.
+struct Dims {
+    int n0, n1, n2;
+    int s1, s2;      // log2(n1), log2(n2)
+    int cells;       // n0 * n1 * n2 (<= 2^30)
+};
+
+inline Dims make_dims(int n0, int n1, int n2) {
+    Dims d;
+    d.n0 = n0, d.n1 = n1, d.n2 = n2;
+    d.s1 = 0;
+    while ((1 << d.s1) < n1) ++d.s1;
+    d.s2 = 0;
+    while ((1 << d.s2) < n2) ++d.s2;
+    d.cells = n0 * n1 * n2;
+    return d;
+}
+
+__host__ __device__ inline int cell_index(const Dims& d, int i, int j, int k) {
+    return ((((i & (d.n0 - 1)) << d.s1) | (j & (d.n1 - 1))) << d.s2) | (k & (d.n2 - 1));
+}
+
+__host__ __device__ inline void cell_coords(const Dims& d, int c, int& i, int& j, int& k) {
+    k = c & (d.n2 - 1);
+    j = (c >> d.s2) & (d.n1 - 1);
+    i = c >> (d.s1 + d.s2);
+}
+
+// Number of blocks of the fixed-size reduction launches (2 x 608 = 8 per SM
+// on a 152-SM part) and their block size.  Reductions write one partial per
+// block and are finished by a single block in a fixed order, so every sum is
+// deterministic.
+constexpr int kRedBlocks = 1216;
+constexpr int kRedThreads = 256;
+
+// Scalars produced on the device and read back by the host.
+enum Scalar {
+    SC_SUM_RHO = 0,   // sum of the deposited density
+    SC_BAD,           // nonzero if an input was NaN/Inf/negative (as double)
+    SC_SUM_T,         // sum of t = Sigma + C + E
+    SC_MIN_DET,       // min det(I + Hess phi)
+    SC_SUM_S2,        // sum of s^2
+    SC_SUM_M,         // sum of m
+    SC_RES2,          // sum of residual^2
+    SC_SUM_DPHI,      // sum of S(phidot)
+    SC_MAX_K,         // max over nodes of the per-node limiter exponent
+    SC_MAX_G,         // max |grad dphi|
+    SC_MIN_LAM,       // min lambda0
+    SC_MAX_DR,        // max delta_r
+    SC_COUNT
+};
+
+// Operator of one multigrid level: 1/h_a^2 per axis.
+struct Level {
+    Dims d;
+    double h2i[3];
+    int coarsen[3];  // axis halved on the way to the next level
+};
+
+struct SourceParams {
+    double xi_m, v_m;
+    int climiter;
+};
+
+struct LimiterParams {
+    double lambda_floor;
+    int kmax;  // largest exponent k with 2^-k >= alpha_min
+};
+
+// ---- reductions -----------------------------------------------------------
+// op: 0 = sum, 1 = min, 2 = max.  Finishes kRedBlocks partials into slot.
+void finish_reduce(const double* partials, int op, double* scalars, int slot, cudaStream_t st);
+
+// ---- multigrid (T = float or double) --------------------------------------
+template <typename T>
+void launch_rbgs_sweep(const Level& L, T* u, const T* f, const T* a, cudaStream_t st);
+template <typename T>
+void launch_residual(const Level& L, const T* u, const T* f, const T* a, T* r, cudaStream_t st);
+template <typename T>
+void launch_restrict(const Level& fine, const Level& coarse, const T* in, T* out, cudaStream_t st);
+template <typename T>
+void launch_prolong_add(const Level& fine, const Level& coarse, const T* uc, T* u, cudaStream_t st);
+// Coarsest (4x4x4) level: invert the bordered 65 x 65 system [L 1; 1^T 0]
+// once per coefficient (FP64), then solve by one matrix-vector product.
+template <typename T>
+void launch_coarse_invert(const Level& L, const T* a, double* minv, cudaStream_t st);
+template <typename T>
+void launch_coarse_solve(const double* minv, const T* f, T* u, cudaStream_t st);
+// FP64 residual of level 0 in mixed mode: r32 = f - L u (FP64), plus sum r^2
+void launch_residual64_to32(const Level& L, const double* u, const double* f, const double* a,
+                            float* r32, double* partials, cudaStream_t st);
+// FP64 residual norm only: partials of (f - L u)^2
+void launch_residual_norm64(const Level& L, const double* u, const double* f, const double* a,
+                            double* partials, cudaStream_t st);
+// u64 += e32
+void launch_correct(int cells, double* u, const float* e, cudaStream_t st);
+
+// ---- steps of the outer iteration -----------------------------------------
+void launch_validate_grid(int cells, const double* rho, double* partials_sum, double* partials_bad,
+                          cudaStream_t st);
+void launch_validate_particles(int64_t np, const double* pos, const double* mass,
+                               double* partials_sum, double* partials_bad, cudaStream_t st);
+void launch_deposit_particles(const Dims& d, int64_t np, const double* pos, const double* mass,
+                              double inv_h, double scale, unsigned long long* mfix, cudaStream_t st);
+void launch_fix_to_double(int cells, unsigned long long* mfix, double inv_scale, double* out,
+                          cudaStream_t st);
+void launch_init_tracers(int cells, const double* rho, double inv_rho_bar, double* w,
+                         double* ox, double* oy, double* oz, double* phi, cudaStream_t st);
+void launch_deposit_tracers(const Dims& d, const double* ox, const double* oy, const double* oz,
+                            const double* w, double scale, unsigned long long* mfix,
+                            cudaStream_t st);
+void launch_mass_coef(int cells, unsigned long long* mfix, double inv_scale, double a_min,
+                      double* m, double* a64, float* a32, double* partials, cudaStream_t st);
+void launch_geometry_source(const Dims& d, const SourceParams& sp, const double* phi,
+                            const double* m, double* t, double* part_sum, double* part_min,
+                            cudaStream_t st);
+void launch_smooth_S(const Dims& d, double s_side, const double* in, const double* shift_scalar,
+                     double* out, double* part_sum, double* part_sq, cudaStream_t st);
+void launch_limiter(const Dims& d, const LimiterParams& lp, const double* phi, const double* dphi,
+                    double* part_k, double* part_g, cudaStream_t st);
+void launch_node_velocity(const Dims& d, const double* phi, const double* dphi, double* vx,
+                          double* vy, double* vz, cudaStream_t st);
+// Tracers move by -alpha V(xi) (CIC-interpolated); phi += alpha (dphi - mean),
+// mean = *sum_dphi / cells.
+void launch_advance(const Dims& d, const double* vx, const double* vy, const double* vz,
+                    double alpha, const double* dphi, const double* sum_dphi, double* ox,
+                    double* oy, double* oz, double* phi, cudaStream_t st);
+// outputs
+void launch_delta_r(const Dims& d, const double* phi, double* out, double* part_max,
+                    cudaStream_t st);
+void launch_mesh_x(const Dims& d, const double* phi, double h, double* out, cudaStream_t st);
+void launch_geometry_out(const Dims& d, const double* phi, double* det, double* lam,
+                         double* part_min_det, double* part_min_lam, cudaStream_t st);
+void launch_scale(int cells, const double* in, double s, double* out, cudaStream_t st);
+
+}  // namespace recon

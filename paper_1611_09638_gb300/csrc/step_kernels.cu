@@ -1,0 +1,568 @@
+// step_kernels.cu -- kernels of one moving-mesh step (Sec. II, App. A) other
+// than the multigrid solve: CIC deposits in 64-bit fixed point, geometry of
+// the map x = xi + grad phi, the limited source of Eq. (elliptic), the
+// smoothing operator S, the step limiter, the mesh advance and the outputs.
+#include "recon_internal.cuh"
+#include "reduce.cuh"
+
+namespace recon {
+
+namespace {
+
+constexpr int kThreads = 256;
+inline int nblocks(long long work) { return (int)((work + kThreads - 1) / kThreads); }
+
+// ---------------------------------------------------------------- helpers
+
+struct Sym3 {
+    double xx, yy, zz, xy, xz, yz;
+};
+
+// Hessian of f at node (i,j,k): 3-point second differences on the diagonal,
+// 4-point centred cross differences off it.
+__device__ inline Sym3 hessian(const Dims& d, const double* __restrict__ f, int i, int j, int k) {
+    const double c = f[cell_index(d, i, j, k)];
+    Sym3 H;
+    H.xx = f[cell_index(d, i + 1, j, k)] - 2.0 * c + f[cell_index(d, i - 1, j, k)];
+    H.yy = f[cell_index(d, i, j + 1, k)] - 2.0 * c + f[cell_index(d, i, j - 1, k)];
+    H.zz = f[cell_index(d, i, j, k + 1)] - 2.0 * c + f[cell_index(d, i, j, k - 1)];
+    H.xy = 0.25 * (f[cell_index(d, i + 1, j + 1, k)] - f[cell_index(d, i + 1, j - 1, k)] -
+                   f[cell_index(d, i - 1, j + 1, k)] + f[cell_index(d, i - 1, j - 1, k)]);
+    H.xz = 0.25 * (f[cell_index(d, i + 1, j, k + 1)] - f[cell_index(d, i + 1, j, k - 1)] -
+                   f[cell_index(d, i - 1, j, k + 1)] + f[cell_index(d, i - 1, j, k - 1)]);
+    H.yz = 0.25 * (f[cell_index(d, i, j + 1, k + 1)] - f[cell_index(d, i, j + 1, k - 1)] -
+                   f[cell_index(d, i, j - 1, k + 1)] + f[cell_index(d, i, j - 1, k - 1)]);
+    return H;
+}
+
+__device__ inline double det3(const Sym3& e) {
+    return e.xx * (e.yy * e.zz - e.yz * e.yz) - e.xy * (e.xy * e.zz - e.yz * e.xz) +
+           e.xz * (e.xy * e.yz - e.yy * e.xz);
+}
+
+// det(e - lam I) and its derivative in lam.
+__device__ inline void charpoly(const Sym3& e, double lam, double& p, double& dp) {
+    const double a = e.xx - lam, b = e.yy - lam, c = e.zz - lam;
+    p = a * (b * c - e.yz * e.yz) - e.xy * (e.xy * c - e.yz * e.xz) + e.xz * (e.xy * e.yz - b * e.xz);
+    dp = -((b * c - e.yz * e.yz) + (a * c - e.xz * e.xz) + (a * b - e.xy * e.xy));
+}
+
+// Smallest eigenvalue of a symmetric 3x3 matrix: the trigonometric closed form
+// of the characteristic cubic (O. K. Smith, CACM 4, 168, 1961), then Newton
+// steps on det(e - lam I) while they reduce |det|.
+__device__ inline double min_eig_sym3(const Sym3& e) {
+    const double p1 = e.xy * e.xy + e.xz * e.xz + e.yz * e.yz;
+    const double q = (e.xx + e.yy + e.zz) * (1.0 / 3.0);
+    const double b11 = e.xx - q, b22 = e.yy - q, b33 = e.zz - q;
+    const double p2 = b11 * b11 + b22 * b22 + b33 * b33 + 2.0 * p1;
+    if (!(p2 > 0.0)) return q;
+    const double pp = sqrt(p2 * (1.0 / 6.0));
+    const double ip = 1.0 / pp;
+    Sym3 B;
+    B.xx = b11 * ip, B.yy = b22 * ip, B.zz = b33 * ip;
+    B.xy = e.xy * ip, B.xz = e.xz * ip, B.yz = e.yz * ip;
+    double r = 0.5 * det3(B);
+    r = fmin(1.0, fmax(-1.0, r));
+    const double ang = acos(r) * (1.0 / 3.0);
+    double lam = q + 2.0 * pp * cos(ang + 2.0943951023931957);  // + 2 pi / 3
+    double p, dp;
+    charpoly(e, lam, p, dp);
+    for (int it = 0; it < 3; ++it) {
+        if (p == 0.0 || dp == 0.0) break;
+        const double cand = lam - p / dp;
+        double pc, dpc;
+        charpoly(e, cand, pc, dpc);
+        if (!(fabs(pc) < fabs(p))) break;
+        lam = cand, p = pc, dp = dpc;
+    }
+    return lam;
+}
+
+__device__ inline double climit(int reading, double xi_m, double lambda0) {
+    const double lam = lambda0 > 1e-12 ? lambda0 : 1e-12;
+    const double q = xi_m / lam;
+    double v;
+    if (reading == 1) v = q - (q - 1.0 > 0.0 ? 1.0 : 0.0);       // literal
+    else if (reading == 2) v = q * (q - 1.0 > 0.0 ? 1.0 : 0.0);  // step
+    else v = q - 1.0 > 0.0 ? q - 1.0 : 0.0;                      // soft
+    return 4.0 * v * v;
+}
+
+// lambda_min(M) > floor by Sylvester's criterion on M - floor I.
+__device__ inline bool pd_above(Sym3 M, double floor) {
+    M.xx -= floor, M.yy -= floor, M.zz -= floor;
+    return M.xx > 0.0 && (M.xx * M.yy - M.xy * M.xy) > 0.0 && det3(M) > 0.0;
+}
+
+// CIC weights along one axis for grid coordinate home + off: lower node and
+// fraction toward the upper one.
+__device__ inline void cic_offset(int home, double off, int& i0, double& f) {
+    const double fl = floor(off);
+    f = off - fl;
+    i0 = home + (int)fl;
+}
+
+__device__ inline void cic_abs(double x, int n, int& i0, double& f) {
+    const double u = x - (double)n * floor(x / (double)n);
+    const double fl = floor(u);
+    f = u - fl;
+    i0 = (int)fl;
+}
+
+__device__ inline void atomic_add_fixed(unsigned long long* p, double v, double scale) {
+    const long long q = llrint(v * scale);
+    atomicAdd(p, (unsigned long long)q);
+}
+
+// ---------------------------------------------------------------- kernels
+
+__global__ void k_validate_grid(int cells, const double* __restrict__ rho, double* ps, double* pb) {
+    double s = 0.0, bad = 0.0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cells; c += gridDim.x * blockDim.x) {
+        const double v = rho[c];
+        if (!(v >= 0.0) || !isfinite(v)) bad = 1.0;
+        else s += v;
+    }
+    s = block_reduce<OpSum>(s);
+    if (threadIdx.x == 0) ps[blockIdx.x] = s;
+    bad = block_reduce<OpMax>(bad);
+    if (threadIdx.x == 0) pb[blockIdx.x] = bad;
+}
+
+__global__ void k_validate_particles(int64_t np, const double* __restrict__ pos,
+                                     const double* __restrict__ mass, double* ps, double* pb) {
+    double s = 0.0, bad = 0.0;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < np;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const double x = pos[3 * p], y = pos[3 * p + 1], z = pos[3 * p + 2];
+        if (!isfinite(x) || !isfinite(y) || !isfinite(z)) bad = 1.0;
+        const double m = mass ? mass[p] : 1.0;
+        if (!(m >= 0.0) || !isfinite(m)) bad = 1.0;
+        else s += m;
+    }
+    s = block_reduce<OpSum>(s);
+    if (threadIdx.x == 0) ps[blockIdx.x] = s;
+    bad = block_reduce<OpMax>(bad);
+    if (threadIdx.x == 0) pb[blockIdx.x] = bad;
+}
+
+__global__ void k_deposit_particles(Dims d, int64_t np, const double* __restrict__ pos,
+                                    const double* __restrict__ mass, double inv_h, double scale,
+                                    unsigned long long* __restrict__ mfix) {
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    int i0, j0, k0;
+    double fx, fy, fz;
+    cic_abs(pos[3 * p] * inv_h, d.n0, i0, fx);
+    cic_abs(pos[3 * p + 1] * inv_h, d.n1, j0, fy);
+    cic_abs(pos[3 * p + 2] * inv_h, d.n2, k0, fz);
+    const double m = mass ? mass[p] : 1.0;
+    for (int di = 0; di < 2; ++di) {
+        const double wx = di ? fx : 1.0 - fx;
+        for (int dj = 0; dj < 2; ++dj) {
+            const double wy = dj ? fy : 1.0 - fy;
+            for (int dk = 0; dk < 2; ++dk) {
+                const double wz = dk ? fz : 1.0 - fz;
+                atomic_add_fixed(&mfix[cell_index(d, i0 + di, j0 + dj, k0 + dk)], m * (wx * wy * wz),
+                                 scale);
+            }
+        }
+    }
+}
+
+__global__ void k_fix_to_double(int cells, unsigned long long* __restrict__ mfix, double inv_scale,
+                                double* __restrict__ out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cells) return;
+    out[c] = (double)(long long)mfix[c] * inv_scale;
+    mfix[c] = 0ull;
+}
+
+__global__ void k_init_tracers(int cells, const double* __restrict__ rho, double inv_rho_bar,
+                               double* __restrict__ w, double* __restrict__ ox,
+                               double* __restrict__ oy, double* __restrict__ oz,
+                               double* __restrict__ phi) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cells) return;
+    w[c] = rho[c] * inv_rho_bar;
+    ox[c] = 0.0, oy[c] = 0.0, oz[c] = 0.0;
+    phi[c] = 0.0;
+}
+
+// Deposit of the tracers on the deformed mesh: tracer c (home node c, mass
+// w_c) sits at curvilinear coordinate c + offset.
+__global__ void k_deposit_tracers(Dims d, const double* __restrict__ ox,
+                                  const double* __restrict__ oy, const double* __restrict__ oz,
+                                  const double* __restrict__ w, double scale,
+                                  unsigned long long* __restrict__ mfix) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= d.cells) return;
+    int i, j, k;
+    cell_coords(d, c, i, j, k);
+    int i0, j0, k0;
+    double fx, fy, fz;
+    cic_offset(i, ox[c], i0, fx);
+    cic_offset(j, oy[c], j0, fy);
+    cic_offset(k, oz[c], k0, fz);
+    const double m = w[c];
+    for (int di = 0; di < 2; ++di) {
+        const double wx = di ? fx : 1.0 - fx;
+        for (int dj = 0; dj < 2; ++dj) {
+            const double wy = dj ? fy : 1.0 - fy;
+            for (int dk = 0; dk < 2; ++dk) {
+                const double wz = dk ? fz : 1.0 - fz;
+                atomic_add_fixed(&mfix[cell_index(d, i0 + di, j0 + dj, k0 + dk)], m * (wx * wy * wz),
+                                 scale);
+            }
+        }
+    }
+}
+
+// m from the fixed-point accumulator (which is cleared for the next deposit),
+// coefficient a = max(m, a_min) in FP64 and FP32, and partial sums of m.
+__global__ void k_mass_coef(int cells, unsigned long long* __restrict__ mfix, double inv_scale,
+                            double a_min, double* __restrict__ m, double* __restrict__ a64,
+                            float* __restrict__ a32, double* __restrict__ part) {
+    double s = 0.0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cells; c += gridDim.x * blockDim.x) {
+        const double v = (double)(long long)mfix[c] * inv_scale;
+        mfix[c] = 0ull;
+        m[c] = v;
+        const double a = v > a_min ? v : a_min;
+        a64[c] = a;
+        if (a32) a32[c] = (float)a;
+        s += v;
+    }
+    s = block_reduce<OpSum>(s);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// Source of App. A Eq. (elliptic) before smoothing: t = Sigma + C + E with
+// Sigma = 1 - m, C(lambda0) the compression limiter of the triad
+// e = I + Hess phi and E = -2 H(sqrt_g - v_m) |Sigma| the expansion limiter.
+// lambda0 only matters where it is below xi_m (for the soft and step readings
+// C vanishes above it); the Gershgorin bound skips the eigenvalue elsewhere.
+__global__ void k_geometry_source(Dims d, SourceParams sp, const double* __restrict__ phi,
+                                  const double* __restrict__ m, double* __restrict__ t,
+                                  double* __restrict__ psum, double* __restrict__ pmin) {
+    double s = 0.0, mdet = INFINITY;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < d.cells; c += gridDim.x * blockDim.x) {
+        int i, j, k;
+        cell_coords(d, c, i, j, k);
+        Sym3 e = hessian(d, phi, i, j, k);
+        e.xx += 1.0, e.yy += 1.0, e.zz += 1.0;
+        const double g = det3(e);
+        double C = 0.0;
+        const double gersh =
+            fmin(fmin(e.xx - fabs(e.xy) - fabs(e.xz), e.yy - fabs(e.xy) - fabs(e.yz)),
+                 e.zz - fabs(e.xz) - fabs(e.yz));
+        if (sp.climiter == 1 || gersh < sp.xi_m) C = climit(sp.climiter, sp.xi_m, min_eig_sym3(e));
+        const double Sigma = 1.0 - m[c];
+        const double E = g - sp.v_m > 0.0 ? -2.0 * fabs(Sigma) : 0.0;
+        const double v = Sigma + C + E;
+        t[c] = v;
+        s += v;
+        mdet = fmin(mdet, g);
+    }
+    s = block_reduce<OpSum>(s);
+    if (threadIdx.x == 0) psum[blockIdx.x] = s;
+    mdet = block_reduce<OpMin>(mdet);
+    if (threadIdx.x == 0) pmin[blockIdx.x] = mdet;
+}
+
+// S u: weighted mean over the 3x3x3 neighbourhood, weights (w, 1-2w, w) per
+// axis, minus (*shift_sum / cells) when shift_sum is given.
+__global__ void k_smooth_S(Dims d, double ws, const double* __restrict__ in,
+                           const double* __restrict__ shift_sum, double* __restrict__ out,
+                           double* __restrict__ psum, double* __restrict__ psq) {
+    const double wt[3] = {ws, 1.0 - 2.0 * ws, ws};
+    const double shift = shift_sum ? *shift_sum / (double)d.cells : 0.0;
+    double s = 0.0, q = 0.0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < d.cells; c += gridDim.x * blockDim.x) {
+        int i, j, k;
+        cell_coords(d, c, i, j, k);
+        double acc = 0.0;
+        for (int oi = -1; oi <= 1; ++oi)
+            for (int oj = -1; oj <= 1; ++oj) {
+                const double wij = wt[oi + 1] * wt[oj + 1];
+                acc += wij * (wt[0] * in[cell_index(d, i + oi, j + oj, k - 1)] +
+                              wt[1] * in[cell_index(d, i + oi, j + oj, k)] +
+                              wt[2] * in[cell_index(d, i + oi, j + oj, k + 1)]);
+            }
+        const double v = acc - shift;
+        out[c] = v;
+        s += v;
+        q += v * v;
+    }
+    if (psum) {
+        s = block_reduce<OpSum>(s);
+        if (threadIdx.x == 0) psum[blockIdx.x] = s;
+    }
+    if (psq) {
+        q = block_reduce<OpSum>(q);
+        if (threadIdx.x == 0) psq[blockIdx.x] = q;
+    }
+}
+
+// Step limiter, per node: the smallest k in [0, kmax] with
+// lambda_min(I + Hess phi + 2^-k Hess dphi) > floor (kmax + 1 if none), and
+// max_a |central grad_a dphi|.  Both are max-reduced over the grid.
+__global__ void k_limiter(Dims d, LimiterParams lp, const double* __restrict__ phi,
+                          const double* __restrict__ dphi, double* __restrict__ pk,
+                          double* __restrict__ pg) {
+    double kk = 0.0, gm = 0.0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < d.cells; c += gridDim.x * blockDim.x) {
+        int i, j, k;
+        cell_coords(d, c, i, j, k);
+        const Sym3 H0 = hessian(d, phi, i, j, k);
+        const Sym3 H1 = hessian(d, dphi, i, j, k);
+        const double gx = 0.5 * (dphi[cell_index(d, i + 1, j, k)] - dphi[cell_index(d, i - 1, j, k)]);
+        const double gy = 0.5 * (dphi[cell_index(d, i, j + 1, k)] - dphi[cell_index(d, i, j - 1, k)]);
+        const double gz = 0.5 * (dphi[cell_index(d, i, j, k + 1)] - dphi[cell_index(d, i, j, k - 1)]);
+        gm = fmax(gm, fmax(fabs(gx), fmax(fabs(gy), fabs(gz))));
+        int kn = lp.kmax + 1;
+        double al = 1.0;
+        for (int q = 0; q <= lp.kmax; ++q, al *= 0.5) {
+            Sym3 M;
+            M.xx = 1.0 + H0.xx + al * H1.xx, M.yy = 1.0 + H0.yy + al * H1.yy;
+            M.zz = 1.0 + H0.zz + al * H1.zz, M.xy = H0.xy + al * H1.xy;
+            M.xz = H0.xz + al * H1.xz, M.yz = H0.yz + al * H1.yz;
+            if (pd_above(M, lp.lambda_floor)) {
+                kn = q;
+                break;
+            }
+        }
+        kk = fmax(kk, (double)kn);
+    }
+    kk = block_reduce<OpMax>(kk);
+    if (threadIdx.x == 0) pk[blockIdx.x] = kk;
+    gm = block_reduce<OpMax>(gm);
+    if (threadIdx.x == 0) pg[blockIdx.x] = gm;
+}
+
+// V = e^-1 G at every node: e = I + Hess phi (before the step), G the
+// central-difference gradient of dphi; solved by Cramer's rule.
+__global__ void k_node_velocity(Dims d, const double* __restrict__ phi,
+                                const double* __restrict__ dphi, double* __restrict__ vx,
+                                double* __restrict__ vy, double* __restrict__ vz) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= d.cells) return;
+    int i, j, k;
+    cell_coords(d, c, i, j, k);
+    Sym3 e = hessian(d, phi, i, j, k);
+    e.xx += 1.0, e.yy += 1.0, e.zz += 1.0;
+    const double gx = 0.5 * (dphi[cell_index(d, i + 1, j, k)] - dphi[cell_index(d, i - 1, j, k)]);
+    const double gy = 0.5 * (dphi[cell_index(d, i, j + 1, k)] - dphi[cell_index(d, i, j - 1, k)]);
+    const double gz = 0.5 * (dphi[cell_index(d, i, j, k + 1)] - dphi[cell_index(d, i, j, k - 1)]);
+    const double inv = 1.0 / det3(e);
+    // columns of e replaced by G in turn
+    const double dx = gx * (e.yy * e.zz - e.yz * e.yz) - e.xy * (gy * e.zz - e.yz * gz) +
+                      e.xz * (gy * e.yz - e.yy * gz);
+    const double dy = e.xx * (gy * e.zz - gz * e.yz) - gx * (e.xy * e.zz - e.yz * e.xz) +
+                      e.xz * (e.xy * gz - gy * e.xz);
+    const double dz = e.xx * (e.yy * gz - e.yz * gy) - e.xy * (e.xy * gz - gy * e.xz) +
+                      gx * (e.xy * e.yz - e.yy * e.xz);
+    vx[c] = dx * inv, vy[c] = dy * inv, vz[c] = dz * inv;
+}
+
+__global__ void k_advance(Dims d, const double* __restrict__ vx, const double* __restrict__ vy,
+                          const double* __restrict__ vz, double alpha,
+                          const double* __restrict__ dphi, const double* __restrict__ sum_dphi,
+                          double* __restrict__ ox, double* __restrict__ oy,
+                          double* __restrict__ oz, double* __restrict__ phi) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= d.cells) return;
+    int i, j, k;
+    cell_coords(d, c, i, j, k);
+    const double px = ox[c], py = oy[c], pz = oz[c];
+    int i0, j0, k0;
+    double fx, fy, fz;
+    cic_offset(i, px, i0, fx);
+    cic_offset(j, py, j0, fy);
+    cic_offset(k, pz, k0, fz);
+    double ux = 0.0, uy = 0.0, uz = 0.0;
+    for (int di = 0; di < 2; ++di) {
+        const double wx = di ? fx : 1.0 - fx;
+        for (int dj = 0; dj < 2; ++dj) {
+            const double wy = dj ? fy : 1.0 - fy;
+            for (int dk = 0; dk < 2; ++dk) {
+                const double w = wx * wy * (dk ? fz : 1.0 - fz);
+                const int n = cell_index(d, i0 + di, j0 + dj, k0 + dk);
+                ux += w * vx[n], uy += w * vy[n], uz += w * vz[n];
+            }
+        }
+    }
+    ox[c] = px - alpha * ux, oy[c] = py - alpha * uy, oz[c] = pz - alpha * uz;
+    const double mean = *sum_dphi / (double)d.cells;
+    phi[c] += alpha * (dphi[c] - mean);
+}
+
+__global__ void k_delta_r(Dims d, const double* __restrict__ phi, double* __restrict__ out,
+                          double* __restrict__ pmax) {
+    double mx = -INFINITY;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < d.cells; c += gridDim.x * blockDim.x) {
+        int i, j, k;
+        cell_coords(d, c, i, j, k);
+        const double p = phi[c];
+        const double lap = (phi[cell_index(d, i + 1, j, k)] - 2.0 * p + phi[cell_index(d, i - 1, j, k)]) +
+                           (phi[cell_index(d, i, j + 1, k)] - 2.0 * p + phi[cell_index(d, i, j - 1, k)]) +
+                           (phi[cell_index(d, i, j, k + 1)] - 2.0 * p + phi[cell_index(d, i, j, k - 1)]);
+        out[c] = -lap;
+        mx = fmax(mx, -lap);
+    }
+    mx = block_reduce<OpMax>(mx);
+    if (threadIdx.x == 0) pmax[blockIdx.x] = mx;
+}
+
+__global__ void k_mesh_x(Dims d, const double* __restrict__ phi, double h, double* __restrict__ out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= d.cells) return;
+    int i, j, k;
+    cell_coords(d, c, i, j, k);
+    out[3 * c + 0] = ((double)i + 0.5 * (phi[cell_index(d, i + 1, j, k)] - phi[cell_index(d, i - 1, j, k)])) * h;
+    out[3 * c + 1] = ((double)j + 0.5 * (phi[cell_index(d, i, j + 1, k)] - phi[cell_index(d, i, j - 1, k)])) * h;
+    out[3 * c + 2] = ((double)k + 0.5 * (phi[cell_index(d, i, j, k + 1)] - phi[cell_index(d, i, j, k - 1)])) * h;
+}
+
+__global__ void k_geometry_out(Dims d, const double* __restrict__ phi, double* __restrict__ det,
+                               double* __restrict__ lam, double* __restrict__ pdet,
+                               double* __restrict__ plam) {
+    double md = INFINITY, ml = INFINITY;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < d.cells; c += gridDim.x * blockDim.x) {
+        int i, j, k;
+        cell_coords(d, c, i, j, k);
+        Sym3 e = hessian(d, phi, i, j, k);
+        e.xx += 1.0, e.yy += 1.0, e.zz += 1.0;
+        const double g = det3(e), l = min_eig_sym3(e);
+        if (det) det[c] = g;
+        if (lam) lam[c] = l;
+        md = fmin(md, g), ml = fmin(ml, l);
+    }
+    md = block_reduce<OpMin>(md);
+    if (threadIdx.x == 0) pdet[blockIdx.x] = md;
+    ml = block_reduce<OpMin>(ml);
+    if (threadIdx.x == 0) plam[blockIdx.x] = ml;
+}
+
+__global__ void k_scale(int cells, const double* __restrict__ in, double s, double* __restrict__ out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < cells) out[c] = in[c] * s;
+}
+
+template <class Op>
+__global__ void k_finish(const double* __restrict__ partials, double* __restrict__ scalars, int slot) {
+    double v = Op::id();
+    for (int b = threadIdx.x; b < kRedBlocks; b += blockDim.x) v = Op::op(v, partials[b]);
+    v = block_reduce<Op>(v);
+    if (threadIdx.x == 0) scalars[slot] = v;
+}
+
+}  // namespace
+
+void finish_reduce(const double* partials, int op, double* scalars, int slot, cudaStream_t st) {
+    if (op == 0) { launch_counter()++; k_finish<OpSum><<<1, 1024, 0, st>>>(partials, scalars, slot); }
+    else if (op == 1) { launch_counter()++; k_finish<OpMin><<<1, 1024, 0, st>>>(partials, scalars, slot); }
+    else { launch_counter()++; k_finish<OpMax><<<1, 1024, 0, st>>>(partials, scalars, slot); }
+}
+
+void launch_validate_grid(int cells, const double* rho, double* ps, double* pb, cudaStream_t st) {
+    launch_counter()++;
+    k_validate_grid<<<kRedBlocks, kRedThreads, 0, st>>>(cells, rho, ps, pb);
+}
+
+void launch_validate_particles(int64_t np, const double* pos, const double* mass, double* ps,
+                               double* pb, cudaStream_t st) {
+    launch_counter()++;
+    k_validate_particles<<<kRedBlocks, kRedThreads, 0, st>>>(np, pos, mass, ps, pb);
+}
+
+void launch_deposit_particles(const Dims& d, int64_t np, const double* pos, const double* mass,
+                              double inv_h, double scale, unsigned long long* mfix, cudaStream_t st) {
+    if (np <= 0) return;
+    launch_counter()++;
+    k_deposit_particles<<<(unsigned)((np + kThreads - 1) / kThreads), kThreads, 0, st>>>(
+        d, np, pos, mass, inv_h, scale, mfix);
+}
+
+void launch_fix_to_double(int cells, unsigned long long* mfix, double inv_scale, double* out,
+                          cudaStream_t st) {
+    launch_counter()++;
+    k_fix_to_double<<<nblocks(cells), kThreads, 0, st>>>(cells, mfix, inv_scale, out);
+}
+
+void launch_init_tracers(int cells, const double* rho, double inv_rho_bar, double* w, double* ox,
+                         double* oy, double* oz, double* phi, cudaStream_t st) {
+    launch_counter()++;
+    k_init_tracers<<<nblocks(cells), kThreads, 0, st>>>(cells, rho, inv_rho_bar, w, ox, oy, oz, phi);
+}
+
+void launch_deposit_tracers(const Dims& d, const double* ox, const double* oy, const double* oz,
+                            const double* w, double scale, unsigned long long* mfix,
+                            cudaStream_t st) {
+    launch_counter()++;
+    k_deposit_tracers<<<nblocks(d.cells), kThreads, 0, st>>>(d, ox, oy, oz, w, scale, mfix);
+}
+
+void launch_mass_coef(int cells, unsigned long long* mfix, double inv_scale, double a_min,
+                      double* m, double* a64, float* a32, double* partials, cudaStream_t st) {
+    launch_counter()++;
+    k_mass_coef<<<kRedBlocks, kRedThreads, 0, st>>>(cells, mfix, inv_scale, a_min, m, a64, a32,
+                                                    partials);
+}
+
+void launch_geometry_source(const Dims& d, const SourceParams& sp, const double* phi,
+                            const double* m, double* t, double* part_sum, double* part_min,
+                            cudaStream_t st) {
+    launch_counter()++;
+    k_geometry_source<<<kRedBlocks, kRedThreads, 0, st>>>(d, sp, phi, m, t, part_sum, part_min);
+}
+
+void launch_smooth_S(const Dims& d, double s_side, const double* in, const double* shift_sum,
+                     double* out, double* part_sum, double* part_sq, cudaStream_t st) {
+    launch_counter()++;
+    k_smooth_S<<<kRedBlocks, kRedThreads, 0, st>>>(d, s_side, in, shift_sum, out, part_sum, part_sq);
+}
+
+void launch_limiter(const Dims& d, const LimiterParams& lp, const double* phi, const double* dphi,
+                    double* part_k, double* part_g, cudaStream_t st) {
+    launch_counter()++;
+    k_limiter<<<kRedBlocks, kRedThreads, 0, st>>>(d, lp, phi, dphi, part_k, part_g);
+}
+
+void launch_node_velocity(const Dims& d, const double* phi, const double* dphi, double* vx,
+                          double* vy, double* vz, cudaStream_t st) {
+    launch_counter()++;
+    k_node_velocity<<<nblocks(d.cells), kThreads, 0, st>>>(d, phi, dphi, vx, vy, vz);
+}
+
+void launch_advance(const Dims& d, const double* vx, const double* vy, const double* vz,
+                    double alpha, const double* dphi, const double* sum_dphi, double* ox,
+                    double* oy, double* oz, double* phi, cudaStream_t st) {
+    launch_counter()++;
+    k_advance<<<nblocks(d.cells), kThreads, 0, st>>>(d, vx, vy, vz, alpha, dphi, sum_dphi, ox, oy,
+                                                     oz, phi);
+}
+
+void launch_delta_r(const Dims& d, const double* phi, double* out, double* part_max,
+                    cudaStream_t st) {
+    launch_counter()++;
+    k_delta_r<<<kRedBlocks, kRedThreads, 0, st>>>(d, phi, out, part_max);
+}
+
+void launch_mesh_x(const Dims& d, const double* phi, double h, double* out, cudaStream_t st) {
+    launch_counter()++;
+    k_mesh_x<<<nblocks(d.cells), kThreads, 0, st>>>(d, phi, h, out);
+}
+
+void launch_geometry_out(const Dims& d, const double* phi, double* det, double* lam,
+                         double* part_min_det, double* part_min_lam, cudaStream_t st) {
+    launch_counter()++;
+    k_geometry_out<<<kRedBlocks, kRedThreads, 0, st>>>(d, phi, det, lam, part_min_det, part_min_lam);
+}
+
+void launch_scale(int cells, const double* in, double s, double* out, cudaStream_t st) {
+    launch_counter()++;
+    k_scale<<<nblocks(cells), kThreads, 0, st>>>(cells, in, s, out);
+}
+
+}  // namespace recon

@@ -1,0 +1,98 @@
+"""The C ABI loads and exports every function include/recon.h declares; the
+host-only entry points behave as documented (no GPU needed)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    with open(os.path.join(ROOT, "include", "recon.h")) as fh:
+        text = fh.read()
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+(recon_\w+)\s*\(", text, re.M)))
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    from paper_1611_09638_gb300 import _abi
+
+    lib = _abi.load()
+    declared = _declared()
+    assert len(declared) >= 8
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert set(declared) <= set(_abi.SYMBOLS)
+
+
+def test_default_params_match_the_paper_and_the_oracle():
+    from paper_1611_09638_gb300 import default_params
+    import oracle as O
+
+    p = default_params((32, 16, 8))
+    q = O.OracleParams()
+    assert list(p.n) == [32, 16, 8]
+    for f in ("xi_m", "v_m", "a_min", "climiter", "s_side", "nu1", "nu2", "tol_in", "max_vcycles",
+              "tol_out", "k_max", "d_max", "alpha_min", "lambda_floor"):
+        assert getattr(p, f) == getattr(q, f), f
+
+
+def test_struct_layout_matches_header(tmp_path):
+    """ctypes mirrors of recon_params / recon_stats have the C compiler's
+    sizes and field offsets."""
+    import subprocess
+
+    from paper_1611_09638_gb300 import _abi
+
+    src = tmp_path / "lay.c"
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "recon.h"', "int main(void){"]
+    for st in (_abi.recon_params, _abi.recon_stats):
+        lines.append(f'printf("%zu\\n", sizeof({st.__name__}));')
+        for f, _ in st._fields_:
+            lines.append(f'printf("%zu\\n", offsetof({st.__name__}, {f}));')
+    lines.append("return 0;}")
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "lay"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True,
+                                          text=True).stdout.split()]
+    want = []
+    for st in (_abi.recon_params, _abi.recon_stats):
+        want.append(C.sizeof(st))
+        want += [getattr(st, f).offset for f, _ in st._fields_]
+    assert got == want
+
+
+def test_adjoint_reports_unsupported_and_errors_are_text():
+    from paper_1611_09638_gb300 import _abi
+
+    lib = _abi.load()
+    assert lib.recon_adjoint(None, None, None) == _abi.RECON_E_UNSUPPORTED
+    assert b"not available" in lib.recon_last_error()
+    assert lib.recon_solve(None, None) == _abi.RECON_E_INVALID
+
+
+def test_create_rejects_bad_params_before_touching_the_device():
+    from paper_1611_09638_gb300 import _abi, default_params
+
+    lib = _abi.load()
+    h = C.c_void_p()
+    for bad in ({"xi_m": 1.5}, {"v_m": 0.5}, {"nu1": 0, "nu2": 0}, {"s_side": 0.3}):
+        p = default_params((16, 16, 16), **bad)
+        assert lib.recon_create(C.byref(h), C.byref(p), None) == _abi.RECON_E_INVALID
+        assert h.value is None
+    p = default_params((12, 16, 16))
+    assert lib.recon_create(C.byref(h), C.byref(p), None) == _abi.RECON_E_INVALID
+    p = default_params((16, 16, 32), box=(100.0, 100.0, 100.0))  # non-cubic cells
+    assert lib.recon_create(C.byref(h), C.byref(p), None) == _abi.RECON_E_INVALID
+
+
+def test_package_has_no_cpu_fallback():
+    import paper_1611_09638_gb300 as R
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    with pytest.raises(RuntimeError):
+        R.Recon((16, 16, 16))

@@ -1,0 +1,224 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU FP64 oracle.
+
+Tolerances: phi relative L2 <= 1e-6 in FP64 and <= 1e-4 in mixed precision;
+|delta r(k)| <= 1e-4 for k <= 1 h/Mpc; the deposit agrees to the 64-bit
+fixed-point quantum (relative 1e-10); the step lengths alpha (powers of two)
+and the V-cycle counts are compared exactly.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1611_09638_gb300 import ReconError, Recon, _abi
+from paper_1611_09638_gb300.diag import cross_correlation
+from paper_1611_09638_gb300.inputs import lpt_particles
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+@pytest.fixture(scope="module")
+def za32():
+    """32^3 Zel'dovich particles in a 100 Mpc/h box (seed 1000), the oracle's
+    density and its full solve."""
+    n, box = 32, 100.0
+    pos, dL = lpt_particles(n, box, 1000, order=1)
+    rho = O.cic_deposit((n, n, n), pos / (box / n))
+    res = O.solve(O.OracleParams(n=(n, n, n)), rho)
+    return dict(n=n, box=box, pos=pos, dL=dL, rho=rho, res=res)
+
+
+def _gpu_solve(n, rho, precision="fp64", box=None, **kw):
+    R = Recon(n, box=box, precision=precision, **kw)
+    R.deposit_grid(torch.from_numpy(np.ascontiguousarray(rho)).cuda())
+    st = R.solve()
+    return R, st
+
+
+def test_particle_deposit_matches_oracle(za32):
+    n, box = za32["n"], za32["box"]
+    with Recon((n, n, n), box=box) as R:
+        R.deposit_particles(torch.from_numpy(za32["pos"]).cuda())
+        got = R.field("density").cpu().numpy()
+    assert np.abs(got - za32["rho"]).max() <= 1e-10 * za32["rho"].max()
+    # host arrays, masses, a non-cubic grid and wrapped coordinates
+    rng = np.random.default_rng(1)
+    nn = (64, 32, 16)
+    x = rng.uniform(-50.0, 150.0, size=(5000, 3))
+    w = rng.uniform(0.0, 2.0, size=5000)
+    with Recon(nn) as R:
+        R.deposit_particles(x, w)
+        got = R.field("density").cpu().numpy()
+    ref = O.cic_deposit(nn, x, w)
+    assert np.abs(got - ref).max() <= 1e-10 * ref.max()
+
+
+def test_fp64_solve_matches_oracle(za32):
+    n, box, res = za32["n"], za32["box"], za32["res"]
+    R, st = _gpu_solve((n, n, n), za32["rho"], box=box)
+    h = box / n
+    assert st.status == res.status and st.steps == res.steps
+    np.testing.assert_array_equal(st.alpha, res.alpha)
+    np.testing.assert_array_equal(st.ncycles, res.ncycles)
+    assert np.all(st.relres <= 1e-8)
+    np.testing.assert_allclose(st.Rk, res.R[:len(st.Rk)], rtol=1e-6)
+    phi = R.field("phi").cpu().numpy() / h ** 2
+    assert rel(phi, res.phi) <= 1e-6
+    assert rel(R.field("delta_r").cpu().numpy(), O.delta_r(res.phi)) <= 1e-6
+    assert rel(R.field("mesh_x").cpu().numpy() / h, O.mesh_x(res.phi)) <= 1e-9
+    assert rel(R.field("mass").cpu().numpy(), res.m) <= 1e-6
+    g, lam = O.geometry(res.phi)
+    assert rel(R.field("det").cpu().numpy(), g) <= 1e-6
+    assert rel(R.field("lambda0").cpu().numpy(), lam) <= 1e-6
+    assert abs(st.min_lambda0 - lam.min()) <= 1e-6 and abs(st.min_det - g.min()) <= 1e-6
+    R.close()
+
+
+def test_mixed_solve_matches_oracle(za32):
+    n, box, res = za32["n"], za32["box"], za32["res"]
+    R, st = _gpu_solve((n, n, n), za32["rho"], precision="mixed", box=box)
+    h = box / n
+    np.testing.assert_array_equal(st.alpha, res.alpha)
+    assert np.all(st.relres <= 1e-8)
+    phi = R.field("phi").cpu().numpy() / h ** 2
+    assert rel(phi, res.phi) <= 1e-4
+    dr_gpu = R.field("delta_r").cpu().numpy()
+    dr_orc = O.delta_r(res.phi)
+    k, r_gpu = cross_correlation(dr_gpu, za32["dL"], box)
+    _, r_orc = cross_correlation(dr_orc, za32["dL"], box)
+    sel = k <= 1.0
+    assert sel.sum() >= 10
+    assert np.abs(r_gpu[sel] - r_orc[sel]).max() <= 1e-4
+    R.close()
+
+
+def test_fp64_anisotropic_grid_several_tiles():
+    """64 x 32 x 16 grid (semi-coarsening on the way to 4^3) with a plane wave
+    plus noise; a few steps."""
+    nn = (64, 32, 16)
+    rng = np.random.default_rng(7)
+    i = np.arange(64)[:, None, None]
+    rho = 1 + 0.4 * np.sin(2 * np.pi * i / 64) + 0.2 * rng.uniform(-1, 1, size=nn)
+    p = O.OracleParams(n=nn, k_max=6)
+    res = O.solve(p, rho)
+    R, st = _gpu_solve(nn, rho, k_max=6)
+    np.testing.assert_array_equal(st.alpha, res.alpha)
+    np.testing.assert_array_equal(st.ncycles, res.ncycles)
+    assert rel(R.field("phi").cpu().numpy(), res.phi) <= 1e-6
+    R.close()
+
+
+def test_one_step_at_128_cubed_matches_oracle():
+    """One full step on the 128^3 / 200 Mpc/h Zel'dovich field (seed 1004)."""
+    n, box = 128, 200.0
+    pos, _ = lpt_particles(n, box, 1004, order=1)
+    rho = O.cic_deposit((n, n, n), pos / (box / n))
+    res = O.solve(O.OracleParams(n=(n, n, n), k_max=1), rho)
+    for prec, tol in (("fp64", 1e-6), ("mixed", 1e-4)):
+        R, st = _gpu_solve((n, n, n), rho, precision=prec, k_max=1)
+        np.testing.assert_array_equal(st.alpha, res.alpha)
+        if prec == "fp64":
+            np.testing.assert_array_equal(st.ncycles, res.ncycles)
+        assert rel(R.field("phi").cpu().numpy(), res.phi) <= tol
+        assert rel(R.field("mass").cpu().numpy(), res.m) <= 1e-9
+        R.close()
+
+
+def test_uniform_density_and_minimal_grid():
+    R, st = _gpu_solve((8, 8, 8), np.full((8, 8, 8), 2.0))
+    assert st.status == _abi.RECON_OK and st.steps == 0 and st.R0 == 0.0
+    assert np.all(R.field("phi").cpu().numpy() == 0.0)
+    R.close()
+    rng = np.random.default_rng(3)
+    rho = rng.uniform(0.0, 3.0, size=(8, 8, 8))
+    res = O.solve(O.OracleParams(n=(8, 8, 8), k_max=5), rho)
+    R, st = _gpu_solve((8, 8, 8), rho, k_max=5)
+    np.testing.assert_array_equal(st.alpha, res.alpha)
+    assert rel(R.field("phi").cpu().numpy(), res.phi) <= 1e-6
+    R.close()
+
+
+def test_errors_are_reported_not_raised_on_device():
+    with Recon((16, 16, 16)) as R:
+        with pytest.raises(ReconError) as e:
+            R.solve()
+        assert e.value.status == _abi.RECON_E_STATE
+        bad = np.ones((16, 16, 16))
+        bad[3, 4, 5] = np.nan
+        with pytest.raises(ReconError) as e:
+            R.deposit_grid(bad)
+        assert e.value.status == _abi.RECON_E_NONFINITE
+        bad[3, 4, 5] = -1.0
+        with pytest.raises(ReconError) as e:
+            R.deposit_grid(bad)
+        assert e.value.status == _abi.RECON_E_NONFINITE
+        with pytest.raises(ReconError) as e:
+            R.deposit_grid(np.zeros((16, 16, 16)))
+        assert e.value.status == _abi.RECON_E_INVALID
+        with pytest.raises(ReconError):
+            R.field("phi")
+        # still usable after the errors
+        R.deposit_grid(np.ones((16, 16, 16)))
+        assert R.solve().steps == 0
+
+
+def test_host_and_device_buffers_agree_and_runs_are_deterministic(za32):
+    n = za32["n"]
+    outs = []
+    for src in ("host", "device", "device"):
+        with Recon((n, n, n), k_max=6, precision="mixed") as R:
+            rho = za32["rho"] if src == "host" else torch.from_numpy(za32["rho"]).cuda()
+            R.deposit_grid(rho)
+            R.solve()
+            host_out = np.empty((n, n, n))
+            R.field("phi", out=host_out)
+            outs.append(host_out)
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[1], outs[2])
+
+
+@pytest.fixture(scope="module")
+def lpt256():
+    n, box = 256, 400.0
+    pos, dL = lpt_particles(n, box, 1001, order=2)
+    return dict(n=n, box=box, pos=pos, dL=dL)
+
+
+def test_full_size_256_deposit_and_invariants(lpt256):
+    """The 256^3 / 400 Mpc/h 2LPT workload in the launch configuration the
+    benchmark times: the deposit against the oracle on every cell, then the
+    properties of the solve that hold at any size, and mixed against FP64."""
+    n, box = lpt256["n"], lpt256["box"]
+    pos = torch.from_numpy(lpt256["pos"]).cuda()
+    phis = {}
+    for prec in ("mixed", "fp64"):
+        with Recon((n, n, n), box=box, precision=prec) as R:
+            R.deposit_particles(pos)
+            if prec == "mixed":
+                rho = R.field("density").cpu().numpy()
+                ref = O.cic_deposit((n, n, n), lpt256["pos"] / (box / n))
+                assert np.abs(rho - ref).max() <= 1e-10 * ref.max()
+            st = R.solve()
+            assert abs(R.field("mass").sum().item() - n ** 3) <= 1e-9 * n ** 3
+            assert st.mass_error <= 1e-12
+            assert st.min_det > 0 and st.min_lambda0 > 0.02
+            assert st.max_delta_r < 3 - 3 * 0.02
+            assert np.all(st.relres <= 1e-8)
+            phi = R.field("phi").cpu().numpy()
+            dr = R.field("delta_r").cpu().numpy()
+            # sampled nodes: delta_r is minus the 7-point Laplacian of phi
+            rng = np.random.default_rng(5)
+            idx = rng.integers(0, n, size=(500, 3))
+            h2 = (box / n) ** 2
+            for i, j, k in idx:
+                lap = sum(phi[(i + di) % n, (j + dj) % n, (k + dk) % n] - phi[i, j, k]
+                          for di, dj, dk in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0),
+                                             (0, 0, 1), (0, 0, -1))) / h2
+                assert abs(dr[i, j, k] + lap) <= 1e-9 * max(1.0, abs(lap))
+            phis[prec] = (phi, st)
+    assert np.array_equal(phis["mixed"][1].alpha, phis["fp64"][1].alpha)
+    assert rel(phis["mixed"][0], phis["fp64"][0]) <= 1e-4
