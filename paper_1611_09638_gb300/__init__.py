@@ -51,6 +51,10 @@ class SolveStats:
     max_delta_r: float
     mass_error: float
     ms: float
+    launches: int = 0
+    smooth_ms: float = 0.0
+    smooth_sweeps: int = 0
+    smooth_bytes: float = 0.0
     alpha: np.ndarray = field(default=None)
     Rk: np.ndarray = field(default=None)
     ncycles: np.ndarray = field(default=None)
@@ -119,7 +123,8 @@ class Recon:
         _abi.check(rc, "recon_solve")
         k = st.steps
         out = SolveStats(rc, k, st.vcycles, st.R0, st.R, st.min_det, st.min_lambda0,
-                         st.max_delta_r, st.mass_error, st.ms)
+                         st.max_delta_r, st.mass_error, st.ms, st.launches, st.smooth_ms,
+                         st.smooth_sweeps, st.smooth_bytes)
         if record:
             out.alpha, out.ncycles, out.relres = arrs["alpha"][:k], arrs["ncycles"][:k], arrs["relres"][:k]
             out.Rk = arrs["Rk"][:min(k + 1, K)] if rc == RECON_OK else arrs["Rk"][:k]

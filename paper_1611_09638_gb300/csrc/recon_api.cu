@@ -110,11 +110,25 @@ void prof_mark(Handle* H) {
     cudaEventRecord(H->prof_ev[H->prof_used++], H->st);
 }
 
+// nu red-black sweeps of level l on u.  Where the level fits the streaming
+// kernel each sweep is one pass u -> tmp (ping-pong, ending in u); elsewhere
+// the two colour passes run in place.
 template <typename T>
-void smooth_sweeps(Handle* H, int l, int nu, T* u, const T* f, const T* c) {
+void smooth_sweeps(Handle* H, int l, int nu, T* u, T* tmp, const T* f, const T* c) {
     const bool prof = H->p.profile && l == 0 && nu > 0;
     if (prof) prof_mark(H);
-    for (int s = 0; s < nu; ++s) launch_rbgs_sweep<T>(H->lv[l], u, f, c, H->st);
+    T* cur = u;
+    T* oth = tmp;
+    for (int s = 0; s < nu; ++s) {
+        if (launch_rbgs_fused<T>(H->lv[l], cur, oth, f, c, H->st)) {
+            T* t = cur;
+            cur = oth, oth = t;
+        } else {
+            launch_rbgs_sweep<T>(H->lv[l], cur, f, c, H->st);
+        }
+    }
+    if (cur != u)
+        cudaMemcpyAsync(u, cur, sizeof(T) * H->lv[l].d.cells, cudaMemcpyDeviceToDevice, H->st);
     if (prof) {
         prof_mark(H);
         H->prof_sweeps += nu;
@@ -190,13 +204,13 @@ void vcycle(Handle* H, MG<T>& g, int l, T* u, const T* f) {
         launch_coarse_solve<T>(H->minv, f, u, H->st);
         return;
     }
-    smooth_sweeps<T>(H, l, H->p.nu1, u, f, g.c[l]);
+    smooth_sweeps<T>(H, l, H->p.nu1, u, g.r[l], f, g.c[l]);
     launch_residual<T>(L, u, f, g.c[l], g.r[l], H->st);
     launch_restrict<T>(L, H->lv[l + 1], g.r[l], g.f[l + 1], H->st);
     cudaMemsetAsync(g.u[l + 1], 0, sizeof(T) * H->lv[l + 1].d.cells, H->st);
     vcycle<T>(H, g, l + 1, g.u[l + 1], g.f[l + 1]);
     launch_prolong_add<T>(L, H->lv[l + 1], g.u[l + 1], u, H->st);
-    smooth_sweeps<T>(H, l, H->p.nu2, u, f, g.c[l]);
+    smooth_sweeps<T>(H, l, H->p.nu2, u, g.r[l], f, g.c[l]);
 }
 
 template <typename T>
@@ -402,7 +416,7 @@ int recon_default_params(recon_params* p, int n0, int n1, int n2) {
     p->k_max = 40;
     p->d_max = 0.5;
     p->alpha_min = std::ldexp(1.0, -20);
-    p->lambda_floor = 0.02;
+    p->lambda_floor = 0.0;
     p->replay_alpha = nullptr;
     return RECON_OK;
 }

@@ -91,6 +91,18 @@ void finish_reduce(const double* partials, int op, double* scalars, int slot, cu
 // ---- multigrid (T = float or double) --------------------------------------
 template <typename T>
 void launch_rbgs_sweep(const Level& L, T* u, const T* f, const T* a, cudaStream_t st);
+// One full red-black sweep u_new <- RBGS(u_old) in a single streaming pass
+// (smoother.cu); returns false, launching nothing, when the level is not a
+// multiple of the kernel's tile.
+template <typename T>
+bool launch_rbgs_fused(const Level& L, const T* u_old, T* u_new, const T* f, const T* a,
+                       cudaStream_t st);
+template <>
+bool launch_rbgs_fused<float>(const Level&, const float*, float*, const float*, const float*,
+                              cudaStream_t);
+template <>
+bool launch_rbgs_fused<double>(const Level&, const double*, double*, const double*,
+                               const double*, cudaStream_t);
 template <typename T>
 void launch_residual(const Level& L, const T* u, const T* f, const T* a, T* r, cudaStream_t st);
 template <typename T>
