@@ -66,6 +66,17 @@ struct Handle {
     std::vector<cudaEvent_t> prof_ev;
     size_t prof_used = 0;
     int prof_sweeps = 0;
+    double prof_ms = 0.0;  // sweep time accumulated over graph launches
+
+    // One multigrid iteration (V-cycle, residual, norm readback) recorded once
+    // as a CUDA graph on a private stream and replayed on the handle's stream.
+    cudaStream_t cap = nullptr;
+    bool capturing = false;
+    cudaGraphExec_t cyc_exec = nullptr;
+    long long cyc_kernels = 0;
+    int cyc_sweeps = 0;
+    std::vector<cudaEvent_t> cyc_ev;
+    size_t cyc_ev_used = 0;
 
     bool have_density = false, solved = false;
     double rho_sum = 0.0;
@@ -95,19 +106,30 @@ void free_all(Handle* H) {
     H->hscal = nullptr, H->ev0 = H->ev1 = nullptr;
     for (cudaEvent_t e : H->prof_ev) cudaEventDestroy(e);
     H->prof_ev.clear();
+    if (H->cyc_exec) cudaGraphExecDestroy(H->cyc_exec);
+    H->cyc_exec = nullptr;
+    for (cudaEvent_t e : H->cyc_ev) cudaEventDestroy(e);
+    H->cyc_ev.clear();
+    if (H->cap) cudaStreamDestroy(H->cap);
+    H->cap = nullptr;
 }
 
-// Record one profiling event on the handle's stream (events are pooled).
+// Record one profiling event on the handle's stream (events are pooled; the
+// ones recorded into the multigrid graph belong to it).
 void prof_mark(Handle* H) {
-    if (H->prof_used == H->prof_ev.size()) {
+    std::vector<cudaEvent_t>& pool = H->capturing ? H->cyc_ev : H->prof_ev;
+    size_t& used = H->capturing ? H->cyc_ev_used : H->prof_used;
+    if (used == pool.size()) {
         cudaEvent_t e;
         if (cudaEventCreate(&e) != cudaSuccess) {
             cudaGetLastError();
             return;
         }
-        H->prof_ev.push_back(e);
+        pool.push_back(e);
     }
-    cudaEventRecord(H->prof_ev[H->prof_used++], H->st);
+    cudaEvent_t e = pool[used++];
+    if (H->capturing) cudaEventRecordWithFlags(e, H->st, cudaEventRecordExternal);
+    else cudaEventRecord(e, H->st);
 }
 
 // nu red-black sweeps of level l on u.  Where the level fits the streaming
@@ -220,41 +242,98 @@ void build_hierarchy(Handle* H, std::vector<T*>& c) {
     launch_coarse_invert<T>(H->lv.back(), c.back(), H->minv, H->st);
 }
 
+// One multigrid iteration after the first residual: the V-cycle (FP64 on
+// phidot, or FP32 on the correction e followed by phidot += e), then the FP64
+// residual of L phidot = s (in mixed mode also handed to the next V-cycle as
+// its FP32 right-hand side), its squared norm, and the scalar readback.
+void cycle_body(Handle* H) {
+    const Level& L0 = H->lv[0];
+    if (!H->mixed) {
+        MG<double> g{H->u64, H->f64, H->c64, H->r64};
+        vcycle<double>(H, g, 0, H->phidot, H->s);
+        launch_residual_norm64(L0, H->phidot, H->s, H->a64, H->part[0], H->st);
+    } else {
+        MG<float> g{H->u32, H->f32, H->c32, H->r32};
+        cudaMemsetAsync(H->u32[0], 0, sizeof(float) * H->cells, H->st);
+        vcycle<float>(H, g, 0, H->u32[0], H->f32[0]);
+        launch_correct(H->cells, H->phidot, H->u32[0], H->st);
+        launch_residual64_to32(L0, H->phidot, H->s, H->a64, H->f32[0], H->part[0], H->st);
+    }
+    finish_reduce(H->part[0], 0, H->scal, SC_RES2, H->st);
+    cudaMemcpyAsync(H->hscal, H->scal, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, H->st);
+}
+
+int record_cycle_graph(Handle* H) {
+    if (!H->cap) CK(cudaStreamCreateWithFlags(&H->cap, cudaStreamNonBlocking));
+    cudaStream_t user = H->st;
+    const long long c0 = launch_counter().load();
+    const int s0 = H->prof_sweeps;
+    CK(cudaStreamBeginCapture(H->cap, cudaStreamCaptureModeRelaxed));
+    H->st = H->cap;
+    H->capturing = true;
+    cycle_body(H);
+    H->capturing = false;
+    H->st = user;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(H->cap, &g);
+    H->cyc_kernels = launch_counter().load() - c0;
+    launch_counter() -= H->cyc_kernels;
+    H->cyc_sweeps = H->prof_sweeps - s0;
+    H->prof_sweeps = s0;
+    if (e != cudaSuccess) return fail(RECON_E_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&H->cyc_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        H->cyc_exec = nullptr;
+        return fail(RECON_E_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+    }
+    return RECON_OK;
+}
+
+int run_cycle(Handle* H) {
+    if (!H->cyc_exec) {
+        int rc = record_cycle_graph(H);
+        if (rc) return rc;
+    }
+    CK(cudaGraphLaunch(H->cyc_exec, H->st));
+    CK(cudaStreamSynchronize(H->st));
+    launch_counter() += H->cyc_kernels;
+    if (H->p.profile) {
+        for (size_t q = 0; q + 1 < H->cyc_ev_used; q += 2) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, H->cyc_ev[q], H->cyc_ev[q + 1]) == cudaSuccess) H->prof_ms += ms;
+        }
+        cudaGetLastError();
+        H->prof_sweeps += H->cyc_sweeps;
+    }
+    return RECON_OK;
+}
+
 // Solve L(a) phidot = s to ||s - L phidot|| <= tol_in ||s||.
 int mg_solve(Handle* H, double snorm2, int* ncyc, double* relres) {
     *ncyc = 0;
     *relres = 0.0;
     CK(cudaMemsetAsync(H->phidot, 0, sizeof(double) * H->cells, H->st));
     if (!(snorm2 > 0.0)) return RECON_OK;
-    const Level& L0 = H->lv[0];
-    if (!H->mixed) {
-        MG<double> g{H->u64, H->f64, H->c64, H->r64};
-        for (int cyc = 1; cyc <= H->p.max_vcycles; ++cyc) {
-            vcycle<double>(H, g, 0, H->phidot, H->s);
-            launch_residual_norm64(L0, H->phidot, H->s, H->a64, H->part[0], H->st);
-            finish_reduce(H->part[0], 0, H->scal, SC_RES2, H->st);
-            int rc = sync_scalars(H);
-            if (rc) return rc;
-            *ncyc = cyc;
-            *relres = std::sqrt(H->hscal[SC_RES2] / snorm2);
-            if (*relres <= H->p.tol_in) break;
-        }
-    } else {
-        MG<float> g{H->u32, H->f32, H->c32, H->r32};
-        for (int cyc = 0;; ++cyc) {
-            // FP64 defect: r = s - L phidot, handed to the FP32 V-cycle as its RHS
-            launch_residual64_to32(L0, H->phidot, H->s, H->a64, H->f32[0], H->part[0], H->st);
-            finish_reduce(H->part[0], 0, H->scal, SC_RES2, H->st);
-            int rc = sync_scalars(H);
-            if (rc) return rc;
-            *ncyc = cyc;
-            *relres = std::sqrt(H->hscal[SC_RES2] / snorm2);
-            if (*relres <= H->p.tol_in || cyc == H->p.max_vcycles) break;
-            CK(cudaMemsetAsync(H->u32[0], 0, sizeof(float) * H->cells, H->st));
-            vcycle<float>(H, g, 0, H->u32[0], H->f32[0]);
-            launch_correct(H->cells, H->phidot, H->u32[0], H->st);
-        }
+    double rel = 1.0;
+    if (H->mixed) {
+        // first FP64 defect r = s (phidot = 0), handed to the FP32 V-cycle
+        launch_residual64_to32(H->lv[0], H->phidot, H->s, H->a64, H->f32[0], H->part[0], H->st);
+        finish_reduce(H->part[0], 0, H->scal, SC_RES2, H->st);
+        int rc = sync_scalars(H);
+        if (rc) return rc;
+        rel = std::sqrt(H->hscal[SC_RES2] / snorm2);
     }
+    int cyc = 0;
+    while (cyc < H->p.max_vcycles && !(H->mixed && rel <= H->p.tol_in)) {
+        int rc = run_cycle(H);
+        if (rc) return rc;
+        ++cyc;
+        rel = std::sqrt(H->hscal[SC_RES2] / snorm2);
+        if (rel <= H->p.tol_in) break;
+    }
+    *ncyc = cyc;
+    *relres = rel;
     return RECON_OK;
 }
 
@@ -273,6 +352,7 @@ int solve(Handle* H, recon_stats* stats) {
     const long long launches0 = launch_counter().load();
     H->prof_used = 0;
     H->prof_sweeps = 0;
+    H->prof_ms = 0.0;
     CK(cudaEventRecord(H->ev0, H->st));
     // init: tracer c = node c with mass rho_c / rho_bar, phi = 0
     const double rho_bar = H->rho_sum / (double)n;
@@ -362,7 +442,7 @@ int solve(Handle* H, recon_stats* stats) {
         stats->ms = ms;
         stats->mass_error = std::fabs(H->last_mass - (double)n) / (double)n;
         stats->launches = launch_counter().load() - launches0;
-        double sm = 0.0;
+        double sm = H->prof_ms;
         for (size_t q = 0; q + 1 < H->prof_used; q += 2) {
             float e = 0.f;
             if (cudaEventElapsedTime(&e, H->prof_ev[q], H->prof_ev[q + 1]) == cudaSuccess) sm += e;
