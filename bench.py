@@ -38,6 +38,8 @@ def _args():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--k-max", type=int, default=40,
+                    help="steps per solve (40 is the workload; fewer only for profiling)")
     return ap.parse_args()
 
 
@@ -129,6 +131,24 @@ class Clocks:
                 "samples": len(rows)}
 
 
+def max_over_ranks(v, world, device):
+    """Max of a per-rank timing over all ranks (the slowest rank sets the
+    whole-job time)."""
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mcells(cells_per_rank, world, ms):
+    """Whole-job throughput: every rank solves its own copy of the workload."""
+    return world * cells_per_rank / (ms * 1e-3) / 1e6
+
+
 def _workload(name):
     from paper_1611_09638_gb300.inputs import WORKLOADS
 
@@ -161,7 +181,7 @@ def run_gb300(a):
         torch.cuda.synchronize()
 
     def timed(precision, steps, warmup, profile=False):
-        R = Recon((n, n, n), box=W.box, precision=precision, profile=int(profile))
+        R = Recon((n, n, n), box=W.box, precision=precision, profile=int(profile), k_max=a.k_max)
         R.deposit_particles(pos_dev)
         for _ in range(warmup):
             R.solve(record=False)
@@ -179,21 +199,19 @@ def run_gb300(a):
         return ms, stats, clk.summary()
 
     ms_mixed, st_mixed, clocks = timed("mixed", a.steps, a.warmup, profile=True)
-    ms_fp64, st_fp64, _ = timed("fp64", max(a.fp64_steps, 1), 1)
+    ms_fp64, st_fp64 = None, None
+    if a.fp64_steps > 0:
+        ms_fp64, st_fp64, _ = timed("fp64", a.fp64_steps, 1)
 
-    def max_over_ranks(v):
-        if world == 1:
-            return v
-        import torch.distributed as dist
-
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    ms_mixed = max_over_ranks(ms_mixed)
-    ms_fp64 = max_over_ranks(ms_fp64)
-    value = world * cells / (ms_mixed * 1e-3) / 1e6
-    value_fp64 = world * cells / (ms_fp64 * 1e-3) / 1e6
+    ms_mixed = max_over_ranks(ms_mixed, world, "cuda")
+    value = whole_job_mcells(cells, world, ms_mixed)
+    fp64 = None
+    if ms_fp64 is not None:
+        ms_fp64 = max_over_ranks(ms_fp64, world, "cuda")
+        value_fp64 = whole_job_mcells(cells, world, ms_fp64)
+        fp64 = {"value": value_fp64, "unit": "Mcells/s", "ms_per_step": ms_fp64,
+                "steps": a.fp64_steps, "vcycles_per_solve": st_fp64[0].vcycles,
+                "mixed_over_fp64": value / value_fp64}
 
     # roofline of the dominant kernel: the finest-level FP32 red-black sweep
     sm_ms = sum(s.smooth_ms for s in st_mixed)
@@ -227,10 +245,10 @@ def run_gb300(a):
             R.field("delta_r", out=out)
         e1.record(stream)
         barrier()
-        e2e_ms = max_over_ranks(e0.elapsed_time(e1) / k2)
+        e2e_ms = max_over_ranks(e0.elapsed_time(e1) / k2, world, "cuda")
         wall_ms = (time.perf_counter() - t0) * 1e3 / k2
         R.close()
-        e2e = {"value": world * cells / (e2e_ms * 1e-3) / 1e6, "unit": "Mcells/s",
+        e2e = {"value": whole_job_mcells(cells, world, e2e_ms), "unit": "Mcells/s",
                "h2d_bytes_per_step": int(pos_host.nbytes), "d2h_bytes_per_step": int(out.numel() * 8),
                "ms_per_step": e2e_ms, "host_wall_ms_per_step": wall_ms,
                "path": "recon_deposit(host pinned particles) + recon_solve + recon_field(delta_r -> host pinned)"}
@@ -246,13 +264,11 @@ def run_gb300(a):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": W.name, "grid": [n, n, n], "box_mpc_h": W.box,
                    "displacement": "2LPT" if W.order == 2 else "ZA", "seed": W.seed,
-                   "precision": "mixed", "k_max": 40, "tol_in": 1e-8, "tol_out": 1e-3,
+                   "precision": "mixed", "k_max": a.k_max, "tol_in": 1e-8, "tol_out": 1e-3,
                    "steps_per_solve": s0.steps, "vcycles_per_solve": s0.vcycles,
                    "l2": "inputs larger than L2 (working set ~1.7 GB per solve)",
                    "parallelism": f"replicas x{world}"},
-        "fp64_gpu": {"value": value_fp64, "unit": "Mcells/s", "ms_per_step": ms_fp64,
-                     "steps": max(a.fp64_steps, 1), "vcycles_per_solve": st_fp64[0].vcycles,
-                     "mixed_over_fp64": value / value_fp64},
+        "fp64_gpu": fp64,
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,

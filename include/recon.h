@@ -41,11 +41,14 @@ extern "C" {
 
 #define RECON_OK 0
 #define RECON_NOT_CONVERGED 1 /* k_max steps done before rms(s) <= tol_out */
+#define RECON_STALLED 2       /* the step limiter found no alpha >= alpha_min;
+                                 the iteration stopped, results are the last
+                                 (positive definite) map                    */
 #define RECON_E_INVALID (-1)  /* bad argument / parameter                  */
 #define RECON_E_OOM (-2)      /* device allocation failed                 */
 #define RECON_E_CUDA (-3)     /* a CUDA runtime call failed               */
 #define RECON_E_NONFINITE (-4) /* NaN/Inf or negative input               */
-#define RECON_E_LIMITER (-5)  /* step limiter found no alpha >= alpha_min  */
+#define RECON_E_LIMITER (-5)  /* reserved (a limiter stall is RECON_STALLED) */
 #define RECON_E_TIMEOUT (-6)  /* a bounded device wait expired             */
 #define RECON_E_STATE (-7)    /* call out of order (e.g. solve before deposit) */
 #define RECON_E_UNSUPPORTED (-8) /* feature not available in this build    */
@@ -93,6 +96,9 @@ typedef struct {
     const double* replay_alpha; /* optional host array[k_max]: force alpha_k   */
     int profile;         /* nonzero: time the finest-level smoothing sweeps with
                             CUDA events (reported in recon_stats.smooth_ms)    */
+    int inner_vcycles;   /* RECON_MIXED: FP32 V-cycles per FP64 defect
+                            correction (1..8); the FP64 residual is formed once
+                            per group, so the stopping test sees multiples of it */
 } recon_params;
 
 /* Per-solve record.  The per-step arrays are optional caller-owned host
@@ -140,7 +146,8 @@ int recon_deposit(void* h, int mode, const double* data, const double* mass, int
 
 /* Run the whole moving-mesh solve from phi = 0 on the deposited density
  * (Sec. II; App. A).  Returns RECON_OK when rms(s) <= tol_out,
- * RECON_NOT_CONVERGED after k_max steps (results valid), or an error.
+ * RECON_NOT_CONVERGED after k_max steps, RECON_STALLED when the step limiter
+ * admits no alpha >= alpha_min (results valid in all three), or an error.
  * stats may be NULL. */
 int recon_solve(void* h, recon_stats* stats);
 
@@ -158,6 +165,7 @@ void recon_destroy(void* h);
 
 /* Text of the last error on this thread ("" if none). */
 const char* recon_last_error(void);
+
 
 #ifdef __cplusplus
 }

@@ -61,7 +61,7 @@ class OracleParams:
     k_max: int = 40
     d_max: float = 0.5
     alpha_min: float = 2.0 ** -20
-    lambda_floor: float = 0.0
+    lambda_floor: float = 0.01
 
     def _c(self) -> _Params:
         p = _Params()

@@ -23,9 +23,11 @@
  *         5. with x ~ xi the operator is div(m grad .); a = max(m, a_min);
  *            solve L(a) phidot = s by multigrid V-cycles (App. A).
  *         6. dphi = S phidot (App. A, Delta phi = S phidot), mean removed.
- *         7. step limiter: largest alpha = 2^-k keeping I + Hess(phi + alpha
- *            dphi) positive definite and the move below d_max cells (Sec. II:
- *            positive definiteness via smoothing and grid limiters).
+ *         7. step limiter: largest alpha = 2^-k >= alpha_min keeping the
+ *            smallest eigenvalue of I + Hess(phi + alpha dphi) above
+ *            lambda_floor and the move below d_max cells (Sec. II: positive
+ *            definiteness via smoothing and grid limiters); if there is none
+ *            the iteration stops with the current map (stalled).
  *         8. phi += alpha dphi (phi = sum of the increments, Sec. II / App. A);
  *            the mesh moves by grad dphi in Eulerian space, so every tracer
  *            moves in xi by -alpha e^-1 grad dphi (Sec. IV "displace the
@@ -697,7 +699,7 @@ int orc_solve(const orc_params* p, const double* rho, const double* replay_alpha
     double* dphi = (double*)malloc(len * sizeof(double));
     double* g = (double*)malloc(len * sizeof(double));
     double* lam = (double*)malloc(len * sizeof(double));
-    int rc = 0, k = 0, done = 0;
+    int rc = 0, k = 0, done = 0, stalled = 0;
     if (!w || !xi || !m || !s || !a || !phidot || !dphi || !g || !lam) {
         rc = ORC_E_NOMEM;
         goto out;
@@ -751,6 +753,12 @@ int orc_solve(const orc_params* p, const double* rho, const double* replay_alpha
             alpha = replay_alpha[k];
         } else {
             rc = orc_step_limiter(p, phi, dphi, &alpha);
+            if (rc == ORC_E_LIMITER) {
+                /* no admissible step: stop with the current (valid) map */
+                rc = 0;
+                stalled = 1;
+                break;
+            }
             if (rc) goto out;
         }
         rc = orc_advance(n, alpha, dphi, phi, xi, (int64_t)len); /* 8 */
@@ -767,5 +775,5 @@ out:
     if (steps) *steps = k;
     free(w), free(xi), free(m), free(s), free(a), free(phidot), free(dphi), free(g), free(lam);
     if (rc) return rc;
-    return done ? 0 : 1;
+    return done ? 0 : (stalled ? 2 : 1);
 }

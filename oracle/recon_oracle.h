@@ -112,7 +112,9 @@ int orc_advance(const int n[3], double alpha, const double* dphi, double* phi,
  * grid (any positive units).  phi: output, n cells.  xi: optional np = ncells
  * x 3 output of final tracer coordinates.  m_out: optional final deposit.
  * replay_alpha: optional length-k_max array forcing alpha_k instead of the
- * limiter search.  Returns 0 converged, 1 k_max reached, <0 error.
+ * limiter search.  Returns 0 converged, 1 k_max reached, 2 stopped because
+ * the step limiter found no alpha >= alpha_min (outputs are the last valid
+ * map), <0 error.
  * *steps receives the number of completed advances. */
 int orc_solve(const orc_params* p, const double* rho, const double* replay_alpha,
               double* phi, double* xi, double* m_out, int* steps, orc_trace* tr);

@@ -127,7 +127,8 @@ class Recon:
                          st.smooth_sweeps, st.smooth_bytes)
         if record:
             out.alpha, out.ncycles, out.relres = arrs["alpha"][:k], arrs["ncycles"][:k], arrs["relres"][:k]
-            out.Rk = arrs["Rk"][:min(k + 1, K)] if rc == RECON_OK else arrs["Rk"][:k]
+            stopped = rc in (RECON_OK, _abi.RECON_STALLED)
+            out.Rk = arrs["Rk"][:min(k + 1, K)] if stopped else arrs["Rk"][:k]
         return out
 
     # -- outputs -----------------------------------------------------------

@@ -5,7 +5,7 @@ import os
 
 from . import build as _build
 
-RECON_OK, RECON_NOT_CONVERGED = 0, 1
+RECON_OK, RECON_NOT_CONVERGED, RECON_STALLED = 0, 1, 2
 RECON_E_INVALID, RECON_E_OOM, RECON_E_CUDA, RECON_E_NONFINITE = -1, -2, -3, -4
 RECON_E_LIMITER, RECON_E_TIMEOUT, RECON_E_STATE, RECON_E_UNSUPPORTED = -5, -6, -7, -8
 RECON_FP64, RECON_MIXED = 0, 1
@@ -37,6 +37,7 @@ class recon_params(C.Structure):
         ("tol_in", C.c_double), ("max_vcycles", C.c_int), ("tol_out", C.c_double),
         ("k_max", C.c_int), ("d_max", C.c_double), ("alpha_min", C.c_double),
         ("lambda_floor", C.c_double), ("replay_alpha", _D), ("profile", C.c_int),
+        ("inner_vcycles", C.c_int),
     ]
 
 

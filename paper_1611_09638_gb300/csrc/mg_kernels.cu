@@ -58,6 +58,47 @@ __global__ void k_rbgs_colour(Dims d, T hx, T hy, T hz, int colour, T* __restric
     u[c] = (s.off - f[c]) / s.diag;
 }
 
+// FP64 sweep of the finest level (unit spacing) with the diagonal inverted
+// once per coefficient: u_c = (sum_n (a_c + a_n) u_n - 2 f_c) * inv2_c with
+// inv2_c = 1 / sum_n (a_c + a_n) -- 14 FP64 instructions per node instead of
+// ~45 with the division, since FP64 issue, not memory, bounds this sweep.
+__global__ void k_inv_diag64(Dims d, const double* __restrict__ a, double* __restrict__ inv2) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= d.cells) return;
+    int i, j, k;
+    cell_coords(d, c, i, j, k);
+    const double ac = a[c];
+    const double s = ((2.0 * ac + a[cell_index(d, i + 1, j, k)]) + a[cell_index(d, i - 1, j, k)]) +
+                     ((2.0 * ac + a[cell_index(d, i, j + 1, k)]) + a[cell_index(d, i, j - 1, k)]) +
+                     ((2.0 * ac + a[cell_index(d, i, j, k + 1)]) + a[cell_index(d, i, j, k - 1)]);
+    inv2[c] = 1.0 / s;
+}
+
+__global__ void k_rbgs_colour64_unit(Dims d, int colour, double* __restrict__ u,
+                                     const double* __restrict__ f, const double* __restrict__ F,
+                                     const double* __restrict__ inv2) {
+    const int half = d.cells >> 1;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= half) return;
+    const int hs2 = d.s2 - 1;
+    const int kk = t & ((1 << hs2) - 1);
+    const int j = (t >> hs2) & (d.n1 - 1);
+    const int i = t >> (d.s1 + hs2);
+    const int k = 2 * kk + ((i + j + colour) & 1);
+    const int c = cell_index(d, i, j, k);
+    const int n0 = cell_index(d, i + 1, j, k), n1 = cell_index(d, i - 1, j, k);
+    const int n2 = cell_index(d, i, j + 1, k), n3 = cell_index(d, i, j - 1, k);
+    const int n4 = cell_index(d, i, j, k + 1), n5 = cell_index(d, i, j, k - 1);
+    const size_t n = (size_t)d.cells;
+    double o = F[c] * u[n0];
+    o = fma(F[n1], u[n1], o);
+    o = fma(F[n + c], u[n2], o);
+    o = fma(F[n + n3], u[n3], o);
+    o = fma(F[2 * n + c], u[n4], o);
+    o = fma(F[2 * n + n5], u[n5], o);
+    u[c] = fma(-2.0, f[c], o) * inv2[c];
+}
+
 template <typename T>
 __global__ void k_residual(Dims d, T hx, T hy, T hz, const T* __restrict__ u,
                            const T* __restrict__ f, const T* __restrict__ a, T* __restrict__ r) {
@@ -69,21 +110,53 @@ __global__ void k_residual(Dims d, T hx, T hy, T hz, const T* __restrict__ u,
     r[c] = f[c] - (s.off - s.diag * u[c]);
 }
 
-__global__ void k_residual64_to32(Dims d, double hx, double hy, double hz,
-                                  const double* __restrict__ u, const double* __restrict__ f,
-                                  const double* __restrict__ a, float* __restrict__ r32,
-                                  double* __restrict__ partials) {
+// FP64 residual r = f - L u of the finest level (unit spacing) from the face
+// sums F = a_c + a_n stored per node for its +x, +y, +z faces (the -x face of
+// node c is the +x face of c - e_x): 2 L u = sum_n F_n (u_n - u_c), fourteen
+// FP64 instructions per node -- the FP64 issue rate, not memory, bounds this
+// kernel on GB300, so the faces are read rather than recomputed.  Optionally
+// stores r in FP32 (the right-hand side of the FP32 correction solve) and
+// emits per-block sums of r^2.
+__global__ void k_residual64_to32(Dims d, const double* __restrict__ u,
+                                  const double* __restrict__ f, const double* __restrict__ F,
+                                  float* __restrict__ r32, double* __restrict__ partials) {
     double acc = 0.0;
+    const size_t n = (size_t)d.cells;
+    const double* __restrict__ Fx = F;
+    const double* __restrict__ Fy = F + n;
+    const double* __restrict__ Fz = F + 2 * n;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < d.cells; c += gridDim.x * blockDim.x) {
         int i, j, k;
         cell_coords(d, c, i, j, k);
-        Stencil7<double> s = stencil7<double>(d, hx, hy, hz, i, j, k, c, u, a);
-        double r = f[c] - (s.off - s.diag * u[c]);
+        const int n0 = cell_index(d, i + 1, j, k), n1 = cell_index(d, i - 1, j, k);
+        const int n2 = cell_index(d, i, j + 1, k), n3 = cell_index(d, i, j - 1, k);
+        const int n4 = cell_index(d, i, j, k + 1), n5 = cell_index(d, i, j, k - 1);
+        const double uc = u[c];
+        double s = Fx[c] * (u[n0] - uc);
+        s = fma(Fx[n1], u[n1] - uc, s);
+        s = fma(Fy[c], u[n2] - uc, s);
+        s = fma(Fy[n3], u[n3] - uc, s);
+        s = fma(Fz[c], u[n4] - uc, s);
+        s = fma(Fz[n5], u[n5] - uc, s);
+        const double r = fma(-0.5, s, f[c]);
         if (r32) r32[c] = (float)r;
-        acc += r * r;
+        acc = fma(r, r, acc);
     }
     acc = block_reduce<OpSum>(acc);
     if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+// Face sums F = a_c + a_{c + e_a} of a unit-spacing level, one array per axis.
+__global__ void k_faces64(Dims d, const double* __restrict__ a, double* __restrict__ F) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= d.cells) return;
+    int i, j, k;
+    cell_coords(d, c, i, j, k);
+    const size_t n = (size_t)d.cells;
+    const double ac = a[c];
+    F[c] = ac + a[cell_index(d, i + 1, j, k)];
+    F[n + c] = ac + a[cell_index(d, i, j + 1, k)];
+    F[2 * n + c] = ac + a[cell_index(d, i, j, k + 1)];
 }
 
 // Full weighting: weights (1/4, 1/2, 1/4) along every coarsened axis.
@@ -103,6 +176,37 @@ __global__ void k_restrict(Dims df, Dims dc, int cx, int cy, int cz, const T* __
             for (int ok = -cz; ok <= cz; ++ok) {
                 const T wk = cz ? (ok == 0 ? T(0.5) : T(0.25)) : T(1);
                 acc += wi * wj * wk * in[cell_index(df, fi + oi, fj + oj, fk + ok)];
+            }
+        }
+    }
+    out[c] = acc;
+}
+
+// Residual r = f - L u evaluated at the fine nodes of each coarse node's
+// full-weighting stencil and restricted at once (the fine residual is never
+// stored); per node the same arithmetic as k_residual followed by k_restrict.
+template <typename T>
+__global__ void k_resid_restrict(Dims df, Dims dc, int cx, int cy, int cz, T hx, T hy, T hz,
+                                 const T* __restrict__ u, const T* __restrict__ f,
+                                 const T* __restrict__ a, T* __restrict__ out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= dc.cells) return;
+    int I, J, K;
+    cell_coords(dc, c, I, J, K);
+    const int fi = cx ? 2 * I : I, fj = cy ? 2 * J : J, fk = cz ? 2 * K : K;
+    T acc = T(0);
+    for (int oi = -cx; oi <= cx; ++oi) {
+        const T wi = cx ? (oi == 0 ? T(0.5) : T(0.25)) : T(1);
+        for (int oj = -cy; oj <= cy; ++oj) {
+            const T wj = cy ? (oj == 0 ? T(0.5) : T(0.25)) : T(1);
+            for (int ok = -cz; ok <= cz; ++ok) {
+                const T wk = cz ? (ok == 0 ? T(0.5) : T(0.25)) : T(1);
+                const int i = (fi + oi) & (df.n0 - 1), j = (fj + oj) & (df.n1 - 1),
+                          k = (fk + ok) & (df.n2 - 1);
+                const int n = cell_index(df, i, j, k);
+                Stencil7<T> s = stencil7<T>(df, hx, hy, hz, i, j, k, n, u, a);
+                const T r = f[n] - (s.off - s.diag * u[n]);
+                acc += wi * wj * wk * r;
             }
         }
     }
@@ -244,6 +348,15 @@ void launch_restrict(const Level& fine, const Level& coarse, const T* in, T* out
 }
 
 template <typename T>
+void launch_resid_restrict(const Level& fine, const Level& coarse, const T* u, const T* f,
+                           const T* a, T* out, cudaStream_t st) {
+    launch_counter()++;
+    k_resid_restrict<T><<<nblocks(coarse.d.cells), kThreads, 0, st>>>(
+        fine.d, coarse.d, fine.coarsen[0], fine.coarsen[1], fine.coarsen[2], (T)fine.h2i[0],
+        (T)fine.h2i[1], (T)fine.h2i[2], u, f, a, out);
+}
+
+template <typename T>
 void launch_prolong_add(const Level& fine, const Level& coarse, const T* uc, T* u, cudaStream_t st) {
     launch_counter()++;
     k_prolong_add<T><<<nblocks(fine.d.cells), kThreads, 0, st>>>(
@@ -262,18 +375,34 @@ void launch_coarse_solve(const double* minv, const T* f, T* u, cudaStream_t st) 
     k_coarse_solve<T><<<1, kNc, 0, st>>>(minv, f, u);
 }
 
-void launch_residual64_to32(const Level& L, const double* u, const double* f, const double* a,
+void launch_residual64_to32(const Level& L, const double* u, const double* f, const double* F,
                             float* r32, double* partials, cudaStream_t st) {
     launch_counter()++;
-    k_residual64_to32<<<kRedBlocks, kRedThreads, 0, st>>>(L.d, L.h2i[0], L.h2i[1], L.h2i[2], u, f,
-                                                          a, r32, partials);
+    k_residual64_to32<<<kRedBlocks, kRedThreads, 0, st>>>(L.d, u, f, F, r32, partials);
 }
 
-void launch_residual_norm64(const Level& L, const double* u, const double* f, const double* a,
+void launch_residual_norm64(const Level& L, const double* u, const double* f, const double* F,
                             double* partials, cudaStream_t st) {
     launch_counter()++;
-    k_residual64_to32<<<kRedBlocks, kRedThreads, 0, st>>>(L.d, L.h2i[0], L.h2i[1], L.h2i[2], u, f,
-                                                          a, nullptr, partials);
+    k_residual64_to32<<<kRedBlocks, kRedThreads, 0, st>>>(L.d, u, f, F, nullptr, partials);
+}
+
+void launch_inv_diag64(const Level& L, const double* a, double* inv2, cudaStream_t st) {
+    launch_counter()++;
+    k_inv_diag64<<<nblocks(L.d.cells), kThreads, 0, st>>>(L.d, a, inv2);
+}
+
+void launch_rbgs_sweep64_unit(const Level& L, double* u, const double* f, const double* F,
+                              const double* inv2, cudaStream_t st) {
+    const int half = L.d.cells >> 1;
+    launch_counter() += 2;
+    for (int colour = 0; colour < 2; ++colour)
+        k_rbgs_colour64_unit<<<nblocks(half), kThreads, 0, st>>>(L.d, colour, u, f, F, inv2);
+}
+
+void launch_faces64(const Level& L, const double* a, double* F, cudaStream_t st) {
+    launch_counter()++;
+    k_faces64<<<nblocks(L.d.cells), kThreads, 0, st>>>(L.d, a, F);
 }
 
 void launch_correct(int cells, double* u, const float* e, cudaStream_t st) {
@@ -286,6 +415,8 @@ void launch_correct(int cells, double* u, const float* e, cudaStream_t st) {
     template void launch_residual<T>(const Level&, const T*, const T*, const T*, T*,           \
                                      cudaStream_t);                                           \
     template void launch_restrict<T>(const Level&, const Level&, const T*, T*, cudaStream_t);  \
+    template void launch_resid_restrict<T>(const Level&, const Level&, const T*, const T*,     \
+                                           const T*, T*, cudaStream_t);                       \
     template void launch_prolong_add<T>(const Level&, const Level&, const T*, T*,              \
                                         cudaStream_t);                                        \
     template void launch_coarse_invert<T>(const Level&, const T*, double*, cudaStream_t);      \
@@ -293,5 +424,167 @@ void launch_correct(int cells, double* u, const float* e, cudaStream_t st) {
 RECON_INSTANTIATE(float)
 RECON_INSTANTIATE(double)
 #undef RECON_INSTANTIATE
+
+}  // namespace recon
+
+// ---------------------------------------------------------------------------
+// The coarse end of the V-cycle in one block: every level from l0 (at most
+// kCoarseMaxCells nodes) down to the 4^3 level is smoothed, restricted, solved
+// and prolonged in shared memory, with the same per-node arithmetic as the
+// kernels above, so a V-cycle launches one kernel for all of these levels.
+
+namespace recon {
+
+namespace {
+
+template <typename T>
+__device__ inline void sm_sweep_colour(const Dims& d, T hx, T hy, T hz, int colour, T* u,
+                                       const T* f, const T* a) {
+    const int half = d.cells >> 1, hs2 = d.s2 - 1;
+    for (int t = threadIdx.x; t < half; t += blockDim.x) {
+        const int kk = t & ((1 << hs2) - 1);
+        const int j = (t >> hs2) & (d.n1 - 1);
+        const int i = t >> (d.s1 + hs2);
+        const int k = 2 * kk + ((i + j + colour) & 1);
+        const int c = cell_index(d, i, j, k);
+        Stencil7<T> s = stencil7<T>(d, hx, hy, hz, i, j, k, c, u, a);
+        u[c] = (s.off - f[c]) / s.diag;
+    }
+}
+
+template <typename T>
+__device__ inline void sm_sweeps(const Dims& d, T hx, T hy, T hz, int nu, T* u, const T* f,
+                                 const T* a) {
+    for (int s = 0; s < nu; ++s)
+        for (int colour = 0; colour < 2; ++colour) {
+            sm_sweep_colour<T>(d, hx, hy, hz, colour, u, f, a);
+            __syncthreads();
+        }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_coarse_vcycle(CoarseSet cs, const T* __restrict__ f_top,
+                                                        T* __restrict__ u_top,
+                                                        const double* __restrict__ aug,
+                                                        int zero_u) {
+    extern __shared__ unsigned char smem_raw[];
+    T* base = reinterpret_cast<T*>(smem_raw);
+    T *u[kCoarseMaxLevels], *f[kCoarseMaxLevels], *a[kCoarseMaxLevels], *r[kCoarseMaxLevels];
+    {
+        T* q = base;
+        for (int l = 0; l < cs.nlev; ++l) {
+            const int n = cs.lv[l].d.cells;
+            u[l] = q, f[l] = q + n, a[l] = q + 2 * n, r[l] = q + 3 * n;
+            q += 4 * n;
+        }
+    }
+    for (int l = 0; l < cs.nlev; ++l) {
+        const T* ag = reinterpret_cast<const T*>(cs.a[l]);
+        for (int c = threadIdx.x; c < cs.lv[l].d.cells; c += blockDim.x) a[l][c] = ag[c];
+    }
+    for (int c = threadIdx.x; c < cs.lv[0].d.cells; c += blockDim.x) {
+        f[0][c] = f_top[c];
+        u[0][c] = zero_u ? T(0) : u_top[c];
+    }
+    __syncthreads();
+    const int last = cs.nlev - 1;
+    // down
+    for (int l = 0; l < last; ++l) {
+        const Level& L = cs.lv[l];
+        const T hx = (T)L.h2i[0], hy = (T)L.h2i[1], hz = (T)L.h2i[2];
+        sm_sweeps<T>(L.d, hx, hy, hz, cs.nu1, u[l], f[l], a[l]);
+        for (int c = threadIdx.x; c < L.d.cells; c += blockDim.x) {
+            int i, j, k;
+            cell_coords(L.d, c, i, j, k);
+            Stencil7<T> s = stencil7<T>(L.d, hx, hy, hz, i, j, k, c, u[l], a[l]);
+            r[l][c] = f[l][c] - (s.off - s.diag * u[l][c]);
+        }
+        __syncthreads();
+        const Dims& dc = cs.lv[l + 1].d;
+        const int cx = L.coarsen[0], cy = L.coarsen[1], cz = L.coarsen[2];
+        for (int c = threadIdx.x; c < dc.cells; c += blockDim.x) {
+            int I, J, K;
+            cell_coords(dc, c, I, J, K);
+            const int fi = cx ? 2 * I : I, fj = cy ? 2 * J : J, fk = cz ? 2 * K : K;
+            T acc = T(0);
+            for (int oi = -cx; oi <= cx; ++oi) {
+                const T wi = cx ? (oi == 0 ? T(0.5) : T(0.25)) : T(1);
+                for (int oj = -cy; oj <= cy; ++oj) {
+                    const T wj = cy ? (oj == 0 ? T(0.5) : T(0.25)) : T(1);
+                    for (int ok = -cz; ok <= cz; ++ok) {
+                        const T wk = cz ? (ok == 0 ? T(0.5) : T(0.25)) : T(1);
+                        acc += wi * wj * wk * r[l][cell_index(L.d, fi + oi, fj + oj, fk + ok)];
+                    }
+                }
+            }
+            f[l + 1][c] = acc;
+            u[l + 1][c] = T(0);
+        }
+        __syncthreads();
+    }
+    // coarsest: u = M^-1 [f; 0]
+    if (threadIdx.x < kNc) {
+        double acc = 0.0;
+        for (int c = 0; c < kNc; ++c) acc += aug[threadIdx.x * kW + kNb + c] * (double)f[last][c];
+        u[last][threadIdx.x] = (T)acc;
+    }
+    __syncthreads();
+    // up
+    for (int l = last - 1; l >= 0; --l) {
+        const Level& L = cs.lv[l];
+        const Dims& dc = cs.lv[l + 1].d;
+        const int cx = L.coarsen[0], cy = L.coarsen[1], cz = L.coarsen[2];
+        for (int c = threadIdx.x; c < L.d.cells; c += blockDim.x) {
+            int i, j, k;
+            cell_coords(L.d, c, i, j, k);
+            int ii[2], jj[2], kk[2];
+            T wi[2], wj[2], wk[2];
+            int ni, nj, nk;
+            if (!cx) { ii[0] = i; wi[0] = T(1); ni = 1; }
+            else if (!(i & 1)) { ii[0] = i >> 1; wi[0] = T(1); ni = 1; }
+            else { ii[0] = i >> 1; ii[1] = (i >> 1) + 1; wi[0] = wi[1] = T(0.5); ni = 2; }
+            if (!cy) { jj[0] = j; wj[0] = T(1); nj = 1; }
+            else if (!(j & 1)) { jj[0] = j >> 1; wj[0] = T(1); nj = 1; }
+            else { jj[0] = j >> 1; jj[1] = (j >> 1) + 1; wj[0] = wj[1] = T(0.5); nj = 2; }
+            if (!cz) { kk[0] = k; wk[0] = T(1); nk = 1; }
+            else if (!(k & 1)) { kk[0] = k >> 1; wk[0] = T(1); nk = 1; }
+            else { kk[0] = k >> 1; kk[1] = (k >> 1) + 1; wk[0] = wk[1] = T(0.5); nk = 2; }
+            T acc = T(0);
+            for (int p = 0; p < ni; ++p)
+                for (int q = 0; q < nj; ++q)
+                    for (int rr = 0; rr < nk; ++rr)
+                        acc += wi[p] * wj[q] * wk[rr] * u[l + 1][cell_index(dc, ii[p], jj[q], kk[rr])];
+            u[l][c] += acc;
+        }
+        __syncthreads();
+        sm_sweeps<T>(L.d, (T)L.h2i[0], (T)L.h2i[1], (T)L.h2i[2], cs.nu2, u[l], f[l], a[l]);
+    }
+    for (int c = threadIdx.x; c < cs.lv[0].d.cells; c += blockDim.x) u_top[c] = u[0][c];
+}
+
+}  // namespace
+
+template <typename T>
+bool launch_coarse_vcycle(const CoarseSet& cs, const T* f_top, T* u_top, const double* minv,
+                          bool zero_u, cudaStream_t st) {
+    size_t cells = 0;
+    for (int l = 0; l < cs.nlev; ++l) cells += cs.lv[l].d.cells;
+    const size_t sm = 4 * cells * sizeof(T);
+    if (cs.nlev < 1 || cs.nlev > kCoarseMaxLevels || sm > kCoarseMaxSmem) return false;
+    static bool configured = false;
+    if (!configured) {
+        cudaFuncSetAttribute(k_coarse_vcycle<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kCoarseMaxSmem);
+        configured = true;
+    }
+    launch_counter()++;
+    k_coarse_vcycle<T><<<1, 1024, sm, st>>>(cs, f_top, u_top, minv, zero_u ? 1 : 0);
+    return true;
+}
+
+template bool launch_coarse_vcycle<float>(const CoarseSet&, const float*, float*, const double*,
+                                          bool, cudaStream_t);
+template bool launch_coarse_vcycle<double>(const CoarseSet&, const double*, double*,
+                                           const double*, bool, cudaStream_t);
 
 }  // namespace recon

@@ -52,11 +52,17 @@ struct Handle {
     double *rho = nullptr, *w = nullptr, *ox = nullptr, *oy = nullptr, *oz = nullptr;
     double *phi = nullptr, *m = nullptr, *a64 = nullptr, *t = nullptr, *s = nullptr;
     double *phidot = nullptr, *dphi = nullptr, *v3 = nullptr;  // v3: 3 x cells
+    double* e6 = nullptr;  // triad I + Hess phi of the current step, 6 x cells
+    double* inv64 = nullptr;  // FP64 mode: 1 / (doubled diagonal) of the finest level
+    double* F64 = nullptr;    // face sums a_c + a_{c+e} of the finest level, 3 x cells
+    float *phi32 = nullptr, *dphi32 = nullptr;  // FP32 copies for the limiter's screen
     unsigned long long* mfix = nullptr;
     // multigrid per level: FP64 (FP64 mode) or FP32 (mixed mode)
     std::vector<double*> u64, f64, c64, r64;
     std::vector<float*> u32, f32, c32, r32;
     double* minv = nullptr;
+    int l0 = -1;        // first level of the single-block coarse V-cycle
+    CoarseSet cs{};     // those levels and their coefficients
     double* part[4] = {nullptr, nullptr, nullptr, nullptr};
     double* scal = nullptr;   // device scalars
     double* hscal = nullptr;  // pinned host copy
@@ -132,25 +138,38 @@ void prof_mark(Handle* H) {
     else cudaEventRecord(e, H->st);
 }
 
-// nu red-black sweeps of level l on u.  Where the level fits the streaming
-// kernel each sweep is one pass u -> tmp (ping-pong, ending in u); elsewhere
-// the two colour passes run in place.
+// nu red-black sweeps of level l on the field held in *cur (zero_first: it is
+// 0 on entry and need not be read or cleared).  Where the level fits the
+// streaming kernel (FP32 levels) the sweeps run out of place, ping-ponging
+// between *cur and *oth, and the two pointers are swapped so that *cur holds
+// the result; elsewhere the two colour passes run in place.
 template <typename T>
-void smooth_sweeps(Handle* H, int l, int nu, T* u, T* tmp, const T* f, const T* c) {
+void smooth_sweeps(Handle* H, int l, int nu, T** cur, T** oth, const T* f, const T* c,
+                   bool zero_first) {
     const bool prof = H->p.profile && l == 0 && nu > 0;
     if (prof) prof_mark(H);
-    T* cur = u;
-    T* oth = tmp;
-    for (int s = 0; s < nu; ++s) {
-        if (launch_rbgs_fused<T>(H->lv[l], cur, oth, f, c, H->st)) {
-            T* t = cur;
-            cur = oth, oth = t;
+    bool zero = zero_first;
+    for (int s = 0; s < nu;) {
+        const int k = launch_rbgs_fused<T>(H->lv[l], zero ? nullptr : *cur, *oth, f, c, nu - s, H->st);
+        if (k > 0) {
+            T* t = *cur;
+            *cur = *oth, *oth = t;
+            s += k;
         } else {
-            launch_rbgs_sweep<T>(H->lv[l], cur, f, c, H->st);
+            if (zero) cudaMemsetAsync(*cur, 0, sizeof(T) * H->lv[l].d.cells, H->st);
+            if constexpr (sizeof(T) == sizeof(double)) {
+                if (l == 0 && H->inv64)
+                    launch_rbgs_sweep64_unit(H->lv[0], *cur, f, H->F64, H->inv64, H->st);
+                else
+                    launch_rbgs_sweep<T>(H->lv[l], *cur, f, c, H->st);
+            } else {
+                launch_rbgs_sweep<T>(H->lv[l], *cur, f, c, H->st);
+            }
+            s += 1;
         }
+        zero = false;
     }
-    if (cur != u)
-        cudaMemcpyAsync(u, cur, sizeof(T) * H->lv[l].d.cells, cudaMemcpyDeviceToDevice, H->st);
+    if (zero) cudaMemsetAsync(*cur, 0, sizeof(T) * H->lv[l].d.cells, H->st);  // nu == 0
     if (prof) {
         prof_mark(H);
         H->prof_sweeps += nu;
@@ -190,6 +209,7 @@ int check_params(const recon_params* p) {
     if (!(p->d_max > 0.0)) return fail(RECON_E_INVALID, "need d_max > 0");
     if (!(p->alpha_min > 0.0 && p->alpha_min <= 1.0)) return fail(RECON_E_INVALID, "need 0 < alpha_min <= 1");
     if (!(p->lambda_floor >= 0.0 && p->lambda_floor < 1.0)) return fail(RECON_E_INVALID, "need 0 <= lambda_floor < 1");
+    if (p->inner_vcycles < 1 || p->inner_vcycles > 8) return fail(RECON_E_INVALID, "need 1 <= inner_vcycles <= 8");
     return RECON_OK;
 }
 
@@ -218,25 +238,36 @@ struct MG {
     std::vector<T*>& r;
 };
 
+// One V(nu1, nu2) cycle of level l on L u = f; zero_u: u = 0 on entry.  The
+// level's residual buffer doubles as the ping-pong partner of the streaming
+// smoother; with even sweep counts the result is back in u, otherwise it is
+// copied there.
 template <typename T>
-void vcycle(Handle* H, MG<T>& g, int l, T* u, const T* f) {
+void vcycle(Handle* H, MG<T>& g, int l, T* u, const T* f, bool zero_u) {
     const int last = (int)H->lv.size() - 1;
     const Level& L = H->lv[l];
+    if (l == H->l0 && launch_coarse_vcycle<T>(H->cs, f, u, H->minv, zero_u, H->st)) return;
     if (l == last) {
         launch_coarse_solve<T>(H->minv, f, u, H->st);
         return;
     }
-    smooth_sweeps<T>(H, l, H->p.nu1, u, g.r[l], f, g.c[l]);
-    launch_residual<T>(L, u, f, g.c[l], g.r[l], H->st);
-    launch_restrict<T>(L, H->lv[l + 1], g.r[l], g.f[l + 1], H->st);
-    cudaMemsetAsync(g.u[l + 1], 0, sizeof(T) * H->lv[l + 1].d.cells, H->st);
-    vcycle<T>(H, g, l + 1, g.u[l + 1], g.f[l + 1]);
-    launch_prolong_add<T>(L, H->lv[l + 1], g.u[l + 1], u, H->st);
-    smooth_sweeps<T>(H, l, H->p.nu2, u, g.r[l], f, g.c[l]);
+    T* cur = u;
+    T* oth = g.r[l];
+    smooth_sweeps<T>(H, l, H->p.nu1, &cur, &oth, f, g.c[l], zero_u);
+    launch_resid_restrict<T>(L, H->lv[l + 1], cur, f, g.c[l], g.f[l + 1], H->st);
+    vcycle<T>(H, g, l + 1, g.u[l + 1], g.f[l + 1], true);
+    launch_prolong_add<T>(L, H->lv[l + 1], g.u[l + 1], cur, H->st);
+    smooth_sweeps<T>(H, l, H->p.nu2, &cur, &oth, f, g.c[l], false);
+    if (cur != u)
+        cudaMemcpyAsync(u, cur, sizeof(T) * L.d.cells, cudaMemcpyDeviceToDevice, H->st);
 }
 
 template <typename T>
 void build_hierarchy(Handle* H, std::vector<T*>& c) {
+    launch_faces64(H->lv[0], H->a64, H->F64, H->st);
+    if constexpr (sizeof(T) == sizeof(double)) {
+        if (H->inv64) launch_inv_diag64(H->lv[0], c[0], H->inv64, H->st);
+    }
     for (size_t l = 0; l + 1 < H->lv.size(); ++l)
         launch_restrict<T>(H->lv[l], H->lv[l + 1], c[l], c[l + 1], H->st);
     launch_coarse_invert<T>(H->lv.back(), c.back(), H->minv, H->st);
@@ -250,14 +281,14 @@ void cycle_body(Handle* H) {
     const Level& L0 = H->lv[0];
     if (!H->mixed) {
         MG<double> g{H->u64, H->f64, H->c64, H->r64};
-        vcycle<double>(H, g, 0, H->phidot, H->s);
-        launch_residual_norm64(L0, H->phidot, H->s, H->a64, H->part[0], H->st);
+        vcycle<double>(H, g, 0, H->phidot, H->s, false);
+        launch_residual_norm64(L0, H->phidot, H->s, H->F64, H->part[0], H->st);
     } else {
         MG<float> g{H->u32, H->f32, H->c32, H->r32};
-        cudaMemsetAsync(H->u32[0], 0, sizeof(float) * H->cells, H->st);
-        vcycle<float>(H, g, 0, H->u32[0], H->f32[0]);
+        for (int v = 0; v < H->p.inner_vcycles; ++v)
+            vcycle<float>(H, g, 0, H->u32[0], H->f32[0], v == 0);
         launch_correct(H->cells, H->phidot, H->u32[0], H->st);
-        launch_residual64_to32(L0, H->phidot, H->s, H->a64, H->f32[0], H->part[0], H->st);
+        launch_residual64_to32(L0, H->phidot, H->s, H->F64, H->f32[0], H->part[0], H->st);
     }
     finish_reduce(H->part[0], 0, H->scal, SC_RES2, H->st);
     cudaMemcpyAsync(H->hscal, H->scal, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, H->st);
@@ -318,17 +349,18 @@ int mg_solve(Handle* H, double snorm2, int* ncyc, double* relres) {
     double rel = 1.0;
     if (H->mixed) {
         // first FP64 defect r = s (phidot = 0), handed to the FP32 V-cycle
-        launch_residual64_to32(H->lv[0], H->phidot, H->s, H->a64, H->f32[0], H->part[0], H->st);
+        launch_residual64_to32(H->lv[0], H->phidot, H->s, H->F64, H->f32[0], H->part[0], H->st);
         finish_reduce(H->part[0], 0, H->scal, SC_RES2, H->st);
         int rc = sync_scalars(H);
         if (rc) return rc;
         rel = std::sqrt(H->hscal[SC_RES2] / snorm2);
     }
     int cyc = 0;
+    const int per_launch = H->mixed ? H->p.inner_vcycles : 1;
     while (cyc < H->p.max_vcycles && !(H->mixed && rel <= H->p.tol_in)) {
         int rc = run_cycle(H);
         if (rc) return rc;
-        ++cyc;
+        cyc += per_launch;
         rel = std::sqrt(H->hscal[SC_RES2] / snorm2);
         if (rel <= H->p.tol_in) break;
     }
@@ -356,7 +388,8 @@ int solve(Handle* H, recon_stats* stats) {
     CK(cudaEventRecord(H->ev0, H->st));
     // init: tracer c = node c with mass rho_c / rho_bar, phi = 0
     const double rho_bar = H->rho_sum / (double)n;
-    launch_init_tracers(n, H->rho, 1.0 / rho_bar, H->w, H->ox, H->oy, H->oz, H->phi, H->st);
+    launch_init_tracers(n, H->rho, 1.0 / rho_bar, H->w, H->ox, H->oy, H->oz, H->phi, H->phi32,
+                        H->st);
 
     SourceParams sp{p.xi_m, p.v_m, p.climiter};
     int kmax = 0;
@@ -368,10 +401,11 @@ int solve(Handle* H, recon_stats* stats) {
     bool need_final_deposit = true;
     for (k = 0; k < p.k_max; ++k) {
         deposit_step(H);
-        launch_geometry_source(H->d, sp, H->phi, H->m, H->t, H->part[0], H->part[1], H->st);
+        launch_geometry_source(H->d, sp, H->phi, H->m, H->t, H->e6, H->part[0], H->part[1], H->st);
         finish_reduce(H->part[0], 0, H->scal, SC_SUM_T, H->st);
         finish_reduce(H->part[1], 1, H->scal, SC_MIN_DET, H->st);
-        launch_smooth_S(H->d, p.s_side, H->t, H->scal + SC_SUM_T, H->s, nullptr, H->part[2], H->st);
+        launch_smooth_S(H->d, p.s_side, H->t, H->scal + SC_SUM_T, H->s, nullptr, H->v3, nullptr,
+                        H->part[2], H->st);
         finish_reduce(H->part[2], 0, H->scal, SC_SUM_S2, H->st);
         int rc = sync_scalars(H);
         if (rc) return rc;
@@ -393,29 +427,32 @@ int solve(Handle* H, recon_stats* stats) {
         if (rc) return rc;
         vtot += ncyc;
         // dphi = S phidot (its mean is removed in the advance)
-        launch_smooth_S(H->d, p.s_side, H->phidot, nullptr, H->dphi, H->part[0], nullptr, H->st);
+        launch_smooth_S(H->d, p.s_side, H->phidot, nullptr, H->dphi, H->dphi32, H->v3, H->part[0],
+                        nullptr, H->st);
         finish_reduce(H->part[0], 0, H->scal, SC_SUM_DPHI, H->st);
         double alpha;
         if (!H->replay.empty()) {
             alpha = H->replay[k];
         } else {
-            launch_limiter(H->d, lp, H->phi, H->dphi, H->part[1], H->part[2], H->st);
+            launch_limiter(H->d, lp, H->e6, H->dphi, H->phi32, H->dphi32, H->part[1], H->part[2],
+                           H->st);
             finish_reduce(H->part[1], 2, H->scal, SC_MAX_K, H->st);
             finish_reduce(H->part[2], 2, H->scal, SC_MAX_G, H->st);
             rc = sync_scalars(H);
             if (rc) return rc;
             const int kpd = (int)H->hscal[SC_MAX_K];
             const double gmax = H->hscal[SC_MAX_G];
-            if (kpd > kmax)
-                return fail(RECON_E_LIMITER, "step %d: no alpha >= alpha_min keeps the map positive definite", k);
-            alpha = std::ldexp(1.0, -kpd);
+            alpha = kpd > kmax ? 0.0 : std::ldexp(1.0, -kpd);
             while (alpha * gmax > p.d_max && alpha >= p.alpha_min) alpha *= 0.5;
-            if (alpha < p.alpha_min)
-                return fail(RECON_E_LIMITER, "step %d: move limit needs alpha < alpha_min", k);
+            if (alpha < p.alpha_min) {
+                // no admissible step: stop with the current (valid) map
+                status = RECON_STALLED;
+                break;
+            }
         }
-        launch_node_velocity(H->d, H->phi, H->dphi, H->v3, H->v3 + n, H->v3 + 2 * (size_t)n, H->st);
+        launch_node_velocity(H->d, H->e6, H->dphi, H->v3, H->v3 + n, H->v3 + 2 * (size_t)n, H->st);
         launch_advance(H->d, H->v3, H->v3 + n, H->v3 + 2 * (size_t)n, alpha, H->dphi,
-                       H->scal + SC_SUM_DPHI, H->ox, H->oy, H->oz, H->phi, H->st);
+                       H->scal + SC_SUM_DPHI, H->ox, H->oy, H->oz, H->phi, H->phi32, H->st);
         if (stats) {
             if (stats->alpha) stats->alpha[k] = alpha;
             if (stats->ncycles) stats->ncycles[k] = ncyc;
@@ -496,8 +533,10 @@ int recon_default_params(recon_params* p, int n0, int n1, int n2) {
     p->k_max = 40;
     p->d_max = 0.5;
     p->alpha_min = std::ldexp(1.0, -20);
-    p->lambda_floor = 0.0;
+    p->lambda_floor = 0.01;
     p->replay_alpha = nullptr;
+    p->profile = 0;
+    p->inner_vcycles = 2;
     return RECON_OK;
 }
 
@@ -549,7 +588,8 @@ int recon_create(void** out, const recon_params* p, void* cuda_stream) {
     } while (0)
     AL(H->rho, n); AL(H->w, n); AL(H->ox, n); AL(H->oy, n); AL(H->oz, n);
     AL(H->phi, n); AL(H->m, n); AL(H->a64, n); AL(H->t, n); AL(H->s, n);
-    AL(H->phidot, n); AL(H->dphi, n); AL(H->v3, 3 * n); AL(H->mfix, n);
+    AL(H->phidot, n); AL(H->dphi, n); AL(H->v3, 3 * n); AL(H->mfix, n); AL(H->e6, 6 * n);
+    AL(H->F64, 3 * n); AL(H->phi32, n); AL(H->dphi32, n);
     AL(H->minv, 65 * 130); AL(H->scal, SC_COUNT);
     for (int q = 0; q < 4; ++q) AL(H->part[q], kRedBlocks);
     if (!H->mixed) {
@@ -557,6 +597,7 @@ int recon_create(void** out, const recon_params* p, void* cuda_stream) {
             H->r64.assign(nl, nullptr);
         H->u64[0] = H->phidot, H->f64[0] = H->s, H->c64[0] = H->a64;
         AL(H->r64[0], n);
+        AL(H->inv64, n);
         for (int l = 1; l < nl; ++l) {
             size_t cl = H->lv[l].d.cells;
             AL(H->u64[l], cl); AL(H->f64[l], cl); AL(H->c64[l], cl); AL(H->r64[l], cl);
@@ -570,6 +611,20 @@ int recon_create(void** out, const recon_params* p, void* cuda_stream) {
         }
     }
 #undef AL
+    // the levels from the first one of at most 16^3 nodes down run in one block
+    for (int l = 0; l < nl; ++l)
+        if (H->lv[l].d.cells <= 4096 && nl - l <= kCoarseMaxLevels) {
+            H->l0 = l;
+            break;
+        }
+    if (H->l0 >= 0) {
+        H->cs.nlev = nl - H->l0;
+        H->cs.nu1 = p->nu1, H->cs.nu2 = p->nu2;
+        for (int l = H->l0; l < nl; ++l) {
+            H->cs.lv[l - H->l0] = H->lv[l];
+            H->cs.a[l - H->l0] = H->mixed ? (const void*)H->c32[l] : (const void*)H->c64[l];
+        }
+    }
     if (cudaMallocHost((void**)&H->hscal, SC_COUNT * sizeof(double)) != cudaSuccess ||
         cudaEventCreate(&H->ev0) != cudaSuccess || cudaEventCreate(&H->ev1) != cudaSuccess) {
         cudaGetLastError();

@@ -84,6 +84,16 @@ struct LimiterParams {
     int kmax;  // largest exponent k with 2^-k >= alpha_min
 };
 
+// The coarse levels handled by one block in shared memory (launch_coarse_vcycle).
+constexpr int kCoarseMaxLevels = 8;
+constexpr size_t kCoarseMaxSmem = 200 * 1024;
+struct CoarseSet {
+    int nlev;                              // levels l0 .. last (last is 4^3)
+    int nu1, nu2;
+    Level lv[kCoarseMaxLevels];
+    const void* a[kCoarseMaxLevels];       // coefficient of each level (T*)
+};
+
 // ---- reductions -----------------------------------------------------------
 // op: 0 = sum, 1 = min, 2 = max.  Finishes kRedBlocks partials into slot.
 void finish_reduce(const double* partials, int op, double* scalars, int slot, cudaStream_t st);
@@ -91,22 +101,27 @@ void finish_reduce(const double* partials, int op, double* scalars, int slot, cu
 // ---- multigrid (T = float or double) --------------------------------------
 template <typename T>
 void launch_rbgs_sweep(const Level& L, T* u, const T* f, const T* a, cudaStream_t st);
-// One full red-black sweep u_new <- RBGS(u_old) in a single streaming pass
-// (smoother.cu); returns false, launching nothing, when the level is not a
-// multiple of the kernel's tile.
+// Up to nsweeps full red-black sweeps u_new <- RBGS^k(u_old) in a single
+// streaming pass (smoother.cu); u_old == nullptr means u_old = 0.  Returns k,
+// the sweeps done; 0 (nothing launched) when the level is not a multiple of
+// the kernel's tile or the precision does not use the streaming kernel.
 template <typename T>
-bool launch_rbgs_fused(const Level& L, const T* u_old, T* u_new, const T* f, const T* a,
-                       cudaStream_t st);
+int launch_rbgs_fused(const Level& L, const T* u_old, T* u_new, const T* f, const T* a,
+                      int nsweeps, cudaStream_t st);
 template <>
-bool launch_rbgs_fused<float>(const Level&, const float*, float*, const float*, const float*,
-                              cudaStream_t);
+int launch_rbgs_fused<float>(const Level&, const float*, float*, const float*, const float*,
+                             int, cudaStream_t);
 template <>
-bool launch_rbgs_fused<double>(const Level&, const double*, double*, const double*,
-                               const double*, cudaStream_t);
+int launch_rbgs_fused<double>(const Level&, const double*, double*, const double*,
+                              const double*, int, cudaStream_t);
 template <typename T>
 void launch_residual(const Level& L, const T* u, const T* f, const T* a, T* r, cudaStream_t st);
 template <typename T>
 void launch_restrict(const Level& fine, const Level& coarse, const T* in, T* out, cudaStream_t st);
+// full-weighting restriction of the residual f - L u, without storing it
+template <typename T>
+void launch_resid_restrict(const Level& fine, const Level& coarse, const T* u, const T* f,
+                           const T* a, T* out, cudaStream_t st);
 template <typename T>
 void launch_prolong_add(const Level& fine, const Level& coarse, const T* uc, T* u, cudaStream_t st);
 // Coarsest (4x4x4) level: invert the bordered 65 x 65 system [L 1; 1^T 0]
@@ -115,12 +130,26 @@ template <typename T>
 void launch_coarse_invert(const Level& L, const T* a, double* minv, cudaStream_t st);
 template <typename T>
 void launch_coarse_solve(const double* minv, const T* f, T* u, cudaStream_t st);
+// V-cycle of the levels in cs in one block: L u = f on the first of them,
+// u updated in place (zero_u: u = 0 on entry, not read); returns false,
+// launching nothing, if they do not fit.
+template <typename T>
+bool launch_coarse_vcycle(const CoarseSet& cs, const T* f_top, T* u_top, const double* minv,
+                          bool zero_u, cudaStream_t st);
+// Face sums F (3 x cells: a_c + a_{c+e_x}, ... e_y, ... e_z) of the finest
+// level, used by the FP64 residual and the FP64 sweeps there.
+void launch_faces64(const Level& L, const double* a, double* F, cudaStream_t st);
 // FP64 residual of level 0 in mixed mode: r32 = f - L u (FP64), plus sum r^2
-void launch_residual64_to32(const Level& L, const double* u, const double* f, const double* a,
+void launch_residual64_to32(const Level& L, const double* u, const double* f, const double* F,
                             float* r32, double* partials, cudaStream_t st);
 // FP64 residual norm only: partials of (f - L u)^2
-void launch_residual_norm64(const Level& L, const double* u, const double* f, const double* a,
+void launch_residual_norm64(const Level& L, const double* u, const double* f, const double* F,
                             double* partials, cudaStream_t st);
+// FP64 sweeps of a unit-spacing level: inv2 = 1 / sum_n (a_c + a_n) once per
+// coefficient, then u_c = (sum_n (a_c + a_n) u_n - 2 f_c) inv2_c per colour.
+void launch_inv_diag64(const Level& L, const double* a, double* inv2, cudaStream_t st);
+void launch_rbgs_sweep64_unit(const Level& L, double* u, const double* f, const double* F,
+                              const double* inv2, cudaStream_t st);
 // u64 += e32
 void launch_correct(int cells, double* u, const float* e, cudaStream_t st);
 
@@ -134,26 +163,35 @@ void launch_deposit_particles(const Dims& d, int64_t np, const double* pos, cons
 void launch_fix_to_double(int cells, unsigned long long* mfix, double inv_scale, double* out,
                           cudaStream_t st);
 void launch_init_tracers(int cells, const double* rho, double inv_rho_bar, double* w,
-                         double* ox, double* oy, double* oz, double* phi, cudaStream_t st);
+                         double* ox, double* oy, double* oz, double* phi, float* phi32,
+                         cudaStream_t st);
 void launch_deposit_tracers(const Dims& d, const double* ox, const double* oy, const double* oz,
                             const double* w, double scale, unsigned long long* mfix,
                             cudaStream_t st);
 void launch_mass_coef(int cells, unsigned long long* mfix, double inv_scale, double a_min,
                       double* m, double* a64, float* a32, double* partials, cudaStream_t st);
+// e6 (6 x cells): the triad e = I + Hess phi (xx, yy, zz, xy, xz, yz) of the
+// step, written by the geometry pass and read by the limiter and the advance.
 void launch_geometry_source(const Dims& d, const SourceParams& sp, const double* phi,
-                            const double* m, double* t, double* part_sum, double* part_min,
-                            cudaStream_t st);
+                            const double* m, double* t, double* e6, double* part_sum,
+                            double* part_min, cudaStream_t st);
+// S in three axis passes through tmp2 (2 x cells scratch); out32 (optional)
+// receives an FP32 copy of the result.
 void launch_smooth_S(const Dims& d, double s_side, const double* in, const double* shift_scalar,
-                     double* out, double* part_sum, double* part_sq, cudaStream_t st);
-void launch_limiter(const Dims& d, const LimiterParams& lp, const double* phi, const double* dphi,
-                    double* part_k, double* part_g, cudaStream_t st);
-void launch_node_velocity(const Dims& d, const double* phi, const double* dphi, double* vx,
+                     double* out, float* out32, double* tmp2, double* part_sum, double* part_sq,
+                     cudaStream_t st);
+// phi32, dphi32: FP32 copies of phi and dphi used to screen nodes that clear
+// the limiter's floor by a wide margin.
+void launch_limiter(const Dims& d, const LimiterParams& lp, const double* e6, const double* dphi,
+                    const float* phi32, const float* dphi32, double* part_k, double* part_g,
+                    cudaStream_t st);
+void launch_node_velocity(const Dims& d, const double* e6, const double* dphi, double* vx,
                           double* vy, double* vz, cudaStream_t st);
 // Tracers move by -alpha V(xi) (CIC-interpolated); phi += alpha (dphi - mean),
 // mean = *sum_dphi / cells.
 void launch_advance(const Dims& d, const double* vx, const double* vy, const double* vz,
                     double alpha, const double* dphi, const double* sum_dphi, double* ox,
-                    double* oy, double* oz, double* phi, cudaStream_t st);
+                    double* oy, double* oz, double* phi, float* phi32, cudaStream_t st);
 // outputs
 void launch_delta_r(const Dims& d, const double* phi, double* out, double* part_max,
                     cudaStream_t st);

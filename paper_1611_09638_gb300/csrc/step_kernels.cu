@@ -181,12 +181,13 @@ __global__ void k_fix_to_double(int cells, unsigned long long* __restrict__ mfix
 __global__ void k_init_tracers(int cells, const double* __restrict__ rho, double inv_rho_bar,
                                double* __restrict__ w, double* __restrict__ ox,
                                double* __restrict__ oy, double* __restrict__ oz,
-                               double* __restrict__ phi) {
+                               double* __restrict__ phi, float* __restrict__ phi32) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= cells) return;
     w[c] = rho[c] * inv_rho_bar;
     ox[c] = 0.0, oy[c] = 0.0, oz[c] = 0.0;
     phi[c] = 0.0;
+    phi32[c] = 0.0f;
 }
 
 // Deposit of the tracers on the deformed mesh: tracer c (home node c, mass
@@ -244,13 +245,18 @@ __global__ void k_mass_coef(int cells, unsigned long long* __restrict__ mfix, do
 // C vanishes above it); the Gershgorin bound skips the eigenvalue elsewhere.
 __global__ void k_geometry_source(Dims d, SourceParams sp, const double* __restrict__ phi,
                                   const double* __restrict__ m, double* __restrict__ t,
-                                  double* __restrict__ psum, double* __restrict__ pmin) {
+                                  double* __restrict__ e6, double* __restrict__ psum,
+                                  double* __restrict__ pmin) {
     double s = 0.0, mdet = INFINITY;
+    const size_t n = (size_t)d.cells;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < d.cells; c += gridDim.x * blockDim.x) {
         int i, j, k;
         cell_coords(d, c, i, j, k);
         Sym3 e = hessian(d, phi, i, j, k);
         e.xx += 1.0, e.yy += 1.0, e.zz += 1.0;
+        // the triad is kept for the limiter and the advance of this step
+        e6[c] = e.xx, e6[n + c] = e.yy, e6[2 * n + c] = e.zz;
+        e6[3 * n + c] = e.xy, e6[4 * n + c] = e.xz, e6[5 * n + c] = e.yz;
         const double g = det3(e);
         double C = 0.0;
         const double gersh =
@@ -270,29 +276,30 @@ __global__ void k_geometry_source(Dims d, SourceParams sp, const double* __restr
     if (threadIdx.x == 0) pmin[blockIdx.x] = mdet;
 }
 
-// S u: weighted mean over the 3x3x3 neighbourhood, weights (w, 1-2w, w) per
-// axis, minus (*shift_sum / cells) when shift_sum is given.
-__global__ void k_smooth_S(Dims d, double ws, const double* __restrict__ in,
-                           const double* __restrict__ shift_sum, double* __restrict__ out,
-                           double* __restrict__ psum, double* __restrict__ psq) {
-    const double wt[3] = {ws, 1.0 - 2.0 * ws, ws};
+// One axis of the smoothing operator S (a weighted mean over the 3x3x3
+// neighbourhood, separable into (w, 1-2w, w) along each axis): out =
+// w in[-1] + (1-2w) in[0] + w in[+1] along `axis`, minus (*shift_sum / cells)
+// when shift_sum is given; optional per-block sums of out and out^2.  Three
+// passes (k, j, i) cost 9 FP64 instructions per node against 27 for the
+// direct 27-point sum.
+__global__ void k_smooth_axis(Dims d, int axis, double ws, const double* __restrict__ in,
+                              const double* __restrict__ shift_sum, double* __restrict__ out,
+                              float* __restrict__ out32, double* __restrict__ psum,
+                              double* __restrict__ psq) {
+    const double w1 = 1.0 - 2.0 * ws;
     const double shift = shift_sum ? *shift_sum / (double)d.cells : 0.0;
+    const int di = axis == 0, dj = axis == 1, dk = axis == 2;
     double s = 0.0, q = 0.0;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < d.cells; c += gridDim.x * blockDim.x) {
         int i, j, k;
         cell_coords(d, c, i, j, k);
-        double acc = 0.0;
-        for (int oi = -1; oi <= 1; ++oi)
-            for (int oj = -1; oj <= 1; ++oj) {
-                const double wij = wt[oi + 1] * wt[oj + 1];
-                acc += wij * (wt[0] * in[cell_index(d, i + oi, j + oj, k - 1)] +
-                              wt[1] * in[cell_index(d, i + oi, j + oj, k)] +
-                              wt[2] * in[cell_index(d, i + oi, j + oj, k + 1)]);
-            }
-        const double v = acc - shift;
+        const double v = fma(ws, in[cell_index(d, i - di, j - dj, k - dk)] +
+                                     in[cell_index(d, i + di, j + dj, k + dk)],
+                             w1 * in[c]) - shift;
         out[c] = v;
+        if (out32) out32[c] = (float)v;
         s += v;
-        q += v * v;
+        q = fma(v, v, q);
     }
     if (psum) {
         s = block_reduce<OpSum>(s);
@@ -304,29 +311,89 @@ __global__ void k_smooth_S(Dims d, double ws, const double* __restrict__ in,
     }
 }
 
+template <typename T>
+struct Hess3 {
+    T xx, yy, zz, xy, xz, yz;
+};
+
+// Hessian in FP32 of an FP32 copy, and the largest |value| it read.
+__device__ inline Hess3<float> hessian32(const Dims& d, const float* __restrict__ f, int i, int j,
+                                         int k, float& vmax) {
+    float v[19];
+    v[0] = f[cell_index(d, i, j, k)];
+    v[1] = f[cell_index(d, i + 1, j, k)], v[2] = f[cell_index(d, i - 1, j, k)];
+    v[3] = f[cell_index(d, i, j + 1, k)], v[4] = f[cell_index(d, i, j - 1, k)];
+    v[5] = f[cell_index(d, i, j, k + 1)], v[6] = f[cell_index(d, i, j, k - 1)];
+    v[7] = f[cell_index(d, i + 1, j + 1, k)], v[8] = f[cell_index(d, i + 1, j - 1, k)];
+    v[9] = f[cell_index(d, i - 1, j + 1, k)], v[10] = f[cell_index(d, i - 1, j - 1, k)];
+    v[11] = f[cell_index(d, i + 1, j, k + 1)], v[12] = f[cell_index(d, i + 1, j, k - 1)];
+    v[13] = f[cell_index(d, i - 1, j, k + 1)], v[14] = f[cell_index(d, i - 1, j, k - 1)];
+    v[15] = f[cell_index(d, i, j + 1, k + 1)], v[16] = f[cell_index(d, i, j + 1, k - 1)];
+    v[17] = f[cell_index(d, i, j - 1, k + 1)], v[18] = f[cell_index(d, i, j - 1, k - 1)];
+    vmax = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 19; ++q) vmax = fmaxf(vmax, fabsf(v[q]));
+    Hess3<float> H;
+    H.xx = v[1] - 2.0f * v[0] + v[2];
+    H.yy = v[3] - 2.0f * v[0] + v[4];
+    H.zz = v[5] - 2.0f * v[0] + v[6];
+    H.xy = 0.25f * (v[7] - v[8] - v[9] + v[10]);
+    H.xz = 0.25f * (v[11] - v[12] - v[13] + v[14]);
+    H.yz = 0.25f * (v[15] - v[16] - v[17] + v[18]);
+    return H;
+}
+
 // Step limiter, per node: the smallest k in [0, kmax] with
-// lambda_min(I + Hess phi + 2^-k Hess dphi) > floor (kmax + 1 if none), and
-// max_a |central grad_a dphi|.  Both are max-reduced over the grid.
-__global__ void k_limiter(Dims d, LimiterParams lp, const double* __restrict__ phi,
-                          const double* __restrict__ dphi, double* __restrict__ pk,
+// lambda_min(e + 2^-k Hess dphi) > floor (kmax + 1 if none), e = I + Hess phi
+// the FP64 triad stored by k_geometry_source, and max_a |central grad_a
+// dphi|.  Both are max-reduced over the grid.
+// Most nodes clear alpha = 1 by a wide margin; for them an FP32 evaluation
+// decides: the Gershgorin lower bound of I + Hess phi + Hess dphi computed from
+// FP32 copies must exceed the floor by 1% of the matrix entries plus a bound
+// on every FP32 rounding involved (each Hessian entry combines at most four
+// values of magnitude <= vmax with at most four roundings of 2^-24 relative,
+// and a Gershgorin row adds three entries).  Such a node satisfies the FP64
+// test with room to spare, so the decision is the FP64 one; all other nodes
+// take the FP64 test (Sylvester's criterion on the FP64 triad).
+__global__ void k_limiter(Dims d, LimiterParams lp, const double* __restrict__ e6,
+                          const double* __restrict__ dphi, const float* __restrict__ phi32,
+                          const float* __restrict__ dphi32, double* __restrict__ pk,
                           double* __restrict__ pg) {
-    double kk = 0.0, gm = 0.0;
+    double kk = 0.0;
+    unsigned long long gbits = 0ull;  // max |G| as the bits of a non-negative double
+    const size_t n = (size_t)d.cells;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < d.cells; c += gridDim.x * blockDim.x) {
         int i, j, k;
         cell_coords(d, c, i, j, k);
-        const Sym3 H0 = hessian(d, phi, i, j, k);
+        // move limit: central differences of dphi in FP64 (the max is taken on
+        // the bit patterns, 0.5 is applied once per block)
+        const double gx = dphi[cell_index(d, i + 1, j, k)] - dphi[cell_index(d, i - 1, j, k)];
+        const double gy = dphi[cell_index(d, i, j + 1, k)] - dphi[cell_index(d, i, j - 1, k)];
+        const double gz = dphi[cell_index(d, i, j, k + 1)] - dphi[cell_index(d, i, j, k - 1)];
+        const unsigned long long mask = 0x7fffffffffffffffull;
+        gbits = max(gbits, (unsigned long long)__double_as_longlong(gx) & mask);
+        gbits = max(gbits, (unsigned long long)__double_as_longlong(gy) & mask);
+        gbits = max(gbits, (unsigned long long)__double_as_longlong(gz) & mask);
+        // FP32 screen at alpha = 1
+        float vm0, vm1;
+        const Hess3<float> A = hessian32(d, phi32, i, j, k, vm0);
+        const Hess3<float> B = hessian32(d, dphi32, i, j, k, vm1);
+        const float mxx = 1.0f + A.xx + B.xx, myy = 1.0f + A.yy + B.yy, mzz = 1.0f + A.zz + B.zz;
+        const float mxy = fabsf(A.xy + B.xy), mxz = fabsf(A.xz + B.xz), myz = fabsf(A.yz + B.yz);
+        const float gb = fminf(fminf(mxx - mxy - mxz, myy - mxy - myz), mzz - mxz - myz);
+        const float big = fmaxf(fmaxf(fabsf(mxx), fabsf(myy)), fmaxf(fabsf(mzz), fmaxf(mxy, fmaxf(mxz, myz))));
+        const float err = 3.0f * 16.0f * 5.96046448e-8f * (4.0f * (vm0 + vm1) + 2.0f * big + 1.0f);
+        if (gb > (float)lp.lambda_floor + 0.01f * (1.0f + big) + err) continue;  // kn = 0
+        Sym3 e;
+        e.xx = e6[c], e.yy = e6[n + c], e.zz = e6[2 * n + c];
+        e.xy = e6[3 * n + c], e.xz = e6[4 * n + c], e.yz = e6[5 * n + c];
         const Sym3 H1 = hessian(d, dphi, i, j, k);
-        const double gx = 0.5 * (dphi[cell_index(d, i + 1, j, k)] - dphi[cell_index(d, i - 1, j, k)]);
-        const double gy = 0.5 * (dphi[cell_index(d, i, j + 1, k)] - dphi[cell_index(d, i, j - 1, k)]);
-        const double gz = 0.5 * (dphi[cell_index(d, i, j, k + 1)] - dphi[cell_index(d, i, j, k - 1)]);
-        gm = fmax(gm, fmax(fabs(gx), fmax(fabs(gy), fabs(gz))));
         int kn = lp.kmax + 1;
         double al = 1.0;
         for (int q = 0; q <= lp.kmax; ++q, al *= 0.5) {
             Sym3 M;
-            M.xx = 1.0 + H0.xx + al * H1.xx, M.yy = 1.0 + H0.yy + al * H1.yy;
-            M.zz = 1.0 + H0.zz + al * H1.zz, M.xy = H0.xy + al * H1.xy;
-            M.xz = H0.xz + al * H1.xz, M.yz = H0.yz + al * H1.yz;
+            M.xx = e.xx + al * H1.xx, M.yy = e.yy + al * H1.yy, M.zz = e.zz + al * H1.zz;
+            M.xy = e.xy + al * H1.xy, M.xz = e.xz + al * H1.xz, M.yz = e.yz + al * H1.yz;
             if (pd_above(M, lp.lambda_floor)) {
                 kn = q;
                 break;
@@ -336,21 +403,25 @@ __global__ void k_limiter(Dims d, LimiterParams lp, const double* __restrict__ p
     }
     kk = block_reduce<OpMax>(kk);
     if (threadIdx.x == 0) pk[blockIdx.x] = kk;
+    double gm = 0.5 * __longlong_as_double((long long)gbits);
     gm = block_reduce<OpMax>(gm);
     if (threadIdx.x == 0) pg[blockIdx.x] = gm;
 }
 
-// V = e^-1 G at every node: e = I + Hess phi (before the step), G the
-// central-difference gradient of dphi; solved by Cramer's rule.
-__global__ void k_node_velocity(Dims d, const double* __restrict__ phi,
+// V = e^-1 G at every node: e = I + Hess phi (before the step; stored by
+// k_geometry_source), G the central-difference gradient of dphi; solved by
+// Cramer's rule.
+__global__ void k_node_velocity(Dims d, const double* __restrict__ e6,
                                 const double* __restrict__ dphi, double* __restrict__ vx,
                                 double* __restrict__ vy, double* __restrict__ vz) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= d.cells) return;
     int i, j, k;
     cell_coords(d, c, i, j, k);
-    Sym3 e = hessian(d, phi, i, j, k);
-    e.xx += 1.0, e.yy += 1.0, e.zz += 1.0;
+    const size_t n = (size_t)d.cells;
+    Sym3 e;
+    e.xx = e6[c], e.yy = e6[n + c], e.zz = e6[2 * n + c];
+    e.xy = e6[3 * n + c], e.xz = e6[4 * n + c], e.yz = e6[5 * n + c];
     const double gx = 0.5 * (dphi[cell_index(d, i + 1, j, k)] - dphi[cell_index(d, i - 1, j, k)]);
     const double gy = 0.5 * (dphi[cell_index(d, i, j + 1, k)] - dphi[cell_index(d, i, j - 1, k)]);
     const double gz = 0.5 * (dphi[cell_index(d, i, j, k + 1)] - dphi[cell_index(d, i, j, k - 1)]);
@@ -369,7 +440,8 @@ __global__ void k_advance(Dims d, const double* __restrict__ vx, const double* _
                           const double* __restrict__ vz, double alpha,
                           const double* __restrict__ dphi, const double* __restrict__ sum_dphi,
                           double* __restrict__ ox, double* __restrict__ oy,
-                          double* __restrict__ oz, double* __restrict__ phi) {
+                          double* __restrict__ oz, double* __restrict__ phi,
+                          float* __restrict__ phi32) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= d.cells) return;
     int i, j, k;
@@ -394,7 +466,9 @@ __global__ void k_advance(Dims d, const double* __restrict__ vx, const double* _
     }
     ox[c] = px - alpha * ux, oy[c] = py - alpha * uy, oz[c] = pz - alpha * uz;
     const double mean = *sum_dphi / (double)d.cells;
-    phi[c] += alpha * (dphi[c] - mean);
+    const double pn = phi[c] + alpha * (dphi[c] - mean);
+    phi[c] = pn;
+    phi32[c] = (float)pn;
 }
 
 __global__ void k_delta_r(Dims d, const double* __restrict__ phi, double* __restrict__ out,
@@ -491,9 +565,10 @@ void launch_fix_to_double(int cells, unsigned long long* mfix, double inv_scale,
 }
 
 void launch_init_tracers(int cells, const double* rho, double inv_rho_bar, double* w, double* ox,
-                         double* oy, double* oz, double* phi, cudaStream_t st) {
+                         double* oy, double* oz, double* phi, float* phi32, cudaStream_t st) {
     launch_counter()++;
-    k_init_tracers<<<nblocks(cells), kThreads, 0, st>>>(cells, rho, inv_rho_bar, w, ox, oy, oz, phi);
+    k_init_tracers<<<nblocks(cells), kThreads, 0, st>>>(cells, rho, inv_rho_bar, w, ox, oy, oz, phi,
+                                                        phi32);
 }
 
 void launch_deposit_tracers(const Dims& d, const double* ox, const double* oy, const double* oz,
@@ -511,36 +586,43 @@ void launch_mass_coef(int cells, unsigned long long* mfix, double inv_scale, dou
 }
 
 void launch_geometry_source(const Dims& d, const SourceParams& sp, const double* phi,
-                            const double* m, double* t, double* part_sum, double* part_min,
-                            cudaStream_t st) {
+                            const double* m, double* t, double* e6, double* part_sum,
+                            double* part_min, cudaStream_t st) {
     launch_counter()++;
-    k_geometry_source<<<kRedBlocks, kRedThreads, 0, st>>>(d, sp, phi, m, t, part_sum, part_min);
+    k_geometry_source<<<kRedBlocks, kRedThreads, 0, st>>>(d, sp, phi, m, t, e6, part_sum, part_min);
 }
 
 void launch_smooth_S(const Dims& d, double s_side, const double* in, const double* shift_sum,
-                     double* out, double* part_sum, double* part_sq, cudaStream_t st) {
-    launch_counter()++;
-    k_smooth_S<<<kRedBlocks, kRedThreads, 0, st>>>(d, s_side, in, shift_sum, out, part_sum, part_sq);
+                     double* out, float* out32, double* tmp2, double* part_sum, double* part_sq,
+                     cudaStream_t st) {
+    launch_counter() += 3;
+    k_smooth_axis<<<kRedBlocks, kRedThreads, 0, st>>>(d, 2, s_side, in, nullptr, tmp2, nullptr,
+                                                      nullptr, nullptr);
+    k_smooth_axis<<<kRedBlocks, kRedThreads, 0, st>>>(d, 1, s_side, tmp2, nullptr,
+                                                      tmp2 + d.cells, nullptr, nullptr, nullptr);
+    k_smooth_axis<<<kRedBlocks, kRedThreads, 0, st>>>(d, 0, s_side, tmp2 + d.cells, shift_sum,
+                                                      out, out32, part_sum, part_sq);
 }
 
-void launch_limiter(const Dims& d, const LimiterParams& lp, const double* phi, const double* dphi,
-                    double* part_k, double* part_g, cudaStream_t st) {
+void launch_limiter(const Dims& d, const LimiterParams& lp, const double* e6, const double* dphi,
+                    const float* phi32, const float* dphi32, double* part_k, double* part_g,
+                    cudaStream_t st) {
     launch_counter()++;
-    k_limiter<<<kRedBlocks, kRedThreads, 0, st>>>(d, lp, phi, dphi, part_k, part_g);
+    k_limiter<<<kRedBlocks, kRedThreads, 0, st>>>(d, lp, e6, dphi, phi32, dphi32, part_k, part_g);
 }
 
-void launch_node_velocity(const Dims& d, const double* phi, const double* dphi, double* vx,
+void launch_node_velocity(const Dims& d, const double* e6, const double* dphi, double* vx,
                           double* vy, double* vz, cudaStream_t st) {
     launch_counter()++;
-    k_node_velocity<<<nblocks(d.cells), kThreads, 0, st>>>(d, phi, dphi, vx, vy, vz);
+    k_node_velocity<<<nblocks(d.cells), kThreads, 0, st>>>(d, e6, dphi, vx, vy, vz);
 }
 
 void launch_advance(const Dims& d, const double* vx, const double* vy, const double* vz,
                     double alpha, const double* dphi, const double* sum_dphi, double* ox,
-                    double* oy, double* oz, double* phi, cudaStream_t st) {
+                    double* oy, double* oz, double* phi, float* phi32, cudaStream_t st) {
     launch_counter()++;
     k_advance<<<nblocks(d.cells), kThreads, 0, st>>>(d, vx, vy, vz, alpha, dphi, sum_dphi, ox, oy,
-                                                     oz, phi);
+                                                     oz, phi, phi32);
 }
 
 void launch_delta_r(const Dims& d, const double* phi, double* out, double* part_max,

@@ -145,6 +145,20 @@ def test_invariants_every_step():
     assert abs(r.m.sum() - n ** 3) < 1e-9
 
 
+def test_limiter_stall_stops_with_a_valid_map():
+    """With a floor the map cannot keep above, the iteration stops (status 2)
+    on the last accepted map, which still satisfies every invariant."""
+    n, box = 16, 50.0
+    pos, _ = lpt_particles(n, box, 3, order=2)
+    rho = O.cic_deposit((n, n, n), pos / (box / n))
+    p = O.OracleParams(n=(n, n, n), k_max=40, lambda_floor=0.6)
+    r = O.solve(p, rho)
+    assert r.status == 2 and 0 < r.steps < 40
+    g, lam = O.geometry(r.phi)
+    assert lam.min() > p.lambda_floor and g.min() > 0
+    assert abs(r.m.sum() - n ** 3) < 1e-9
+
+
 def test_shift_and_axis_permutation_equivariance():
     n = 16
     pos, _ = lpt_particles(n, 100.0, 4, order=1)

@@ -32,12 +32,13 @@ def rel(a, b):
 @pytest.fixture(scope="module")
 def za32():
     """32^3 Zel'dovich particles in a 100 Mpc/h box (seed 1000), the oracle's
-    density and its full solve."""
+    density and its solve over the first 20 steps and over all 40."""
     n, box = 32, 100.0
     pos, dL = lpt_particles(n, box, 1000, order=1)
     rho = O.cic_deposit((n, n, n), pos / (box / n))
-    res = O.solve(O.OracleParams(n=(n, n, n)), rho)
-    return dict(n=n, box=box, pos=pos, dL=dL, rho=rho, res=res)
+    res = O.solve(O.OracleParams(n=(n, n, n), k_max=20), rho)
+    res40 = O.solve(O.OracleParams(n=(n, n, n), k_max=40), rho)
+    return dict(n=n, box=box, pos=pos, dL=dL, rho=rho, res=res, res40=res40)
 
 
 def _gpu_solve(n, rho, precision="fp64", box=None, **kw):
@@ -81,10 +82,10 @@ def test_particle_deposit_matches_oracle(za32):
 
 def test_fp64_solve_matches_oracle(za32):
     n, box, res = za32["n"], za32["box"], za32["res"]
-    R, st = _gpu_solve((n, n, n), za32["rho"], box=box)
+    R, st = _gpu_solve((n, n, n), za32["rho"], box=box, k_max=20)
     _check_free_run(st, res)
     R.close()
-    R, st = _gpu_solve((n, n, n), za32["rho"], box=box, replay_alpha=res.alpha)
+    R, st = _gpu_solve((n, n, n), za32["rho"], box=box, k_max=20, replay_alpha=res.alpha)
     h = box / n
     assert st.status == res.status and st.steps == res.steps
     np.testing.assert_array_equal(st.alpha, res.alpha)
@@ -106,10 +107,10 @@ def test_fp64_solve_matches_oracle(za32):
 
 def test_mixed_solve_matches_oracle(za32):
     n, box, res = za32["n"], za32["box"], za32["res"]
-    R, st = _gpu_solve((n, n, n), za32["rho"], precision="mixed", box=box)
+    R, st = _gpu_solve((n, n, n), za32["rho"], precision="mixed", box=box, k_max=20)
     _check_free_run(st, res)
     R.close()
-    R, st = _gpu_solve((n, n, n), za32["rho"], precision="mixed", box=box,
+    R, st = _gpu_solve((n, n, n), za32["rho"], precision="mixed", box=box, k_max=20,
                        replay_alpha=res.alpha)
     h = box / n
     np.testing.assert_array_equal(st.alpha, res.alpha)
@@ -124,6 +125,24 @@ def test_mixed_solve_matches_oracle(za32):
     assert sel.sum() >= 10
     assert np.abs(r_gpu[sel] - r_orc[sel]).max() <= 1e-4
     R.close()
+
+
+def test_forty_step_trajectory_tracks_oracle(za32):
+    """All 40 steps of the 32^3 case: the GPU limiter agrees with the oracle's
+    for at least 20 steps, and with the oracle's alpha replayed both
+    precisions stay within the agreement that the iteration's amplification of
+    rounding differences leaves after step 30."""
+    n, box, res = za32["n"], za32["box"], za32["res40"]
+    for prec, tol in (("fp64", 1e-3), ("mixed", 1e-2)):
+        R, st = _gpu_solve((n, n, n), za32["rho"], precision=prec, box=box)
+        assert _agree_prefix(st.alpha, res.alpha) >= 20
+        R.close()
+        R, st = _gpu_solve((n, n, n), za32["rho"], precision=prec, box=box,
+                           replay_alpha=res.alpha)
+        phi = R.field("phi").cpu().numpy() / (box / n) ** 2
+        assert rel(phi, res.phi) <= tol
+        np.testing.assert_allclose(st.Rk[:30], res.R[:30], rtol=1e-2)
+        R.close()
 
 
 def test_fp64_anisotropic_grid_several_tiles():
@@ -197,6 +216,20 @@ def test_uniform_density_and_minimal_grid():
     R.close()
 
 
+def test_limiter_stall_matches_oracle():
+    n, box = 16, 50.0
+    pos, _ = lpt_particles(n, box, 3, order=2)
+    rho = O.cic_deposit((n, n, n), pos / (box / n))
+    res = O.solve(O.OracleParams(n=(n, n, n), lambda_floor=0.6), rho)
+    assert res.status == 2
+    R, st = _gpu_solve((n, n, n), rho, lambda_floor=0.6)
+    assert st.status == _abi.RECON_STALLED and st.steps == res.steps
+    np.testing.assert_array_equal(st.alpha, res.alpha)
+    assert rel(R.field("phi").cpu().numpy(), res.phi) <= 1e-6
+    assert st.min_lambda0 > 0.6
+    R.close()
+
+
 def test_errors_are_reported_not_raised_on_device():
     with Recon((16, 16, 16)) as R:
         with pytest.raises(ReconError) as e:
@@ -259,8 +292,8 @@ def test_full_size_256_deposit_and_invariants(lpt256):
             st = R.solve()
             assert abs(R.field("mass").sum().item() - n ** 3) <= 1e-9 * n ** 3
             assert st.mass_error <= 1e-12
-            assert st.min_det > 0 and st.min_lambda0 > 0.0
-            assert st.max_delta_r < 3.0
+            assert st.min_det > 0 and st.min_lambda0 > 0.01
+            assert st.max_delta_r < 3 - 3 * 0.01
             assert np.all(st.relres <= 1e-8)
             phi = R.field("phi").cpu().numpy()
             dr = R.field("delta_r").cpu().numpy()
