@@ -166,6 +166,28 @@ void recon_destroy(void* h);
 /* Text of the last error on this thread ("" if none). */
 const char* recon_last_error(void);
 
+/* CIC deposit of particles without any device allocation.  The paper has no
+ * counterpart: this is the deposit of recon_deposit(RECON_PARTICLES) for
+ * callers that cannot call cudaMalloc where they need it -- e.g. while a CUDA
+ * graph is being captured, under an external allocator that owns all device
+ * memory, or in a loop where an allocation would stall the device.
+ *   n0, n1, n2  grid dims, powers of two; n0*n1*n2 <= 2^21 (128^3) cells
+ *   cell        cell side in the units of pos (positions wrap periodically)
+ *   pos         device array of np x 3 doubles; mass: device array of np
+ *               doubles, or NULL for unit masses
+ *   rho         device array of n0*n1*n2 doubles, receives the mass per cell
+ *   cuda_stream stream for the work (cudaStream_t, NULL = legacy stream)
+ * The accumulators live in one fixed 16 MiB device array of the library
+ * (allocated when the library is loaded, on every GPU that loads it, until
+ * exit).  The first call on a device looks up that array's device address;
+ * make that first call before any stream capture.  Every call reuses the same
+ * array, so calls that overlap on the GPU (other streams or threads) race.
+ * The call synchronises the stream once to check the inputs.  Larger grids,
+ * host pointers, NaN/Inf or negative inputs and zero total mass are rejected
+ * with a status (RECON_E_INVALID / RECON_E_NONFINITE); nothing is allocated
+ * or freed. */
+int recon_deposit_cic_noalloc(int n0, int n1, int n2, double cell, const double* pos,
+                              const double* mass, int64_t np, double* rho, void* cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -26,6 +26,7 @@ SYMBOLS = {
     "recon_adjoint": (C.c_int, None),
     "recon_destroy": (None, None),
     "recon_last_error": (C.c_char_p, None),
+    "recon_deposit_cic_noalloc": (C.c_int, None),
 }
 
 
@@ -84,6 +85,9 @@ def load(build_if_missing: bool = True):
     lib.recon_destroy.argtypes = [C.c_void_p]
     lib.recon_last_error.restype = C.c_char_p
     lib.recon_last_error.argtypes = []
+    lib.recon_deposit_cic_noalloc.restype = C.c_int
+    lib.recon_deposit_cic_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_void_p,
+                                              C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]
     _lib = lib
     return lib
 

@@ -514,6 +514,15 @@ bool is_device_ptr(const void* p) {
 
 }  // namespace
 
+namespace recon {
+// Set the thread-local error text read by recon_last_error (used by entry
+// points defined in other translation units); returns code.
+int set_last_error(int code, const char* msg) {
+    snprintf(g_err, sizeof(g_err), "%s", msg ? msg : "");
+    return code;
+}
+}  // namespace recon
+
 extern "C" {
 
 int recon_default_params(recon_params* p, int n0, int n1, int n2) {
