@@ -12,8 +12,9 @@
 // node; the last stage's plane is written out.  u is read from u_old and
 // written to u_new (another buffer), so halos read by a block are never values
 // another block has already updated.  Shared memory holds rings of u and a
-// planes (tile + 2 NS-node ring) and of f planes; plane q + 2 is fetched with
-// cp.async while plane q is processed.  DRAM traffic for NS sweeps is one read
+// planes (tile + 2 NS-node ring; rows padded to 16-byte chunks) and of f
+// planes; plane q + 2 is fetched with 16-byte cp.async copies while plane q is
+// processed.  DRAM traffic for NS sweeps is one read
 // of u, a, f and one write of u.  With u_old == nullptr the sweeps start from
 // u = 0 and u is not read.
 #include "recon_internal.cuh"
@@ -22,31 +23,31 @@ namespace recon {
 
 namespace {
 
-__device__ inline void cp_async4(void* smem, const void* gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
-}
-__device__ inline void cp_async8(void* smem, const void* gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
-}
 __device__ inline void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ inline void cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
 
-template <typename T>
-__device__ inline void cp_async_elem(T* smem, const T* gmem) {
-    if constexpr (sizeof(T) == 4) cp_async4(smem, gmem);
-    else cp_async8(smem, gmem);
-}
+// Division of the smoother update: the fast approximate reciprocal in FP32
+// (a smoother needs no correctly rounded quotient), IEEE in FP64.
+__device__ inline float fast_div(float a, float b) { return __fdividef(a, b); }
+__device__ inline double fast_div(double a, double b) { return a / b; }
 
 template <typename T, int NS, int TJ, int TK>
 struct SweepShape {
-    static constexpr int H = 2 * NS;  // halo of the loaded planes
-    static constexpr int RJ = TJ + 2 * H, RK = TK + 2 * H, PL = RJ * RK;
+    static constexpr int H = 2 * NS;  // halo of the loaded planes (rows)
+    static constexpr int V = 16 / (int)sizeof(T);  // elements per 16-byte copy
+    static constexpr int KO = V;      // column halo, rounded up to one 16-byte chunk
+    static_assert(H <= KO, "column halo must cover the stencil halo");
+    static constexpr int RJ = TJ + 2 * H, RK = TK + 2 * KO, PL = RJ * RK;
+    static constexpr int CH = RK / V;  // 16-byte chunks per row
     static constexpr int SU = 2 * NS + 3;  // u / a ring slots
     static constexpr int SF = 2 * NS + 1;  // f ring slots
     static constexpr int smem = (int)sizeof(T) * PL * (2 * SU + SF);
 };
+
+__device__ inline void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
 
 template <typename T, int NS, int TJ, int TK, int NT>
 __global__ void __launch_bounds__(NT) k_rbgs_stream(Dims d, T hx, T hy, T hz, int CI,
@@ -55,7 +56,8 @@ __global__ void __launch_bounds__(NT) k_rbgs_stream(Dims d, T hx, T hy, T hz, in
                                                     const T* __restrict__ f,
                                                     const T* __restrict__ a) {
     using S = SweepShape<T, NS, TJ, TK>;
-    constexpr int H = S::H, RK = S::RK, PL = S::PL, SU = S::SU, SF = S::SF;
+    constexpr int H = S::H, KO = S::KO, V = S::V, CH = S::CH, RK = S::RK, PL = S::PL;
+    constexpr int SU = S::SU, SF = S::SF;
     constexpr int NST = 2 * NS;  // stages
     extern __shared__ unsigned char smem_raw[];
     T* su = reinterpret_cast<T*>(smem_raw);
@@ -69,26 +71,29 @@ __global__ void __launch_bounds__(NT) k_rbgs_stream(Dims d, T hx, T hy, T hz, in
     auto su_of = [&](int q) { return su + ((q - base) % SU) * PL; };
     auto sa_of = [&](int q) { return sa + ((q - base) % SU) * PL; };
     auto sf_of = [&](int q) { return sf + ((q - base) % SF) * PL; };
-    // old u and a of plane q on the tile + H ring
+    // old u and a of plane q: rows j0-H .. j0+TJ+H-1, columns k0-KO ..
+    // k0+TK+KO-1, in 16-byte chunks (n2 is a multiple of the chunk, so a chunk
+    // never straddles the periodic seam)
     auto fetch_ua = [&](int q) {
         T* du = su_of(q);
         T* da = sa_of(q);
-        for (int e = threadIdx.x; e < PL; e += NT) {
-            const int r = e / RK;
-            const int g = cell_index(d, q, j0 + r - H, k0 + (e - r * RK) - H);
-            if (u_old) cp_async_elem(du + e, u_old + g);
-            else du[e] = T(0);
-            cp_async_elem(da + e, a + g);
+        for (int e = threadIdx.x; e < S::RJ * CH; e += NT) {
+            const int r = e / CH, ch = e - r * CH;
+            const int g = cell_index(d, q, j0 + r - H, k0 - KO + ch * V);
+            const int o = r * RK + ch * V;
+            if (u_old) cp_async16(du + o, u_old + g);
+            else *reinterpret_cast<float4*>(du + o) = make_float4(0.f, 0.f, 0.f, 0.f);
+            cp_async16(da + o, a + g);
         }
     };
-    // f of plane q on the tile + (H - 1) ring (the widest stage region)
+    // f of plane q on the rows of the widest stage region (tile + H - 1)
     auto fetch_f = [&](int q) {
-        constexpr int FJ = TJ + 2 * (H - 1), FK = TK + 2 * (H - 1);
+        constexpr int FJ = TJ + 2 * (H - 1);
         T* df = sf_of(q);
-        for (int e = threadIdx.x; e < FJ * FK; e += NT) {
-            const int r = e / FK, c = e - r * FK;
-            const int g = cell_index(d, q, j0 + r - (H - 1), k0 + c - (H - 1));
-            cp_async_elem(df + (r + 1) * RK + (c + 1), f + g);
+        for (int e = threadIdx.x; e < FJ * CH; e += NT) {
+            const int r = e / CH, ch = e - r * CH;
+            const int g = cell_index(d, q, j0 + r - (H - 1), k0 - KO + ch * V);
+            cp_async16(df + (r + 1) * RK + ch * V, f + g);
         }
     };
 
@@ -108,7 +113,7 @@ __global__ void __launch_bounds__(NT) k_rbgs_stream(Dims d, T hx, T hy, T hz, in
         const T diag = (apx + amx) + (apy + amy) + (apz + amz);
         const T off = (apx * up[e] + amx * um[e]) + (apy * uc[e + RK] + amy * uc[e - RK]) +
                       (apz * uc[e + 1] + amz * uc[e - 1]);
-        return (off - sf_of(q)[e]) / diag;
+        return fast_div(off - sf_of(q)[e], diag);
     };
 
     // prologue: u, a of planes q0-1 .. q0+1; f of plane q0
@@ -139,7 +144,7 @@ __global__ void __launch_bounds__(NT) k_rbgs_stream(Dims d, T hx, T hy, T hz, in
                     // first kk >= -ring with (p + j + k) of the stage's parity
                     const int sh = (p + j0 + jj + k0 - ring + colour) & 1;
                     const int kk = -ring + 2 * c + sh;
-                    const int e = (jj + H) * RK + (kk + H);
+                    const int e = (jj + H) * RK + (kk + KO);
                     upl[e] = gs(p, e);
                 }
             }
@@ -150,7 +155,7 @@ __global__ void __launch_bounds__(NT) k_rbgs_stream(Dims d, T hx, T hy, T hz, in
             const T* upl = su_of(pout);
             for (int e = threadIdx.x; e < TJ * TK; e += NT) {
                 const int jj = e / TK, kk = e - jj * TK;
-                u_new[cell_index(d, pout, j0 + jj, k0 + kk)] = upl[(jj + H) * RK + (kk + H)];
+                u_new[cell_index(d, pout, j0 + jj, k0 + kk)] = upl[(jj + H) * RK + (kk + KO)];
             }
         }
         cp_wait_all();

@@ -343,25 +343,50 @@ __device__ inline Hess3<float> hessian32(const Dims& d, const float* __restrict_
     return H;
 }
 
+// Sylvester's test of N = M - floor I in FP32 with a bound on its error:
+// returns +1 when N is certainly positive definite, -1 when it certainly is
+// not, 0 when FP32 cannot tell.  eps bounds the error of every entry of M;
+// the minors' bounds add the propagated entry errors and the FP32 roundings
+// of their own evaluation (u = 2^-24).
+__device__ inline int sylvester32(float xx, float yy, float zz, float xy, float xz, float yz,
+                                  float floor, float eps) {
+    constexpr float u = 5.96046448e-8f;
+    xx -= floor, yy -= floor, zz -= floor;
+    const float big = fmaxf(fmaxf(fabsf(xx), fabsf(yy)), fmaxf(fabsf(zz),
+                            fmaxf(fabsf(xy), fmaxf(fabsf(xz), fabsf(yz)))));
+    const float en = eps + 2.0f * u * (big + floor);  // entries of N
+    const float m1 = xx;
+    const float m2 = xx * yy - xy * xy;
+    const float m3 = xx * (yy * zz - yz * yz) - xy * (xy * zz - yz * xz) + xz * (xy * yz - yy * xz);
+    const float e1 = en;
+    const float e2 = 4.0f * en * big + en * en + 8.0f * u * big * big;
+    const float e3 = 9.0f * en * big * big + 3.0f * en * en * big + en * en * en + 72.0f * u * big * big * big;
+    if (m1 < -e1 || m2 < -e2 || m3 < -e3) return -1;
+    if (m1 > e1 && m2 > e2 && m3 > e3) return 1;
+    return 0;
+}
+
 // Step limiter, per node: the smallest k in [0, kmax] with
 // lambda_min(e + 2^-k Hess dphi) > floor (kmax + 1 if none), e = I + Hess phi
 // the FP64 triad stored by k_geometry_source, and max_a |central grad_a
 // dphi|.  Both are max-reduced over the grid.
-// Most nodes clear alpha = 1 by a wide margin; for them an FP32 evaluation
-// decides: the Gershgorin lower bound of I + Hess phi + Hess dphi computed from
-// FP32 copies must exceed the floor by 1% of the matrix entries plus a bound
-// on every FP32 rounding involved (each Hessian entry combines at most four
-// values of magnitude <= vmax with at most four roundings of 2^-24 relative,
-// and a Gershgorin row adds three entries).  Such a node satisfies the FP64
-// test with room to spare, so the decision is the FP64 one; all other nodes
-// take the FP64 test (Sylvester's criterion on the FP64 triad).
+// Each alpha is first tested in FP32 on Hessians of FP32 copies of phi and
+// dphi, with a bound on every rounding involved (an entry of a Hessian
+// combines at most four stencil values of magnitude <= vmax; the FP32 copies
+// and at most four operations each round by 2^-24 relative, so 32 u vmax
+// bounds its error with room to spare).  Only when FP32 cannot certify the answer does the node
+// take the FP64 test (Sylvester's criterion on the FP64 triad); where FP32
+// certifies it, the FP64 test gives the same answer, so every decision is the
+// FP64 one while most nodes issue no FP64 arithmetic beyond the move limit.
 __global__ void k_limiter(Dims d, LimiterParams lp, const double* __restrict__ e6,
                           const double* __restrict__ dphi, const float* __restrict__ phi32,
                           const float* __restrict__ dphi32, double* __restrict__ pk,
                           double* __restrict__ pg) {
+    constexpr float u = 5.96046448e-8f;
     double kk = 0.0;
     unsigned long long gbits = 0ull;  // max |G| as the bits of a non-negative double
     const size_t n = (size_t)d.cells;
+    const float floor32 = (float)lp.lambda_floor;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < d.cells; c += gridDim.x * blockDim.x) {
         int i, j, k;
         cell_coords(d, c, i, j, k);
@@ -374,27 +399,40 @@ __global__ void k_limiter(Dims d, LimiterParams lp, const double* __restrict__ e
         gbits = max(gbits, (unsigned long long)__double_as_longlong(gx) & mask);
         gbits = max(gbits, (unsigned long long)__double_as_longlong(gy) & mask);
         gbits = max(gbits, (unsigned long long)__double_as_longlong(gz) & mask);
-        // FP32 screen at alpha = 1
         float vm0, vm1;
         const Hess3<float> A = hessian32(d, phi32, i, j, k, vm0);
         const Hess3<float> B = hessian32(d, dphi32, i, j, k, vm1);
-        const float mxx = 1.0f + A.xx + B.xx, myy = 1.0f + A.yy + B.yy, mzz = 1.0f + A.zz + B.zz;
-        const float mxy = fabsf(A.xy + B.xy), mxz = fabsf(A.xz + B.xz), myz = fabsf(A.yz + B.yz);
-        const float gb = fminf(fminf(mxx - mxy - mxz, myy - mxy - myz), mzz - mxz - myz);
-        const float big = fmaxf(fmaxf(fabsf(mxx), fabsf(myy)), fmaxf(fabsf(mzz), fmaxf(mxy, fmaxf(mxz, myz))));
-        const float err = 3.0f * 16.0f * 5.96046448e-8f * (4.0f * (vm0 + vm1) + 2.0f * big + 1.0f);
-        if (gb > (float)lp.lambda_floor + 0.01f * (1.0f + big) + err) continue;  // kn = 0
-        Sym3 e;
-        e.xx = e6[c], e.yy = e6[n + c], e.zz = e6[2 * n + c];
-        e.xy = e6[3 * n + c], e.xz = e6[4 * n + c], e.yz = e6[5 * n + c];
-        const Sym3 H1 = hessian(d, dphi, i, j, k);
+        bool have64 = false;
+        Sym3 e, H1;
         int kn = lp.kmax + 1;
-        double al = 1.0;
-        for (int q = 0; q <= lp.kmax; ++q, al *= 0.5) {
-            Sym3 M;
-            M.xx = e.xx + al * H1.xx, M.yy = e.yy + al * H1.yy, M.zz = e.zz + al * H1.zz;
-            M.xy = e.xy + al * H1.xy, M.xz = e.xz + al * H1.xz, M.yz = e.yz + al * H1.yz;
-            if (pd_above(M, lp.lambda_floor)) {
+        float al = 1.0f;
+        for (int q = 0; q <= lp.kmax; ++q, al *= 0.5f) {
+            const float mxx = 1.0f + A.xx + al * B.xx, myy = 1.0f + A.yy + al * B.yy;
+            const float mzz = 1.0f + A.zz + al * B.zz, mxy = A.xy + al * B.xy;
+            const float mxz = A.xz + al * B.xz, myz = A.yz + al * B.yz;
+            const float big = fmaxf(fmaxf(fabsf(mxx), fabsf(myy)),
+                                    fmaxf(fabsf(mzz), fmaxf(fabsf(mxy), fmaxf(fabsf(mxz), fabsf(myz)))));
+            // inputs and Hessian arithmetic (|entry| <= 4 vmax), then the two
+            // additions forming M
+            const float eps = 32.0f * u * (vm0 + al * vm1) + 4.0f * u * (big + 1.0f);
+            const int v = sylvester32(mxx, myy, mzz, mxy, mxz, myz, floor32, eps);
+            bool pass;
+            if (v != 0) {
+                pass = v > 0;
+            } else {
+                if (!have64) {
+                    e.xx = e6[c], e.yy = e6[n + c], e.zz = e6[2 * n + c];
+                    e.xy = e6[3 * n + c], e.xz = e6[4 * n + c], e.yz = e6[5 * n + c];
+                    H1 = hessian(d, dphi, i, j, k);
+                    have64 = true;
+                }
+                const double al64 = ldexp(1.0, -q);
+                Sym3 M;
+                M.xx = e.xx + al64 * H1.xx, M.yy = e.yy + al64 * H1.yy, M.zz = e.zz + al64 * H1.zz;
+                M.xy = e.xy + al64 * H1.xy, M.xz = e.xz + al64 * H1.xz, M.yz = e.yz + al64 * H1.yz;
+                pass = pd_above(M, lp.lambda_floor);
+            }
+            if (pass) {
                 kn = q;
                 break;
             }
