@@ -16,7 +16,7 @@ from .build import build
 __all__ = [
     "OracleParams", "CLIM_SOFT", "CLIM_LITERAL", "CLIM_STEP", "cic_deposit", "apply_L",
     "rbgs_sweep", "restrict", "prolong_add", "apply_S", "vcycle", "mg_solve", "geometry",
-    "source", "step_limiter", "advance", "solve", "delta_r", "mesh_x", "min_eig_sym3",
+    "source", "step_limiter", "advance", "solve", "delta_r", "mesh_x", "min_eig_sym3", "mass_change",
     "coarse_dims", "levels",
 ]
 
@@ -33,7 +33,7 @@ class _Params(C.Structure):
         ("climiter", C.c_int), ("s_side", C.c_double),
         ("nu1", C.c_int), ("nu2", C.c_int), ("tol_in", C.c_double), ("max_vcycles", C.c_int),
         ("tol_out", C.c_double), ("k_max", C.c_int), ("d_max", C.c_double),
-        ("alpha_min", C.c_double), ("lambda_floor", C.c_double),
+        ("alpha_min", C.c_double), ("lambda_floor", C.c_double), ("density_update", C.c_int),
     ]
 
 
@@ -62,13 +62,14 @@ class OracleParams:
     d_max: float = 0.5
     alpha_min: float = 2.0 ** -20
     lambda_floor: float = 0.01
+    density_update: int = 0
 
     def _c(self) -> _Params:
         p = _Params()
         p.n[:] = [int(v) for v in self.n]
         for f in ("xi_m", "v_m", "a_min", "climiter", "s_side", "nu1", "nu2",
                   "tol_in", "max_vcycles", "tol_out", "k_max", "d_max", "alpha_min",
-                  "lambda_floor"):
+                  "lambda_floor", "density_update"):
             setattr(p, f, getattr(self, f))
         return p
 
@@ -80,7 +81,7 @@ def _load():
         for name in ("orc_cic_deposit", "orc_apply_L", "orc_rbgs_sweep", "orc_restrict",
                      "orc_prolong_add", "orc_apply_S", "orc_vcycle", "orc_mg_solve",
                      "orc_geometry", "orc_source", "orc_step_limiter", "orc_advance",
-                     "orc_solve", "orc_delta_r", "orc_mesh_x"):
+                     "orc_solve", "orc_delta_r", "orc_mesh_x", "orc_mass_change"):
             getattr(_lib, name).restype = C.c_int
         _lib.orc_min_eig_sym3.restype = C.c_double
     return _lib
@@ -216,6 +217,14 @@ def advance(alpha, dphi, phi, xi):
     _check(_load().orc_advance(_n3(phi.shape), C.c_double(alpha), _dp(dphi), _dp(phi), _dp(xi),
                                C.c_int64(xi.shape[0])), "advance")
     return phi, xi
+
+
+def mass_change(phi, m, v):
+    phi, m, v = _f64(phi), _f64(m), _f64(v)
+    out = np.empty_like(phi)
+    _check(_load().orc_mass_change(_n3(phi.shape), _dp(phi), _dp(m), _dp(v), _dp(out)),
+           "mass_change")
+    return out
 
 
 def delta_r(phi):

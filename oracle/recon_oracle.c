@@ -640,6 +640,63 @@ int orc_advance(const int n[3], double alpha, const double* dphi, double* phi, d
     return 0;
 }
 
+/* ------------------------------------------------ paper-literal update */
+
+int orc_mass_change(const int n[3], const double* phi, const double* m, const double* v,
+                    double* out) {
+    if (!n || !phi || !m || !v || !out || !dims_ok(n, 1)) return ORC_E_INVALID;
+    size_t len = ncells(n);
+    double* K = (double*)malloc(9 * len * sizeof(double));
+    if (!K) return ORC_E_NOMEM;
+    /* K = m e^-1 at every node, the inverse by cofactors / det */
+    for (long i = 0; i < n[0]; ++i)
+        for (long j = 0; j < n[1]; ++j)
+            for (long k = 0; k < n[2]; ++k) {
+                double H[3][3], e[3][3];
+                hessian(n, phi, i, j, k, H);
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b) e[a][b] = (a == b ? 1.0 : 0.0) + H[a][b];
+                double det = det3(e);
+                size_t c = at(n, i, j, k);
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b) {
+                        /* cofactor of e[b][a] (adjugate = transpose of cofactors) */
+                        int r0 = b == 0 ? 1 : 0, r1 = b == 2 ? 1 : 2;
+                        int c0 = a == 0 ? 1 : 0, c1 = a == 2 ? 1 : 2;
+                        double cof = e[r0][c0] * e[r1][c1] - e[r0][c1] * e[r1][c0];
+                        if ((a + b) % 2) cof = -cof;
+                        K[9 * c + 3 * a + b] = m[c] * cof / det;
+                    }
+            }
+    for (long i = 0; i < n[0]; ++i)
+        for (long j = 0; j < n[1]; ++j)
+            for (long k = 0; k < n[2]; ++k) {
+                long o[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+                size_t c = at(n, i, j, k);
+                double acc = 0.0;
+                for (int a = 0; a < 3; ++a) {
+                    size_t pl = at(n, i + o[a][0], j + o[a][1], k + o[a][2]);
+                    size_t mi = at(n, i - o[a][0], j - o[a][1], k - o[a][2]);
+                    double kp = 0.5 * (K[9 * c + 4 * a] + K[9 * pl + 4 * a]);
+                    double km = 0.5 * (K[9 * c + 4 * a] + K[9 * mi + 4 * a]);
+                    acc += kp * (v[pl] - v[c]) - km * (v[c] - v[mi]);
+                    for (int b = 0; b < 3; ++b) {
+                        if (b == a) continue;
+                        long pi = i + o[a][0], pj = j + o[a][1], pk = k + o[a][2];
+                        long qi = i - o[a][0], qj = j - o[a][1], qk = k - o[a][2];
+                        double dp = v[at(n, pi + o[b][0], pj + o[b][1], pk + o[b][2])] -
+                                    v[at(n, pi - o[b][0], pj - o[b][1], pk - o[b][2])];
+                        double dm = v[at(n, qi + o[b][0], qj + o[b][1], qk + o[b][2])] -
+                                    v[at(n, qi - o[b][0], qj - o[b][1], qk - o[b][2])];
+                        acc += 0.25 * (K[9 * pl + 3 * a + b] * dp - K[9 * mi + 3 * a + b] * dm);
+                    }
+                }
+                out[c] = acc;
+            }
+    free(K);
+    return 0;
+}
+
 /* ---------------------------------------------------------------- outputs */
 
 int orc_delta_r(const int n[3], const double* phi, double* out) {
@@ -674,7 +731,8 @@ static int params_ok(const orc_params* p) {
            p->a_min > 0.0 && p->s_side >= 0.0 && p->s_side <= 0.25 && p->nu1 >= 0 && p->nu2 >= 0 && p->nu1 + p->nu2 > 0 &&
            p->tol_in > 0.0 && p->max_vcycles > 0 && p->tol_out >= 0.0 && p->k_max >= 0 &&
            p->d_max > 0.0 && p->alpha_min > 0.0 && p->alpha_min <= 1.0 &&
-           p->lambda_floor >= 0.0 && p->lambda_floor < 1.0;
+           p->lambda_floor >= 0.0 && p->lambda_floor < 1.0 &&
+           (p->density_update == 0 || p->density_update == 1);
 }
 
 int orc_solve(const orc_params* p, const double* rho, const double* replay_alpha,
@@ -699,6 +757,7 @@ int orc_solve(const orc_params* p, const double* rho, const double* replay_alpha
     double* dphi = (double*)malloc(len * sizeof(double));
     double* g = (double*)malloc(len * sizeof(double));
     double* lam = (double*)malloc(len * sizeof(double));
+    double* dm = NULL; /* mass change of the App. A update (density_update = 1) */
     int rc = 0, k = 0, done = 0, stalled = 0;
     if (!w || !xi || !m || !s || !a || !phidot || !dphi || !g || !lam) {
         rc = ORC_E_NOMEM;
@@ -716,8 +775,18 @@ int orc_solve(const orc_params* p, const double* rho, const double* replay_alpha
             }
     memset(phi, 0, len * sizeof(double));
 
+    if (p->density_update == 1) {
+        /* App. A: the mass per cell starts as the density on the undeformed
+         * mesh and is carried by its exact linear change each step */
+        dm = (double*)malloc(len * sizeof(double));
+        if (!dm) {
+            rc = ORC_E_NOMEM;
+            goto out;
+        }
+        memcpy(m, w, len * sizeof(double));
+    }
     for (k = 0; k < p->k_max; ++k) {
-        orc_cic_deposit(n, xi, w, (int64_t)len, m);              /* 1 */
+        if (p->density_update == 0) orc_cic_deposit(n, xi, w, (int64_t)len, m); /* 1 */
         rc = orc_source(p, phi, m, s, NULL);                      /* 2, 3 */
         if (rc) goto out;
         double R = 0.0;
@@ -761,6 +830,12 @@ int orc_solve(const orc_params* p, const double* rho, const double* replay_alpha
             }
             if (rc) goto out;
         }
+        if (p->density_update == 1) {
+            /* m' = m + alpha D(dphi) with the triad of the current map */
+            rc = orc_mass_change(n, phi, m, dphi, dm);
+            if (rc) goto out;
+            for (size_t c = 0; c < len; ++c) m[c] += alpha * dm[c];
+        }
         rc = orc_advance(n, alpha, dphi, phi, xi, (int64_t)len); /* 8 */
         if (rc) goto out;
         if (tr) {
@@ -769,10 +844,14 @@ int orc_solve(const orc_params* p, const double* rho, const double* replay_alpha
             if (tr->relres) tr->relres[k] = rel;
         }
     }
-    if (m_out) orc_cic_deposit(n, xi, w, (int64_t)len, m_out);
+    if (m_out) {
+        if (p->density_update == 0) orc_cic_deposit(n, xi, w, (int64_t)len, m_out);
+        else memcpy(m_out, m, len * sizeof(double));
+    }
     if (xi_out) memcpy(xi_out, xi, 3 * len * sizeof(double));
 out:
     if (steps) *steps = k;
+    free(dm);
     free(w), free(xi), free(m), free(s), free(a), free(phidot), free(dphi), free(g), free(lam);
     if (rc) return rc;
     return done ? 0 : (stalled ? 2 : 1);

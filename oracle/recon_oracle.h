@@ -45,6 +45,8 @@ typedef struct {
     double d_max;           /* step limiter: max |alpha grad dphi| in cells      */
     double alpha_min;       /* step limiter: smallest admissible alpha           */
     double lambda_floor;    /* step limiter: required lambda_min(I + Hess phi)   */
+    int density_update;     /* 0: CIC re-deposit of tracers each step; 1: the
+                               linear update m += alpha D(dphi) of App. A      */
 } orc_params;
 
 /* Per-step record of orc_solve (arrays of length k_max, caller-owned; any may
@@ -107,6 +109,14 @@ int orc_step_limiter(const orc_params* p, const double* phi, const double* dphi,
  * dphi, interpolated with CIC weights; then phi += alpha dphi. */
 int orc_advance(const int n[3], double alpha, const double* dphi, double* phi,
                 double* xi, int64_t np);
+
+/* Exact change of the mass per curvilinear cell under a mesh motion grad v
+ * (App. A, Eq. elliptic_diff): out = d_mu (m (e^-1)^{mu nu} d_nu v), e = I +
+ * Hess phi, in flux form: each axis' second difference with face coefficients
+ * (K_c + K_n)/2 of K = m e^-1, and each cross term as the difference of
+ * centred differences, so that sum(out) = 0. */
+int orc_mass_change(const int n[3], const double* phi, const double* m, const double* v,
+                    double* out);
 
 /* Whole solve (Sec. II moving-mesh iteration, App. A).  rho: density on the
  * grid (any positive units).  phi: output, n cells.  xi: optional np = ncells

@@ -328,3 +328,54 @@ def test_paper_constants_are_the_defaults():
     # delta_r = 3 - tr(e); a triad with every diagonal entry >= 0.1 gives <= 2.7
     assert 3 - 3 * g["min_diag_triad"]["value"] == pytest.approx(g["delta_r_bound"]["value"])
     assert g["delta_r_max_observed"]["value"] <= g["delta_r_bound"]["value"]
+
+
+# ------------------------------------------------- paper-literal mass update
+
+def test_mass_change_reduces_to_the_solve_operator_and_conserves_mass():
+    n = (16, 8, 16)
+    m = np.exp(0.3 * RNG.normal(size=n))
+    v = RNG.normal(size=n)
+    assert np.abs(O.mass_change(np.zeros(n), m, v) - O.apply_L(m, v)).max() < 1e-13
+    i = np.indices(n)
+    phi = 0.4 * np.cos(2 * np.pi * (i[0] / 16 + i[2] / 16)) + 0.3 * np.sin(2 * np.pi * i[1] / 8)
+    d = O.mass_change(phi, m, v)
+    assert abs(d.sum()) < 1e-11 * np.abs(d).sum()
+
+
+def _continuum_mass_change(N):
+    """d_mu(m (I + Hess phi)^-1 d_nu v) of smooth periodic fields, with the
+    derivatives of phi and v analytic and the outer divergence spectral."""
+    x = np.indices((N, N, N)) * (2 * np.pi / N)
+    A, B = 0.25 * (N / (2 * np.pi)) ** 2, 0.15 * (N / (2 * np.pi)) ** 2
+    m = 1.0 + 0.3 * np.sin(x[0]) * np.cos(x[1]) + 0.2 * np.cos(x[2])
+    phi = A * np.cos(x[0] + x[1]) + B * np.sin(x[2] - x[0])
+    v = np.sin(x[0] + 2 * x[2]) + 0.5 * np.cos(x[1])
+    s = 2 * np.pi / N  # d/d(grid index) of the phase
+    H = np.zeros((3, 3) + m.shape)
+    c1, c2 = -A * np.cos(x[0] + x[1]) * s * s, -B * np.sin(x[2] - x[0]) * s * s
+    for a, b, w in ((0, 0, c1 + c2), (1, 1, c1), (2, 2, c2), (0, 1, c1), (0, 2, -c2)):
+        H[a, b] += w
+        if a != b:
+            H[b, a] += w
+    e = np.moveaxis(H, (0, 1), (-2, -1)) + np.eye(3)
+    Kt = m[..., None, None] * np.linalg.inv(e)
+    gv = np.stack([np.cos(x[0] + 2 * x[2]) * s, -0.5 * np.sin(x[1]) * s,
+                   2 * np.cos(x[0] + 2 * x[2]) * s], -1)
+    flux = np.einsum("...ab,...b->...a", Kt, gv)
+    k = np.fft.fftfreq(N) * 2 * np.pi
+    out = np.zeros_like(m)
+    for a in range(3):
+        shape = [1, 1, 1]
+        shape[a] = N
+        out += np.fft.ifftn(1j * k.reshape(shape) * np.fft.fftn(flux[..., a])).real
+    return m, phi, v, out
+
+
+def test_mass_change_converges_to_the_continuum_divergence_at_second_order():
+    errs = []
+    for N in (16, 32):
+        m, phi, v, ref = _continuum_mass_change(N)
+        got = O.mass_change(phi, m, v)
+        errs.append(np.abs(got - ref).max() / np.abs(ref).max())
+    assert errs[1] < 0.02 and 3.0 < errs[0] / errs[1] < 5.0, errs
