@@ -99,6 +99,14 @@ typedef struct {
     int inner_vcycles;   /* RECON_MIXED: FP32 V-cycles per FP64 defect
                             correction (1..8); the FP64 residual is formed once
                             per group, so the stopping test sees multiples of it */
+    int density_update;  /* 0: CIC re-deposit of the tracers on the deformed mesh
+                            every step (default); 1: App. A's linear update
+                            m += alpha d_mu(m e^-1 d dphi) of the mass per cell  */
+    int device_loop;     /* 1 (default): the whole iteration runs as one CUDA graph
+                            whose conditional nodes the device sets (step loop,
+                            multigrid loop, step acceptance), with no host round
+                            trip until the solve ends; 0: host-driven loop that
+                            reads each decision back.  profile forces 0.        */
 } recon_params;
 
 /* Per-solve record.  The per-step arrays are optional caller-owned host
@@ -150,6 +158,21 @@ int recon_deposit(void* h, int mode, const double* data, const double* mass, int
  * admits no alpha >= alpha_min (results valid in all three), or an error.
  * stats may be NULL. */
 int recon_solve(void* h, recon_stats* stats);
+
+/* recon_solve_batch: solves count independent problems (for example many
+ * mock catalogues of different sizes), one per handle, each as recon_solve
+ * would.  Every handle created with device_loop = 1 has its whole solve
+ * launched (as one CUDA graph on the handle's own stream) before the call
+ * waits for any of them, so handles created on distinct streams run their
+ * solves concurrently on the device; handles with device_loop = 0 are solved
+ * one after another while the others run.  Each handle must have a deposited
+ * density and may appear once.  stats: NULL, or an array of count records
+ * filled as by recon_solve.  Returns RECON_OK when every solve returned a
+ * non-negative status (RECON_NOT_CONVERGED / RECON_STALLED are reported per
+ * handle in stats), else the first negative status; the handles whose solve
+ * failed are left without a result.  Not a method of the paper: it batches
+ * the iteration of Sec. II / App. A over independent inputs. */
+int recon_solve_batch(void* const* handles, int count, recon_stats* stats);
 
 /* Copy one output field (RECON_FIELD_*) of the last solve to dst (host or
  * device), dst_bytes >= its size (ncells x 8, MESH_X ncells x 24). */

@@ -17,7 +17,7 @@ from . import _abi
 from ._abi import (RECON_FP64, RECON_MIXED, RECON_OK, RECON_NOT_CONVERGED, ReconError,  # noqa: F401
                    FIELDS)
 
-__all__ = ["Recon", "SolveStats", "default_params", "RECON_FP64", "RECON_MIXED", "ReconError"]
+__all__ = ["Recon", "SolveStats", "default_params", "solve_batch", "RECON_FP64", "RECON_MIXED", "ReconError"]
 
 
 def default_params(n, box=None, precision="fp64", **overrides):
@@ -109,8 +109,8 @@ class Recon:
                                                   int(np.prod(rho.shape))), "recon_deposit")
 
     # -- solve -------------------------------------------------------------
-    def solve(self, record=True) -> SolveStats:
-        st = _abi.recon_stats()
+    def _stats_record(self, st, record):
+        """Attach per-step host arrays of length k_max to a recon_stats."""
         K = max(int(self.params.k_max), 1)
         arrs = {}
         if record:
@@ -119,8 +119,10 @@ class Recon:
                 setattr(st, k, arrs[k].ctypes.data_as(C.POINTER(C.c_double)))
             arrs["ncycles"] = np.zeros(K, dtype=np.int32)
             st.ncycles = arrs["ncycles"].ctypes.data_as(C.POINTER(C.c_int))
-        rc = self._lib.recon_solve(self._h, C.byref(st))
-        _abi.check(rc, "recon_solve")
+        return arrs
+
+    def _stats_out(self, rc, st, arrs, record):
+        K = max(int(self.params.k_max), 1)
         k = st.steps
         out = SolveStats(rc, k, st.vcycles, st.R0, st.R, st.min_det, st.min_lambda0,
                          st.max_delta_r, st.mass_error, st.ms, st.launches, st.smooth_ms,
@@ -130,6 +132,13 @@ class Recon:
             stopped = rc in (RECON_OK, _abi.RECON_STALLED)
             out.Rk = arrs["Rk"][:min(k + 1, K)] if stopped else arrs["Rk"][:k]
         return out
+
+    def solve(self, record=True) -> SolveStats:
+        st = _abi.recon_stats()
+        arrs = self._stats_record(st, record)
+        rc = self._lib.recon_solve(self._h, C.byref(st))
+        _abi.check(rc, "recon_solve")
+        return self._stats_out(rc, st, arrs, record)
 
     # -- outputs -----------------------------------------------------------
     def field(self, which, out=None):
@@ -165,3 +174,20 @@ class Recon:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def solve_batch(recons, record=True):
+    """Solve several independent problems at once (recon_solve_batch): every
+    handle's solve is launched on its own stream before any is waited for, so
+    handles created on distinct streams run concurrently.  Returns one
+    SolveStats per handle; raises if any solve failed."""
+    recons = list(recons)
+    if not recons:
+        return []
+    lib = recons[0]._lib
+    sts = (_abi.recon_stats * len(recons))()
+    arrs = [r._stats_record(sts[b], record) for b, r in enumerate(recons)]
+    hs = (C.c_void_p * len(recons))(*[r._h.value for r in recons])
+    rc = lib.recon_solve_batch(hs, len(recons), sts)
+    _abi.check(rc, "recon_solve_batch")
+    return [r._stats_out(sts[b].status, sts[b], arrs[b], record) for b, r in enumerate(recons)]

@@ -22,6 +22,7 @@ SYMBOLS = {
     "recon_create": (C.c_int, None),
     "recon_deposit": (C.c_int, None),
     "recon_solve": (C.c_int, None),
+    "recon_solve_batch": (C.c_int, None),
     "recon_field": (C.c_int, None),
     "recon_adjoint": (C.c_int, None),
     "recon_destroy": (None, None),
@@ -38,7 +39,7 @@ class recon_params(C.Structure):
         ("tol_in", C.c_double), ("max_vcycles", C.c_int), ("tol_out", C.c_double),
         ("k_max", C.c_int), ("d_max", C.c_double), ("alpha_min", C.c_double),
         ("lambda_floor", C.c_double), ("replay_alpha", _D), ("profile", C.c_int),
-        ("inner_vcycles", C.c_int),
+        ("inner_vcycles", C.c_int), ("density_update", C.c_int), ("device_loop", C.c_int),
     ]
 
 
@@ -77,6 +78,8 @@ def load(build_if_missing: bool = True):
     lib.recon_deposit.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int64]
     lib.recon_solve.restype = C.c_int
     lib.recon_solve.argtypes = [C.c_void_p, C.POINTER(recon_stats)]
+    lib.recon_solve_batch.restype = C.c_int
+    lib.recon_solve_batch.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.POINTER(recon_stats)]
     lib.recon_field.restype = C.c_int
     lib.recon_field.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t]
     lib.recon_adjoint.restype = C.c_int

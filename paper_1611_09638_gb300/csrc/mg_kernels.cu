@@ -62,21 +62,12 @@ __global__ void k_rbgs_colour(Dims d, T hx, T hy, T hz, int colour, T* __restric
 // once per coefficient: u_c = (sum_n (a_c + a_n) u_n - 2 f_c) * inv2_c with
 // inv2_c = 1 / sum_n (a_c + a_n) -- 14 FP64 instructions per node instead of
 // ~45 with the division, since FP64 issue, not memory, bounds this sweep.
-__global__ void k_inv_diag64(Dims d, const double* __restrict__ a, double* __restrict__ inv2) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= d.cells) return;
-    int i, j, k;
-    cell_coords(d, c, i, j, k);
-    const double ac = a[c];
-    const double s = ((2.0 * ac + a[cell_index(d, i + 1, j, k)]) + a[cell_index(d, i - 1, j, k)]) +
-                     ((2.0 * ac + a[cell_index(d, i, j + 1, k)]) + a[cell_index(d, i, j - 1, k)]) +
-                     ((2.0 * ac + a[cell_index(d, i, j, k + 1)]) + a[cell_index(d, i, j, k - 1)]);
-    inv2[c] = 1.0 / s;
-}
-
+// One colour of a red-black sweep of the finest FP64 level (unit spacing)
+// from the stored face coefficients A = (a_c + a_n) / 2 (F: +x, +y, +z face
+// of each node) and the inverse of the node's diagonal D = sum of its six A.
 __global__ void k_rbgs_colour64_unit(Dims d, int colour, double* __restrict__ u,
                                      const double* __restrict__ f, const double* __restrict__ F,
-                                     const double* __restrict__ inv2) {
+                                     const double* __restrict__ inv_d) {
     const int half = d.cells >> 1;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= half) return;
@@ -96,7 +87,7 @@ __global__ void k_rbgs_colour64_unit(Dims d, int colour, double* __restrict__ u,
     o = fma(F[n + n3], u[n3], o);
     o = fma(F[2 * n + c], u[n4], o);
     o = fma(F[2 * n + n5], u[n5], o);
-    u[c] = fma(-2.0, f[c], o) * inv2[c];
+    u[c] = (o - f[c]) * inv_d[c];
 }
 
 template <typename T>
@@ -110,16 +101,19 @@ __global__ void k_residual(Dims d, T hx, T hy, T hz, const T* __restrict__ u,
     r[c] = f[c] - (s.off - s.diag * u[c]);
 }
 
-// FP64 residual r = f - L u of the finest level (unit spacing) from the face
-// sums F = a_c + a_n stored per node for its +x, +y, +z faces (the -x face of
-// node c is the +x face of c - e_x): 2 L u = sum_n F_n (u_n - u_c), fourteen
-// FP64 instructions per node -- the FP64 issue rate, not memory, bounds this
-// kernel on GB300, so the faces are read rather than recomputed.  Optionally
-// stores r in FP32 (the right-hand side of the FP32 correction solve) and
-// emits per-block sums of r^2.
+// FP64 residual r = f - L u of the finest level (unit spacing) from the
+// stored face coefficients A (F) and node diagonals D: since
+// L u = sum_n A_n u_n - D u_c, r = f + D u_c - sum_n A_n u_n is a chain of
+// seven FMAs.  The FP64 issue rate, not memory, bounds this kernel on GB300,
+// so coefficients are read rather than recomputed.  The rounding error of the
+// undifferenced form is ~8 eps D |u|, i.e. ~1e-12 relative to |f| even for
+// the smoothest mode of a 512^3 grid, far below the stopping tolerance.
+// Optionally also writes r in FP32 (the next V-cycle's right-hand side);
+// always the per-block partial sums of r^2.
 __global__ void k_residual64_to32(Dims d, const double* __restrict__ u,
                                   const double* __restrict__ f, const double* __restrict__ F,
-                                  float* __restrict__ r32, double* __restrict__ partials) {
+                                  const double* __restrict__ D, float* __restrict__ r32,
+                                  double* __restrict__ partials) {
     double acc = 0.0;
     const size_t n = (size_t)d.cells;
     const double* __restrict__ Fx = F;
@@ -131,14 +125,13 @@ __global__ void k_residual64_to32(Dims d, const double* __restrict__ u,
         const int n0 = cell_index(d, i + 1, j, k), n1 = cell_index(d, i - 1, j, k);
         const int n2 = cell_index(d, i, j + 1, k), n3 = cell_index(d, i, j - 1, k);
         const int n4 = cell_index(d, i, j, k + 1), n5 = cell_index(d, i, j, k - 1);
-        const double uc = u[c];
-        double s = Fx[c] * (u[n0] - uc);
-        s = fma(Fx[n1], u[n1] - uc, s);
-        s = fma(Fy[c], u[n2] - uc, s);
-        s = fma(Fy[n3], u[n3] - uc, s);
-        s = fma(Fz[c], u[n4] - uc, s);
-        s = fma(Fz[n5], u[n5] - uc, s);
-        const double r = fma(-0.5, s, f[c]);
+        double r = fma(D[c], u[c], f[c]);
+        r = fma(-Fx[c], u[n0], r);
+        r = fma(-Fx[n1], u[n1], r);
+        r = fma(-Fy[c], u[n2], r);
+        r = fma(-Fy[n3], u[n3], r);
+        r = fma(-Fz[c], u[n4], r);
+        r = fma(-Fz[n5], u[n5], r);
         if (r32) r32[c] = (float)r;
         acc = fma(r, r, acc);
     }
@@ -146,17 +139,27 @@ __global__ void k_residual64_to32(Dims d, const double* __restrict__ u,
     if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 
-// Face sums F = a_c + a_{c + e_a} of a unit-spacing level, one array per axis.
-__global__ void k_faces64(Dims d, const double* __restrict__ a, double* __restrict__ F) {
+// Face coefficients A = (a_c + a_{c + e_a}) / 2 of a unit-spacing level, one
+// array per axis, the node diagonal D = sum of the node's six A, and
+// optionally 1 / D.
+__global__ void k_faces64(Dims d, const double* __restrict__ a, double* __restrict__ F,
+                          double* __restrict__ D, double* __restrict__ inv_d) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= d.cells) return;
     int i, j, k;
     cell_coords(d, c, i, j, k);
     const size_t n = (size_t)d.cells;
     const double ac = a[c];
-    F[c] = ac + a[cell_index(d, i + 1, j, k)];
-    F[n + c] = ac + a[cell_index(d, i, j + 1, k)];
-    F[2 * n + c] = ac + a[cell_index(d, i, j, k + 1)];
+    const double xp = 0.5 * (ac + a[cell_index(d, i + 1, j, k)]);
+    const double xm = 0.5 * (ac + a[cell_index(d, i - 1, j, k)]);
+    const double yp = 0.5 * (ac + a[cell_index(d, i, j + 1, k)]);
+    const double ym = 0.5 * (ac + a[cell_index(d, i, j - 1, k)]);
+    const double zp = 0.5 * (ac + a[cell_index(d, i, j, k + 1)]);
+    const double zm = 0.5 * (ac + a[cell_index(d, i, j, k - 1)]);
+    F[c] = xp, F[n + c] = yp, F[2 * n + c] = zp;
+    const double dg = ((xp + xm) + (yp + ym)) + (zp + zm);
+    D[c] = dg;
+    if (inv_d) inv_d[c] = 1.0 / dg;
 }
 
 // Full weighting: weights (1/4, 1/2, 1/4) along every coarsened axis.
@@ -376,33 +379,29 @@ void launch_coarse_solve(const double* minv, const T* f, T* u, cudaStream_t st) 
 }
 
 void launch_residual64_to32(const Level& L, const double* u, const double* f, const double* F,
-                            float* r32, double* partials, cudaStream_t st) {
+                            const double* D, float* r32, double* partials, cudaStream_t st) {
     launch_counter()++;
-    k_residual64_to32<<<kRedBlocks, kRedThreads, 0, st>>>(L.d, u, f, F, r32, partials);
+    k_residual64_to32<<<kRedBlocks, kRedThreads, 0, st>>>(L.d, u, f, F, D, r32, partials);
 }
 
 void launch_residual_norm64(const Level& L, const double* u, const double* f, const double* F,
-                            double* partials, cudaStream_t st) {
+                            const double* D, double* partials, cudaStream_t st) {
     launch_counter()++;
-    k_residual64_to32<<<kRedBlocks, kRedThreads, 0, st>>>(L.d, u, f, F, nullptr, partials);
-}
-
-void launch_inv_diag64(const Level& L, const double* a, double* inv2, cudaStream_t st) {
-    launch_counter()++;
-    k_inv_diag64<<<nblocks(L.d.cells), kThreads, 0, st>>>(L.d, a, inv2);
+    k_residual64_to32<<<kRedBlocks, kRedThreads, 0, st>>>(L.d, u, f, F, D, nullptr, partials);
 }
 
 void launch_rbgs_sweep64_unit(const Level& L, double* u, const double* f, const double* F,
-                              const double* inv2, cudaStream_t st) {
+                              const double* inv_d, cudaStream_t st) {
     const int half = L.d.cells >> 1;
     launch_counter() += 2;
     for (int colour = 0; colour < 2; ++colour)
-        k_rbgs_colour64_unit<<<nblocks(half), kThreads, 0, st>>>(L.d, colour, u, f, F, inv2);
+        k_rbgs_colour64_unit<<<nblocks(half), kThreads, 0, st>>>(L.d, colour, u, f, F, inv_d);
 }
 
-void launch_faces64(const Level& L, const double* a, double* F, cudaStream_t st) {
+void launch_faces64(const Level& L, const double* a, double* F, double* D, double* inv_d,
+                    cudaStream_t st) {
     launch_counter()++;
-    k_faces64<<<nblocks(L.d.cells), kThreads, 0, st>>>(L.d, a, F);
+    k_faces64<<<nblocks(L.d.cells), kThreads, 0, st>>>(L.d, a, F, D, inv_d);
 }
 
 void launch_correct(int cells, double* u, const float* e, cudaStream_t st) {

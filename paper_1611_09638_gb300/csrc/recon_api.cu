@@ -5,6 +5,7 @@
 // defect correction), the smoothed increment, the step limiter and the advance.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -37,6 +38,11 @@ int fail(int code, const char* fmt, ...) {
                         __FILE__, __LINE__);                                                  \
     } while (0)
 
+// Kernels recorded in each body of the solve graph.
+struct GraphCounts {
+    long long init = 0, step = 0, cont = 0, mg = 0, adv = 0, fin = 0;
+};
+
 struct Handle {
     recon_params p{};
     std::vector<double> replay;
@@ -53,9 +59,11 @@ struct Handle {
     double *phi = nullptr, *m = nullptr, *a64 = nullptr, *t = nullptr, *s = nullptr;
     double *phidot = nullptr, *dphi = nullptr, *v3 = nullptr;  // v3: 3 x cells
     double* e6 = nullptr;  // triad I + Hess phi of the current step, 6 x cells
-    double* inv64 = nullptr;  // FP64 mode: 1 / (doubled diagonal) of the finest level
-    double* F64 = nullptr;    // face sums a_c + a_{c+e} of the finest level, 3 x cells
+    double* inv64 = nullptr;  // FP64 mode: 1 / diagonal of the finest level
+    double* F64 = nullptr;    // face coefficients (a_c + a_{c+e}) / 2 of the finest level, 3 x cells
+    double* D64 = nullptr;    // node diagonal: sum of the node's six face coefficients
     float *phi32 = nullptr, *dphi32 = nullptr;  // FP32 copies for the limiter's screen
+    double* v3m = nullptr;  // density_update = 1: K = m e^-1 (6 x cells)
     unsigned long long* mfix = nullptr;
     // multigrid per level: FP64 (FP64 mode) or FP32 (mixed mode)
     std::vector<double*> u64, f64, c64, r64;
@@ -84,9 +92,22 @@ struct Handle {
     std::vector<cudaEvent_t> cyc_ev;
     size_t cyc_ev_used = 0;
 
+    // control of the iteration (control.cu): device block, pinned copy, and
+    // the per-step records (Rk, alpha, relres, ncycles; harr: pinned copy)
+    Ctl* ctl = nullptr;
+    Ctl* hctl = nullptr;
+    CtlArrays arr{};
+    double* harr = nullptr;
+    double* replay_d = nullptr;  // replay_alpha on the device (or null)
+    LimiterParams lp{};
+
+    // params.device_loop: the whole solve as one graph with conditional nodes
+    cudaStream_t gst[4] = {nullptr, nullptr, nullptr, nullptr};  // capture streams
+    cudaGraphExec_t solve_exec = nullptr;
+    GraphCounts gn{};
+
     bool have_density = false, solved = false;
     double rho_sum = 0.0;
-    double last_mass = 0.0;
 };
 
 template <typename T>
@@ -118,6 +139,15 @@ void free_all(Handle* H) {
     H->cyc_ev.clear();
     if (H->cap) cudaStreamDestroy(H->cap);
     H->cap = nullptr;
+    if (H->solve_exec) cudaGraphExecDestroy(H->solve_exec);
+    H->solve_exec = nullptr;
+    for (int q = 0; q < 4; ++q) {
+        if (H->gst[q]) cudaStreamDestroy(H->gst[q]);
+        H->gst[q] = nullptr;
+    }
+    if (H->hctl) cudaFreeHost(H->hctl);
+    if (H->harr) cudaFreeHost(H->harr);
+    H->hctl = nullptr, H->harr = nullptr;
 }
 
 // Record one profiling event on the handle's stream (events are pooled; the
@@ -210,6 +240,8 @@ int check_params(const recon_params* p) {
     if (!(p->alpha_min > 0.0 && p->alpha_min <= 1.0)) return fail(RECON_E_INVALID, "need 0 < alpha_min <= 1");
     if (!(p->lambda_floor >= 0.0 && p->lambda_floor < 1.0)) return fail(RECON_E_INVALID, "need 0 <= lambda_floor < 1");
     if (p->inner_vcycles < 1 || p->inner_vcycles > 8) return fail(RECON_E_INVALID, "need 1 <= inner_vcycles <= 8");
+    if (p->density_update != 0 && p->density_update != 1) return fail(RECON_E_INVALID, "density_update must be 0 or 1");
+    if (p->device_loop != 0 && p->device_loop != 1) return fail(RECON_E_INVALID, "device_loop must be 0 or 1");
     return RECON_OK;
 }
 
@@ -254,7 +286,10 @@ void vcycle(Handle* H, MG<T>& g, int l, T* u, const T* f, bool zero_u) {
     T* cur = u;
     T* oth = g.r[l];
     smooth_sweeps<T>(H, l, H->p.nu1, &cur, &oth, f, g.c[l], zero_u);
-    launch_resid_restrict<T>(L, H->lv[l + 1], cur, f, g.c[l], g.f[l + 1], H->st);
+    bool streamed = false;
+    if constexpr (sizeof(T) == sizeof(float))
+        streamed = launch_resid_restrict_stream(L, H->lv[l + 1], cur, f, g.c[l], g.f[l + 1], H->st);
+    if (!streamed) launch_resid_restrict<T>(L, H->lv[l + 1], cur, f, g.c[l], g.f[l + 1], H->st);
     vcycle<T>(H, g, l + 1, g.u[l + 1], g.f[l + 1], true);
     launch_prolong_add<T>(L, H->lv[l + 1], g.u[l + 1], cur, H->st);
     smooth_sweeps<T>(H, l, H->p.nu2, &cur, &oth, f, g.c[l], false);
@@ -264,36 +299,149 @@ void vcycle(Handle* H, MG<T>& g, int l, T* u, const T* f, bool zero_u) {
 
 template <typename T>
 void build_hierarchy(Handle* H, std::vector<T*>& c) {
-    launch_faces64(H->lv[0], H->a64, H->F64, H->st);
-    if constexpr (sizeof(T) == sizeof(double)) {
-        if (H->inv64) launch_inv_diag64(H->lv[0], c[0], H->inv64, H->st);
-    }
+    launch_faces64(H->lv[0], H->a64, H->F64, H->D64, H->inv64, H->st);
     for (size_t l = 0; l + 1 < H->lv.size(); ++l)
         launch_restrict<T>(H->lv[l], H->lv[l + 1], c[l], c[l + 1], H->st);
     launch_coarse_invert<T>(H->lv.back(), c.back(), H->minv, H->st);
 }
 
-// One multigrid iteration after the first residual: the V-cycle (FP64 on
-// phidot, or FP32 on the correction e followed by phidot += e), then the FP64
-// residual of L phidot = s (in mixed mode also handed to the next V-cycle as
-// its FP32 right-hand side), its squared norm, and the scalar readback.
-void cycle_body(Handle* H) {
+// Mass per current curvilinear cell (tracer CIC deposit, or the carried m
+// of App. A's variant), the operator coefficient a = max(m, a_min) and sum m.
+int deposit_step(Handle* H) {
+    if (H->p.density_update == 1) {
+        // the carried mass per cell: only the coefficient and the mass sum
+        launch_coef_from_m(H->cells, H->m, H->p.a_min, H->a64, H->mixed ? H->c32[0] : nullptr,
+                           H->part[0], H->st);
+        finish_reduce(H->part[0], 0, H->scal, SC_SUM_M, H->st);
+        return RECON_OK;
+    }
+    const double scale = fixed_scale((double)H->cells);
+    launch_deposit_tracers(H->d, H->ox, H->oy, H->oz, H->w, scale, H->mfix, H->st);
+    launch_mass_coef(H->cells, H->mfix, 1.0 / scale, H->p.a_min, H->m, H->a64,
+                     H->mixed ? H->c32[0] : nullptr, H->part[0], H->st);
+    finish_reduce(H->part[0], 0, H->scal, SC_SUM_M, H->st);
+    return RECON_OK;
+}
+
+// ------------------------------------------------------------ the iteration
+//
+// One solve is a sequence of segments, each a fixed list of kernel launches
+// ending in a control kernel (control.cu) that takes the segment's decision:
+//   init;  while (go_step) { step head [R_k test];  if (go_cont) {
+//       multigrid head;  while (go_mg) multigrid iteration;
+//       step tail [alpha];  if (go_adv) advance [k += 1] } }
+//   if (go_fin) final deposit.
+// The host-driven loop launches the segments and reads the control block
+// back after each decision; with device_loop the same segments are recorded
+// once into a CUDA graph whose conditional nodes the control kernels set.
+
+// Step head: deposit on the deformed mesh, geometry and limited source
+// t = Sigma + C + E, s = S t - mean (Eq. elliptic of App. A), R_k test.
+void step_head(Handle* H, const CtlHandles& h) {
+    const recon_params& p = H->p;
+    deposit_step(H);
+    SourceParams sp{p.xi_m, p.v_m, p.climiter};
+    launch_geometry_source(H->d, sp, H->phi, H->m, H->t, H->e6, H->part[0], H->part[1], H->st);
+    finish_reduce(H->part[0], 0, H->scal, SC_SUM_T, H->st);
+    finish_reduce(H->part[1], 1, H->scal, SC_MIN_DET, H->st);
+    launch_smooth_S(H->d, p.s_side, H->t, H->scal + SC_SUM_T, H->s, nullptr, H->v3, nullptr,
+                    H->part[2], H->st);
+    finish_reduce(H->part[2], 0, H->scal, SC_SUM_S2, H->st);
+    launch_ctl_step_begin(H->ctl, H->scal, H->arr, (double)H->cells, p.tol_out, h, H->st);
+}
+
+// Multigrid head: coefficient hierarchy, phidot = 0 and (mixed) the first
+// FP64 defect handed to the FP32 V-cycle.
+void mg_head(Handle* H, const CtlHandles& h) {
+    if (H->mixed) build_hierarchy<float>(H, H->c32);
+    else build_hierarchy<double>(H, H->c64);
+    cudaMemsetAsync(H->phidot, 0, sizeof(double) * H->cells, H->st);
+    if (H->mixed) {
+        launch_residual64_to32(H->lv[0], H->phidot, H->s, H->F64, H->D64, H->f32[0], H->part[0], H->st);
+        finish_reduce(H->part[0], 0, H->scal, SC_RES2, H->st);
+    }
+    launch_ctl_mg_begin(H->ctl, H->scal, H->arr, H->mixed ? 1 : 0, H->p.tol_in, H->p.max_vcycles,
+                        h, H->st);
+}
+
+// One multigrid iteration: the V-cycle (FP64 on phidot, or inner_vcycles FP32
+// V-cycles on the correction e followed by phidot += e), then the FP64
+// residual of L phidot = s (in mixed mode also the next FP32 right-hand side)
+// and its squared norm, and the stopping test.
+void mg_iter(Handle* H, const CtlHandles& h) {
     const Level& L0 = H->lv[0];
     if (!H->mixed) {
         MG<double> g{H->u64, H->f64, H->c64, H->r64};
         vcycle<double>(H, g, 0, H->phidot, H->s, false);
-        launch_residual_norm64(L0, H->phidot, H->s, H->F64, H->part[0], H->st);
+        launch_residual_norm64(L0, H->phidot, H->s, H->F64, H->D64, H->part[0], H->st);
     } else {
         MG<float> g{H->u32, H->f32, H->c32, H->r32};
         for (int v = 0; v < H->p.inner_vcycles; ++v)
             vcycle<float>(H, g, 0, H->u32[0], H->f32[0], v == 0);
         launch_correct(H->cells, H->phidot, H->u32[0], H->st);
-        launch_residual64_to32(L0, H->phidot, H->s, H->F64, H->f32[0], H->part[0], H->st);
+        launch_residual64_to32(L0, H->phidot, H->s, H->F64, H->D64, H->f32[0], H->part[0], H->st);
     }
     finish_reduce(H->part[0], 0, H->scal, SC_RES2, H->st);
-    cudaMemcpyAsync(H->hscal, H->scal, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, H->st);
+    launch_ctl_mg_check(H->ctl, H->scal, H->arr, H->mixed ? H->p.inner_vcycles : 1, H->p.tol_in,
+                        H->p.max_vcycles, h, H->st);
 }
 
+// Step tail: dphi = S phidot (mean removed in the advance), the limiter and
+// the choice of alpha.
+void step_tail(Handle* H, const CtlHandles& h) {
+    const recon_params& p = H->p;
+    launch_smooth_S(H->d, p.s_side, H->phidot, nullptr, H->dphi, H->dphi32, H->v3, H->part[0],
+                    nullptr, H->st);
+    finish_reduce(H->part[0], 0, H->scal, SC_SUM_DPHI, H->st);
+    if (!H->replay_d) {
+        launch_limiter(H->d, H->lp, H->e6, H->dphi, H->phi32, H->dphi32, H->part[1], H->part[2],
+                       H->st);
+        finish_reduce(H->part[1], 2, H->scal, SC_MAX_K, H->st);
+        finish_reduce(H->part[2], 2, H->scal, SC_MAX_G, H->st);
+    }
+    launch_ctl_select_alpha(H->ctl, H->scal, H->arr, H->replay_d, H->lp.kmax, p.d_max, p.alpha_min,
+                            h, H->st);
+}
+
+// Advance by the chosen alpha: tracers and phi (or, App. A's variant, the
+// mass per cell and phi), then k += 1.
+void advance(Handle* H, const CtlHandles& h) {
+    const int n = H->cells;
+    const double* alpha = H->scal + SC_ALPHA;
+    if (H->p.density_update == 1) {
+        launch_mass_literal(H->d, H->e6, H->dphi, alpha, H->m, H->v3m, H->st);
+        launch_phi_advance(n, alpha, H->dphi, H->scal + SC_SUM_DPHI, H->phi, H->phi32, H->st);
+    } else {
+        launch_node_velocity(H->d, H->e6, H->dphi, H->v3, H->v3 + n, H->v3 + 2 * (size_t)n, H->st);
+        launch_advance(H->d, H->v3, H->v3 + n, H->v3 + 2 * (size_t)n, alpha, H->dphi,
+                       H->scal + SC_SUM_DPHI, H->ox, H->oy, H->oz, H->phi, H->phi32, H->st);
+    }
+    launch_ctl_step_end(H->ctl, H->p.k_max, h, H->st);
+}
+
+// init: tracer c = node c with mass rho_c / rho_bar, phi = 0
+void solve_init(Handle* H) {
+    launch_ctl_init(H->ctl, H->st);
+    launch_init_tracers(H->cells, H->rho, H->scal + SC_SUM_RHO, H->w, H->ox, H->oy, H->oz, H->phi,
+                        H->phi32, H->st);
+    if (H->p.density_update == 1)  // App. A: the mass per cell starts as rho / rho_bar
+        cudaMemcpyAsync(H->m, H->w, sizeof(double) * H->cells, cudaMemcpyDeviceToDevice, H->st);
+}
+
+void final_body(Handle* H) {
+    deposit_step(H);
+    launch_ctl_final_mass(H->ctl, H->scal, H->st);
+}
+
+int read_ctl(Handle* H) {
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(H->hctl, H->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, H->st));
+    CK(cudaStreamSynchronize(H->st));
+    return RECON_OK;
+}
+
+// The multigrid iteration with the control block's readback, recorded once as
+// a CUDA graph on a private stream and replayed on the handle's stream.
 int record_cycle_graph(Handle* H) {
     if (!H->cap) CK(cudaStreamCreateWithFlags(&H->cap, cudaStreamNonBlocking));
     cudaStream_t user = H->st;
@@ -302,7 +450,8 @@ int record_cycle_graph(Handle* H) {
     CK(cudaStreamBeginCapture(H->cap, cudaStreamCaptureModeRelaxed));
     H->st = H->cap;
     H->capturing = true;
-    cycle_body(H);
+    mg_iter(H, CtlHandles{});
+    cudaMemcpyAsync(H->hctl, H->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, H->st);
     H->capturing = false;
     H->st = user;
     cudaGraph_t g = nullptr;
@@ -340,145 +489,278 @@ int run_cycle(Handle* H) {
     return RECON_OK;
 }
 
-// Solve L(a) phidot = s to ||s - L phidot|| <= tol_in ||s||.
-int mg_solve(Handle* H, double snorm2, int* ncyc, double* relres) {
-    *ncyc = 0;
-    *relres = 0.0;
-    CK(cudaMemsetAsync(H->phidot, 0, sizeof(double) * H->cells, H->st));
-    if (!(snorm2 > 0.0)) return RECON_OK;
-    double rel = 1.0;
-    if (H->mixed) {
-        // first FP64 defect r = s (phidot = 0), handed to the FP32 V-cycle
-        launch_residual64_to32(H->lv[0], H->phidot, H->s, H->F64, H->f32[0], H->part[0], H->st);
-        finish_reduce(H->part[0], 0, H->scal, SC_RES2, H->st);
-        int rc = sync_scalars(H);
+// The host-driven loop: each decision is read back from the control block.
+int solve_host(Handle* H) {
+    const CtlHandles none{};
+    solve_init(H);
+    for (int k = 0; k < H->p.k_max; ++k) {
+        step_head(H, none);
+        int rc = read_ctl(H);
         if (rc) return rc;
-        rel = std::sqrt(H->hscal[SC_RES2] / snorm2);
+        if (!H->hctl->go_cont) break;
+        mg_head(H, none);
+        if ((rc = read_ctl(H))) return rc;
+        while (H->hctl->go_mg)
+            if ((rc = run_cycle(H))) return rc;
+        step_tail(H, none);
+        if ((rc = read_ctl(H))) return rc;
+        if (!H->hctl->go_adv) break;
+        advance(H, none);
     }
-    int cyc = 0;
-    const int per_launch = H->mixed ? H->p.inner_vcycles : 1;
-    while (cyc < H->p.max_vcycles && !(H->mixed && rel <= H->p.tol_in)) {
-        int rc = run_cycle(H);
+    if (H->p.density_update == 0) {  // the carried m of App. A's variant is current
+        launch_ctl_final(H->ctl, 1, none, H->st);
+        int rc = read_ctl(H);
         if (rc) return rc;
-        cyc += per_launch;
-        rel = std::sqrt(H->hscal[SC_RES2] / snorm2);
-        if (rel <= H->p.tol_in) break;
+        if (H->hctl->go_fin) final_body(H);
     }
-    *ncyc = cyc;
-    *relres = rel;
     return RECON_OK;
 }
 
-int deposit_step(Handle* H) {
-    const double scale = fixed_scale((double)H->cells);
-    launch_deposit_tracers(H->d, H->ox, H->oy, H->oz, H->w, scale, H->mfix, H->st);
-    launch_mass_coef(H->cells, H->mfix, 1.0 / scale, H->p.a_min, H->m, H->a64,
-                     H->mixed ? H->c32[0] : nullptr, H->part[0], H->st);
-    finish_reduce(H->part[0], 0, H->scal, SC_SUM_M, H->st);
+// ---- the solve as one CUDA graph with conditional nodes
+
+// Adds a conditional node of the given type after everything captured so far
+// on stream s (which is capturing into some graph) and returns its body.
+int add_conditional(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                    cudaGraph_t* body) {
+    cudaStreamCaptureStatus cs;
+    unsigned long long id = 0;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* edges = nullptr;
+    size_t nd = 0;
+    CK(cudaStreamGetCaptureInfo(s, &cs, &id, &g, &deps, &edges, &nd));
+    if (cs != cudaStreamCaptureStatusActive) return fail(RECON_E_CUDA, "stream is not capturing");
+    cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+    np.conditional.handle = h;
+    np.conditional.type = type;
+    np.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    CK(cudaGraphAddNode(&node, g, deps, edges, nd, &np));
+    CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    *body = np.conditional.phGraph_out[0];
     return RECON_OK;
 }
+
+// A conditional handle on the graph stream s is capturing into, reset to
+// def at every launch of the graph.
+int new_handle(cudaStream_t s, unsigned def, cudaGraphConditionalHandle* h) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+    CK(cudaGraphConditionalHandleCreate(h, g, def, cudaGraphCondAssignDefault));
+    return RECON_OK;
+}
+
+// Records the segments into body graph g on stream s; returns the kernels
+// recorded (the launch counter is restored).
+template <typename F>
+int capture_into(Handle* H, cudaStream_t s, cudaGraph_t g, long long* kernels, F&& segment) {
+    CK(cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    cudaStream_t prev = H->st;
+    H->st = s;
+    const long long c0 = launch_counter().load();
+    int rc = segment();
+    const long long kk = launch_counter().load() - c0;
+    launch_counter() -= kk;
+    if (kernels) *kernels += kk;
+    H->st = prev;
+    cudaGraph_t out = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &out);
+    if (rc) return rc;
+    if (e != cudaSuccess) return fail(RECON_E_CUDA, "solve graph capture failed: %s", cudaGetErrorString(e));
+    return RECON_OK;
+}
+
+int build_solve_graph(Handle* H) {
+    for (int q = 0; q < 4; ++q)
+        if (!H->gst[q]) CK(cudaStreamCreateWithFlags(&H->gst[q], cudaStreamNonBlocking));
+    cudaGraph_t top = nullptr;
+    CK(cudaGraphCreate(&top, 0));
+    GraphCounts& n = H->gn;
+    n = GraphCounts{};
+    CtlHandles h{};
+    h.active = 1;
+    H->capturing = true;
+    int rc = capture_into(H, H->gst[0], top, &n.init, [&]() -> int {
+        solve_init(H);
+        if (H->p.k_max > 0) {
+            int r = new_handle(H->gst[0], 1, &h.step);
+            if (r) return r;
+            cudaGraph_t b_step = nullptr;
+            if ((r = add_conditional(H->gst[0], h.step, cudaGraphCondTypeWhile, &b_step))) return r;
+            r = capture_into(H, H->gst[1], b_step, &n.step, [&]() -> int {
+                int r1 = new_handle(H->gst[1], 0, &h.cont);
+                if (r1) return r1;
+                step_head(H, h);
+                cudaGraph_t b_cont = nullptr;
+                if ((r1 = add_conditional(H->gst[1], h.cont, cudaGraphCondTypeIf, &b_cont))) return r1;
+                return capture_into(H, H->gst[2], b_cont, &n.cont, [&]() -> int {
+                    int r2 = new_handle(H->gst[2], 0, &h.mg);
+                    if (!r2) r2 = new_handle(H->gst[2], 0, &h.adv);
+                    if (r2) return r2;
+                    mg_head(H, h);
+                    cudaGraph_t b_mg = nullptr, b_adv = nullptr;
+                    if ((r2 = add_conditional(H->gst[2], h.mg, cudaGraphCondTypeWhile, &b_mg))) return r2;
+                    r2 = capture_into(H, H->gst[3], b_mg, &n.mg, [&]() -> int {
+                        mg_iter(H, h);
+                        return RECON_OK;
+                    });
+                    if (r2) return r2;
+                    step_tail(H, h);
+                    if ((r2 = add_conditional(H->gst[2], h.adv, cudaGraphCondTypeIf, &b_adv))) return r2;
+                    return capture_into(H, H->gst[3], b_adv, &n.adv, [&]() -> int {
+                        advance(H, h);
+                        return RECON_OK;
+                    });
+                });
+            });
+            if (r) return r;
+        }
+        if (H->p.density_update == 0) {
+            int r = new_handle(H->gst[0], 0, &h.fin);
+            if (r) return r;
+            launch_ctl_final(H->ctl, 1, h, H->st);
+            cudaGraph_t b_fin = nullptr;
+            if ((r = add_conditional(H->gst[0], h.fin, cudaGraphCondTypeIf, &b_fin))) return r;
+            return capture_into(H, H->gst[1], b_fin, &n.fin, [&]() -> int {
+                final_body(H);
+                return RECON_OK;
+            });
+        }
+        return RECON_OK;
+    });
+    H->capturing = false;
+    if (rc) {
+        cudaGraphDestroy(top);
+        cudaGetLastError();
+        return rc;
+    }
+    cudaError_t e = cudaGraphInstantiate(&H->solve_exec, top, 0);
+    cudaGraphDestroy(top);
+    if (e != cudaSuccess) {
+        H->solve_exec = nullptr;
+        cudaGetLastError();
+        return fail(RECON_E_CUDA, "solve graph instantiation failed: %s", cudaGetErrorString(e));
+    }
+    return RECON_OK;
+}
+
+// Kernels of the end-of-solve statistics (geometry, delta_r, 3 reductions).
+constexpr int kStatsKernels = 5;
+
+// Launches the whole solve (graph mode) and, with stats, the end-of-solve
+// statistics and the readback of the control block and the per-step
+// records; nothing waits for the device.
+int solve_launch(Handle* H, bool want_stats) {
+    if (!H->solve_exec) {
+        int rc = build_solve_graph(H);
+        if (rc) return rc;
+    }
+    CK(cudaEventRecord(H->ev0, H->st));
+    CK(cudaGraphLaunch(H->solve_exec, H->st));
+    CK(cudaEventRecord(H->ev1, H->st));
+    if (want_stats) {
+        launch_geometry_out(H->d, H->phi, nullptr, nullptr, H->part[0], H->part[1], H->st);
+        finish_reduce(H->part[0], 1, H->scal, SC_MIN_DET, H->st);
+        finish_reduce(H->part[1], 1, H->scal, SC_MIN_LAM, H->st);
+        launch_delta_r(H->d, H->phi, H->t, H->part[2], H->st);
+        finish_reduce(H->part[2], 2, H->scal, SC_MAX_DR, H->st);
+        CK(cudaMemcpyAsync(H->hscal, H->scal, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, H->st));
+    }
+    CK(cudaMemcpyAsync(H->hctl, H->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, H->st));
+    const size_t km = (size_t)std::max(H->p.k_max, 1);
+    CK(cudaMemcpyAsync(H->harr, H->arr.Rk, 4 * km * sizeof(double), cudaMemcpyDeviceToHost, H->st));
+    return RECON_OK;
+}
+
+// Fills the record from the control block (after the solve has finished).
+void fill_stats(Handle* H, recon_stats* stats, float ms, long long launches, bool stats_kernels) {
+    const Ctl& c = *H->hctl;
+    stats->status = c.status;
+    stats->steps = c.k;
+    stats->vcycles = c.vtot;
+    stats->R0 = c.R0;
+    stats->R = c.R;
+    stats->ms = ms;
+    stats->mass_error = std::fabs(c.last_mass - (double)H->cells) / (double)H->cells;
+    stats->launches = launches;
+    const size_t km = (size_t)std::max(H->p.k_max, 1);
+    const double* Rk = H->harr;
+    const double* al = H->harr + km;
+    const double* rr = H->harr + 2 * km;
+    const int* nc = (const int*)(H->harr + 3 * km);
+    for (int q = 0; q < c.n_step; ++q)
+        if (stats->Rk) stats->Rk[q] = Rk[q];
+    for (int q = 0; q < c.n_adv; ++q) {
+        if (stats->alpha) stats->alpha[q] = al[q];
+        if (stats->ncycles) stats->ncycles[q] = nc[q];
+        if (stats->relres) stats->relres[q] = rr[q];
+    }
+    if (stats_kernels) {
+        stats->min_det = H->hscal[SC_MIN_DET];
+        stats->min_lambda0 = H->hscal[SC_MIN_LAM];
+        stats->max_delta_r = H->hscal[SC_MAX_DR];
+    }
+}
+
+// Kernels one graph-mode solve launched, from the body counts of the graph
+// and the control block's execution counters.
+long long graph_launches(const Handle* H) {
+    const Ctl& c = *H->hctl;
+    const GraphCounts& n = H->gn;
+    return n.init + c.n_step * n.step + c.n_cont * n.cont + (long long)c.n_mg * n.mg +
+           c.n_adv * n.adv + c.n_fin * n.fin;
+}
+
+int solve_finish(Handle* H, recon_stats* stats) {
+    CK(cudaStreamSynchronize(H->st));
+    // the statistics kernels after the graph were counted at their launch
+    const long long kk = graph_launches(H);
+    launch_counter() += kk;
+    H->solved = true;
+    if (stats) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, H->ev0, H->ev1);
+        fill_stats(H, stats, ms, kk + kStatsKernels, true);
+        stats->smooth_ms = 0.0;
+        stats->smooth_sweeps = 0;
+        stats->smooth_bytes = 4.0 * (H->mixed ? sizeof(float) : sizeof(double)) * (double)H->cells;
+    }
+    return H->hctl->status;
+}
+
+bool use_graph(const Handle* H) { return H->p.device_loop && !H->p.profile; }
 
 int solve(Handle* H, recon_stats* stats) {
-    const recon_params& p = H->p;
-    const int n = H->cells;
+    if (use_graph(H)) {
+        int rc = solve_launch(H, stats != nullptr);
+        if (rc) return rc;
+        return solve_finish(H, stats);
+    }
     const long long launches0 = launch_counter().load();
     H->prof_used = 0;
     H->prof_sweeps = 0;
     H->prof_ms = 0.0;
     CK(cudaEventRecord(H->ev0, H->st));
-    // init: tracer c = node c with mass rho_c / rho_bar, phi = 0
-    const double rho_bar = H->rho_sum / (double)n;
-    launch_init_tracers(n, H->rho, 1.0 / rho_bar, H->w, H->ox, H->oy, H->oz, H->phi, H->phi32,
-                        H->st);
-
-    SourceParams sp{p.xi_m, p.v_m, p.climiter};
-    int kmax = 0;
-    while (kmax < 1100 && std::ldexp(1.0, -(kmax + 1)) >= p.alpha_min) ++kmax;
-    LimiterParams lp{p.lambda_floor, kmax};
-
-    int status = RECON_NOT_CONVERGED, k = 0, vtot = 0;
-    double R0 = 0.0, R = 0.0;
-    bool need_final_deposit = true;
-    for (k = 0; k < p.k_max; ++k) {
-        deposit_step(H);
-        launch_geometry_source(H->d, sp, H->phi, H->m, H->t, H->e6, H->part[0], H->part[1], H->st);
-        finish_reduce(H->part[0], 0, H->scal, SC_SUM_T, H->st);
-        finish_reduce(H->part[1], 1, H->scal, SC_MIN_DET, H->st);
-        launch_smooth_S(H->d, p.s_side, H->t, H->scal + SC_SUM_T, H->s, nullptr, H->v3, nullptr,
-                        H->part[2], H->st);
-        finish_reduce(H->part[2], 0, H->scal, SC_SUM_S2, H->st);
-        int rc = sync_scalars(H);
-        if (rc) return rc;
-        const double s2 = H->hscal[SC_SUM_S2];
-        R = std::sqrt(s2 / (double)n);
-        if (k == 0) R0 = R;
-        H->last_mass = H->hscal[SC_SUM_M];
-        if (stats && stats->Rk) stats->Rk[k] = R;
-        if (R <= p.tol_out) {
-            status = RECON_OK;
-            need_final_deposit = false;
-            break;
-        }
-        if (H->mixed) build_hierarchy<float>(H, H->c32);
-        else build_hierarchy<double>(H, H->c64);
-        int ncyc = 0;
-        double rel = 0.0;
-        rc = mg_solve(H, s2, &ncyc, &rel);
-        if (rc) return rc;
-        vtot += ncyc;
-        // dphi = S phidot (its mean is removed in the advance)
-        launch_smooth_S(H->d, p.s_side, H->phidot, nullptr, H->dphi, H->dphi32, H->v3, H->part[0],
-                        nullptr, H->st);
-        finish_reduce(H->part[0], 0, H->scal, SC_SUM_DPHI, H->st);
-        double alpha;
-        if (!H->replay.empty()) {
-            alpha = H->replay[k];
-        } else {
-            launch_limiter(H->d, lp, H->e6, H->dphi, H->phi32, H->dphi32, H->part[1], H->part[2],
-                           H->st);
-            finish_reduce(H->part[1], 2, H->scal, SC_MAX_K, H->st);
-            finish_reduce(H->part[2], 2, H->scal, SC_MAX_G, H->st);
-            rc = sync_scalars(H);
-            if (rc) return rc;
-            const int kpd = (int)H->hscal[SC_MAX_K];
-            const double gmax = H->hscal[SC_MAX_G];
-            alpha = kpd > kmax ? 0.0 : std::ldexp(1.0, -kpd);
-            while (alpha * gmax > p.d_max && alpha >= p.alpha_min) alpha *= 0.5;
-            if (alpha < p.alpha_min) {
-                // no admissible step: stop with the current (valid) map
-                status = RECON_STALLED;
-                break;
-            }
-        }
-        launch_node_velocity(H->d, H->e6, H->dphi, H->v3, H->v3 + n, H->v3 + 2 * (size_t)n, H->st);
-        launch_advance(H->d, H->v3, H->v3 + n, H->v3 + 2 * (size_t)n, alpha, H->dphi,
-                       H->scal + SC_SUM_DPHI, H->ox, H->oy, H->oz, H->phi, H->phi32, H->st);
-        if (stats) {
-            if (stats->alpha) stats->alpha[k] = alpha;
-            if (stats->ncycles) stats->ncycles[k] = ncyc;
-            if (stats->relres) stats->relres[k] = rel;
-        }
-    }
-    if (need_final_deposit) {
-        deposit_step(H);
-        int rc = sync_scalars(H);
-        if (rc) return rc;
-        H->last_mass = H->hscal[SC_SUM_M];
-    }
+    int rc = solve_host(H);
+    if (rc) return rc;
     CK(cudaEventRecord(H->ev1, H->st));
     CK(cudaEventSynchronize(H->ev1));
     H->solved = true;
     if (stats) {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, H->ev0, H->ev1);
-        stats->status = status;
-        stats->steps = k;
-        stats->vcycles = vtot;
-        stats->R0 = R0;
-        stats->R = R;
-        stats->ms = ms;
-        stats->mass_error = std::fabs(H->last_mass - (double)n) / (double)n;
-        stats->launches = launch_counter().load() - launches0;
+        launch_geometry_out(H->d, H->phi, nullptr, nullptr, H->part[0], H->part[1], H->st);
+        finish_reduce(H->part[0], 1, H->scal, SC_MIN_DET, H->st);
+        finish_reduce(H->part[1], 1, H->scal, SC_MIN_LAM, H->st);
+        launch_delta_r(H->d, H->phi, H->t, H->part[2], H->st);
+        finish_reduce(H->part[2], 2, H->scal, SC_MAX_DR, H->st);
+        CK(cudaMemcpyAsync(H->hscal, H->scal, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, H->st));
+        CK(cudaMemcpyAsync(H->hctl, H->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, H->st));
+        const size_t km = (size_t)std::max(H->p.k_max, 1);
+        CK(cudaMemcpyAsync(H->harr, H->arr.Rk, 4 * km * sizeof(double), cudaMemcpyDeviceToHost, H->st));
+        CK(cudaStreamSynchronize(H->st));
+        fill_stats(H, stats, ms, launch_counter().load() - launches0, true);
         double sm = H->prof_ms;
         for (size_t q = 0; q + 1 < H->prof_used; q += 2) {
             float e = 0.f;
@@ -488,19 +770,9 @@ int solve(Handle* H, recon_stats* stats) {
         stats->smooth_ms = sm;
         stats->smooth_sweeps = H->prof_sweeps;
         // one sweep reads u, a, f and writes u at the finest level
-        stats->smooth_bytes = 4.0 * (H->mixed ? sizeof(float) : sizeof(double)) * (double)n;
-        launch_geometry_out(H->d, H->phi, nullptr, nullptr, H->part[0], H->part[1], H->st);
-        finish_reduce(H->part[0], 1, H->scal, SC_MIN_DET, H->st);
-        finish_reduce(H->part[1], 1, H->scal, SC_MIN_LAM, H->st);
-        launch_delta_r(H->d, H->phi, H->t, H->part[2], H->st);
-        finish_reduce(H->part[2], 2, H->scal, SC_MAX_DR, H->st);
-        int rc = sync_scalars(H);
-        if (rc) return rc;
-        stats->min_det = H->hscal[SC_MIN_DET];
-        stats->min_lambda0 = H->hscal[SC_MIN_LAM];
-        stats->max_delta_r = H->hscal[SC_MAX_DR];
+        stats->smooth_bytes = 4.0 * (H->mixed ? sizeof(float) : sizeof(double)) * (double)H->cells;
     }
-    return status;
+    return H->hctl->status;
 }
 
 bool is_device_ptr(const void* p) {
@@ -546,6 +818,8 @@ int recon_default_params(recon_params* p, int n0, int n1, int n2) {
     p->replay_alpha = nullptr;
     p->profile = 0;
     p->inner_vcycles = 2;
+    p->density_update = 0;
+    p->device_loop = 1;
     return RECON_OK;
 }
 
@@ -598,8 +872,16 @@ int recon_create(void** out, const recon_params* p, void* cuda_stream) {
     AL(H->rho, n); AL(H->w, n); AL(H->ox, n); AL(H->oy, n); AL(H->oz, n);
     AL(H->phi, n); AL(H->m, n); AL(H->a64, n); AL(H->t, n); AL(H->s, n);
     AL(H->phidot, n); AL(H->dphi, n); AL(H->v3, 3 * n); AL(H->mfix, n); AL(H->e6, 6 * n);
-    AL(H->F64, 3 * n); AL(H->phi32, n); AL(H->dphi32, n);
+    AL(H->F64, 3 * n); AL(H->D64, n); AL(H->phi32, n); AL(H->dphi32, n);
+    if (p->density_update == 1) AL(H->v3m, 6 * n);
     AL(H->minv, 65 * 130); AL(H->scal, SC_COUNT);
+    const size_t km = (size_t)std::max(p->k_max, 1);
+    // the per-step records share one block (Rk | alpha | relres | ncycles) so
+    // that one copy brings them back
+    AL(H->ctl, 1); AL(H->arr.Rk, 4 * km);
+    H->arr.alpha = H->arr.Rk + km, H->arr.relres = H->arr.Rk + 2 * km;
+    H->arr.ncycles = (int*)(H->arr.Rk + 3 * km);
+    if (!H->replay.empty()) AL(H->replay_d, km);
     for (int q = 0; q < 4; ++q) AL(H->part[q], kRedBlocks);
     if (!H->mixed) {
         H->u64.assign(nl, nullptr), H->f64.assign(nl, nullptr), H->c64.assign(nl, nullptr),
@@ -635,13 +917,24 @@ int recon_create(void** out, const recon_params* p, void* cuda_stream) {
         }
     }
     if (cudaMallocHost((void**)&H->hscal, SC_COUNT * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost((void**)&H->hctl, sizeof(Ctl)) != cudaSuccess ||
+        cudaMallocHost((void**)&H->harr, 4 * km * sizeof(double)) != cudaSuccess ||
         cudaEventCreate(&H->ev0) != cudaSuccess || cudaEventCreate(&H->ev1) != cudaSuccess) {
         cudaGetLastError();
         free_all(H);
         delete H;
         return fail(RECON_E_OOM, "pinned host buffer or event creation failed");
     }
+    {
+        int kmax = 0;
+        while (kmax < 1100 && std::ldexp(1.0, -(kmax + 1)) >= p->alpha_min) ++kmax;
+        H->lp = LimiterParams{p->lambda_floor, kmax};
+    }
+    std::memset(H->hctl, 0, sizeof(Ctl));
     cudaError_t e = cudaMemsetAsync(H->mfix, 0, n * sizeof(unsigned long long), H->st);
+    if (e == cudaSuccess && H->replay_d)
+        e = cudaMemcpyAsync(H->replay_d, H->replay.data(), H->replay.size() * sizeof(double),
+                            cudaMemcpyHostToDevice, H->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(H->st);
     if (e != cudaSuccess) {
         free_all(H);
@@ -734,6 +1027,41 @@ int recon_solve(void* hp, recon_stats* stats) {
         if (stats) stats->status = rc;
     }
     return rc;
+}
+
+int recon_solve_batch(void* const* handles, int count, recon_stats* stats) {
+    g_err[0] = 0;
+    if (count < 0 || (count > 0 && !handles)) return fail(RECON_E_INVALID, "bad handle array");
+    for (int b = 0; b < count; ++b) {
+        Handle* H = (Handle*)handles[b];
+        if (!H) return fail(RECON_E_INVALID, "handle %d is NULL", b);
+        if (!H->have_density)
+            return fail(RECON_E_STATE, "handle %d: recon_deposit must succeed before recon_solve", b);
+        for (int c = 0; c < b; ++c)
+            if (handles[c] == handles[b]) return fail(RECON_E_INVALID, "handle %d appears twice", b);
+    }
+    // every graph-mode solve is launched before any is waited for; solves on
+    // distinct streams then run concurrently on the device
+    std::vector<int> rc(count, RECON_OK);
+    for (int b = 0; b < count; ++b) {
+        Handle* H = (Handle*)handles[b];
+        H->solved = false;
+        if (use_graph(H)) rc[b] = solve_launch(H, stats != nullptr);
+    }
+    int worst = RECON_OK;
+    for (int b = 0; b < count; ++b) {
+        Handle* H = (Handle*)handles[b];
+        recon_stats* st = stats ? stats + b : nullptr;
+        int r = rc[b];
+        if (r == RECON_OK) r = use_graph(H) ? solve_finish(H, st) : solve(H, st);
+        if (r < 0) {
+            cudaStreamSynchronize(H->st);
+            H->solved = false;
+            if (st) st->status = r;
+            if (worst >= 0) worst = r;
+        }
+    }
+    return worst;
 }
 
 int recon_field(void* hp, int which, void* dst, size_t dst_bytes) {

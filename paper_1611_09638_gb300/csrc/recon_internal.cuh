@@ -64,6 +64,7 @@ enum Scalar {
     SC_MAX_G,         // max |grad dphi|
     SC_MIN_LAM,       // min lambda0
     SC_MAX_DR,        // max delta_r
+    SC_ALPHA,         // step length of the current step
     SC_COUNT
 };
 
@@ -105,6 +106,12 @@ void launch_rbgs_sweep(const Level& L, T* u, const T* f, const T* a, cudaStream_
 // streaming pass (smoother.cu); u_old == nullptr means u_old = 0.  Returns k,
 // the sweeps done; 0 (nothing launched) when the level is not a multiple of
 // the kernel's tile or the precision does not use the streaming kernel.
+// Residual and full-weighting restriction of an FP32 level in one streaming
+// pass; returns 1, or 0 with nothing launched where the level does not fit
+// its tiles (then launch_resid_restrict does the work).
+int launch_resid_restrict_stream(const Level& fine, const Level& coarse, const float* u,
+                                 const float* f, const float* a, float* out, cudaStream_t st);
+
 template <typename T>
 int launch_rbgs_fused(const Level& L, const T* u_old, T* u_new, const T* f, const T* a,
                       int nsweeps, cudaStream_t st);
@@ -136,20 +143,20 @@ void launch_coarse_solve(const double* minv, const T* f, T* u, cudaStream_t st);
 template <typename T>
 bool launch_coarse_vcycle(const CoarseSet& cs, const T* f_top, T* u_top, const double* minv,
                           bool zero_u, cudaStream_t st);
-// Face sums F (3 x cells: a_c + a_{c+e_x}, ... e_y, ... e_z) of the finest
-// level, used by the FP64 residual and the FP64 sweeps there.
-void launch_faces64(const Level& L, const double* a, double* F, cudaStream_t st);
+// Finest FP64 level (unit spacing): face coefficients F (3 x cells:
+// A = (a_c + a_{c+e}) / 2 for the +x, +y, +z face of each node), the node
+// diagonal D = sum of its six A, and optionally inv_d = 1 / D.
+void launch_faces64(const Level& L, const double* a, double* F, double* D, double* inv_d,
+                    cudaStream_t st);
 // FP64 residual of level 0 in mixed mode: r32 = f - L u (FP64), plus sum r^2
 void launch_residual64_to32(const Level& L, const double* u, const double* f, const double* F,
-                            float* r32, double* partials, cudaStream_t st);
+                            const double* D, float* r32, double* partials, cudaStream_t st);
 // FP64 residual norm only: partials of (f - L u)^2
 void launch_residual_norm64(const Level& L, const double* u, const double* f, const double* F,
-                            double* partials, cudaStream_t st);
-// FP64 sweeps of a unit-spacing level: inv2 = 1 / sum_n (a_c + a_n) once per
-// coefficient, then u_c = (sum_n (a_c + a_n) u_n - 2 f_c) inv2_c per colour.
-void launch_inv_diag64(const Level& L, const double* a, double* inv2, cudaStream_t st);
+                            const double* D, double* partials, cudaStream_t st);
+// FP64 red-black sweep of the finest level: u_c = (sum_n A_n u_n - f_c) / D_c
 void launch_rbgs_sweep64_unit(const Level& L, double* u, const double* f, const double* F,
-                              const double* inv2, cudaStream_t st);
+                              const double* inv_d, cudaStream_t st);
 // u64 += e32
 void launch_correct(int cells, double* u, const float* e, cudaStream_t st);
 
@@ -162,7 +169,7 @@ void launch_deposit_particles(const Dims& d, int64_t np, const double* pos, cons
                               double inv_h, double scale, unsigned long long* mfix, cudaStream_t st);
 void launch_fix_to_double(int cells, unsigned long long* mfix, double inv_scale, double* out,
                           cudaStream_t st);
-void launch_init_tracers(int cells, const double* rho, double inv_rho_bar, double* w,
+void launch_init_tracers(int cells, const double* rho, const double* sum_rho, double* w,
                          double* ox, double* oy, double* oz, double* phi, float* phi32,
                          cudaStream_t st);
 void launch_deposit_tracers(const Dims& d, const double* ox, const double* oy, const double* oz,
@@ -190,8 +197,17 @@ void launch_node_velocity(const Dims& d, const double* e6, const double* dphi, d
 // Tracers move by -alpha V(xi) (CIC-interpolated); phi += alpha (dphi - mean),
 // mean = *sum_dphi / cells.
 void launch_advance(const Dims& d, const double* vx, const double* vy, const double* vz,
-                    double alpha, const double* dphi, const double* sum_dphi, double* ox,
+                    const double* alpha, const double* dphi, const double* sum_dphi, double* ox,
                     double* oy, double* oz, double* phi, float* phi32, cudaStream_t st);
+// App. A's linear density update: m += alpha d_mu(m (e^-1)^{mu nu} d_nu dphi)
+// (K6: 6 x cells scratch), the coefficient from a carried m, and phi's update
+// without tracers.
+void launch_mass_literal(const Dims& d, const double* e6, const double* dphi,
+                         const double* alpha, double* m, double* K6, cudaStream_t st);
+void launch_coef_from_m(int cells, const double* m, double a_min, double* a64, float* a32,
+                        double* partials, cudaStream_t st);
+void launch_phi_advance(int cells, const double* alpha, const double* dphi,
+                        const double* sum_dphi, double* phi, float* phi32, cudaStream_t st);
 // outputs
 void launch_delta_r(const Dims& d, const double* phi, double* out, double* part_max,
                     cudaStream_t st);
@@ -199,5 +215,48 @@ void launch_mesh_x(const Dims& d, const double* phi, double h, double* out, cuda
 void launch_geometry_out(const Dims& d, const double* phi, double* det, double* lam,
                          double* part_min_det, double* part_min_lam, cudaStream_t st);
 void launch_scale(int cells, const double* in, double s, double* out, cudaStream_t st);
+
+// ---- device-side control of the iteration (control.cu) -----------------
+// The control block of one solve: every decision of the iteration is taken by
+// a one-thread kernel and recorded here (the host-driven loop reads it back;
+// inside the solve graph the same kernels also set the conditional nodes).
+struct Ctl {
+    int k;              // steps advanced so far
+    int status;         // RECON_OK / RECON_NOT_CONVERGED / RECON_STALLED
+    int vtot, ncyc;     // V-cycles in total and in the current step's solve
+    int final_deposit;  // the last map still needs its deposit
+    int n_step, n_cont, n_mg, n_adv, n_fin;  // executions of each graph body
+    int go_cont, go_mg, go_adv, go_step, go_fin;
+    int pad;
+    double R0, R, s2, rel, alpha, last_mass;
+};
+
+// Per-step records on the device (k_max entries each).
+struct CtlArrays {
+    double* Rk;
+    double* alpha;
+    double* relres;
+    int* ncycles;
+};
+
+// Conditional nodes of the solve graph; active = 0 outside a graph.
+struct CtlHandles {
+    int active;
+    cudaGraphConditionalHandle step, cont, mg, adv, fin;
+};
+
+void launch_ctl_init(Ctl* c, cudaStream_t st);
+void launch_ctl_step_begin(Ctl* c, const double* scal, const CtlArrays& a, double ncells,
+                           double tol_out, const CtlHandles& h, cudaStream_t st);
+void launch_ctl_mg_begin(Ctl* c, const double* scal, const CtlArrays& a, int mixed, double tol_in,
+                         int max_vcycles, const CtlHandles& h, cudaStream_t st);
+void launch_ctl_mg_check(Ctl* c, const double* scal, const CtlArrays& a, int per_launch,
+                         double tol_in, int max_vcycles, const CtlHandles& h, cudaStream_t st);
+void launch_ctl_select_alpha(Ctl* c, double* scal, const CtlArrays& a, const double* replay,
+                             int kmax_exp, double d_max, double alpha_min, const CtlHandles& h,
+                             cudaStream_t st);
+void launch_ctl_step_end(Ctl* c, int k_max, const CtlHandles& h, cudaStream_t st);
+void launch_ctl_final(Ctl* c, int want, const CtlHandles& h, cudaStream_t st);
+void launch_ctl_final_mass(Ctl* c, const double* scal, cudaStream_t st);
 
 }  // namespace recon

@@ -1,203 +1,218 @@
-// smoother.cu -- NS full red-black Gauss-Seidel sweeps (red, then black,
-// NS times) of L u = f (App. A, Eq. elliptic with x ~ xi; the 7-point
+// smoother.cu -- one full red-black Gauss-Seidel sweep (red, then black) of
+// L u = f in FP32 (App. A, Eq. elliptic with x ~ xi; the 7-point
 // variable-coefficient operator with face coefficients (a + a_nbr)/2) in a
 // single pass over memory.
 //
-// Each block owns a TJ x TK tile of the (j, k) plane and streams planes along
-// i.  The 2 NS colour updates form a pipeline of stages: at iteration q, stage
-// s (colour s % 2, 0 = red) updates plane q - s on the tile grown by a ring of
-// 2 NS - 1 - s nodes in j and k.  Every stage reads only values that earlier
-// stages (or the initial load, for stage 0) have brought to the state the
-// sweep order prescribes, so the result equals NS in-place sweeps node for
-// node; the last stage's plane is written out.  u is read from u_old and
-// written to u_new (another buffer), so halos read by a block are never values
-// another block has already updated.  Shared memory holds rings of u and a
-// planes (tile + 2 NS-node ring; rows padded to 16-byte chunks) and of f
-// planes; plane q + 2 is fetched with 16-byte cp.async copies while plane q is
-// processed.  DRAM traffic for NS sweeps is one read
-// of u, a, f and one write of u.  With u_old == nullptr the sweeps start from
-// u = 0 and u is not read.
+// Each block owns a TJ x TK tile of the (j, k) plane and streams CI planes
+// along i.  At iteration q the red update of plane q runs on the tile plus a
+// one-node ring (it reads old black values on a two-node ring), then the black
+// update of plane q - 1 runs on the tile from those red values, and plane q - 1
+// of the tile is written out.  u is read from u_old and written to u_new
+// (another buffer), so halos read by a block are never values another block
+// has already updated: the result equals the in-place sweep node for node.
+// Shared memory holds rings of five u and a planes (tile + two-node ring in j,
+// four-node in k so that every row is whole 16-byte chunks) and three f
+// planes; plane q + 2 is fetched with 16-byte cp.async copies while planes q
+// and q - 1 are updated.  DRAM traffic is one read of u, a, f and one write
+// of u.  With u_old == nullptr the sweep starts from u = 0 and u is not read.
+//
+// The kernel is bound by instruction issue rather than DRAM, so every
+// shared-memory and global offset a thread uses is computed once per block:
+// the per-plane work is the cp.async issue, the stencil arithmetic and the
+// stores.
+#include "async_copy.cuh"
 #include "recon_internal.cuh"
 
 namespace recon {
 
 namespace {
 
-__device__ inline void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-__device__ inline void cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
+constexpr int TJ = 8, TK = 64, NT = 256;
+constexpr int H = 2;                   // rows of halo (stencil ring of the red stage + 1)
+constexpr int KO = 4;                  // columns of halo: one 16-byte chunk
+constexpr int RJ = TJ + 2 * H;         // 12 rows held per plane
+constexpr int RK = TK + 2 * KO;        // 72 columns held per plane
+constexpr int PL = RJ * RK;            // floats per plane
+constexpr int CH = RK / 4;             // 16-byte chunks per row
+constexpr int SU = 5, SF = 3;          // ring slots of u / a and of f
+constexpr int SMEM = (int)sizeof(float) * PL * (2 * SU + SF);
+constexpr int NUA = RJ * CH;           // chunks of one u (or a) plane: 216
+constexpr int NF = (TJ + 2) * CH;      // chunks of one f plane (rows of the red ring): 180
+constexpr int NR = (TJ + 2) * ((TK + 2) / 2);  // red nodes on tile + ring: 330
+constexpr int NB = TJ * (TK / 2);      // black nodes on the tile: 256
+constexpr int NO = TJ * TK;            // outputs per plane: 512
+static_assert(NUA <= NT && NF <= NT && NB == NT && NO == 2 * NT && NR <= 2 * NT, "tile");
+static_assert(TJ % 2 == 0 && RK % 2 == 0 && TK == 64, "row-pair colour mapping");
+static_assert(NR == 330 && (TJ + 2) * 32 == 320, "red task split");
 
-// Division of the smoother update: the fast approximate reciprocal in FP32
-// (a smoother needs no correctly rounded quotient), IEEE in FP64.
-__device__ inline float fast_div(float a, float b) { return __fdividef(a, b); }
-__device__ inline double fast_div(double a, double b) { return a / b; }
-
-template <typename T, int NS, int TJ, int TK>
-struct SweepShape {
-    static constexpr int H = 2 * NS;  // halo of the loaded planes (rows)
-    static constexpr int V = 16 / (int)sizeof(T);  // elements per 16-byte copy
-    static constexpr int KO = V;      // column halo, rounded up to one 16-byte chunk
-    static_assert(H <= KO, "column halo must cover the stencil halo");
-    static constexpr int RJ = TJ + 2 * H, RK = TK + 2 * KO, PL = RJ * RK;
-    static constexpr int CH = RK / V;  // 16-byte chunks per row
-    static constexpr int SU = 2 * NS + 3;  // u / a ring slots
-    static constexpr int SF = 2 * NS + 1;  // f ring slots
-    static constexpr int smem = (int)sizeof(T) * PL * (2 * SU + SF);
-};
-
-__device__ inline void cp_async16(void* smem, const void* gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
-}
-
-template <typename T, int NS, int TJ, int TK, int NT>
-__global__ void __launch_bounds__(NT) k_rbgs_stream(Dims d, T hx, T hy, T hz, int CI,
-                                                    const T* __restrict__ u_old,
-                                                    T* __restrict__ u_new,
-                                                    const T* __restrict__ f,
-                                                    const T* __restrict__ a) {
-    using S = SweepShape<T, NS, TJ, TK>;
-    constexpr int H = S::H, KO = S::KO, V = S::V, CH = S::CH, RK = S::RK, PL = S::PL;
-    constexpr int SU = S::SU, SF = S::SF;
-    constexpr int NST = 2 * NS;  // stages
-    extern __shared__ unsigned char smem_raw[];
-    T* su = reinterpret_cast<T*>(smem_raw);
-    T* sa = su + SU * PL;
-    T* sf = sa + SU * PL;
+__global__ void __launch_bounds__(NT) k_rbgs_stream(Dims d, float hx, float hy, float hz, int CI,
+                                                    const float* __restrict__ u_old,
+                                                    float* __restrict__ u_new,
+                                                    const float* __restrict__ f,
+                                                    const float* __restrict__ a) {
+    extern __shared__ float4 smem_f4[];
+    float* su = reinterpret_cast<float*>(smem_f4);
+    float* sa = su + SU * PL;
+    float* sf = sa + SU * PL;
+    const int t = threadIdx.x;
     const int k0 = blockIdx.x * TK, j0 = blockIdx.y * TJ, i0 = blockIdx.z * CI;
     const int iend = i0 + CI;
-    const int q0 = i0 - (NST - 1), q1 = iend - 1 + (NST - 1);
-    const int base = q0 - 1;  // first plane held
+    const int base = i0 - 2;  // first plane held
+    const int plane = d.n1 * d.n2;
 
-    auto su_of = [&](int q) { return su + ((q - base) % SU) * PL; };
-    auto sa_of = [&](int q) { return sa + ((q - base) % SU) * PL; };
-    auto sf_of = [&](int q) { return sf + ((q - base) % SF) * PL; };
-    // old u and a of plane q: rows j0-H .. j0+TJ+H-1, columns k0-KO ..
-    // k0+TK+KO-1, in 16-byte chunks (n2 is a multiple of the chunk, so a chunk
-    // never straddles the periodic seam)
+    // ---- offsets fixed for the whole block -------------------------------
+    // fetch: this thread's chunk of a u/a plane and of an f plane
+    int ua_s = -1, ua_g = 0, f_s = -1, f_g = 0;
+    if (t < NUA) {
+        const int r = t / CH, ch = t - r * CH;
+        ua_s = r * RK + ch * 4;
+        ua_g = (((j0 + r - H) & (d.n1 - 1)) << d.s2) + ((k0 - KO + ch * 4) & (d.n2 - 1));
+    }
+    if (t < NF) {
+        const int r = t / CH, ch = t - r * CH;
+        f_s = (r + 1) * RK + ch * 4;
+        f_g = (((j0 + r - 1) & (d.n1 - 1)) << d.s2) + ((k0 - KO + ch * 4) & (d.n2 - 1));
+    }
+    // Colour nodes are assigned so that each warp takes 16 nodes of a row and
+    // the 16 nodes below them in the next row: the colours alternate from row
+    // to row and RK is even, so the two half-warps read opposite bank parities
+    // and the stride-2 access is free of bank conflicts.
+    // Red tasks r = t and t + NT cover the 33 red nodes c = 0 .. 32 of each of
+    // the ring rows jj = -1 .. TJ: r < 320 takes c = 1 .. 32 by row pairs, and
+    // r = 320 .. 329 takes c = 0 of the ten rows.  Stored: smem offset of the
+    // node with zero parity shift and the row's parity (the shift is
+    // (q + j0 + jj + k0 - 1) & 1, i.e. the plane parity xor the row's).
+    int red_e[2], red_p[2];
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+        const int r = t + m * NT;
+        int jj = 0, c = -1;
+        if (r < 320) {
+            const int wt = r >> 5, lane = r & 31;
+            jj = 2 * (wt >> 1) + (lane >> 4) - 1;
+            c = 1 + 16 * (wt & 1) + (lane & 15);
+        } else if (r < NR) {
+            jj = r - 320 - 1;
+            c = 0;
+        }
+        if (c >= 0) {
+            red_e[m] = (jj + H) * RK + (2 * c - 1 + KO);
+            red_p[m] = (j0 + jj + k0 - 1) & 1;
+        } else {
+            red_e[m] = -1, red_p[m] = 0;
+        }
+    }
+    // black node t on the tile: 4 row pairs x 2 chunks of 16 of the 32 black
+    // nodes per row; shift (p + j0 + jj + k0 + 1) & 1
+    const int bw = t >> 5, blane = t & 31;
+    const int blk_row = 2 * (bw >> 1) + (blane >> 4), blk_c = 16 * (bw & 1) + (blane & 15);
+    const int blk_e = (blk_row + H) * RK + (2 * blk_c + KO);
+    const int blk_p = (j0 + blk_row + k0 + 1) & 1;
+    // outputs t and t + NT
+    int out_s[2], out_g[2];
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+        const int e = t + m * NT;
+        const int jj = e / TK, kk = e - jj * TK;
+        out_s[m] = (jj + H) * RK + (kk + KO);
+        out_g[m] = ((j0 + jj) << d.s2) + k0 + kk;
+    }
+
+    auto slot_u = [&](int q) { return ((q - base) % SU) * PL; };
+    auto slot_f = [&](int q) { return ((q - base) % SF) * PL; };
+    auto pbase = [&](int q) { return (q & (d.n0 - 1)) * plane; };
     auto fetch_ua = [&](int q) {
-        T* du = su_of(q);
-        T* da = sa_of(q);
-        for (int e = threadIdx.x; e < S::RJ * CH; e += NT) {
-            const int r = e / CH, ch = e - r * CH;
-            const int g = cell_index(d, q, j0 + r - H, k0 - KO + ch * V);
-            const int o = r * RK + ch * V;
-            if (u_old) cp_async16(du + o, u_old + g);
-            else *reinterpret_cast<float4*>(du + o) = make_float4(0.f, 0.f, 0.f, 0.f);
-            cp_async16(da + o, a + g);
+        if (ua_s >= 0) {
+            const int so = slot_u(q) + ua_s, g = pbase(q) + ua_g;
+            if (u_old) cp_async16(su + so, u_old + g);
+            else *reinterpret_cast<float4*>(su + so) = make_float4(0.f, 0.f, 0.f, 0.f);
+            cp_async16(sa + so, a + g);
         }
     };
-    // f of plane q on the rows of the widest stage region (tile + H - 1)
     auto fetch_f = [&](int q) {
-        constexpr int FJ = TJ + 2 * (H - 1);
-        T* df = sf_of(q);
-        for (int e = threadIdx.x; e < FJ * CH; e += NT) {
-            const int r = e / CH, ch = e - r * CH;
-            const int g = cell_index(d, q, j0 + r - (H - 1), k0 - KO + ch * V);
-            cp_async16(df + (r + 1) * RK + ch * V, f + g);
-        }
+        if (f_s >= 0) cp_async16(sf + slot_f(q) + f_s, f + pbase(q) + f_g);
+    };
+    // Gauss-Seidel value at smem offset e of the plane in slots (cu, mu, pu)
+    // of u and a (current, previous, next plane) and cf of f.
+    auto gs = [&](int cu, int mu, int pu, int cf, int e) -> float {
+        const float* ac = sa + cu;
+        const float c = ac[e];
+        const float apx = 0.5f * (c + sa[pu + e]) * hx, amx = 0.5f * (c + sa[mu + e]) * hx;
+        const float apy = 0.5f * (c + ac[e + RK]) * hy, amy = 0.5f * (c + ac[e - RK]) * hy;
+        const float apz = 0.5f * (c + ac[e + 1]) * hz, amz = 0.5f * (c + ac[e - 1]) * hz;
+        const float diag = (apx + amx) + (apy + amy) + (apz + amz);
+        const float* uc = su + cu;
+        const float off = (apx * su[pu + e] + amx * su[mu + e]) + (apy * uc[e + RK] + amy * uc[e - RK]) +
+                          (apz * uc[e + 1] + amz * uc[e - 1]);
+        return __fdividef(off - sf[cf + e], diag);
     };
 
-    const T half = T(0.5);
-    // Gauss-Seidel value at smem offset e of plane q from its six neighbours.
-    auto gs = [&](int q, int e) -> T {
-        const T* uc = su_of(q);
-        const T* um = su_of(q - 1);
-        const T* up = su_of(q + 1);
-        const T* ac = sa_of(q);
-        const T* am = sa_of(q - 1);
-        const T* ap = sa_of(q + 1);
-        const T c = ac[e];
-        const T apx = half * (c + ap[e]) * hx, amx = half * (c + am[e]) * hx;
-        const T apy = half * (c + ac[e + RK]) * hy, amy = half * (c + ac[e - RK]) * hy;
-        const T apz = half * (c + ac[e + 1]) * hz, amz = half * (c + ac[e - 1]) * hz;
-        const T diag = (apx + amx) + (apy + amy) + (apz + amz);
-        const T off = (apx * up[e] + amx * um[e]) + (apy * uc[e + RK] + amy * uc[e - RK]) +
-                      (apz * uc[e + 1] + amz * uc[e - 1]);
-        return fast_div(off - sf_of(q)[e], diag);
-    };
-
-    // prologue: u, a of planes q0-1 .. q0+1; f of plane q0
-    fetch_ua(q0 - 1);
-    fetch_ua(q0);
-    fetch_ua(q0 + 1);
-    fetch_f(q0);
+    // prologue: u, a of planes i0-2 .. i0; f of plane i0-1
+    fetch_ua(i0 - 2);
+    fetch_ua(i0 - 1);
+    fetch_ua(i0);
+    fetch_f(i0 - 1);
     cp_commit();
     cp_wait_all();
     __syncthreads();
 
-    for (int q = q0; q <= q1; ++q) {
-        if (q + 2 <= q1 + 1) fetch_ua(q + 2);
-        if (q + 1 <= q1) fetch_f(q + 1);
+    for (int q = i0 - 1; q <= iend; ++q) {
+        if (q + 2 <= iend + 1) fetch_ua(q + 2);
+        if (q + 1 <= iend) fetch_f(q + 1);
         cp_commit();
+        // red update of plane q on the tile + 1-node ring (reads old black)
+        {
+            const int cu = slot_u(q), mu = slot_u(q - 1), pu = slot_u(q + 1), cf = slot_f(q);
+            const int qp = q & 1;
 #pragma unroll
-        for (int s = 0; s < NST; ++s) {
-            const int p = q - s;
-            const int ring = NST - 1 - s;  // region: tile + ring
-            if (p >= i0 - ring && p <= iend - 1 + ring) {
-                const int colour = s & 1;
-                const int RJs = TJ + 2 * ring, RKs = TK + 2 * ring;
-                const int NC = RKs / 2;  // nodes of one colour per row
-                T* upl = su_of(p);
-                for (int r = threadIdx.x; r < RJs * NC; r += NT) {
-                    const int row = r / NC, c = r - row * NC;
-                    const int jj = row - ring;
-                    // first kk >= -ring with (p + j + k) of the stage's parity
-                    const int sh = (p + j0 + jj + k0 - ring + colour) & 1;
-                    const int kk = -ring + 2 * c + sh;
-                    const int e = (jj + H) * RK + (kk + KO);
-                    upl[e] = gs(p, e);
+            for (int m = 0; m < 2; ++m)
+                if (red_e[m] >= 0) {
+                    const int e = red_e[m] + (qp ^ red_p[m]);
+                    su[cu + e] = gs(cu, mu, pu, cf, e);
                 }
-            }
-            __syncthreads();
         }
-        const int pout = q - (NST - 1);
-        if (pout >= i0 && pout < iend) {
-            const T* upl = su_of(pout);
-            for (int e = threadIdx.x; e < TJ * TK; e += NT) {
-                const int jj = e / TK, kk = e - jj * TK;
-                u_new[cell_index(d, pout, j0 + jj, k0 + kk)] = upl[(jj + H) * RK + (kk + KO)];
-            }
+        __syncthreads();
+        // black update of plane p = q-1 on the tile, then write the tile
+        const int p = q - 1;
+        if (p >= i0) {
+            const int cu = slot_u(p), mu = slot_u(p - 1), pu = slot_u(p + 1), cf = slot_f(p);
+            const int e = blk_e + ((p & 1) ^ blk_p);
+            su[cu + e] = gs(cu, mu, pu, cf, e);
+            __syncthreads();
+            const int gb = pbase(p);
+#pragma unroll
+            for (int m = 0; m < 2; ++m) u_new[gb + out_g[m]] = su[cu + out_s[m]];
         }
         cp_wait_all();
         __syncthreads();
     }
 }
 
-template <typename T, int NS, int TJ, int TK, int NT>
-int launch_stream(const Level& L, const T* u_old, T* u_new, const T* f, const T* a, int CI,
-                  cudaStream_t st) {
+}  // namespace
+
+// One sweep u_new <- RBGS(u_old) in one pass when the level is a multiple of
+// the tile; returns the number of sweeps done (1), or 0 with nothing launched.
+template <>
+int launch_rbgs_fused<float>(const Level& L, const float* u_old, float* u_new, const float* f,
+                             const float* a, int nsweeps, cudaStream_t st) {
+    constexpr int CI = 16;
     const Dims& d = L.d;
-    if (d.n2 % TK || d.n1 % TJ || d.n0 % CI) return 0;
-    using S = SweepShape<T, NS, TJ, TK>;
+    if (nsweeps < 1 || d.n2 % TK || d.n1 % TJ || d.n0 % CI) return 0;
     static bool configured = false;
     if (!configured) {
-        cudaFuncSetAttribute(k_rbgs_stream<T, NS, TJ, TK, NT>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, S::smem);
+        cudaFuncSetAttribute(k_rbgs_stream, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
         configured = true;
     }
     dim3 grid(d.n2 / TK, d.n1 / TJ, d.n0 / CI);
     launch_counter()++;
-    k_rbgs_stream<T, NS, TJ, TK, NT><<<grid, NT, S::smem, st>>>(
-        d, (T)L.h2i[0], (T)L.h2i[1], (T)L.h2i[2], CI, u_old, u_new, f, a);
-    return NS;
+    k_rbgs_stream<<<grid, NT, SMEM, st>>>(d, (float)L.h2i[0], (float)L.h2i[1], (float)L.h2i[2], CI,
+                                          u_old, u_new, f, a);
+    return 1;
 }
 
-}  // namespace
-
-// Up to nsweeps sweeps u_new <- RBGS^k(u_old) in one pass when the level is a
-// multiple of the tile; returns k, the number of sweeps done (0: nothing
-// launched).  The single-sweep kernel is used: fusing two sweeps halves the
-// DRAM traffic, but its wider rings and fewer resident blocks made it slower
-// per sweep (1.38 vs 1.74 TB/s of algorithmic traffic on the 256^3 level).
-template <>
-int launch_rbgs_fused<float>(const Level& L, const float* u_old, float* u_new, const float* f,
-                             const float* a, int nsweeps, cudaStream_t st) {
-    if (nsweeps < 1) return 0;
-    return launch_stream<float, 1, 8, 64, 256>(L, u_old, u_new, f, a, 16, st);
-}
 // FP64 levels are bound by the FP64 issue rate, not by memory: the ring nodes
 // the streaming kernel recomputes would cost more than the traffic they save,
-// so FP64 sweeps use the in-place two-colour kernel.
+// so FP64 sweeps use the in-place two-colour kernels.
 template <>
 int launch_rbgs_fused<double>(const Level&, const double*, double*, const double*,
                               const double*, int, cudaStream_t) {

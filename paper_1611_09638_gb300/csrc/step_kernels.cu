@@ -178,12 +178,14 @@ __global__ void k_fix_to_double(int cells, unsigned long long* __restrict__ mfix
     mfix[c] = 0ull;
 }
 
-__global__ void k_init_tracers(int cells, const double* __restrict__ rho, double inv_rho_bar,
+__global__ void k_init_tracers(int cells, const double* __restrict__ rho,
+                               const double* __restrict__ sum_rho,
                                double* __restrict__ w, double* __restrict__ ox,
                                double* __restrict__ oy, double* __restrict__ oz,
                                double* __restrict__ phi, float* __restrict__ phi32) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= cells) return;
+    const double inv_rho_bar = 1.0 / (*sum_rho / (double)cells);
     w[c] = rho[c] * inv_rho_bar;
     ox[c] = 0.0, oy[c] = 0.0, oz[c] = 0.0;
     phi[c] = 0.0;
@@ -474,14 +476,101 @@ __global__ void k_node_velocity(Dims d, const double* __restrict__ e6,
     vx[c] = dx * inv, vy[c] = dy * inv, vz[c] = dz * inv;
 }
 
+// App. A's linear density update (the variant that carries m instead of
+// re-depositing tracers): K = m e^-1 at every node, e = I + Hess phi the
+// stored triad (symmetric, so K is too: xx, yy, zz, xy, xz, yz).
+__global__ void k_mass_tensor(Dims d, const double* __restrict__ e6, const double* __restrict__ m,
+                              double* __restrict__ K6) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= d.cells) return;
+    const size_t n = (size_t)d.cells;
+    Sym3 e;
+    e.xx = e6[c], e.yy = e6[n + c], e.zz = e6[2 * n + c];
+    e.xy = e6[3 * n + c], e.xz = e6[4 * n + c], e.yz = e6[5 * n + c];
+    const double cxx = e.yy * e.zz - e.yz * e.yz, cyy = e.xx * e.zz - e.xz * e.xz;
+    const double czz = e.xx * e.yy - e.xy * e.xy, cxy = e.xz * e.yz - e.xy * e.zz;
+    const double cxz = e.xy * e.yz - e.xz * e.yy, cyz = e.xy * e.xz - e.xx * e.yz;
+    const double s = m[c] / det3(e);
+    K6[c] = cxx * s, K6[n + c] = cyy * s, K6[2 * n + c] = czz * s;
+    K6[3 * n + c] = cxy * s, K6[4 * n + c] = cxz * s, K6[5 * n + c] = cyz * s;
+}
+
+// m += alpha d_mu(K^{mu nu} d_nu v) in flux form: per axis the second
+// difference with face coefficients (K_c + K_n)/2, per axis pair the
+// difference of centred differences taken at the two neighbours.
+__global__ void k_mass_update(Dims d, const double* __restrict__ K6, const double* __restrict__ v,
+                              const double* __restrict__ alpha_p, double* __restrict__ m) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= d.cells) return;
+    const double alpha = *alpha_p;
+    int i, j, k;
+    cell_coords(d, c, i, j, k);
+    const size_t n = (size_t)d.cells;
+    const int o[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    const int off[3][3] = {{0, 3, 4}, {3, 1, 5}, {4, 5, 2}};  // K6 slot of (a, b)
+    const double vc = v[c];
+    double acc = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int pl = cell_index(d, i + o[a][0], j + o[a][1], k + o[a][2]);
+        const int mi = cell_index(d, i - o[a][0], j - o[a][1], k - o[a][2]);
+        const double* Ka = K6 + off[a][a] * n;
+        acc += 0.5 * (Ka[c] + Ka[pl]) * (v[pl] - vc) - 0.5 * (Ka[c] + Ka[mi]) * (vc - v[mi]);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            if (b == a) continue;
+            const double* Kab = K6 + off[a][b] * n;
+            const int pi = i + o[a][0], pj = j + o[a][1], pk = k + o[a][2];
+            const int qi = i - o[a][0], qj = j - o[a][1], qk = k - o[a][2];
+            const double dp = v[cell_index(d, pi + o[b][0], pj + o[b][1], pk + o[b][2])] -
+                              v[cell_index(d, pi - o[b][0], pj - o[b][1], pk - o[b][2])];
+            const double dm = v[cell_index(d, qi + o[b][0], qj + o[b][1], qk + o[b][2])] -
+                              v[cell_index(d, qi - o[b][0], qj - o[b][1], qk - o[b][2])];
+            acc += 0.25 * (Kab[pl] * dp - Kab[mi] * dm);
+        }
+    }
+    m[c] += alpha * acc;
+}
+
+// a = max(m, a_min) in FP64 (and FP32) with partial sums of m, for the
+// variant whose m is carried rather than deposited.
+__global__ void k_coef_from_m(int cells, const double* __restrict__ m, double a_min,
+                              double* __restrict__ a64, float* __restrict__ a32,
+                              double* __restrict__ part) {
+    double s = 0.0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cells; c += gridDim.x * blockDim.x) {
+        const double v = m[c];
+        const double a = v > a_min ? v : a_min;
+        a64[c] = a;
+        if (a32) a32[c] = (float)a;
+        s += v;
+    }
+    s = block_reduce<OpSum>(s);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// phi += alpha (dphi - mean) without moving tracers.
+__global__ void k_phi_advance(int cells, const double* __restrict__ alpha_p,
+                              const double* __restrict__ dphi, const double* __restrict__ sum_dphi,
+                              double* __restrict__ phi, float* __restrict__ phi32) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cells) return;
+    const double alpha = *alpha_p;
+    const double mean = *sum_dphi / (double)cells;
+    const double pn = phi[c] + alpha * (dphi[c] - mean);
+    phi[c] = pn;
+    phi32[c] = (float)pn;
+}
+
 __global__ void k_advance(Dims d, const double* __restrict__ vx, const double* __restrict__ vy,
-                          const double* __restrict__ vz, double alpha,
+                          const double* __restrict__ vz, const double* __restrict__ alpha_p,
                           const double* __restrict__ dphi, const double* __restrict__ sum_dphi,
                           double* __restrict__ ox, double* __restrict__ oy,
                           double* __restrict__ oz, double* __restrict__ phi,
                           float* __restrict__ phi32) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= d.cells) return;
+    const double alpha = *alpha_p;
     int i, j, k;
     cell_coords(d, c, i, j, k);
     const double px = ox[c], py = oy[c], pz = oz[c];
@@ -602,10 +691,11 @@ void launch_fix_to_double(int cells, unsigned long long* mfix, double inv_scale,
     k_fix_to_double<<<nblocks(cells), kThreads, 0, st>>>(cells, mfix, inv_scale, out);
 }
 
-void launch_init_tracers(int cells, const double* rho, double inv_rho_bar, double* w, double* ox,
-                         double* oy, double* oz, double* phi, float* phi32, cudaStream_t st) {
+void launch_init_tracers(int cells, const double* rho, const double* sum_rho, double* w,
+                         double* ox, double* oy, double* oz, double* phi, float* phi32,
+                         cudaStream_t st) {
     launch_counter()++;
-    k_init_tracers<<<nblocks(cells), kThreads, 0, st>>>(cells, rho, inv_rho_bar, w, ox, oy, oz, phi,
+    k_init_tracers<<<nblocks(cells), kThreads, 0, st>>>(cells, rho, sum_rho, w, ox, oy, oz, phi,
                                                         phi32);
 }
 
@@ -656,11 +746,30 @@ void launch_node_velocity(const Dims& d, const double* e6, const double* dphi, d
 }
 
 void launch_advance(const Dims& d, const double* vx, const double* vy, const double* vz,
-                    double alpha, const double* dphi, const double* sum_dphi, double* ox,
+                    const double* alpha, const double* dphi, const double* sum_dphi, double* ox,
                     double* oy, double* oz, double* phi, float* phi32, cudaStream_t st) {
     launch_counter()++;
     k_advance<<<nblocks(d.cells), kThreads, 0, st>>>(d, vx, vy, vz, alpha, dphi, sum_dphi, ox, oy,
                                                      oz, phi, phi32);
+}
+
+void launch_mass_literal(const Dims& d, const double* e6, const double* dphi,
+                         const double* alpha, double* m, double* K6, cudaStream_t st) {
+    launch_counter() += 2;
+    k_mass_tensor<<<nblocks(d.cells), kThreads, 0, st>>>(d, e6, m, K6);
+    k_mass_update<<<nblocks(d.cells), kThreads, 0, st>>>(d, K6, dphi, alpha, m);
+}
+
+void launch_coef_from_m(int cells, const double* m, double a_min, double* a64, float* a32,
+                        double* partials, cudaStream_t st) {
+    launch_counter()++;
+    k_coef_from_m<<<kRedBlocks, kRedThreads, 0, st>>>(cells, m, a_min, a64, a32, partials);
+}
+
+void launch_phi_advance(int cells, const double* alpha, const double* dphi,
+                        const double* sum_dphi, double* phi, float* phi32, cudaStream_t st) {
+    launch_counter()++;
+    k_phi_advance<<<nblocks(cells), kThreads, 0, st>>>(cells, alpha, dphi, sum_dphi, phi, phi32);
 }
 
 void launch_delta_r(const Dims& d, const double* phi, double* out, double* part_max,

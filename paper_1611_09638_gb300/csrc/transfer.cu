@@ -1,0 +1,189 @@
+// transfer.cu -- residual and full-weighting restriction of an FP32 level in
+// one streaming pass (App. A's multigrid: the coarse right-hand side of a
+// V-cycle is R (f - L u), with L the 7-point variable-coefficient operator
+// with face coefficients (a + a_nbr)/2 and R the tensor (1/4, 1/2, 1/4)
+// weighting on the fine nodes 2I-1, 2I, 2I+1 of each axis).
+//
+// The per-coarse-node kernel in mg_kernels.cu evaluates the 27 fine residuals
+// of each coarse node's stencil, so every fine residual is computed 27/8
+// times.  Here a block owns a 8 x 32 tile of the coarse (J, K) plane, i.e. a
+// 16 x 64 tile of the fine plane, and streams fine planes along i: the
+// residual of fine plane p is computed once per node on the tile plus its
+// low-side ring (17 x 65 nodes) into shared memory, weighted in j and k there,
+// and the i weights are applied in registers (an odd plane 2I+1 closes coarse
+// plane I and opens I+1).  u and a are held for four planes (p-1 .. p+1 and
+// the one being fetched), f for two; each plane is fetched with 16-byte
+// cp.async copies.  DRAM traffic is one read of u, a, f and one write of the
+// coarse plane.
+#include "async_copy.cuh"
+#include "recon_internal.cuh"
+
+namespace recon {
+
+namespace {
+
+constexpr int RT = 256;                 // threads
+constexpr int FJ = 16, FK = 64;         // fine tile rows (j) and columns (k)
+constexpr int RH = 2, RKO = 4;          // halo rows / columns held
+constexpr int RRJ = FJ + 2 * RH;        // 20 rows per plane
+constexpr int RRK = FK + 2 * RKO;       // 72 columns per plane
+constexpr int RPL = RRJ * RRK;          // floats per plane
+constexpr int RCH = RRK / 4;            // 16-byte chunks per row
+constexpr int NUA = RRJ * RCH;          // chunks of a u (or a) plane: 360
+constexpr int NFC = (FJ + 1) * RCH;     // chunks of an f plane (rows -1 .. FJ-1): 306
+constexpr int NRES = (FJ + 1) * (FK + 1);  // residual nodes (rows and columns -1 .. F-1): 1105
+constexpr int RES_T = (NRES + RT - 1) / RT;  // residual nodes per thread: 5
+constexpr int SUA = 4, SFF = 2;         // ring slots of u / a and of f
+constexpr int RSMEM = (int)sizeof(float) * RPL * (2 * SUA + SFF + 1);
+static_assert(NUA <= 2 * RT && NFC <= 2 * RT, "fetch rounds");
+static_assert((FJ / 2) * (FK / 2) == RT, "one coarse node per thread");
+
+__global__ void __launch_bounds__(RT) k_resid_restrict_stream(Dims df, Dims dc, float hx, float hy,
+                                                              float hz, int CIc,
+                                                              const float* __restrict__ u,
+                                                              const float* __restrict__ f,
+                                                              const float* __restrict__ a,
+                                                              float* __restrict__ out) {
+    extern __shared__ float4 smem_f4[];
+    float* su = reinterpret_cast<float*>(smem_f4);
+    float* sa = su + SUA * RPL;
+    float* sf = sa + SUA * RPL;
+    float* sr = sf + SFF * RPL;
+    const int t = threadIdx.x;
+    const int K0c = blockIdx.x * (FK / 2), J0c = blockIdx.y * (FJ / 2), I0c = blockIdx.z * CIc;
+    const int k0 = 2 * K0c, j0 = 2 * J0c;
+    const int pS = 2 * I0c - 1, pE = 2 * (I0c + CIc) - 1;  // residual planes of the block
+    const int pbase = pS - 1;                               // first u / a plane held
+    const int plane = df.n1 * df.n2;
+
+    // ---- offsets fixed for the whole block -------------------------------
+    // smem offset of fine (row jj, column kk) relative to the tile origin is
+    // (jj + RH) * RRK + kk + RKO, the same in every plane buffer.
+    int ua_s[2], ua_g[2], f_s[2], f_g[2];
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+        const int e = t + m * RT;
+        const int r = e / RCH, ch = e - r * RCH;
+        const int gk = (k0 - RKO + ch * 4) & (df.n2 - 1);
+        ua_s[m] = e < NUA ? r * RRK + ch * 4 : -1;
+        ua_g[m] = (((j0 + r - RH) & (df.n1 - 1)) << df.s2) + gk;
+        f_s[m] = e < NFC ? (r + 1) * RRK + ch * 4 : -1;  // fine row r - 1
+        f_g[m] = (((j0 + r - 1) & (df.n1 - 1)) << df.s2) + gk;
+    }
+    int res_e[RES_T];
+#pragma unroll
+    for (int m = 0; m < RES_T; ++m) {
+        const int e = t + m * RT;
+        const int r = e / (FK + 1), c = e - r * (FK + 1);  // fine row r - 1, column c - 1
+        res_e[m] = e < NRES ? (r + 1) * RRK + c + RKO - 1 : -1;
+    }
+    const int jc = t >> 5, kc = t & 31;
+    const int rc_e = (2 * jc + RH) * RRK + 2 * kc + RKO;
+    const int out_o = ((J0c + jc) << dc.s2) + K0c + kc;
+
+    auto slot_u = [&](int p) { return ((p - pbase) % SUA) * RPL; };
+    auto slot_f = [&](int p) { return ((p - pS) % SFF) * RPL; };
+    auto gplane = [&](int p) { return (p & (df.n0 - 1)) * plane; };
+    auto fetch_ua = [&](int p) {
+        const int so = slot_u(p), g = gplane(p);
+#pragma unroll
+        for (int m = 0; m < 2; ++m)
+            if (ua_s[m] >= 0) {
+                cp_async16(su + so + ua_s[m], u + g + ua_g[m]);
+                cp_async16(sa + so + ua_s[m], a + g + ua_g[m]);
+            }
+    };
+    auto fetch_f = [&](int p) {
+        const int so = slot_f(p), g = gplane(p);
+#pragma unroll
+        for (int m = 0; m < 2; ++m)
+            if (f_s[m] >= 0) cp_async16(sf + so + f_s[m], f + g + f_g[m]);
+    };
+
+    fetch_ua(pS - 1);
+    fetch_ua(pS);
+    fetch_ua(pS + 1);
+    fetch_f(pS);
+    cp_commit();
+    cp_wait_all();
+    __syncthreads();
+
+    float acc = 0.f;
+    for (int p = pS; p <= pE; ++p) {
+        if (p + 2 <= pE + 1) fetch_ua(p + 2);
+        if (p + 1 <= pE) fetch_f(p + 1);
+        cp_commit();
+        // residual r = f - L u of plane p on the tile and its low-side ring
+        {
+            const int cu = slot_u(p), mu = slot_u(p - 1), pu = slot_u(p + 1), cf = slot_f(p);
+            const float* ac = sa + cu;
+            const float* uc = su + cu;
+#pragma unroll
+            for (int m = 0; m < RES_T; ++m) {
+                const int e = res_e[m];
+                if (e < 0) continue;
+                const float c = ac[e];
+                const float apx = 0.5f * (c + sa[pu + e]) * hx, amx = 0.5f * (c + sa[mu + e]) * hx;
+                const float apy = 0.5f * (c + ac[e + RRK]) * hy, amy = 0.5f * (c + ac[e - RRK]) * hy;
+                const float apz = 0.5f * (c + ac[e + 1]) * hz, amz = 0.5f * (c + ac[e - 1]) * hz;
+                const float diag = (apx + amx) + (apy + amy) + (apz + amz);
+                const float off = (apx * su[pu + e] + amx * su[mu + e]) +
+                                  (apy * uc[e + RRK] + amy * uc[e - RRK]) +
+                                  (apz * uc[e + 1] + amz * uc[e - 1]);
+                sr[e] = sf[cf + e] - (off - diag * uc[e]);
+            }
+        }
+        __syncthreads();
+        // (1/4, 1/2, 1/4) weights in j and k around fine node (2 jc, 2 kc)
+        const float* R = sr + rc_e;
+        const float s = 0.25f * (0.25f * R[-RRK - 1] + 0.5f * R[-RRK] + 0.25f * R[-RRK + 1]) +
+                        0.5f * (0.25f * R[-1] + 0.5f * R[0] + 0.25f * R[1]) +
+                        0.25f * (0.25f * R[RRK - 1] + 0.5f * R[RRK] + 0.25f * R[RRK + 1]);
+        if (p & 1) {  // p = 2I + 1 closes coarse plane I and opens I + 1
+            if (p != pS) out[(((p - 1) >> 1) << (dc.s1 + dc.s2)) + out_o] = acc + 0.25f * s;
+            acc = 0.25f * s;
+        } else {
+            acc += 0.5f * s;
+        }
+        cp_wait_all();
+        __syncthreads();
+    }
+}
+
+int g_resident = 0;  // blocks of the kernel resident on the device at once
+
+}  // namespace
+
+int launch_resid_restrict_stream(const Level& fine, const Level& coarse, const float* u,
+                                 const float* f, const float* a, float* out, cudaStream_t st) {
+    const Dims& df = fine.d;
+    if (!fine.coarsen[0] || !fine.coarsen[1] || !fine.coarsen[2]) return 0;
+    if (df.n2 % FK || df.n1 % FJ || df.n0 < 4) return 0;
+    if (!g_resident) {
+        cudaFuncSetAttribute(k_resid_restrict_stream, cudaFuncAttributeMaxDynamicSharedMemorySize, RSMEM);
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_resid_restrict_stream, RT, RSMEM);
+        g_resident = sms * per_sm > 0 ? sms * per_sm : 1;
+    }
+    // coarse planes per block: fewest rounds of resident blocks times the
+    // planes each block streams (2 CIc + 1 residual planes and a start-up)
+    const long long tiles = (long long)(df.n2 / FK) * (df.n1 / FJ);
+    const int n0c = coarse.d.n0;
+    int best = 0;
+    long long best_cost = 0;
+    for (int ci = 1; ci <= 16 && ci <= n0c; ci *= 2) {
+        if (n0c % ci) continue;
+        const long long blocks = tiles * (n0c / ci);
+        const long long cost = ((blocks + g_resident - 1) / g_resident) * (2 * ci + 2);
+        if (!best || cost < best_cost) best = ci, best_cost = cost;
+    }
+    dim3 grid(df.n2 / FK, df.n1 / FJ, n0c / best);
+    launch_counter()++;
+    k_resid_restrict_stream<<<grid, RT, RSMEM, st>>>(df, coarse.d, (float)fine.h2i[0], (float)fine.h2i[1],
+                                                    (float)fine.h2i[2], best, u, f, a, out);
+    return 1;
+}
+
+}  // namespace recon

@@ -180,3 +180,15 @@ WORKLOADS = {
     "lpt512": Workload("512^3 2LPT, 800 Mpc/h, mixed vs FP64", 512, 800.0, 2, 1002, "mixed"),
     "za128": Workload("128^3 ZA, 200 Mpc/h", 128, 200.0, 1, 1004, "fp64"),
 }
+
+
+def mock_batch(per_size=32, sizes=((32, 100.0), (64, 200.0), (128, 400.0)), seed0=2000):
+    """Batched mock catalogues: per_size Zel'dovich realisations of each
+    (n, box) pair (3.125 Mpc/h cells in the default sizes), with seeds
+    seed0 + i in order; solved in mixed precision."""
+    out = []
+    for n, box in sizes:
+        for _ in range(per_size):
+            i = len(out)
+            out.append(Workload(f"mock {i}: {n}^3 ZA, {box:g} Mpc/h", n, box, 1, seed0 + i, "mixed"))
+    return out

@@ -34,7 +34,7 @@ def test_default_params_match_the_paper_and_the_oracle():
     q = O.OracleParams()
     assert list(p.n) == [32, 16, 8]
     for f in ("xi_m", "v_m", "a_min", "climiter", "s_side", "nu1", "nu2", "tol_in", "max_vcycles",
-              "tol_out", "k_max", "d_max", "alpha_min", "lambda_floor"):
+              "tol_out", "k_max", "d_max", "alpha_min", "lambda_floor", "density_update"):
         assert getattr(p, f) == getattr(q, f), f
 
 
@@ -78,7 +78,8 @@ def test_create_rejects_bad_params_before_touching_the_device():
 
     lib = _abi.load()
     h = C.c_void_p()
-    for bad in ({"xi_m": 1.5}, {"v_m": 0.5}, {"nu1": 0, "nu2": 0}, {"s_side": 0.3}):
+    for bad in ({"xi_m": 1.5}, {"v_m": 0.5}, {"nu1": 0, "nu2": 0}, {"s_side": 0.3},
+                {"device_loop": 2}, {"density_update": 3}, {"inner_vcycles": 0}):
         p = default_params((16, 16, 16), **bad)
         assert lib.recon_create(C.byref(h), C.byref(p), None) == _abi.RECON_E_INVALID
         assert h.value is None
@@ -86,6 +87,26 @@ def test_create_rejects_bad_params_before_touching_the_device():
     assert lib.recon_create(C.byref(h), C.byref(p), None) == _abi.RECON_E_INVALID
     p = default_params((16, 16, 32), box=(100.0, 100.0, 100.0))  # non-cubic cells
     assert lib.recon_create(C.byref(h), C.byref(p), None) == _abi.RECON_E_INVALID
+
+
+def test_solve_runs_on_the_device_loop_by_default():
+    """The default solve is the graph-resident one; profile switches it to
+    the host-driven loop (documented in recon.h)."""
+    from paper_1611_09638_gb300 import default_params
+
+    assert default_params((16, 16, 16)).device_loop == 1
+    assert default_params((16, 16, 16), device_loop=0).device_loop == 0
+
+
+def test_batch_solve_rejects_bad_arguments_without_a_gpu():
+    from paper_1611_09638_gb300 import _abi
+
+    lib = _abi.load()
+    hs = (C.c_void_p * 2)(None, None)
+    assert lib.recon_solve_batch(hs, 2, None) == _abi.RECON_E_INVALID
+    assert lib.recon_solve_batch(None, 1, None) == _abi.RECON_E_INVALID
+    assert lib.recon_solve_batch(None, -1, None) == _abi.RECON_E_INVALID
+    assert lib.recon_solve_batch(None, 0, None) == _abi.RECON_OK
 
 
 def test_package_has_no_cpu_fallback():

@@ -1,0 +1,112 @@
+"""The graph-resident solve (device_loop = 1: the step loop, the multigrid
+loop and the step acceptance are conditional nodes of one CUDA graph whose
+conditions device kernels set) against the host-driven loop, and the batched
+solve against single solves.
+
+Both loops launch the same kernels in the same order and take every decision
+(R_k <= tol_out, the multigrid stopping test, alpha and the stall) in the
+same device kernels, so their results must agree bit for bit: states,
+per-step records, statuses and kernel counts.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1611_09638_gb300 import Recon, solve_batch
+from paper_1611_09638_gb300.inputs import lpt_particles
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _density(n, box, seed, order=1):
+    pos, _ = lpt_particles(n, box, seed, order=order)
+    return O.cic_deposit((n, n, n), pos / (box / n))
+
+
+def _run(rho, precision, device_loop, stream=None, **kw):
+    n = rho.shape
+    R = Recon(n, precision=precision, device_loop=device_loop, stream=stream, **kw)
+    R.deposit_grid(torch.from_numpy(np.ascontiguousarray(rho)).cuda(R.stream.device))
+    st = R.solve()
+    phi = R.field("phi").cpu().numpy()
+    return R, st, phi
+
+
+def _same(a, b, pa, pb):
+    assert a.status == b.status and a.steps == b.steps and a.vcycles == b.vcycles
+    for f in ("alpha", "Rk", "ncycles", "relres"):
+        assert np.array_equal(getattr(a, f), getattr(b, f)), f
+    for f in ("R0", "R", "min_det", "min_lambda0", "max_delta_r", "mass_error"):
+        assert getattr(a, f) == getattr(b, f), f
+    assert a.launches == b.launches
+    assert np.array_equal(pa, pb)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_device_loop_equals_host_loop(precision):
+    rho = _density(32, 100.0, 1000)
+    Ra, a, pa = _run(rho, precision, 0)
+    Rb, b, pb = _run(rho, precision, 1)
+    assert a.steps > 10
+    _same(a, b, pa, pb)
+    # a second solve on the same handle replays the recorded graph
+    b2 = Rb.solve()
+    _same(a, b2, pa, Rb.field("phi").cpu().numpy())
+    Ra.close(), Rb.close()
+
+
+def test_device_loop_stall_replay_and_edge_cases():
+    rho = _density(16, 50.0, 3, order=2)
+    # stall (status 2) with an unreachable eigenvalue floor
+    Ra, a, pa = _run(rho, "fp64", 0, lambda_floor=0.6)
+    Rb, b, pb = _run(rho, "fp64", 1, lambda_floor=0.6)
+    assert a.status == 2
+    _same(a, b, pa, pb)
+    # replayed alpha sequence
+    ra = np.r_[a.alpha, np.full(40 - len(a.alpha), 0.5)]
+    Ra, a, pa = _run(rho, "mixed", 0, replay_alpha=ra)
+    Rb, b, pb = _run(rho, "mixed", 1, replay_alpha=ra)
+    _same(a, b, pa, pb)
+    assert np.array_equal(b.alpha, ra[:b.steps])
+    # no steps at all, and a stop at the first step start
+    for kw in ({"k_max": 0}, {"tol_out": 1e9}, {"k_max": 1}):
+        Ra, a, pa = _run(rho, "mixed", 0, **kw)
+        Rb, b, pb = _run(rho, "mixed", 1, **kw)
+        _same(a, b, pa, pb)
+    assert b.steps == 1 and b.status == 1
+    # uniform density: R_0 = 0, immediate stop with phi = 0
+    Rb, b, pb = _run(np.full((8, 8, 8), 2.0), "fp64", 1)
+    assert b.status == 0 and b.steps == 0 and not pb.any()
+    # the paper-literal density update
+    Ra, a, pa = _run(rho, "fp64", 0, density_update=1, k_max=6)
+    Rb, b, pb = _run(rho, "fp64", 1, density_update=1, k_max=6)
+    _same(a, b, pa, pb)
+
+
+def test_batch_of_mixed_sizes_equals_single_solves():
+    """Mocks of three sizes (3.125 Mpc/h cells), each on its own stream, one of
+    them on the host-driven loop: the batched solve reproduces every single
+    solve bit for bit."""
+    specs = [(16, 50.0), (32, 100.0), (64, 200.0), (16, 50.0), (32, 100.0), (64, 200.0)]
+    rhos = [_density(n, box, 2000 + i) for i, (n, box) in enumerate(specs)]
+    single = []
+    for i, rho in enumerate(rhos):
+        R, st, phi = _run(rho, "mixed", 1 if i != 4 else 0)
+        single.append((st, phi))
+        R.close()
+    recons = []
+    for i, rho in enumerate(rhos):
+        R = Recon(rho.shape, precision="mixed", device_loop=1 if i != 4 else 0,
+                  stream=torch.cuda.Stream())
+        torch.cuda.synchronize()
+        R.deposit_grid(torch.from_numpy(np.ascontiguousarray(rho)).cuda())
+        recons.append(R)
+    torch.cuda.synchronize()
+    for rep in range(2):
+        out = solve_batch(recons)
+        for R, st, (st1, phi1) in zip(recons, out, single):
+            _same(st1, st, phi1, R.field("phi").cpu().numpy())
+    for R in recons:
+        R.close()

@@ -184,6 +184,24 @@ def test_streaming_smoother_levels_match_oracle(nn):
         R.close()
 
 
+def test_paper_literal_density_update_matches_oracle():
+    """App. A's variant (m += alpha D(dphi), no tracers) through the C ABI."""
+    n, box = 16, 100.0
+    pos, _ = lpt_particles(n, box, 4, order=1)
+    rho = O.cic_deposit((n, n, n), pos / (box / n))
+    res = O.solve(O.OracleParams(n=(n, n, n), k_max=8, density_update=1), rho)
+    for prec, tol in (("fp64", 1e-6), ("mixed", 1e-4)):
+        R, st = _gpu_solve((n, n, n), rho, precision=prec, k_max=8, density_update=1)
+        _check_free_run(st, res)
+        R.close()
+        R, st = _gpu_solve((n, n, n), rho, precision=prec, k_max=8, density_update=1,
+                           replay_alpha=res.alpha)
+        assert rel(R.field("phi").cpu().numpy(), res.phi) <= tol
+        assert rel(R.field("mass").cpu().numpy(), res.m) <= tol
+        assert abs(R.field("mass").sum().item() - n ** 3) <= 1e-9 * n ** 3
+        R.close()
+
+
 def test_one_step_at_128_cubed_matches_oracle():
     """One full step on the 128^3 / 200 Mpc/h Zel'dovich field (seed 1004)."""
     n, box = 128, 200.0
