@@ -58,13 +58,11 @@ __global__ void k_rbgs_colour(Dims d, T hx, T hy, T hz, int colour, T* __restric
     u[c] = (s.off - f[c]) / s.diag;
 }
 
-// FP64 sweep of the finest level (unit spacing) with the diagonal inverted
-// once per coefficient: u_c = (sum_n (a_c + a_n) u_n - 2 f_c) * inv2_c with
-// inv2_c = 1 / sum_n (a_c + a_n) -- 14 FP64 instructions per node instead of
-// ~45 with the division, since FP64 issue, not memory, bounds this sweep.
 // One colour of a red-black sweep of the finest FP64 level (unit spacing)
 // from the stored face coefficients A = (a_c + a_n) / 2 (F: +x, +y, +z face
-// of each node) and the inverse of the node's diagonal D = sum of its six A.
+// of each node) and the inverse of the node's diagonal D = sum of its six A:
+// u_c = (sum_n A_n u_n - f_c) / D_c in 8 FP64 instructions per node, since
+// FP64 issue, not memory, bounds this sweep on GB300.
 __global__ void k_rbgs_colour64_unit(Dims d, int colour, double* __restrict__ u,
                                      const double* __restrict__ f, const double* __restrict__ F,
                                      const double* __restrict__ inv_d) {
@@ -246,18 +244,24 @@ __global__ void k_prolong_add(Dims df, Dims dc, int cx, int cy, int cz, const T*
 
 // Coarsest level (64 nodes): Gauss-Jordan inversion with partial pivoting of
 // the bordered system [L 1; 1^T 0] (65 x 65), in FP64, by one block working
-// on the augmented matrix [M | I] held in global memory (65 x 130).
+// on the augmented matrix [M | I] (65 x 130) in shared memory; the result is
+// written to global memory in the same layout.
 constexpr int kNc = 64, kNb = 65, kW = 130;
+constexpr int kInvThreads = 1024;
+constexpr size_t kInvSmem = sizeof(double) * kNb * kW;
 
 template <typename T>
-__global__ void k_coarse_invert(Dims d, double hx, double hy, double hz, const T* __restrict__ a,
-                                double* __restrict__ aug) {
+__global__ void __launch_bounds__(kInvThreads) k_coarse_invert(Dims d, double hx, double hy,
+                                                              double hz, const T* __restrict__ a,
+                                                              double* __restrict__ out) {
+    extern __shared__ double aug[];
     __shared__ double fac[kNb];
     __shared__ int piv_row;
-    for (int e = threadIdx.x; e < kNb * kW; e += blockDim.x) aug[e] = 0.0;
+    const int t = threadIdx.x;
+    for (int e = t; e < kNb * kW; e += blockDim.x) aug[e] = 0.0;
     __syncthreads();
-    if (threadIdx.x < kNc) {
-        const int c = threadIdx.x;
+    if (t < kNc) {
+        const int c = t;
         int i, j, k;
         cell_coords(d, c, i, j, k);
         const int nb[6] = {cell_index(d, i + 1, j, k), cell_index(d, i - 1, j, k),
@@ -275,39 +279,47 @@ __global__ void k_coarse_invert(Dims d, double hx, double hy, double hz, const T
         aug[kNc * kW + c] = 1.0;
     }
     __syncthreads();
-    for (int r = threadIdx.x; r < kNb; r += blockDim.x) aug[r * kW + kNb + r] = 1.0;
+    for (int r = t; r < kNb; r += blockDim.x) aug[r * kW + kNb + r] = 1.0;
     __syncthreads();
     for (int p = 0; p < kNb; ++p) {
-        if (threadIdx.x == 0) {
-            int best = p;
-            double bv = fabs(aug[p * kW + p]);
-            for (int r = p + 1; r < kNb; ++r) {
-                double v = fabs(aug[r * kW + p]);
-                if (v > bv) { bv = v; best = r; }
+        if (t < 32) {
+            // largest |entry| of column p at or below row p; the first such
+            // row on ties (as a serial scan with a strict comparison)
+            int best = -1;
+            double bv = -1.0;
+            for (int r = p + t; r < kNb; r += 32) {
+                const double v = fabs(aug[r * kW + p]);
+                if (v > bv) bv = v, best = r;
             }
-            piv_row = best;
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ov = __shfl_down_sync(0xffffffffu, bv, o);
+                const int ob = __shfl_down_sync(0xffffffffu, best, o);
+                if (ob >= 0 && (ov > bv || (ov == bv && (best < 0 || ob < best)))) bv = ov, best = ob;
+            }
+            if (t == 0) piv_row = best;
         }
         __syncthreads();
         const int pr = piv_row;
         if (pr != p)
-            for (int cc = threadIdx.x; cc < kW; cc += blockDim.x) {
-                double t = aug[p * kW + cc];
+            for (int cc = t; cc < kW; cc += blockDim.x) {
+                const double x = aug[p * kW + cc];
                 aug[p * kW + cc] = aug[pr * kW + cc];
-                aug[pr * kW + cc] = t;
+                aug[pr * kW + cc] = x;
             }
         __syncthreads();
         const double pv = aug[p * kW + p];
         __syncthreads();
-        for (int cc = threadIdx.x; cc < kW; cc += blockDim.x) aug[p * kW + cc] /= pv;
+        for (int cc = t; cc < kW; cc += blockDim.x) aug[p * kW + cc] /= pv;
         __syncthreads();
-        for (int r = threadIdx.x; r < kNb; r += blockDim.x) fac[r] = aug[r * kW + p];
+        for (int r = t; r < kNb; r += blockDim.x) fac[r] = aug[r * kW + p];
         __syncthreads();
-        for (int e = threadIdx.x; e < kNb * kW; e += blockDim.x) {
+        for (int e = t; e < kNb * kW; e += blockDim.x) {
             const int r = e / kW, cc = e - r * kW;
             if (r != p) aug[e] -= fac[r] * aug[p * kW + cc];
         }
         __syncthreads();
     }
+    for (int e = t; e < kNb * kW; e += blockDim.x) out[e] = aug[e];
 }
 
 template <typename T>
@@ -368,8 +380,15 @@ void launch_prolong_add(const Level& fine, const Level& coarse, const T* uc, T* 
 
 template <typename T>
 void launch_coarse_invert(const Level& L, const T* a, double* minv, cudaStream_t st) {
+    static bool configured = false;
+    if (!configured) {
+        cudaFuncSetAttribute(k_coarse_invert<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kInvSmem);
+        configured = true;
+    }
     launch_counter()++;
-    k_coarse_invert<T><<<1, 256, 0, st>>>(L.d, L.h2i[0], L.h2i[1], L.h2i[2], a, minv);
+    k_coarse_invert<T><<<1, kInvThreads, kInvSmem, st>>>(L.d, L.h2i[0], L.h2i[1], L.h2i[2], a,
+                                                         minv);
 }
 
 template <typename T>
