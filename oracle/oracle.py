@@ -17,7 +17,7 @@ __all__ = [
     "OracleParams", "CLIM_SOFT", "CLIM_LITERAL", "CLIM_STEP", "cic_deposit", "apply_L",
     "rbgs_sweep", "restrict", "prolong_add", "apply_S", "vcycle", "mg_solve", "geometry",
     "source", "step_limiter", "advance", "solve", "delta_r", "mesh_x", "min_eig_sym3", "mass_change",
-    "coarse_dims", "levels",
+    "coarse_dims", "levels", "adjoint",
 ]
 
 CLIM_SOFT, CLIM_LITERAL, CLIM_STEP = 0, 1, 2
@@ -81,7 +81,7 @@ def _load():
         for name in ("orc_cic_deposit", "orc_apply_L", "orc_rbgs_sweep", "orc_restrict",
                      "orc_prolong_add", "orc_apply_S", "orc_vcycle", "orc_mg_solve",
                      "orc_geometry", "orc_source", "orc_step_limiter", "orc_advance",
-                     "orc_solve", "orc_delta_r", "orc_mesh_x", "orc_mass_change"):
+                     "orc_solve", "orc_delta_r", "orc_mesh_x", "orc_mass_change", "orc_adjoint"):
             getattr(_lib, name).restype = C.c_int
         _lib.orc_min_eig_sym3.restype = C.c_double
     return _lib
@@ -282,3 +282,17 @@ def solve(params: OracleParams, rho, replay_alpha=None) -> SolveResult:
     return SolveResult(rc, k, phi, xi, m, arrs["alpha"][:k], arrs["R"][:nrec], ncyc[:k],
                        arrs["relres"][:k], arrs["min_det"][:nrec], arrs["min_lam"][:nrec],
                        arrs["mass"][:nrec])
+
+
+def adjoint(params: OracleParams, rho, alpha, gbar):
+    """dL/d rho from gbar = dL/d delta_r for the solve's len(alpha) advances
+    with those step lengths held fixed (orc_adjoint)."""
+    rho = _f64(rho)
+    assert tuple(rho.shape) == tuple(params.n)
+    al = _f64(np.asarray(alpha, dtype=np.float64).reshape(-1))
+    g = _f64(gbar)
+    out = np.empty_like(rho)
+    p = params._c()
+    _check(_load().orc_adjoint(C.byref(p), _dp(rho), _dp(al) if al.size else None, int(al.size),
+                               _dp(g), _dp(out)), "adjoint")
+    return out

@@ -856,3 +856,334 @@ out:
     if (rc) return rc;
     return done ? 0 : (stalled ? 2 : 1);
 }
+
+/* ---------------------------------------------------------------- adjoint */
+
+/* Smallest eigenvalue of a symmetric 3x3 matrix with a unit eigenvector, by
+ * the same cyclic Jacobi rotations as orc_min_eig_sym3, accumulated into V
+ * (columns: eigenvectors, A = V diag V^T). */
+static double min_eig_vec_sym3(const double A[3][3], double v[3]) {
+    double m[3][3], V[3][3] = {{1.0, 0.0, 0.0}, {0.0, 1.0, 0.0}, {0.0, 0.0, 1.0}};
+    memcpy(m, A, sizeof(m));
+    for (int sweep = 0; sweep < 64; ++sweep) {
+        double off = m[0][1] * m[0][1] + m[0][2] * m[0][2] + m[1][2] * m[1][2];
+        if (off == 0.0) break;
+        for (int p = 0; p < 2; ++p)
+            for (int q = p + 1; q < 3; ++q) {
+                if (m[p][q] == 0.0) continue;
+                double theta = (m[q][q] - m[p][p]) / (2.0 * m[p][q]);
+                double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                for (int r = 0; r < 3; ++r) {
+                    double mrp = m[r][p], mrq = m[r][q];
+                    m[r][p] = c * mrp - s * mrq;
+                    m[r][q] = s * mrp + c * mrq;
+                }
+                for (int r = 0; r < 3; ++r) {
+                    double mpr = m[p][r], mqr = m[q][r];
+                    m[p][r] = c * mpr - s * mqr;
+                    m[q][r] = s * mpr + c * mqr;
+                }
+                m[p][q] = m[q][p] = 0.0;
+                for (int r = 0; r < 3; ++r) {
+                    double vrp = V[r][p], vrq = V[r][q];
+                    V[r][p] = c * vrp - s * vrq;
+                    V[r][q] = s * vrp + c * vrq;
+                }
+            }
+    }
+    int best = 0;
+    if (m[1][1] < m[best][best]) best = 1;
+    if (m[2][2] < m[best][best]) best = 2;
+    for (int r = 0; r < 3; ++r) v[r] = V[r][best];
+    return m[best][best];
+}
+
+/* dC/dlambda0 of the compression limiter under the chosen reading (zero
+ * where lambda0 is clamped). */
+static double climit_deriv(int reading, double xi_m, double lambda0) {
+    if (!(lambda0 > 1e-12)) return 0.0;
+    double q = xi_m / lambda0, dq = -xi_m / (lambda0 * lambda0);
+    double v, dv;
+    switch (reading) {
+        case ORC_CLIM_LITERAL: v = q - heaviside(q - 1.0); dv = dq; break;
+        case ORC_CLIM_STEP: v = q * heaviside(q - 1.0); dv = heaviside(q - 1.0) * dq; break;
+        default: v = q - 1.0 > 0.0 ? q - 1.0 : 0.0; dv = q - 1.0 > 0.0 ? dq : 0.0; break;
+    }
+    return 8.0 * v * dv;
+}
+
+/* Transpose of the Hessian stencil: phibar += sum_ab H_ab^T Ebar_ab, Ebar a
+ * full 3x3 matrix per node (both off-diagonal entries use the same cross
+ * stencil). */
+static void hessian_adj(const int n[3], const double* Ebar, double* phibar) {
+    long o[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    for (long i = 0; i < n[0]; ++i)
+        for (long j = 0; j < n[1]; ++j)
+            for (long k = 0; k < n[2]; ++k) {
+                const double* E = Ebar + 9 * at(n, i, j, k);
+                for (int a = 0; a < 3; ++a) {
+                    double d = E[3 * a + a];
+                    phibar[at(n, i + o[a][0], j + o[a][1], k + o[a][2])] += d;
+                    phibar[at(n, i, j, k)] -= 2.0 * d;
+                    phibar[at(n, i - o[a][0], j - o[a][1], k - o[a][2])] += d;
+                    for (int b = a + 1; b < 3; ++b) {
+                        double x = 0.25 * (E[3 * a + b] + E[3 * b + a]);
+                        long pi = o[a][0] + o[b][0], pj = o[a][1] + o[b][1], pk = o[a][2] + o[b][2];
+                        long qi = o[a][0] - o[b][0], qj = o[a][1] - o[b][1], qk = o[a][2] - o[b][2];
+                        phibar[at(n, i + pi, j + pj, k + pk)] += x;
+                        phibar[at(n, i + qi, j + qj, k + qk)] -= x;
+                        phibar[at(n, i - qi, j - qj, k - qk)] -= x;
+                        phibar[at(n, i - pi, j - pj, k - pk)] += x;
+                    }
+                }
+            }
+}
+
+/* CIC weight of corner (di, dj, dk) of a tracer with fractions f and its
+ * derivatives with respect to the three coordinates. */
+static double cic_weight(const double f[3], int di, int dj, int dk, double dw[3]) {
+    double wx = di ? f[0] : 1.0 - f[0], wy = dj ? f[1] : 1.0 - f[1], wz = dk ? f[2] : 1.0 - f[2];
+    double sx = di ? 1.0 : -1.0, sy = dj ? 1.0 : -1.0, sz = dk ? 1.0 : -1.0;
+    dw[0] = sx * wy * wz, dw[1] = wx * sy * wz, dw[2] = wx * wy * sz;
+    return wx * wy * wz;
+}
+
+static void project_mean(double* v, size_t len) {
+    double mu = mean(v, len);
+    for (size_t c = 0; c < len; ++c) v[c] -= mu;
+}
+
+int orc_adjoint(const orc_params* p, const double* rho, const double* alpha, int K,
+                const double* gbar, double* grad) {
+    if (!params_ok(p) || !rho || !gbar || !grad || K < 0 || (K > 0 && !alpha) ||
+        p->density_update != 0)
+        return ORC_E_INVALID;
+    const int* n = p->n;
+    const size_t len = ncells(n);
+    double rho_sum = 0.0;
+    for (size_t c = 0; c < len; ++c) {
+        if (!(rho[c] >= 0.0) || !isfinite(rho[c])) return ORC_E_INVALID;
+        rho_sum += rho[c];
+    }
+    if (!(rho_sum > 0.0)) return ORC_E_INVALID;
+    const double rho_bar = rho_sum / (double)len;
+    const size_t K1 = (size_t)K + 1;
+    double* w = (double*)malloc(len * sizeof(double));
+    double* XI = (double*)malloc(K1 * 3 * len * sizeof(double));  /* xi_k, k = 0..K */
+    double* PHI = (double*)malloc(K1 * len * sizeof(double));     /* phi_k */
+    double* PD = (double*)malloc((K > 0 ? (size_t)K : 1) * len * sizeof(double)); /* phidot_k */
+    double* m = (double*)malloc(len * sizeof(double));
+    double* s = (double*)malloc(len * sizeof(double));
+    double* a = (double*)malloc(len * sizeof(double));
+    double* dphi = (double*)malloc(len * sizeof(double));
+    double* V = (double*)malloc(3 * len * sizeof(double));
+    double* Ein = (double*)malloc(9 * len * sizeof(double));  /* e^-1 per node */
+    double* gdet = (double*)malloc(len * sizeof(double));
+    double* lam = (double*)malloc(len * sizeof(double));
+    double* evec = (double*)malloc(3 * len * sizeof(double));
+    double* phibar = (double*)malloc(len * sizeof(double));
+    double* xibar = (double*)malloc(3 * len * sizeof(double));
+    double* xinew = (double*)malloc(3 * len * sizeof(double));
+    double* wbar = (double*)malloc(len * sizeof(double));
+    double* dbar = (double*)malloc(len * sizeof(double));
+    double* Vbar = (double*)malloc(3 * len * sizeof(double));
+    double* Ebar = (double*)malloc(9 * len * sizeof(double));
+    double* tmp = (double*)malloc(len * sizeof(double));
+    double* lamb = (double*)malloc(len * sizeof(double));
+    double* mbar = (double*)malloc(len * sizeof(double));
+    int rc = 0;
+    if (!w || !XI || !PHI || !PD || !m || !s || !a || !dphi || !V || !Ein || !gdet || !lam ||
+        !evec || !phibar || !xibar || !xinew || !wbar || !dbar || !Vbar || !Ebar || !tmp ||
+        !lamb || !mbar) {
+        rc = ORC_E_NOMEM;
+        goto out;
+    }
+
+    /* forward: the solve's K advances with the given step lengths, keeping
+     * xi_k, phi_k and phidot_k (same steps as orc_solve) */
+    for (long i = 0; i < n[0]; ++i)
+        for (long j = 0; j < n[1]; ++j)
+            for (long kk = 0; kk < n[2]; ++kk) {
+                size_t c = at(n, i, j, kk);
+                w[c] = rho[c] / rho_bar;
+                XI[3 * c + 0] = (double)i, XI[3 * c + 1] = (double)j, XI[3 * c + 2] = (double)kk;
+            }
+    memset(PHI, 0, len * sizeof(double));
+    for (int k = 0; k < K; ++k) {
+        double* xi = XI + (size_t)k * 3 * len;
+        double* phi = PHI + (size_t)k * len;
+        orc_cic_deposit(n, xi, w, (int64_t)len, m);
+        if ((rc = orc_source(p, phi, m, s, NULL))) goto out;
+        for (size_t c = 0; c < len; ++c) a[c] = m[c] > p->a_min ? m[c] : p->a_min;
+        if ((rc = orc_mg_solve(p, a, s, PD + (size_t)k * len, NULL, NULL))) goto out;
+        orc_apply_S(n, p->s_side, PD + (size_t)k * len, dphi);
+        project_mean(dphi, len);
+        memcpy(phi + len, phi, len * sizeof(double));
+        memcpy(xi + 3 * len, xi, 3 * len * sizeof(double));
+        if ((rc = orc_advance(n, alpha[k], dphi, phi + len, xi + 3 * len, (int64_t)len))) goto out;
+    }
+
+    /* delta_r = -lap phi_K: phibar_K = -lap^T gbar (the 7-point stencil is
+     * symmetric) */
+    for (long i = 0; i < n[0]; ++i)
+        for (long j = 0; j < n[1]; ++j)
+            for (long k = 0; k < n[2]; ++k) {
+                size_t c = at(n, i, j, k);
+                double acc = 0.0;
+                for (int ax = 0; ax < 3; ++ax) {
+                    long di = ax == 0, dj = ax == 1, dk = ax == 2;
+                    acc += gbar[at(n, i + di, j + dj, k + dk)] + gbar[at(n, i - di, j - dj, k - dk)] -
+                           2.0 * gbar[c];
+                }
+                phibar[c] = -acc;
+            }
+    memset(xibar, 0, 3 * len * sizeof(double));
+    memset(wbar, 0, len * sizeof(double));
+
+    for (int k = K - 1; k >= 0; --k) {
+        const double al = alpha[k];
+        const double* xi = XI + (size_t)k * 3 * len;
+        const double* phi = PHI + (size_t)k * len;
+        const double* pd = PD + (size_t)k * len;
+        /* step k's forward quantities */
+        orc_cic_deposit(n, xi, w, (int64_t)len, m);
+        for (size_t c = 0; c < len; ++c) a[c] = m[c] > p->a_min ? m[c] : p->a_min;
+        orc_apply_S(n, p->s_side, pd, dphi);
+        project_mean(dphi, len);
+        for (long i = 0; i < n[0]; ++i)
+            for (long j = 0; j < n[1]; ++j)
+                for (long kk = 0; kk < n[2]; ++kk) {
+                    size_t c = at(n, i, j, kk);
+                    double H[3][3], e[3][3], G[3];
+                    hessian(n, phi, i, j, kk, H);
+                    for (int x = 0; x < 3; ++x) {
+                        for (int y = 0; y < 3; ++y) e[x][y] = (x == y ? 1.0 : 0.0) + H[x][y];
+                        G[x] = cgrad(n, dphi, i, j, kk, x);
+                    }
+                    double d = det3(e);
+                    gdet[c] = d;
+                    lam[c] = min_eig_vec_sym3(e, evec + 3 * c);
+                    /* e^-1 by cofactors (e symmetric) */
+                    double* Ei = Ein + 9 * c;
+                    Ei[0] = (e[1][1] * e[2][2] - e[1][2] * e[2][1]) / d;
+                    Ei[1] = (e[0][2] * e[2][1] - e[0][1] * e[2][2]) / d;
+                    Ei[2] = (e[0][1] * e[1][2] - e[0][2] * e[1][1]) / d;
+                    Ei[3] = (e[1][2] * e[2][0] - e[1][0] * e[2][2]) / d;
+                    Ei[4] = (e[0][0] * e[2][2] - e[0][2] * e[2][0]) / d;
+                    Ei[5] = (e[0][2] * e[1][0] - e[0][0] * e[1][2]) / d;
+                    Ei[6] = (e[1][0] * e[2][1] - e[1][1] * e[2][0]) / d;
+                    Ei[7] = (e[0][1] * e[2][0] - e[0][0] * e[2][1]) / d;
+                    Ei[8] = (e[0][0] * e[1][1] - e[0][1] * e[1][0]) / d;
+                    for (int x = 0; x < 3; ++x)
+                        V[3 * c + x] = Ei[3 * x] * G[0] + Ei[3 * x + 1] * G[1] + Ei[3 * x + 2] * G[2];
+                }
+        /* phi_{k+1} = phi_k + alpha dphi: phibar passes through, dbar = alpha phibar */
+        for (size_t c = 0; c < len; ++c) dbar[c] = al * phibar[c];
+        /* tracers xi_{k+1} = xi_k - alpha V(xi_k) (CIC interpolation) */
+        memset(Vbar, 0, 3 * len * sizeof(double));
+        memcpy(xinew, xibar, 3 * len * sizeof(double));
+        for (size_t t = 0; t < len; ++t) {
+            long i0[3];
+            double f[3];
+            for (int x = 0; x < 3; ++x) cic_axis(xi[3 * t + x], n[x], &i0[x], &f[x]);
+            const double* xb = xibar + 3 * t;
+            for (int di = 0; di < 2; ++di)
+                for (int dj = 0; dj < 2; ++dj)
+                    for (int dk = 0; dk < 2; ++dk) {
+                        double dw[3];
+                        double wgt = cic_weight(f, di, dj, dk, dw);
+                        size_t c = at(n, i0[0] + di, i0[1] + dj, i0[2] + dk);
+                        double vdot = V[3 * c] * xb[0] + V[3 * c + 1] * xb[1] + V[3 * c + 2] * xb[2];
+                        for (int x = 0; x < 3; ++x) {
+                            Vbar[3 * c + x] -= al * wgt * xb[x];
+                            xinew[3 * t + x] -= al * dw[x] * vdot;
+                        }
+                    }
+        }
+        memcpy(xibar, xinew, 3 * len * sizeof(double));
+        /* V = e^-1 G: Gbar = e^-1 Vbar, Ebar = -Gbar V^T */
+        memset(tmp, 0, len * sizeof(double));
+        for (long i = 0; i < n[0]; ++i)
+            for (long j = 0; j < n[1]; ++j)
+                for (long kk = 0; kk < n[2]; ++kk) {
+                    size_t c = at(n, i, j, kk);
+                    const double* Ei = Ein + 9 * c;
+                    const double* vb = Vbar + 3 * c;
+                    double Gb[3];
+                    for (int x = 0; x < 3; ++x)
+                        Gb[x] = Ei[3 * x] * vb[0] + Ei[3 * x + 1] * vb[1] + Ei[3 * x + 2] * vb[2];
+                    for (int x = 0; x < 3; ++x)
+                        for (int y = 0; y < 3; ++y) Ebar[9 * c + 3 * x + y] = -Gb[x] * V[3 * c + y];
+                    /* G = central difference of dphi */
+                    for (int ax = 0; ax < 3; ++ax) {
+                        long di = ax == 0, dj = ax == 1, dk = ax == 2;
+                        tmp[at(n, i + di, j + dj, kk + dk)] += 0.5 * Gb[ax];
+                        tmp[at(n, i - di, j - dj, kk - dk)] -= 0.5 * Gb[ax];
+                    }
+                }
+        for (size_t c = 0; c < len; ++c) dbar[c] += tmp[c];
+        /* dphi = S phidot - mean: phidotbar = S P dbar */
+        project_mean(dbar, len);
+        orc_apply_S(n, p->s_side, dbar, tmp);
+        /* phidot = P L(a)^+ P s: sbar = P L(a)^+ P phidotbar (L symmetric) */
+        if ((rc = orc_mg_solve(p, a, tmp, lamb, NULL, NULL))) goto out;
+        project_mean(lamb, len);
+        /* coefficient: abar_j = sum over the faces f of node j of
+         * (1/2) (lamb_n - lamb_j)(phidot_n - phidot_j); a = max(m, a_min) */
+        memset(mbar, 0, len * sizeof(double));
+        for (long i = 0; i < n[0]; ++i)
+            for (long j = 0; j < n[1]; ++j)
+                for (long kk = 0; kk < n[2]; ++kk) {
+                    size_t c = at(n, i, j, kk);
+                    for (int ax = 0; ax < 3; ++ax) {
+                        long di = ax == 0, dj = ax == 1, dk = ax == 2;
+                        size_t q = at(n, i + di, j + dj, kk + dk);
+                        double A = 0.5 * (lamb[q] - lamb[c]) * (pd[q] - pd[c]);
+                        mbar[c] += A;
+                        mbar[q] += A;
+                    }
+                }
+        for (size_t c = 0; c < len; ++c)
+            if (!(m[c] > p->a_min)) mbar[c] = 0.0;
+        /* s = P S t: tbar = S P sbar */
+        orc_apply_S(n, p->s_side, lamb, tmp);
+        /* t = Sigma + C(lambda0) + E(sqrt g, Sigma), Sigma = 1 - m */
+        for (size_t c = 0; c < len; ++c) {
+            double Sig = 1.0 - m[c];
+            double sg = Sig > 0.0 ? 1.0 : (Sig < 0.0 ? -1.0 : 0.0);
+            mbar[c] += tmp[c] * (-1.0 + 2.0 * heaviside(gdet[c] - p->v_m) * sg);
+            double lb = tmp[c] * climit_deriv(p->climiter, p->xi_m, lam[c]);
+            const double* v = evec + 3 * c;
+            for (int x = 0; x < 3; ++x)
+                for (int y = 0; y < 3; ++y) Ebar[9 * c + 3 * x + y] += lb * v[x] * v[y];
+        }
+        hessian_adj(n, Ebar, phibar);
+        /* m = CIC deposit of the tracers' masses at xi_k */
+        for (size_t t = 0; t < len; ++t) {
+            long i0[3];
+            double f[3];
+            for (int x = 0; x < 3; ++x) cic_axis(xi[3 * t + x], n[x], &i0[x], &f[x]);
+            for (int di = 0; di < 2; ++di)
+                for (int dj = 0; dj < 2; ++dj)
+                    for (int dk = 0; dk < 2; ++dk) {
+                        double dw[3];
+                        double wgt = cic_weight(f, di, dj, dk, dw);
+                        double mb = mbar[at(n, i0[0] + di, i0[1] + dj, i0[2] + dk)];
+                        wbar[t] += wgt * mb;
+                        for (int x = 0; x < 3; ++x) xibar[3 * t + x] += w[t] * dw[x] * mb;
+                    }
+        }
+    }
+    /* w = rho / rho_bar with rho_bar the mean of rho */
+    {
+        double sw = 0.0;
+        for (size_t c = 0; c < len; ++c) sw += wbar[c] * w[c];
+        for (size_t c = 0; c < len; ++c) grad[c] = (wbar[c] - sw / (double)len) / rho_bar;
+    }
+out:
+    free(w), free(XI), free(PHI), free(PD), free(m), free(s), free(a), free(dphi), free(V);
+    free(Ein), free(gdet), free(lam), free(evec), free(phibar), free(xibar), free(xinew);
+    free(wbar), free(dbar), free(Vbar), free(Ebar), free(tmp), free(lamb), free(mbar);
+    return rc;
+}

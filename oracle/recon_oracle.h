@@ -137,6 +137,24 @@ int orc_mesh_x(const int n[3], const double* phi, double* out);
 /* Minimum eigenvalue of a symmetric 3x3 matrix by cyclic Jacobi rotations. */
 double orc_min_eig_sym3(const double A[3][3]);
 
+/* Vector-Jacobian product of the map rho -> delta_r of a solve (Sec. II,
+ * App. A; tracer re-deposit form) over its K advances with the step lengths
+ * alpha[0..K-1] held fixed (the limiter's choice is piecewise constant in
+ * rho).  gbar: dL/d delta_r (ncells, grid units); grad: dL/d rho (ncells).
+ * The reverse sweep goes through the steps in the opposite order: the phi
+ * update, the tracer advance xi -= alpha e^-1 grad dphi (CIC interpolation),
+ * dphi = S phidot - mean, the linear solve L(a) phidot = s (its adjoint is a
+ * solve with the same symmetric operator, and the coefficient sensitivity
+ * is (1/2) sum over a node's faces of the face differences of the two
+ * solutions), a = max(m, a_min), s = S t - mean, the source
+ * t = Sigma + C(lambda0) + E (d lambda0 = v^T de v with v the eigenvector of
+ * lambda0; the Heaviside factors have zero derivative almost everywhere),
+ * the geometry e = I + Hess phi, and the CIC deposit of the tracers' masses;
+ * finally w = rho / mean(rho).  Both linear solves run to p->tol_in.
+ * Requires density_update = 0.  Returns 0 or <0 (invalid input, no memory). */
+int orc_adjoint(const orc_params* p, const double* rho, const double* alpha, int K,
+                const double* gbar, double* grad);
+
 #ifdef __cplusplus
 }
 #endif
