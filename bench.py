@@ -39,6 +39,7 @@ def _args():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--k-max", type=int, default=40,
                     help="steps per solve (40 is the workload; fewer only for profiling)")
     return ap.parse_args()
@@ -259,6 +260,8 @@ def run_gb300(a):
                "ms_per_step": e2e_ms, "host_wall_ms_per_step": wall_ms,
                "path": "recon_deposit(host pinned particles) + recon_solve + recon_field(delta_r -> host pinned)"}
 
+    adj = None if a.no_adjoint else adjoint_timing(a, stream, barrier)
+
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cpu = cpu_baseline(W, st_mixed[0])
@@ -279,6 +282,7 @@ def run_gb300(a):
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "adjoint": adj,
         "gpu_launches": int(sum(s.launches for s in st_mixed)),
         "clocks": clocks,
     }
@@ -289,6 +293,44 @@ def run_gb300(a):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line))
+
+
+def adjoint_timing(a, stream, barrier, steps=3):
+    """recon_adjoint on the 128^3 / 200 Mpc/h ZA configuration (seed 1004) in
+    mixed precision with checkpoints: the forward solve and the sweep back
+    (dL/d rho from a band-limited dL/d delta_r), each timed with CUDA events."""
+    import torch
+
+    from paper_1611_09638_gb300 import Recon
+    from paper_1611_09638_gb300.inputs import WORKLOADS
+
+    W = WORKLOADS["za128"]
+    n = W.n
+    pos, _ = W.particles()
+    R = Recon((n, n, n), box=W.box, precision="mixed", checkpoint=1, k_max=a.k_max)
+    R.deposit_particles(torch.from_numpy(pos).cuda())
+    st = R.solve()
+    g = torch.from_numpy(np.random.default_rng(1004).standard_normal((n, n, n))).cuda()
+    out = torch.empty((n, n, n), dtype=torch.float64, device="cuda")
+    R.adjoint(g, out)
+    barrier()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    fwd = bwd = 0.0
+    for _ in range(steps):
+        e[0].record(stream)
+        R.solve(record=False)
+        e[1].record(stream)
+        R.adjoint(g, out)
+        e[2].record(stream)
+        barrier()
+        fwd += e[0].elapsed_time(e[1])
+        bwd += e[1].elapsed_time(e[2])
+    R.close()
+    fwd, bwd = fwd / steps, bwd / steps
+    return {"workload": W.name, "precision": "mixed", "steps_per_solve": st.steps,
+            "forward_ms": fwd, "adjoint_ms": bwd, "adjoint_over_forward": bwd / fwd,
+            "adjoint_mcells_s": n ** 3 / (bwd * 1e-3) / 1e6,
+            "checkpoint_bytes": 5 * 8 * n ** 3 * a.k_max}
 
 
 def run_batch(a):

@@ -107,6 +107,10 @@ typedef struct {
                             multigrid loop, step acceptance), with no host round
                             trip until the solve ends; 0: host-driven loop that
                             reads each decision back.  profile forces 0.        */
+    int checkpoint;      /* 1: every step keeps phi_k, the tracer offsets and
+                            phidot_k on the device for recon_adjoint
+                            (5 x 8 bytes x cells x k_max, allocated at create);
+                            needs density_update = 0.  Default 0.               */
 } recon_params;
 
 /* Per-solve record.  The per-step arrays are optional caller-owned host
@@ -178,9 +182,21 @@ int recon_solve_batch(void* const* handles, int count, recon_stats* stats);
  * device), dst_bytes >= its size (ncells x 8, MESH_X ncells x 24). */
 int recon_field(void* h, int which, void* dst, size_t dst_bytes);
 
-/* Vector-Jacobian product of the last solve, from dL/d(delta_r) to
- * dL/d(rho) (the differentiable map rho -> delta_r).  Not available in this
- * build: returns RECON_E_UNSUPPORTED. */
+/* recon_adjoint: vector-Jacobian product of the last solve (Sec. II, App. A)
+ * from grad_delta_r = dL/d(delta_r) to grad_rho = dL/d(rho), with the step
+ * lengths alpha_k held at the values that solve chose (the limiter's choice
+ * is piecewise constant in rho; the Heaviside switches of the limiters have
+ * zero derivative almost everywhere).  rho is the density grid of the last
+ * recon_deposit (for RECON_PARTICLES: the particles' CIC grid).  Both buffers
+ * hold ncells doubles in C order (z fastest), host or device, caller-owned;
+ * delta_r is in the units recon_field returns it.  The sweep goes back
+ * through the steps with the states the solve kept (params.checkpoint = 1)
+ * and runs one adjoint linear solve per step with the forward's multigrid
+ * and tolerance.  One step of the sweep (the transpose of the tracers' CIC
+ * interpolation) accumulates with FP64 atomics, so results agree between runs
+ * to rounding, not bit for bit.  Afterwards recon_field returns the solve's
+ * outputs as before.  Returns RECON_E_INVALID for NULL arguments and
+ * RECON_E_STATE without checkpoints or a completed solve. */
 int recon_adjoint(void* h, const double* grad_delta_r, double* grad_rho);
 
 /* Release every device buffer of the handle (after finishing its stream). */

@@ -17,7 +17,7 @@ from . import _abi
 from ._abi import (RECON_FP64, RECON_MIXED, RECON_OK, RECON_NOT_CONVERGED, ReconError,  # noqa: F401
                    FIELDS)
 
-__all__ = ["Recon", "SolveStats", "default_params", "solve_batch", "RECON_FP64", "RECON_MIXED", "ReconError"]
+__all__ = ["Recon", "SolveStats", "default_params", "solve_batch", "reconstruct", "RECON_FP64", "RECON_MIXED", "ReconError"]
 
 
 def default_params(n, box=None, precision="fp64", **overrides):
@@ -154,9 +154,17 @@ class Recon:
         _abi.check(self._lib.recon_field(self._h, code, _ptr(out), nbytes), "recon_field")
         return out
 
-    def adjoint(self, grad_delta_r, grad_rho):
-        return _abi.check(self._lib.recon_adjoint(self._h, _ptr(grad_delta_r), _ptr(grad_rho)),
-                          "recon_adjoint")
+    def adjoint(self, grad_delta_r, grad_rho=None):
+        """dL/d rho of the last solve from dL/d delta_r (recon_adjoint; the
+        handle needs checkpoint=1).  Returns grad_rho (a new device tensor if
+        none is given)."""
+        import torch
+
+        if grad_rho is None:
+            grad_rho = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        _abi.check(self._lib.recon_adjoint(self._h, _ptr(grad_delta_r), _ptr(grad_rho)),
+                   "recon_adjoint")
+        return grad_rho
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -191,3 +199,24 @@ def solve_batch(recons, record=True):
     rc = lib.recon_solve_batch(hs, len(recons), sts)
     _abi.check(rc, "recon_solve_batch")
     return [r._stats_out(sts[b].status, sts[b], arrs[b], record) for b, r in enumerate(recons)]
+
+
+def reconstruct(recon, rho):
+    """delta_r of a density grid as a differentiable torch operation: the
+    forward pass deposits rho on the handle and solves; the backward pass is
+    recon_adjoint (the step lengths held fixed).  The handle must have been
+    created with checkpoint=1."""
+    import torch
+
+    class _Reconstruct(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, r):
+            recon.deposit_grid(r.detach().contiguous())
+            recon.solve(record=False)
+            return recon.field("delta_r")
+
+        @staticmethod
+        def backward(ctx, g):
+            return recon.adjoint(g.detach().contiguous())
+
+    return _Reconstruct.apply(rho)

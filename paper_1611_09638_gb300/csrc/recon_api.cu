@@ -101,6 +101,16 @@ struct Handle {
     double* replay_d = nullptr;  // replay_alpha on the device (or null)
     LimiterParams lp{};
 
+    // params.checkpoint: phi_k, tracer offsets and phidot_k of every step
+    // (5 x cells doubles per step) and the adjoint sweep's buffers
+    double* ckpt = nullptr;
+    struct {
+        double *phibar = nullptr, *xib = nullptr, *wbar = nullptr, *vb = nullptr, *gb = nullptr;
+        double *eb = nullptr, *dbar = nullptr, *mbar = nullptr;
+    } adj;
+    Ctl* actl = nullptr;   // control block of the adjoint's linear solves
+    CtlArrays aarr{};
+
     // params.device_loop: the whole solve as one graph with conditional nodes
     cudaStream_t gst[4] = {nullptr, nullptr, nullptr, nullptr};  // capture streams
     cudaGraphExec_t solve_exec = nullptr;
@@ -242,6 +252,9 @@ int check_params(const recon_params* p) {
     if (p->inner_vcycles < 1 || p->inner_vcycles > 8) return fail(RECON_E_INVALID, "need 1 <= inner_vcycles <= 8");
     if (p->density_update != 0 && p->density_update != 1) return fail(RECON_E_INVALID, "density_update must be 0 or 1");
     if (p->device_loop != 0 && p->device_loop != 1) return fail(RECON_E_INVALID, "device_loop must be 0 or 1");
+    if (p->checkpoint != 0 && p->checkpoint != 1) return fail(RECON_E_INVALID, "checkpoint must be 0 or 1");
+    if (p->checkpoint && p->density_update != 0)
+        return fail(RECON_E_INVALID, "checkpoint (the adjoint) needs density_update = 0");
     return RECON_OK;
 }
 
@@ -339,6 +352,7 @@ int deposit_step(Handle* H) {
 // t = Sigma + C + E, s = S t - mean (Eq. elliptic of App. A), R_k test.
 void step_head(Handle* H, const CtlHandles& h) {
     const recon_params& p = H->p;
+    if (H->ckpt) launch_ckpt_state(H->ctl, H->cells, H->phi, H->ox, H->oy, H->oz, H->ckpt, H->st);
     deposit_step(H);
     SourceParams sp{p.xi_m, p.v_m, p.climiter};
     launch_geometry_source(H->d, sp, H->phi, H->m, H->t, H->e6, H->part[0], H->part[1], H->st);
@@ -390,6 +404,7 @@ void mg_iter(Handle* H, const CtlHandles& h) {
 // the choice of alpha.
 void step_tail(Handle* H, const CtlHandles& h) {
     const recon_params& p = H->p;
+    if (H->ckpt) launch_ckpt_phidot(H->ctl, H->cells, H->phidot, H->ckpt, H->st);
     launch_smooth_S(H->d, p.s_side, H->phidot, nullptr, H->dphi, H->dphi32, H->v3, H->part[0],
                     nullptr, H->st);
     finish_reduce(H->part[0], 0, H->scal, SC_SUM_DPHI, H->st);
@@ -775,6 +790,93 @@ int solve(Handle* H, recon_stats* stats) {
     return H->hctl->status;
 }
 
+// ---- the adjoint sweep (adjoint.cu has the kernels)
+
+// Runs the linear solve L(a) u = rhs (rhs already in H->s, its sum of
+// squares in scal[SC_SUM_S2]) with the forward solve's multigrid, on the
+// adjoint's own control block; u is left in H->phidot.
+int adjoint_mg(Handle* H) {
+    const CtlHandles none{};
+    launch_ctl_init(H->ctl, H->st);
+    launch_ctl_step_begin(H->ctl, H->scal, H->arr, (double)H->cells, -1.0, none, H->st);
+    mg_head(H, none);
+    int rc = read_ctl(H);
+    while (!rc && H->hctl->go_mg) {
+        mg_iter(H, none);
+        rc = read_ctl(H);
+    }
+    return rc;
+}
+
+int adjoint(Handle* H, const double* gbar, double* grad) {
+    const Dims& d = H->d;
+    const int cells = H->cells;
+    const size_t n = (size_t)cells;
+    const recon_params& p = H->p;
+    cudaStream_t st = H->st;
+    const int K = H->hctl->k;  // advances of the last solve
+    const Ctl saved = *H->hctl;
+    const double* alpha_dev = H->arr.alpha;  // the forward's step lengths
+    auto& A = H->adj;
+    CK(cudaMemcpyAsync(A.dbar, gbar, n * sizeof(double), cudaMemcpyDefault, st));
+    launch_adj_lap(d, A.dbar, A.phibar, st);
+    CK(cudaMemsetAsync(A.xib, 0, 3 * n * sizeof(double), st));
+    CK(cudaMemsetAsync(A.wbar, 0, n * sizeof(double), st));
+    std::swap(H->ctl, H->actl);
+    std::swap(H->arr, H->aarr);
+    SourceParams sp{p.xi_m, p.v_m, p.climiter};
+    const double scale = fixed_scale((double)cells);
+    int rc = RECON_OK;
+    for (int k = K - 1; k >= 0 && !rc; --k) {
+        const double* base = H->ckpt + (size_t)k * 5 * n;
+        const double *phi_k = base, *ox = base + n, *oy = base + 2 * n, *oz = base + 3 * n;
+        const double* pd = base + 4 * n;
+        const double* alpha = alpha_dev + k;
+        // step k's forward quantities: m_k (and a_k), e_k, dphi_k, V_k
+        launch_deposit_tracers(d, ox, oy, oz, H->w, scale, H->mfix, st);
+        launch_mass_coef(cells, H->mfix, 1.0 / scale, p.a_min, H->m, H->a64,
+                         H->mixed ? H->c32[0] : nullptr, H->part[0], st);
+        launch_geometry_source(d, sp, phi_k, H->m, H->t, H->e6, H->part[0], H->part[1], st);
+        launch_smooth_S(d, p.s_side, pd, nullptr, H->dphi, nullptr, H->v3, nullptr, nullptr, st);
+        launch_node_velocity(d, H->e6, H->dphi, H->v3, H->v3 + n, H->v3 + 2 * n, st);
+        // back through the advance, V = e^-1 G and dphi = S phidot - mean
+        CK(cudaMemsetAsync(A.vb, 0, 3 * n * sizeof(double), st));
+        launch_adj_tracers(d, ox, oy, oz, H->v3, alpha, A.xib, A.vb, st);
+        launch_adj_velocity(d, H->e6, H->v3, A.vb, A.gb, A.eb, st);
+        launch_adj_dbar(d, alpha, A.phibar, A.gb, A.dbar, H->part[0], st);
+        finish_reduce(H->part[0], 0, H->scal, SC_ADJ_A, st);
+        launch_smooth_S(d, p.s_side, A.dbar, H->scal + SC_ADJ_A, H->s, nullptr, H->v3, nullptr,
+                        H->part[2], st);
+        finish_reduce(H->part[2], 0, H->scal, SC_SUM_S2, st);
+        // the linear solve: the adjoint solve with the same operator
+        rc = adjoint_mg(H);
+        if (rc) break;
+        // back through a = max(m, a_min), s = S t - mean, the source, the
+        // Hessian and the deposit
+        launch_adj_coef(d, H->phidot, pd, H->m, p.a_min, A.mbar, H->part[0], st);
+        finish_reduce(H->part[0], 0, H->scal, SC_ADJ_B, st);
+        launch_smooth_S(d, p.s_side, H->phidot, H->scal + SC_ADJ_B, H->t, nullptr, H->v3, nullptr,
+                        nullptr, st);
+        launch_adj_source(d, sp, H->e6, H->m, H->t, A.mbar, A.eb, st);
+        launch_adj_hess(d, A.eb, A.phibar, st);
+        launch_adj_deposit(d, ox, oy, oz, H->w, A.mbar, A.wbar, A.xib, st);
+    }
+    std::swap(H->ctl, H->actl);
+    std::swap(H->arr, H->aarr);
+    *H->hctl = saved;
+    if (rc) return rc;
+    // w = rho / mean(rho)
+    launch_adj_dot(cells, A.wbar, H->w, H->part[0], st);
+    finish_reduce(H->part[0], 0, H->scal, SC_ADJ_A, st);
+    launch_adj_final(cells, A.wbar, H->scal + SC_ADJ_A, H->scal + SC_SUM_RHO, A.dbar, st);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(grad, A.dbar, n * sizeof(double), cudaMemcpyDefault, st));
+    // the mass and coefficient of the final map again (recon_field)
+    deposit_step(H);
+    CK(cudaStreamSynchronize(st));
+    return RECON_OK;
+}
+
 bool is_device_ptr(const void* p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -820,6 +922,7 @@ int recon_default_params(recon_params* p, int n0, int n1, int n2) {
     p->inner_vcycles = 2;
     p->density_update = 0;
     p->device_loop = 1;
+    p->checkpoint = 0;
     return RECON_OK;
 }
 
@@ -882,6 +985,14 @@ int recon_create(void** out, const recon_params* p, void* cuda_stream) {
     H->arr.alpha = H->arr.Rk + km, H->arr.relres = H->arr.Rk + 2 * km;
     H->arr.ncycles = (int*)(H->arr.Rk + 3 * km);
     if (!H->replay.empty()) AL(H->replay_d, km);
+    if (p->checkpoint) {
+        AL(H->ckpt, 5 * n * km);
+        AL(H->adj.phibar, n); AL(H->adj.xib, 3 * n); AL(H->adj.wbar, n); AL(H->adj.vb, 3 * n);
+        AL(H->adj.gb, 3 * n); AL(H->adj.eb, 6 * n); AL(H->adj.dbar, n); AL(H->adj.mbar, n);
+        AL(H->actl, 1); AL(H->aarr.Rk, 4);
+        H->aarr.alpha = H->aarr.Rk + 1, H->aarr.relres = H->aarr.Rk + 2;
+        H->aarr.ncycles = (int*)(H->aarr.Rk + 3);
+    }
     for (int q = 0; q < 4; ++q) AL(H->part[q], kRedBlocks);
     if (!H->mixed) {
         H->u64.assign(nl, nullptr), H->f64.assign(nl, nullptr), H->c64.assign(nl, nullptr),
@@ -1113,8 +1224,14 @@ int recon_field(void* hp, int which, void* dst, size_t dst_bytes) {
 }
 
 int recon_adjoint(void* hp, const double* grad_delta_r, double* grad_rho) {
-    (void)hp, (void)grad_delta_r, (void)grad_rho;
-    return fail(RECON_E_UNSUPPORTED, "recon_adjoint is not available in this build");
+    g_err[0] = 0;
+    Handle* H = (Handle*)hp;
+    if (!H || !grad_delta_r || !grad_rho) return fail(RECON_E_INVALID, "handle or buffer is NULL");
+    if (!H->ckpt) return fail(RECON_E_STATE, "recon_adjoint needs params.checkpoint = 1 at create");
+    if (!H->solved) return fail(RECON_E_STATE, "recon_adjoint needs a completed recon_solve");
+    int rc = adjoint(H, grad_delta_r, grad_rho);
+    if (rc) cudaStreamSynchronize(H->st);
+    return rc;
 }
 
 void recon_destroy(void* hp) {

@@ -65,6 +65,8 @@ enum Scalar {
     SC_MIN_LAM,       // min lambda0
     SC_MAX_DR,        // max delta_r
     SC_ALPHA,         // step length of the current step
+    SC_ADJ_A,         // adjoint sweep: sums used for mean projections
+    SC_ADJ_B,
     SC_COUNT
 };
 
@@ -258,5 +260,32 @@ void launch_ctl_select_alpha(Ctl* c, double* scal, const CtlArrays& a, const dou
 void launch_ctl_step_end(Ctl* c, int k_max, const CtlHandles& h, cudaStream_t st);
 void launch_ctl_final(Ctl* c, int want, const CtlHandles& h, cudaStream_t st);
 void launch_ctl_final_mass(Ctl* c, const double* scal, cudaStream_t st);
+
+// ---- per-step checkpoints and the adjoint sweep (adjoint.cu) --------------
+// Slot k (= ctl->k) of base holds phi_k, the tracer offsets ox, oy, oz and
+// phidot_k of step k, 5 x cells doubles.
+void launch_ckpt_state(const Ctl* ctl, int cells, const double* phi, const double* ox,
+                       const double* oy, const double* oz, double* base, cudaStream_t st);
+void launch_ckpt_phidot(const Ctl* ctl, int cells, const double* phidot, double* base,
+                        cudaStream_t st);
+void launch_adj_lap(const Dims& d, const double* gbar, double* phibar, cudaStream_t st);
+void launch_adj_tracers(const Dims& d, const double* ox, const double* oy, const double* oz,
+                        const double* v3, const double* alpha, double* xb3, double* vb3,
+                        cudaStream_t st);
+void launch_adj_velocity(const Dims& d, const double* e6, const double* v3, const double* vb3,
+                         double* gb3, double* eb6, cudaStream_t st);
+void launch_adj_dbar(const Dims& d, const double* alpha, const double* phibar, const double* gb3,
+                     double* dbar, double* psum, cudaStream_t st);
+void launch_adj_coef(const Dims& d, const double* lam, const double* pd, const double* m,
+                     double a_min, double* mbar, double* psum, cudaStream_t st);
+void launch_adj_source(const Dims& d, const SourceParams& sp, const double* e6, const double* m,
+                       const double* tbar, double* mbar, double* eb6, cudaStream_t st);
+void launch_adj_hess(const Dims& d, const double* eb6, double* phibar, cudaStream_t st);
+void launch_adj_deposit(const Dims& d, const double* ox, const double* oy, const double* oz,
+                        const double* w, const double* mbar, double* wbar, double* xb3,
+                        cudaStream_t st);
+void launch_adj_dot(int cells, const double* a, const double* b, double* psum, cudaStream_t st);
+void launch_adj_final(int cells, const double* wbar, const double* sum_wbw, const double* sum_rho,
+                      double* grad, cudaStream_t st);
 
 }  // namespace recon

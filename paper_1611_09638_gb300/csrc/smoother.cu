@@ -45,6 +45,11 @@ static_assert(NUA <= NT && NF <= NT && NB == NT && NO == 2 * NT && NR <= 2 * NT,
 static_assert(TJ % 2 == 0 && RK % 2 == 0 && TK == 64, "row-pair colour mapping");
 static_assert(NR == 330 && (TJ + 2) * 32 == 320, "red task split");
 
+// ISO: the level has one spacing on every axis, so every face coefficient
+// carries the same factor hh = h^-2 / 2: the update sums the face sums
+// c + a_n and applies hh once, u = (sum (c + a_n) u_n - f / hh) / sum (c + a_n)
+// (1 / hh is a power of two); otherwise each face is scaled by its axis.
+template <bool ISO>
 __global__ void __launch_bounds__(NT) k_rbgs_stream(Dims d, float hx, float hy, float hz, int CI,
                                                     const float* __restrict__ u_old,
                                                     float* __restrict__ u_new,
@@ -134,14 +139,24 @@ __global__ void __launch_bounds__(NT) k_rbgs_stream(Dims d, float hx, float hy, 
     };
     // Gauss-Seidel value at smem offset e of the plane in slots (cu, mu, pu)
     // of u and a (current, previous, next plane) and cf of f.
+    const float ihh = 1.0f / hx;  // ISO: hx holds hh, a power of two
     auto gs = [&](int cu, int mu, int pu, int cf, int e) -> float {
         const float* ac = sa + cu;
+        const float* uc = su + cu;
         const float c = ac[e];
+        if (ISO) {
+            const float px = c + sa[pu + e], mx = c + sa[mu + e];
+            const float py = c + ac[e + RK], my = c + ac[e - RK];
+            const float pz = c + ac[e + 1], mz = c + ac[e - 1];
+            const float diag = (px + mx) + (py + my) + (pz + mz);
+            const float off = (px * su[pu + e] + mx * su[mu + e]) + (py * uc[e + RK] + my * uc[e - RK]) +
+                              (pz * uc[e + 1] + mz * uc[e - 1]);
+            return __fdividef(fmaf(-ihh, sf[cf + e], off), diag);
+        }
         const float apx = 0.5f * (c + sa[pu + e]) * hx, amx = 0.5f * (c + sa[mu + e]) * hx;
         const float apy = 0.5f * (c + ac[e + RK]) * hy, amy = 0.5f * (c + ac[e - RK]) * hy;
         const float apz = 0.5f * (c + ac[e + 1]) * hz, amz = 0.5f * (c + ac[e - 1]) * hz;
         const float diag = (apx + amx) + (apy + amy) + (apz + amz);
-        const float* uc = su + cu;
         const float off = (apx * su[pu + e] + amx * su[mu + e]) + (apy * uc[e + RK] + amy * uc[e - RK]) +
                           (apz * uc[e + 1] + amz * uc[e - 1]);
         return __fdividef(off - sf[cf + e], diag);
@@ -200,13 +215,19 @@ int launch_rbgs_fused<float>(const Level& L, const float* u_old, float* u_new, c
     if (nsweeps < 1 || d.n2 % TK || d.n1 % TJ || d.n0 % CI) return 0;
     static bool configured = false;
     if (!configured) {
-        cudaFuncSetAttribute(k_rbgs_stream, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        cudaFuncSetAttribute(k_rbgs_stream<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        cudaFuncSetAttribute(k_rbgs_stream<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
         configured = true;
     }
     dim3 grid(d.n2 / TK, d.n1 / TJ, d.n0 / CI);
     launch_counter()++;
-    k_rbgs_stream<<<grid, NT, SMEM, st>>>(d, (float)L.h2i[0], (float)L.h2i[1], (float)L.h2i[2], CI,
-                                          u_old, u_new, f, a);
+    if (L.h2i[0] == L.h2i[1] && L.h2i[1] == L.h2i[2]) {
+        const float hh = (float)(0.5 * L.h2i[0]);  // 2^-(2l+1): exact
+        k_rbgs_stream<true><<<grid, NT, SMEM, st>>>(d, hh, hh, hh, CI, u_old, u_new, f, a);
+    } else {
+        k_rbgs_stream<false><<<grid, NT, SMEM, st>>>(d, (float)L.h2i[0], (float)L.h2i[1],
+                                                     (float)L.h2i[2], CI, u_old, u_new, f, a);
+    }
     return 1;
 }
 

@@ -2,6 +2,7 @@
 // than the multigrid solve: CIC deposits in 64-bit fixed point, geometry of
 // the map x = xi + grad phi, the limited source of Eq. (elliptic), the
 // smoothing operator S, the step limiter, the mesh advance and the outputs.
+#include "geometry.cuh"
 #include "recon_internal.cuh"
 #include "reduce.cuh"
 
@@ -14,92 +15,10 @@ inline int nblocks(long long work) { return (int)((work + kThreads - 1) / kThrea
 
 // ---------------------------------------------------------------- helpers
 
-struct Sym3 {
-    double xx, yy, zz, xy, xz, yz;
-};
-
-// Hessian of f at node (i,j,k): 3-point second differences on the diagonal,
-// 4-point centred cross differences off it.
-__device__ inline Sym3 hessian(const Dims& d, const double* __restrict__ f, int i, int j, int k) {
-    const double c = f[cell_index(d, i, j, k)];
-    Sym3 H;
-    H.xx = f[cell_index(d, i + 1, j, k)] - 2.0 * c + f[cell_index(d, i - 1, j, k)];
-    H.yy = f[cell_index(d, i, j + 1, k)] - 2.0 * c + f[cell_index(d, i, j - 1, k)];
-    H.zz = f[cell_index(d, i, j, k + 1)] - 2.0 * c + f[cell_index(d, i, j, k - 1)];
-    H.xy = 0.25 * (f[cell_index(d, i + 1, j + 1, k)] - f[cell_index(d, i + 1, j - 1, k)] -
-                   f[cell_index(d, i - 1, j + 1, k)] + f[cell_index(d, i - 1, j - 1, k)]);
-    H.xz = 0.25 * (f[cell_index(d, i + 1, j, k + 1)] - f[cell_index(d, i + 1, j, k - 1)] -
-                   f[cell_index(d, i - 1, j, k + 1)] + f[cell_index(d, i - 1, j, k - 1)]);
-    H.yz = 0.25 * (f[cell_index(d, i, j + 1, k + 1)] - f[cell_index(d, i, j + 1, k - 1)] -
-                   f[cell_index(d, i, j - 1, k + 1)] + f[cell_index(d, i, j - 1, k - 1)]);
-    return H;
-}
-
-__device__ inline double det3(const Sym3& e) {
-    return e.xx * (e.yy * e.zz - e.yz * e.yz) - e.xy * (e.xy * e.zz - e.yz * e.xz) +
-           e.xz * (e.xy * e.yz - e.yy * e.xz);
-}
-
-// det(e - lam I) and its derivative in lam.
-__device__ inline void charpoly(const Sym3& e, double lam, double& p, double& dp) {
-    const double a = e.xx - lam, b = e.yy - lam, c = e.zz - lam;
-    p = a * (b * c - e.yz * e.yz) - e.xy * (e.xy * c - e.yz * e.xz) + e.xz * (e.xy * e.yz - b * e.xz);
-    dp = -((b * c - e.yz * e.yz) + (a * c - e.xz * e.xz) + (a * b - e.xy * e.xy));
-}
-
-// Smallest eigenvalue of a symmetric 3x3 matrix: the trigonometric closed form
-// of the characteristic cubic (O. K. Smith, CACM 4, 168, 1961), then Newton
-// steps on det(e - lam I) while they reduce |det|.
-__device__ inline double min_eig_sym3(const Sym3& e) {
-    const double p1 = e.xy * e.xy + e.xz * e.xz + e.yz * e.yz;
-    const double q = (e.xx + e.yy + e.zz) * (1.0 / 3.0);
-    const double b11 = e.xx - q, b22 = e.yy - q, b33 = e.zz - q;
-    const double p2 = b11 * b11 + b22 * b22 + b33 * b33 + 2.0 * p1;
-    if (!(p2 > 0.0)) return q;
-    const double pp = sqrt(p2 * (1.0 / 6.0));
-    const double ip = 1.0 / pp;
-    Sym3 B;
-    B.xx = b11 * ip, B.yy = b22 * ip, B.zz = b33 * ip;
-    B.xy = e.xy * ip, B.xz = e.xz * ip, B.yz = e.yz * ip;
-    double r = 0.5 * det3(B);
-    r = fmin(1.0, fmax(-1.0, r));
-    const double ang = acos(r) * (1.0 / 3.0);
-    double lam = q + 2.0 * pp * cos(ang + 2.0943951023931957);  // + 2 pi / 3
-    double p, dp;
-    charpoly(e, lam, p, dp);
-    for (int it = 0; it < 3; ++it) {
-        if (p == 0.0 || dp == 0.0) break;
-        const double cand = lam - p / dp;
-        double pc, dpc;
-        charpoly(e, cand, pc, dpc);
-        if (!(fabs(pc) < fabs(p))) break;
-        lam = cand, p = pc, dp = dpc;
-    }
-    return lam;
-}
-
-__device__ inline double climit(int reading, double xi_m, double lambda0) {
-    const double lam = lambda0 > 1e-12 ? lambda0 : 1e-12;
-    const double q = xi_m / lam;
-    double v;
-    if (reading == 1) v = q - (q - 1.0 > 0.0 ? 1.0 : 0.0);       // literal
-    else if (reading == 2) v = q * (q - 1.0 > 0.0 ? 1.0 : 0.0);  // step
-    else v = q - 1.0 > 0.0 ? q - 1.0 : 0.0;                      // soft
-    return 4.0 * v * v;
-}
-
 // lambda_min(M) > floor by Sylvester's criterion on M - floor I.
 __device__ inline bool pd_above(Sym3 M, double floor) {
     M.xx -= floor, M.yy -= floor, M.zz -= floor;
     return M.xx > 0.0 && (M.xx * M.yy - M.xy * M.xy) > 0.0 && det3(M) > 0.0;
-}
-
-// CIC weights along one axis for grid coordinate home + off: lower node and
-// fraction toward the upper one.
-__device__ inline void cic_offset(int home, double off, int& i0, double& f) {
-    const double fl = floor(off);
-    f = off - fl;
-    i0 = home + (int)fl;
 }
 
 __device__ inline void cic_abs(double x, int n, int& i0, double& f) {
@@ -218,6 +137,65 @@ __global__ void k_deposit_tracers(Dims d, const double* __restrict__ ox,
                                  scale);
             }
         }
+    }
+}
+
+// The same deposit with shared-memory accumulation: a block takes the
+// tracers whose home nodes form a DTI x DTJ x DTK tile and adds each corner
+// weight into a copy of the tile plus DH nodes on every side held in shared
+// memory, then adds the non-zero cells of that copy to the grid.  A tracer
+// whose stencil leaves the copy adds to the grid directly.  The fixed-point
+// sums are integers, so the result is bit-identical to k_deposit_tracers
+// while the grid sees ~4x fewer atomics.
+constexpr int DTI = 8, DTJ = 16, DTK = 32, DH = 2;
+constexpr int DRI = DTI + 2 * DH, DRJ = DTJ + 2 * DH, DRK = DTK + 2 * DH;
+constexpr int DCELLS = DRI * DRJ * DRK;
+constexpr size_t kDepSmem = sizeof(unsigned long long) * DCELLS;
+
+__global__ void __launch_bounds__(256) k_deposit_tracers_tiled(Dims d, const double* __restrict__ ox,
+                                                               const double* __restrict__ oy,
+                                                               const double* __restrict__ oz,
+                                                               const double* __restrict__ w,
+                                                               double scale,
+                                                               unsigned long long* __restrict__ mfix) {
+    extern __shared__ unsigned long long acc[];
+    const int t = threadIdx.x;
+    for (int e = t; e < DCELLS; e += blockDim.x) acc[e] = 0ull;
+    __syncthreads();
+    const int ti = blockIdx.z * DTI, tj = blockIdx.y * DTJ, tk = blockIdx.x * DTK;
+    for (int q = t; q < DTI * DTJ * DTK; q += blockDim.x) {
+        const int li = q / (DTJ * DTK), lj = (q / DTK) % DTJ, lk = q % DTK;
+        const int i = ti + li, j = tj + lj, k = tk + lk;
+        const int c = cell_index(d, i, j, k);
+        int i0, j0, k0;
+        double fx, fy, fz;
+        cic_offset(i, ox[c], i0, fx);
+        cic_offset(j, oy[c], j0, fy);
+        cic_offset(k, oz[c], k0, fz);
+        const double m = w[c];
+        const int bi = i0 - ti + DH, bj = j0 - tj + DH, bk = k0 - tk + DH;
+        const bool local = bi >= 0 && bi + 1 < DRI && bj >= 0 && bj + 1 < DRJ && bk >= 0 && bk + 1 < DRK;
+        for (int di = 0; di < 2; ++di) {
+            const double wx = di ? fx : 1.0 - fx;
+            for (int dj = 0; dj < 2; ++dj) {
+                const double wy = dj ? fy : 1.0 - fy;
+                for (int dk = 0; dk < 2; ++dk) {
+                    const double wz = dk ? fz : 1.0 - fz;
+                    const unsigned long long qv = (unsigned long long)llrint(m * (wx * wy * wz) * scale);
+                    if (local)
+                        atomicAdd(&acc[((bi + di) * DRJ + (bj + dj)) * DRK + (bk + dk)], qv);
+                    else
+                        atomicAdd(&mfix[cell_index(d, i0 + di, j0 + dj, k0 + dk)], qv);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int e = t; e < DCELLS; e += blockDim.x) {
+        const unsigned long long v = acc[e];
+        if (!v) continue;  // every contribution is >= 0, so 0 means none
+        const int ri = e / (DRJ * DRK), rj = (e / DRK) % DRJ, rk = e % DRK;
+        atomicAdd(&mfix[cell_index(d, ti - DH + ri, tj - DH + rj, tk - DH + rk)], v);
     }
 }
 
@@ -703,6 +681,17 @@ void launch_deposit_tracers(const Dims& d, const double* ox, const double* oy, c
                             const double* w, double scale, unsigned long long* mfix,
                             cudaStream_t st) {
     launch_counter()++;
+    if (d.n0 % DTI == 0 && d.n1 % DTJ == 0 && d.n2 % DTK == 0) {
+        static bool configured = false;
+        if (!configured) {
+            cudaFuncSetAttribute(k_deposit_tracers_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kDepSmem);
+            configured = true;
+        }
+        dim3 grid(d.n2 / DTK, d.n1 / DTJ, d.n0 / DTI);
+        k_deposit_tracers_tiled<<<grid, 256, kDepSmem, st>>>(d, ox, oy, oz, w, scale, mfix);
+        return;
+    }
     k_deposit_tracers<<<nblocks(d.cells), kThreads, 0, st>>>(d, ox, oy, oz, w, scale, mfix);
 }
 

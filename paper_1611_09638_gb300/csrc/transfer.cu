@@ -38,6 +38,9 @@ constexpr int RSMEM = (int)sizeof(float) * RPL * (2 * SUA + SFF + 1);
 static_assert(NUA <= 2 * RT && NFC <= 2 * RT, "fetch rounds");
 static_assert((FJ / 2) * (FK / 2) == RT, "one coarse node per thread");
 
+// ISO: one spacing on every axis; hx then holds hh = h^-2 / 2, applied once
+// to the sums of the face sums c + a_n (see k_rbgs_stream).
+template <bool ISO>
 __global__ void __launch_bounds__(RT) k_resid_restrict_stream(Dims df, Dims dc, float hx, float hy,
                                                               float hz, int CIc,
                                                               const float* __restrict__ u,
@@ -123,14 +126,25 @@ __global__ void __launch_bounds__(RT) k_resid_restrict_stream(Dims df, Dims dc, 
                 const int e = res_e[m];
                 if (e < 0) continue;
                 const float c = ac[e];
-                const float apx = 0.5f * (c + sa[pu + e]) * hx, amx = 0.5f * (c + sa[mu + e]) * hx;
-                const float apy = 0.5f * (c + ac[e + RRK]) * hy, amy = 0.5f * (c + ac[e - RRK]) * hy;
-                const float apz = 0.5f * (c + ac[e + 1]) * hz, amz = 0.5f * (c + ac[e - 1]) * hz;
-                const float diag = (apx + amx) + (apy + amy) + (apz + amz);
-                const float off = (apx * su[pu + e] + amx * su[mu + e]) +
-                                  (apy * uc[e + RRK] + amy * uc[e - RRK]) +
-                                  (apz * uc[e + 1] + amz * uc[e - 1]);
-                sr[e] = sf[cf + e] - (off - diag * uc[e]);
+                if (ISO) {
+                    const float px = c + sa[pu + e], mx = c + sa[mu + e];
+                    const float py = c + ac[e + RRK], my = c + ac[e - RRK];
+                    const float pz = c + ac[e + 1], mz = c + ac[e - 1];
+                    const float diag = (px + mx) + (py + my) + (pz + mz);
+                    const float off = (px * su[pu + e] + mx * su[mu + e]) +
+                                      (py * uc[e + RRK] + my * uc[e - RRK]) +
+                                      (pz * uc[e + 1] + mz * uc[e - 1]);
+                    sr[e] = fmaf(-hx, fmaf(-diag, uc[e], off), sf[cf + e]);
+                } else {
+                    const float apx = 0.5f * (c + sa[pu + e]) * hx, amx = 0.5f * (c + sa[mu + e]) * hx;
+                    const float apy = 0.5f * (c + ac[e + RRK]) * hy, amy = 0.5f * (c + ac[e - RRK]) * hy;
+                    const float apz = 0.5f * (c + ac[e + 1]) * hz, amz = 0.5f * (c + ac[e - 1]) * hz;
+                    const float diag = (apx + amx) + (apy + amy) + (apz + amz);
+                    const float off = (apx * su[pu + e] + amx * su[mu + e]) +
+                                      (apy * uc[e + RRK] + amy * uc[e - RRK]) +
+                                      (apz * uc[e + 1] + amz * uc[e - 1]);
+                    sr[e] = sf[cf + e] - (off - diag * uc[e]);
+                }
             }
         }
         __syncthreads();
@@ -160,11 +174,12 @@ int launch_resid_restrict_stream(const Level& fine, const Level& coarse, const f
     if (!fine.coarsen[0] || !fine.coarsen[1] || !fine.coarsen[2]) return 0;
     if (df.n2 % FK || df.n1 % FJ || df.n0 < 4) return 0;
     if (!g_resident) {
-        cudaFuncSetAttribute(k_resid_restrict_stream, cudaFuncAttributeMaxDynamicSharedMemorySize, RSMEM);
+        cudaFuncSetAttribute(k_resid_restrict_stream<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, RSMEM);
+        cudaFuncSetAttribute(k_resid_restrict_stream<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, RSMEM);
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_resid_restrict_stream, RT, RSMEM);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_resid_restrict_stream<true>, RT, RSMEM);
         g_resident = sms * per_sm > 0 ? sms * per_sm : 1;
     }
     // coarse planes per block: fewest rounds of resident blocks times the
@@ -181,8 +196,15 @@ int launch_resid_restrict_stream(const Level& fine, const Level& coarse, const f
     }
     dim3 grid(df.n2 / FK, df.n1 / FJ, n0c / best);
     launch_counter()++;
-    k_resid_restrict_stream<<<grid, RT, RSMEM, st>>>(df, coarse.d, (float)fine.h2i[0], (float)fine.h2i[1],
-                                                    (float)fine.h2i[2], best, u, f, a, out);
+    if (fine.h2i[0] == fine.h2i[1] && fine.h2i[1] == fine.h2i[2]) {
+        const float hh = (float)(0.5 * fine.h2i[0]);  // 2^-(2l+1): exact
+        k_resid_restrict_stream<true><<<grid, RT, RSMEM, st>>>(df, coarse.d, hh, hh, hh, best, u, f, a,
+                                                               out);
+    } else {
+        k_resid_restrict_stream<false><<<grid, RT, RSMEM, st>>>(df, coarse.d, (float)fine.h2i[0],
+                                                                (float)fine.h2i[1], (float)fine.h2i[2],
+                                                                best, u, f, a, out);
+    }
     return 1;
 }
 

@@ -64,12 +64,12 @@ def test_struct_layout_matches_header(tmp_path):
     assert got == want
 
 
-def test_adjoint_reports_unsupported_and_errors_are_text():
+def test_errors_are_reported_as_status_and_text():
     from paper_1611_09638_gb300 import _abi
 
     lib = _abi.load()
-    assert lib.recon_adjoint(None, None, None) == _abi.RECON_E_UNSUPPORTED
-    assert b"not available" in lib.recon_last_error()
+    assert lib.recon_adjoint(None, None, None) == _abi.RECON_E_INVALID
+    assert b"NULL" in lib.recon_last_error()
     assert lib.recon_solve(None, None) == _abi.RECON_E_INVALID
 
 
@@ -79,7 +79,8 @@ def test_create_rejects_bad_params_before_touching_the_device():
     lib = _abi.load()
     h = C.c_void_p()
     for bad in ({"xi_m": 1.5}, {"v_m": 0.5}, {"nu1": 0, "nu2": 0}, {"s_side": 0.3},
-                {"device_loop": 2}, {"density_update": 3}, {"inner_vcycles": 0}):
+                {"device_loop": 2}, {"density_update": 3}, {"inner_vcycles": 0},
+                {"checkpoint": 2}, {"checkpoint": 1, "density_update": 1}):
         p = default_params((16, 16, 16), **bad)
         assert lib.recon_create(C.byref(h), C.byref(p), None) == _abi.RECON_E_INVALID
         assert h.value is None
@@ -95,6 +96,7 @@ def test_solve_runs_on_the_device_loop_by_default():
     from paper_1611_09638_gb300 import default_params
 
     assert default_params((16, 16, 16)).device_loop == 1
+    assert default_params((16, 16, 16)).checkpoint == 0
     assert default_params((16, 16, 16), device_loop=0).device_loop == 0
 
 

@@ -110,3 +110,19 @@ def test_batch_of_mixed_sizes_equals_single_solves():
             _same(st1, st, phi1, R.field("phi").cpu().numpy())
     for R in recons:
         R.close()
+
+
+def test_limiter_parameter_sweep_runs_every_setting():
+    """The App. B sweep driver on the 32^3 workload: every (xi_m, v_m) setting
+    gives a valid map and an r(k) record; the settings share the input."""
+    from paper_1611_09638_gb300 import sweeps
+
+    out = sweeps.run("za32", settings=sweeps.XI_M_SWEEP + sweeps.V_M_SWEEP, k_max=8)
+    assert len(out) == 6
+    for rec in out:
+        assert rec["status"] in (0, 1, 2) and rec["min_lambda0"] > 0.0
+        assert len(rec["k"]) == len(rec["r"]) > 3 and max(abs(x) for x in rec["r"]) <= 1.0
+        assert rec["R0"] == out[0]["R0"]  # the first step's source does not see C or E at phi = 0
+    # the duplicated (1/10, 10) setting is the same solve
+    a = [r for r in out if r["xi_m"] == 0.1 and r["v_m"] == 10.0]
+    assert len(a) == 2 and a[0]["r"] == a[1]["r"] and a[0]["Rk"] == a[1]["Rk"]

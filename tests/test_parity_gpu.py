@@ -330,3 +330,39 @@ def test_full_size_256_deposit_and_invariants(lpt256):
     assert k >= len(af) // 2
     if k == len(af):
         assert rel(phis["mixed"][0], phis["fp64"][0]) <= 1e-4
+
+
+def test_full_size_512_deposit_and_invariants():
+    """The 512^3 / 800 Mpc/h 2LPT configuration (seed 1002) in mixed precision:
+    the deposit against the oracle on every cell, then the properties of the
+    solve that hold at any size (mass, positive-definite map above the floor,
+    delta_r bound, inner tolerance met every step, delta_r = -lap phi on
+    sampled nodes)."""
+    n, box = 512, 800.0
+    pos_h, _ = lpt_particles(n, box, 1002, order=2)
+    ref = O.cic_deposit((n, n, n), pos_h / (box / n))
+    with Recon((n, n, n), box=box, precision="mixed") as R:
+        R.deposit_particles(torch.from_numpy(pos_h).cuda())
+        del pos_h
+        rho = R.field("density").cpu().numpy()
+        assert np.abs(rho - ref).max() <= 1e-10 * ref.max()
+        d = rho / rho.mean() - 1.0
+        print(f"512^3 deposit: rms delta {d.std():.3f}, max {d.max():.1f}, "
+              f"empty cells {np.mean(rho == 0):.4f}")
+        assert d.std() > 1.0
+        del rho, ref, d
+        st = R.solve()
+        assert st.steps > 0 and st.status in (0, 1, 2)
+        assert st.mass_error <= 1e-12
+        assert st.min_det > 0 and st.min_lambda0 > 0.01
+        assert st.max_delta_r < 3 - 3 * 0.01
+        assert np.all(st.relres <= 1e-8)
+        phi = R.field("phi").cpu().numpy()
+        dr = R.field("delta_r").cpu().numpy()
+    rng = np.random.default_rng(6)
+    h2 = (box / n) ** 2
+    for i, j, k in rng.integers(0, n, size=(500, 3)):
+        lap = sum(phi[(i + di) % n, (j + dj) % n, (k + dk) % n] - phi[i, j, k]
+                  for di, dj, dk in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0),
+                                     (0, 0, 1), (0, 0, -1))) / h2
+        assert abs(dr[i, j, k] + lap) <= 1e-9 * max(1.0, abs(lap))
