@@ -11,5 +11,7 @@ __device__ inline void cp_async16(void* smem, const void* gmem) {
 }
 __device__ inline void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ inline void cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
+// all but the most recently committed group complete
+__device__ inline void cp_wait_prior() { asm volatile("cp.async.wait_group 1;\n" ::); }
 
 }  // namespace recon

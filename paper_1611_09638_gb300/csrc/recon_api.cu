@@ -12,6 +12,8 @@
 #include <cstring>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/recon.h"
 #include "recon_internal.cuh"
 
@@ -39,6 +41,12 @@ int fail(int code, const char* fmt, ...) {
     } while (0)
 
 // Kernels recorded in each body of the solve graph.
+// NVTX range for profiler timelines (no cost without a tool attached).
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
+
 struct GraphCounts {
     long long init = 0, step = 0, cont = 0, mg = 0, adv = 0, fin = 0;
 };
@@ -509,14 +517,18 @@ int solve_host(Handle* H) {
     const CtlHandles none{};
     solve_init(H);
     for (int k = 0; k < H->p.k_max; ++k) {
+        Range step_range("recon step");
         step_head(H, none);
         int rc = read_ctl(H);
         if (rc) return rc;
         if (!H->hctl->go_cont) break;
-        mg_head(H, none);
-        if ((rc = read_ctl(H))) return rc;
-        while (H->hctl->go_mg)
-            if ((rc = run_cycle(H))) return rc;
+        {
+            Range mg_range("recon multigrid");
+            mg_head(H, none);
+            if ((rc = read_ctl(H))) return rc;
+            while (H->hctl->go_mg)
+                if ((rc = run_cycle(H))) return rc;
+        }
         step_tail(H, none);
         if ((rc = read_ctl(H))) return rc;
         if (!H->hctl->go_adv) break;
@@ -747,6 +759,7 @@ int solve_finish(Handle* H, recon_stats* stats) {
 bool use_graph(const Handle* H) { return H->p.device_loop && !H->p.profile; }
 
 int solve(Handle* H, recon_stats* stats) {
+    Range range(use_graph(H) ? "recon_solve (graph)" : "recon_solve (host loop)");
     if (use_graph(H)) {
         int rc = solve_launch(H, stats != nullptr);
         if (rc) return rc;
@@ -809,6 +822,7 @@ int adjoint_mg(Handle* H) {
 }
 
 int adjoint(Handle* H, const double* gbar, double* grad) {
+    Range range("recon_adjoint");
     const Dims& d = H->d;
     const int cells = H->cells;
     const size_t n = (size_t)cells;
@@ -1142,6 +1156,7 @@ int recon_solve(void* hp, recon_stats* stats) {
 
 int recon_solve_batch(void* const* handles, int count, recon_stats* stats) {
     g_err[0] = 0;
+    Range range("recon_solve_batch");
     if (count < 0 || (count > 0 && !handles)) return fail(RECON_E_INVALID, "bad handle array");
     for (int b = 0; b < count; ++b) {
         Handle* H = (Handle*)handles[b];

@@ -10,16 +10,17 @@
 // of the tile is written out.  u is read from u_old and written to u_new
 // (another buffer), so halos read by a block are never values another block
 // has already updated: the result equals the in-place sweep node for node.
-// Shared memory holds rings of five u and a planes (tile + two-node ring in j,
-// four-node in k so that every row is whole 16-byte chunks) and three f
-// planes; plane q + 2 is fetched with 16-byte cp.async copies while planes q
-// and q - 1 are updated.  DRAM traffic is one read of u, a, f and one write
+// Shared memory holds rings of six u and a planes (tile + two-node ring in j,
+// four-node in k so that every row is whole 16-byte chunks) and four f
+// planes; while planes q and q - 1 are updated, the 16-byte cp.async copies
+// of plane q + 3 (u, a) and q + 2 (f) are issued and those of the plane
+// before them complete.  DRAM traffic is one read of u, a, f and one write
 // of u.  With u_old == nullptr the sweep starts from u = 0 and u is not read.
 //
-// The kernel is bound by instruction issue rather than DRAM, so every
-// shared-memory and global offset a thread uses is computed once per block:
-// the per-plane work is the cp.async issue, the stencil arithmetic and the
-// stores.
+// Every shared-memory and global offset a thread uses is computed once per
+// block, and the plane loop is unrolled so that the ring slots are
+// compile-time constants: the per-plane work is the cp.async issue, the
+// stencil arithmetic and the stores.
 #include "async_copy.cuh"
 #include "recon_internal.cuh"
 
@@ -34,7 +35,7 @@ constexpr int RJ = TJ + 2 * H;         // 12 rows held per plane
 constexpr int RK = TK + 2 * KO;        // 72 columns held per plane
 constexpr int PL = RJ * RK;            // floats per plane
 constexpr int CH = RK / 4;             // 16-byte chunks per row
-constexpr int SU = 5, SF = 3;          // ring slots of u / a and of f
+constexpr int SU = 6, SF = 4;          // ring slots of u / a and of f (two planes ahead)
 constexpr int SMEM = (int)sizeof(float) * PL * (2 * SU + SF);
 constexpr int NUA = RJ * CH;           // chunks of one u (or a) plane: 216
 constexpr int NF = (TJ + 2) * CH;      // chunks of one f plane (rows of the red ring): 180
@@ -49,8 +50,8 @@ static_assert(NR == 330 && (TJ + 2) * 32 == 320, "red task split");
 // carries the same factor hh = h^-2 / 2: the update sums the face sums
 // c + a_n and applies hh once, u = (sum (c + a_n) u_n - f / hh) / sum (c + a_n)
 // (1 / hh is a power of two); otherwise each face is scaled by its axis.
-template <bool ISO>
-__global__ void __launch_bounds__(NT) k_rbgs_stream(Dims d, float hx, float hy, float hz, int CI,
+template <bool ISO, int CI>
+__global__ void __launch_bounds__(NT) k_rbgs_stream(Dims d, float hx, float hy, float hz,
                                                     const float* __restrict__ u_old,
                                                     float* __restrict__ u_new,
                                                     const float* __restrict__ f,
@@ -61,8 +62,7 @@ __global__ void __launch_bounds__(NT) k_rbgs_stream(Dims d, float hx, float hy, 
     float* sf = sa + SU * PL;
     const int t = threadIdx.x;
     const int k0 = blockIdx.x * TK, j0 = blockIdx.y * TJ, i0 = blockIdx.z * CI;
-    const int iend = i0 + CI;
-    const int base = i0 - 2;  // first plane held
+    static_assert(CI % 2 == 0, "the plane parity of iteration it is (it + 1) & 1");
     const int plane = d.n1 * d.n2;
 
     // ---- offsets fixed for the whole block -------------------------------
@@ -113,6 +113,11 @@ __global__ void __launch_bounds__(NT) k_rbgs_stream(Dims d, float hx, float hy, 
     const int blk_row = 2 * (bw >> 1) + (blane >> 4), blk_c = 16 * (bw & 1) + (blane & 15);
     const int blk_e = (blk_row + H) * RK + (2 * blk_c + KO);
     const int blk_p = (j0 + blk_row + k0 + 1) & 1;
+    // the node offsets for an even and an odd plane
+    int red0[2], red1[2];
+#pragma unroll
+    for (int m = 0; m < 2; ++m) red0[m] = red_e[m] + red_p[m], red1[m] = red_e[m] + (1 ^ red_p[m]);
+    const int blk0 = blk_e + blk_p, blk1 = blk_e + (1 ^ blk_p);
     // outputs t and t + NT
     int out_s[2], out_g[2];
 #pragma unroll
@@ -123,19 +128,23 @@ __global__ void __launch_bounds__(NT) k_rbgs_stream(Dims d, float hx, float hy, 
         out_g[m] = ((j0 + jj) << d.s2) + k0 + kk;
     }
 
-    auto slot_u = [&](int q) { return ((q - base) % SU) * PL; };
-    auto slot_f = [&](int q) { return ((q - base) % SF) * PL; };
+    // Plane x is held in ring slot (x - (i0 - 2)) mod SU of u and a and
+    // (x - (i0 - 2)) mod SF of f.  The plane loop is unrolled, so with
+    // q = i0 - 1 + it every slot offset below is a compile-time constant.
+    // Copies run two planes ahead: iteration it issues u, a of plane q + 3
+    // and f of plane q + 2 and then waits only for the previous iteration's
+    // copies, so one group is always in flight while a plane is updated.
     auto pbase = [&](int q) { return (q & (d.n0 - 1)) * plane; };
-    auto fetch_ua = [&](int q) {
+    auto fetch_ua = [&](int q, int slot) {
         if (ua_s >= 0) {
-            const int so = slot_u(q) + ua_s, g = pbase(q) + ua_g;
+            const int so = slot + ua_s, g = pbase(q) + ua_g;
             if (u_old) cp_async16(su + so, u_old + g);
             else *reinterpret_cast<float4*>(su + so) = make_float4(0.f, 0.f, 0.f, 0.f);
             cp_async16(sa + so, a + g);
         }
     };
-    auto fetch_f = [&](int q) {
-        if (f_s >= 0) cp_async16(sf + slot_f(q) + f_s, f + pbase(q) + f_g);
+    auto fetch_f = [&](int q, int slot) {
+        if (f_s >= 0) cp_async16(sf + slot + f_s, f + pbase(q) + f_g);
     };
     // Gauss-Seidel value at smem offset e of the plane in slots (cu, mu, pu)
     // of u and a (current, previous, next plane) and cf of f.
@@ -162,43 +171,51 @@ __global__ void __launch_bounds__(NT) k_rbgs_stream(Dims d, float hx, float hy, 
         return __fdividef(off - sf[cf + e], diag);
     };
 
-    // prologue: u, a of planes i0-2 .. i0; f of plane i0-1
-    fetch_ua(i0 - 2);
-    fetch_ua(i0 - 1);
-    fetch_ua(i0);
-    fetch_f(i0 - 1);
+    // prologue: u, a of planes i0-2 .. i0 and f of plane i0-1 (waited for);
+    // u, a of plane i0+1 and f of plane i0 (left in flight)
+    fetch_ua(i0 - 2, 0 * PL);
+    fetch_ua(i0 - 1, 1 * PL);
+    fetch_ua(i0, 2 * PL);
+    fetch_f(i0 - 1, 1 * PL);
     cp_commit();
     cp_wait_all();
     __syncthreads();
+    fetch_ua(i0 + 1, 3 * PL);
+    fetch_f(i0, 2 * PL);
+    cp_commit();
 
-    for (int q = i0 - 1; q <= iend; ++q) {
-        if (q + 2 <= iend + 1) fetch_ua(q + 2);
-        if (q + 1 <= iend) fetch_f(q + 1);
+#pragma unroll
+    for (int it = 0; it < CI + 2; ++it) {
+        const int q = i0 - 1 + it;  // plane of the red update
+        if (it < CI) {
+            fetch_ua(q + 3, ((it + 4) % SU) * PL);
+            fetch_f(q + 2, ((it + 3) % SF) * PL);
+        }
         cp_commit();
         // red update of plane q on the tile + 1-node ring (reads old black)
         {
-            const int cu = slot_u(q), mu = slot_u(q - 1), pu = slot_u(q + 1), cf = slot_f(q);
-            const int qp = q & 1;
+            const int cu = ((it + 1) % SU) * PL, mu = (it % SU) * PL, pu = ((it + 2) % SU) * PL;
+            const int cf = ((it + 1) % SF) * PL;
 #pragma unroll
             for (int m = 0; m < 2; ++m)
                 if (red_e[m] >= 0) {
-                    const int e = red_e[m] + (qp ^ red_p[m]);
+                    const int e = ((it + 1) & 1) ? red1[m] : red0[m];
                     su[cu + e] = gs(cu, mu, pu, cf, e);
                 }
         }
         __syncthreads();
-        // black update of plane p = q-1 on the tile, then write the tile
-        const int p = q - 1;
-        if (p >= i0) {
-            const int cu = slot_u(p), mu = slot_u(p - 1), pu = slot_u(p + 1), cf = slot_f(p);
-            const int e = blk_e + ((p & 1) ^ blk_p);
+        // black update of plane p = q - 1 on the tile, then write the tile
+        if (it >= 2) {
+            const int cu = (it % SU) * PL, mu = ((it - 1) % SU) * PL, pu = ((it + 1) % SU) * PL;
+            const int cf = (it % SF) * PL;
+            const int e = (it & 1) ? blk1 : blk0;
             su[cu + e] = gs(cu, mu, pu, cf, e);
             __syncthreads();
-            const int gb = pbase(p);
+            const int gb = pbase(q - 1);
 #pragma unroll
             for (int m = 0; m < 2; ++m) u_new[gb + out_g[m]] = su[cu + out_s[m]];
         }
-        cp_wait_all();
+        cp_wait_prior();
         __syncthreads();
     }
 }
@@ -215,18 +232,18 @@ int launch_rbgs_fused<float>(const Level& L, const float* u_old, float* u_new, c
     if (nsweeps < 1 || d.n2 % TK || d.n1 % TJ || d.n0 % CI) return 0;
     static bool configured = false;
     if (!configured) {
-        cudaFuncSetAttribute(k_rbgs_stream<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
-        cudaFuncSetAttribute(k_rbgs_stream<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        cudaFuncSetAttribute(k_rbgs_stream<true, CI>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        cudaFuncSetAttribute(k_rbgs_stream<false, CI>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
         configured = true;
     }
     dim3 grid(d.n2 / TK, d.n1 / TJ, d.n0 / CI);
     launch_counter()++;
     if (L.h2i[0] == L.h2i[1] && L.h2i[1] == L.h2i[2]) {
         const float hh = (float)(0.5 * L.h2i[0]);  // 2^-(2l+1): exact
-        k_rbgs_stream<true><<<grid, NT, SMEM, st>>>(d, hh, hh, hh, CI, u_old, u_new, f, a);
+        k_rbgs_stream<true, CI><<<grid, NT, SMEM, st>>>(d, hh, hh, hh, u_old, u_new, f, a);
     } else {
-        k_rbgs_stream<false><<<grid, NT, SMEM, st>>>(d, (float)L.h2i[0], (float)L.h2i[1],
-                                                     (float)L.h2i[2], CI, u_old, u_new, f, a);
+        k_rbgs_stream<false, CI><<<grid, NT, SMEM, st>>>(d, (float)L.h2i[0], (float)L.h2i[1],
+                                                         (float)L.h2i[2], u_old, u_new, f, a);
     }
     return 1;
 }

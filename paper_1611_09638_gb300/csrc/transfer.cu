@@ -40,9 +40,9 @@ static_assert((FJ / 2) * (FK / 2) == RT, "one coarse node per thread");
 
 // ISO: one spacing on every axis; hx then holds hh = h^-2 / 2, applied once
 // to the sums of the face sums c + a_n (see k_rbgs_stream).
-template <bool ISO>
+template <bool ISO, int CIc>
 __global__ void __launch_bounds__(RT) k_resid_restrict_stream(Dims df, Dims dc, float hx, float hy,
-                                                              float hz, int CIc,
+                                                              float hz,
                                                               const float* __restrict__ u,
                                                               const float* __restrict__ f,
                                                               const float* __restrict__ a,
@@ -55,8 +55,7 @@ __global__ void __launch_bounds__(RT) k_resid_restrict_stream(Dims df, Dims dc, 
     const int t = threadIdx.x;
     const int K0c = blockIdx.x * (FK / 2), J0c = blockIdx.y * (FJ / 2), I0c = blockIdx.z * CIc;
     const int k0 = 2 * K0c, j0 = 2 * J0c;
-    const int pS = 2 * I0c - 1, pE = 2 * (I0c + CIc) - 1;  // residual planes of the block
-    const int pbase = pS - 1;                               // first u / a plane held
+    const int pS = 2 * I0c - 1;  // first residual plane of the block (odd)
     const int plane = df.n1 * df.n2;
 
     // ---- offsets fixed for the whole block -------------------------------
@@ -84,11 +83,12 @@ __global__ void __launch_bounds__(RT) k_resid_restrict_stream(Dims df, Dims dc, 
     const int rc_e = (2 * jc + RH) * RRK + 2 * kc + RKO;
     const int out_o = ((J0c + jc) << dc.s2) + K0c + kc;
 
-    auto slot_u = [&](int p) { return ((p - pbase) % SUA) * RPL; };
-    auto slot_f = [&](int p) { return ((p - pS) % SFF) * RPL; };
+    // Plane p is held in u / a slot (p - pS + 1) mod SUA and f slot
+    // (p - pS) mod SFF; the plane loop is unrolled (p = pS + it), so every
+    // slot offset is a compile-time constant.
     auto gplane = [&](int p) { return (p & (df.n0 - 1)) * plane; };
-    auto fetch_ua = [&](int p) {
-        const int so = slot_u(p), g = gplane(p);
+    auto fetch_ua = [&](int p, int so) {
+        const int g = gplane(p);
 #pragma unroll
         for (int m = 0; m < 2; ++m)
             if (ua_s[m] >= 0) {
@@ -96,29 +96,34 @@ __global__ void __launch_bounds__(RT) k_resid_restrict_stream(Dims df, Dims dc, 
                 cp_async16(sa + so + ua_s[m], a + g + ua_g[m]);
             }
     };
-    auto fetch_f = [&](int p) {
-        const int so = slot_f(p), g = gplane(p);
+    auto fetch_f = [&](int p, int so) {
+        const int g = gplane(p);
 #pragma unroll
         for (int m = 0; m < 2; ++m)
             if (f_s[m] >= 0) cp_async16(sf + so + f_s[m], f + g + f_g[m]);
     };
 
-    fetch_ua(pS - 1);
-    fetch_ua(pS);
-    fetch_ua(pS + 1);
-    fetch_f(pS);
+    fetch_ua(pS - 1, 0 * RPL);
+    fetch_ua(pS, 1 * RPL);
+    fetch_ua(pS + 1, 2 * RPL);
+    fetch_f(pS, 0 * RPL);
     cp_commit();
     cp_wait_all();
     __syncthreads();
 
     float acc = 0.f;
-    for (int p = pS; p <= pE; ++p) {
-        if (p + 2 <= pE + 1) fetch_ua(p + 2);
-        if (p + 1 <= pE) fetch_f(p + 1);
+#pragma unroll
+    for (int it = 0; it <= 2 * CIc; ++it) {
+        const int p = pS + it;
+        if (it < 2 * CIc) {
+            fetch_ua(p + 2, ((it + 3) % SUA) * RPL);
+            fetch_f(p + 1, ((it + 1) % SFF) * RPL);
+        }
         cp_commit();
         // residual r = f - L u of plane p on the tile and its low-side ring
         {
-            const int cu = slot_u(p), mu = slot_u(p - 1), pu = slot_u(p + 1), cf = slot_f(p);
+            const int cu = ((it + 1) % SUA) * RPL, mu = (it % SUA) * RPL;
+            const int pu = ((it + 2) % SUA) * RPL, cf = (it % SFF) * RPL;
             const float* ac = sa + cu;
             const float* uc = su + cu;
 #pragma unroll
@@ -153,8 +158,8 @@ __global__ void __launch_bounds__(RT) k_resid_restrict_stream(Dims df, Dims dc, 
         const float s = 0.25f * (0.25f * R[-RRK - 1] + 0.5f * R[-RRK] + 0.25f * R[-RRK + 1]) +
                         0.5f * (0.25f * R[-1] + 0.5f * R[0] + 0.25f * R[1]) +
                         0.25f * (0.25f * R[RRK - 1] + 0.5f * R[RRK] + 0.25f * R[RRK + 1]);
-        if (p & 1) {  // p = 2I + 1 closes coarse plane I and opens I + 1
-            if (p != pS) out[(((p - 1) >> 1) << (dc.s1 + dc.s2)) + out_o] = acc + 0.25f * s;
+        if (!(it & 1)) {  // p = 2I + 1 (odd) closes coarse plane I and opens I + 1
+            if (it > 0) out[((I0c - 1 + (it >> 1)) << (dc.s1 + dc.s2)) + out_o] = acc + 0.25f * s;
             acc = 0.25f * s;
         } else {
             acc += 0.5f * s;
@@ -166,6 +171,30 @@ __global__ void __launch_bounds__(RT) k_resid_restrict_stream(Dims df, Dims dc, 
 
 int g_resident = 0;  // blocks of the kernel resident on the device at once
 
+template <bool ISO, int CIc>
+void launch_rr(dim3 grid, const Dims& df, const Dims& dc, float hx, float hy, float hz,
+               const float* u, const float* f, const float* a, float* out, cudaStream_t st) {
+    static bool configured = false;
+    if (!configured) {
+        cudaFuncSetAttribute(k_resid_restrict_stream<ISO, CIc>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, RSMEM);
+        configured = true;
+    }
+    k_resid_restrict_stream<ISO, CIc><<<grid, RT, RSMEM, st>>>(df, dc, hx, hy, hz, u, f, a, out);
+}
+
+template <bool ISO>
+void launch_rr_ci(int ci, dim3 grid, const Dims& df, const Dims& dc, float hx, float hy, float hz,
+                  const float* u, const float* f, const float* a, float* out, cudaStream_t st) {
+    switch (ci) {
+        case 1: launch_rr<ISO, 1>(grid, df, dc, hx, hy, hz, u, f, a, out, st); break;
+        case 2: launch_rr<ISO, 2>(grid, df, dc, hx, hy, hz, u, f, a, out, st); break;
+        case 4: launch_rr<ISO, 4>(grid, df, dc, hx, hy, hz, u, f, a, out, st); break;
+        case 8: launch_rr<ISO, 8>(grid, df, dc, hx, hy, hz, u, f, a, out, st); break;
+        default: launch_rr<ISO, 16>(grid, df, dc, hx, hy, hz, u, f, a, out, st); break;
+    }
+}
+
 }  // namespace
 
 int launch_resid_restrict_stream(const Level& fine, const Level& coarse, const float* u,
@@ -174,12 +203,12 @@ int launch_resid_restrict_stream(const Level& fine, const Level& coarse, const f
     if (!fine.coarsen[0] || !fine.coarsen[1] || !fine.coarsen[2]) return 0;
     if (df.n2 % FK || df.n1 % FJ || df.n0 < 4) return 0;
     if (!g_resident) {
-        cudaFuncSetAttribute(k_resid_restrict_stream<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, RSMEM);
-        cudaFuncSetAttribute(k_resid_restrict_stream<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, RSMEM);
+        cudaFuncSetAttribute(k_resid_restrict_stream<true, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             RSMEM);
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_resid_restrict_stream<true>, RT, RSMEM);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_resid_restrict_stream<true, 8>, RT, RSMEM);
         g_resident = sms * per_sm > 0 ? sms * per_sm : 1;
     }
     // coarse planes per block: fewest rounds of resident blocks times the
@@ -198,12 +227,10 @@ int launch_resid_restrict_stream(const Level& fine, const Level& coarse, const f
     launch_counter()++;
     if (fine.h2i[0] == fine.h2i[1] && fine.h2i[1] == fine.h2i[2]) {
         const float hh = (float)(0.5 * fine.h2i[0]);  // 2^-(2l+1): exact
-        k_resid_restrict_stream<true><<<grid, RT, RSMEM, st>>>(df, coarse.d, hh, hh, hh, best, u, f, a,
-                                                               out);
+        launch_rr_ci<true>(best, grid, df, coarse.d, hh, hh, hh, u, f, a, out, st);
     } else {
-        k_resid_restrict_stream<false><<<grid, RT, RSMEM, st>>>(df, coarse.d, (float)fine.h2i[0],
-                                                                (float)fine.h2i[1], (float)fine.h2i[2],
-                                                                best, u, f, a, out);
+        launch_rr_ci<false>(best, grid, df, coarse.d, (float)fine.h2i[0], (float)fine.h2i[1],
+                            (float)fine.h2i[2], u, f, a, out, st);
     }
     return 1;
 }
