@@ -291,6 +291,69 @@ __global__ void k_smooth_axis(Dims d, int axis, double ws, const double* __restr
     }
 }
 
+// S in one pass: a block takes SJ x SK tiles of the (j, k) plane and streams
+// SCI planes along i; each plane (with a one-node ring) is staged in shared
+// memory and smoothed along k, then along j, and each thread keeps the last
+// two (j, k)-smoothed values of its column in registers for the pass along
+// i.  The three passes use the expressions of k_smooth_axis in the same order
+// (k, j, i), so the output equals the three-kernel form bit for bit; only the
+// order of the partial sums differs.  The grid is kRedBlocks blocks looping
+// over the tiles, so the partial sums are those of fixed blocks.
+constexpr int SJ = 8, SK = 32, SCI = 16;
+
+__global__ void __launch_bounds__(256) k_smooth_S_stream(Dims d, double ws,
+                                                         const double* __restrict__ in,
+                                                         const double* __restrict__ shift_sum,
+                                                         double* __restrict__ out,
+                                                         float* __restrict__ out32,
+                                                         double* __restrict__ psum,
+                                                         double* __restrict__ psq) {
+    __shared__ double pl[SJ + 2][SK + 2];  // plane with a one-node ring
+    __shared__ double sk[SJ + 2][SK];      // smoothed along k
+    const double w1 = 1.0 - 2.0 * ws;
+    const double shift = shift_sum ? *shift_sum / (double)d.cells : 0.0;
+    const int t = threadIdx.x, lj = t / SK, lk = t % SK;
+    const int tiles_k = d.n2 / SK, tiles_j = d.n1 / SJ;
+    const int ntiles = tiles_k * tiles_j * (d.n0 / SCI);
+    double s = 0.0, q = 0.0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int tk = tile % tiles_k, tj = (tile / tiles_k) % tiles_j, ti = tile / (tiles_k * tiles_j);
+        const int k0 = tk * SK, j0 = tj * SJ, i0 = ti * SCI;
+        double a2 = 0.0, a1 = 0.0;  // (j, k)-smoothed values of planes p - 2, p - 1
+        for (int p = i0 - 1; p <= i0 + SCI; ++p) {
+            for (int e = t; e < (SJ + 2) * (SK + 2); e += blockDim.x) {
+                const int r = e / (SK + 2), c = e - r * (SK + 2);
+                pl[r][c] = in[cell_index(d, p, j0 - 1 + r, k0 - 1 + c)];
+            }
+            __syncthreads();
+            for (int e = t; e < (SJ + 2) * SK; e += blockDim.x) {
+                const int r = e / SK, c = e - r * SK;
+                sk[r][c] = fma(ws, pl[r][c] + pl[r][c + 2], w1 * pl[r][c + 1]);
+            }
+            __syncthreads();
+            const double v = fma(ws, sk[lj][lk] + sk[lj + 2][lk], w1 * sk[lj + 1][lk]);
+            if (p > i0) {  // plane p - 1 is complete
+                const double o = fma(ws, a2 + v, w1 * a1) - shift;
+                const int c = cell_index(d, p - 1, j0 + lj, k0 + lk);
+                out[c] = o;
+                if (out32) out32[c] = (float)o;
+                s += o;
+                q = fma(o, o, q);
+            }
+            a2 = a1, a1 = v;
+            __syncthreads();  // pl and sk are refilled for the next plane
+        }
+    }
+    if (psum) {
+        s = block_reduce<OpSum>(s);
+        if (threadIdx.x == 0) psum[blockIdx.x] = s;
+    }
+    if (psq) {
+        q = block_reduce<OpSum>(q);
+        if (threadIdx.x == 0) psq[blockIdx.x] = q;
+    }
+}
+
 template <typename T>
 struct Hess3 {
     T xx, yy, zz, xy, xz, yz;
@@ -712,6 +775,12 @@ void launch_geometry_source(const Dims& d, const SourceParams& sp, const double*
 void launch_smooth_S(const Dims& d, double s_side, const double* in, const double* shift_sum,
                      double* out, float* out32, double* tmp2, double* part_sum, double* part_sq,
                      cudaStream_t st) {
+    if (d.n2 % SK == 0 && d.n1 % SJ == 0 && d.n0 % SCI == 0) {
+        launch_counter()++;
+        k_smooth_S_stream<<<kRedBlocks, 256, 0, st>>>(d, s_side, in, shift_sum, out, out32, part_sum,
+                                                      part_sq);
+        return;
+    }
     launch_counter() += 3;
     k_smooth_axis<<<kRedBlocks, kRedThreads, 0, st>>>(d, 2, s_side, in, nullptr, tmp2, nullptr,
                                                       nullptr, nullptr);
