@@ -88,17 +88,6 @@ __global__ void k_rbgs_colour64_unit(Dims d, int colour, double* __restrict__ u,
     u[c] = (o - f[c]) * inv_d[c];
 }
 
-template <typename T>
-__global__ void k_residual(Dims d, T hx, T hy, T hz, const T* __restrict__ u,
-                           const T* __restrict__ f, const T* __restrict__ a, T* __restrict__ r) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= d.cells) return;
-    int i, j, k;
-    cell_coords(d, c, i, j, k);
-    Stencil7<T> s = stencil7<T>(d, hx, hy, hz, i, j, k, c, u, a);
-    r[c] = f[c] - (s.off - s.diag * u[c]);
-}
-
 // FP64 residual r = f - L u of the finest level (unit spacing) from the
 // stored face coefficients A (F) and node diagonals D: since
 // L u = sum_n A_n u_n - D u_c, r = f + D u_c - sum_n A_n u_n is a chain of
@@ -185,7 +174,7 @@ __global__ void k_restrict(Dims df, Dims dc, int cx, int cy, int cz, const T* __
 
 // Residual r = f - L u evaluated at the fine nodes of each coarse node's
 // full-weighting stencil and restricted at once (the fine residual is never
-// stored); per node the same arithmetic as k_residual followed by k_restrict.
+// stored): per node the 7-point residual f - L u followed by the full weighting.
 template <typename T>
 __global__ void k_resid_restrict(Dims df, Dims dc, int cx, int cy, int cz, T hx, T hy, T hz,
                                  const T* __restrict__ u, const T* __restrict__ f,
@@ -349,13 +338,6 @@ void launch_rbgs_sweep(const Level& L, T* u, const T* f, const T* a, cudaStream_
 }
 
 template <typename T>
-void launch_residual(const Level& L, const T* u, const T* f, const T* a, T* r, cudaStream_t st) {
-    launch_counter()++;
-    k_residual<T><<<nblocks(L.d.cells), kThreads, 0, st>>>(L.d, (T)L.h2i[0], (T)L.h2i[1],
-                                                           (T)L.h2i[2], u, f, a, r);
-}
-
-template <typename T>
 void launch_restrict(const Level& fine, const Level& coarse, const T* in, T* out, cudaStream_t st) {
     launch_counter()++;
     k_restrict<T><<<nblocks(coarse.d.cells), kThreads, 0, st>>>(
@@ -430,8 +412,6 @@ void launch_correct(int cells, double* u, const float* e, cudaStream_t st) {
 
 #define RECON_INSTANTIATE(T)                                                                    \
     template void launch_rbgs_sweep<T>(const Level&, T*, const T*, const T*, cudaStream_t);   \
-    template void launch_residual<T>(const Level&, const T*, const T*, const T*, T*,           \
-                                     cudaStream_t);                                           \
     template void launch_restrict<T>(const Level&, const Level&, const T*, T*, cudaStream_t);  \
     template void launch_resid_restrict<T>(const Level&, const Level&, const T*, const T*,     \
                                            const T*, T*, cudaStream_t);                       \

@@ -124,8 +124,6 @@ template <>
 int launch_rbgs_fused<double>(const Level&, const double*, double*, const double*,
                               const double*, int, cudaStream_t);
 template <typename T>
-void launch_residual(const Level& L, const T* u, const T* f, const T* a, T* r, cudaStream_t st);
-template <typename T>
 void launch_restrict(const Level& fine, const Level& coarse, const T* in, T* out, cudaStream_t st);
 // full-weighting restriction of the residual f - L u, without storing it
 template <typename T>

@@ -126,27 +126,29 @@ __global__ void k_deposit_tracers(Dims d, const double* __restrict__ ox,
     cic_offset(i, ox[c], i0, fx);
     cic_offset(j, oy[c], j0, fy);
     cic_offset(k, oz[c], k0, fz);
-    const double m = w[c];
+    const double msc = w[c] * scale;
     for (int di = 0; di < 2; ++di) {
         const double wx = di ? fx : 1.0 - fx;
         for (int dj = 0; dj < 2; ++dj) {
-            const double wy = dj ? fy : 1.0 - fy;
+            const double wxy = wx * (dj ? fy : 1.0 - fy);
             for (int dk = 0; dk < 2; ++dk) {
                 const double wz = dk ? fz : 1.0 - fz;
-                atomic_add_fixed(&mfix[cell_index(d, i0 + di, j0 + dj, k0 + dk)], m * (wx * wy * wz),
-                                 scale);
+                atomicAdd(&mfix[cell_index(d, i0 + di, j0 + dj, k0 + dk)],
+                          (unsigned long long)llrint(msc * (wxy * wz)));
             }
         }
     }
 }
 
-// The same deposit with shared-memory accumulation: a block takes the
-// tracers whose home nodes form a DTI x DTJ x DTK tile and adds each corner
-// weight into a copy of the tile plus DH nodes on every side held in shared
-// memory, then adds the non-zero cells of that copy to the grid.  A tracer
+// The same deposit (same fixed-point values) with shared-memory accumulation:
+// a block takes the tracers whose home nodes form a DTI x DTJ x DTK tile and
+// adds each corner weight into a copy of the tile plus DH nodes on every side
+// held in shared memory, then adds the non-zero cells of that copy to the
+// grid.  A tracer
 // whose stencil leaves the copy adds to the grid directly.  The fixed-point
 // sums are integers, so the result is bit-identical to k_deposit_tracers
-// while the grid sees ~4x fewer atomics.
+// while the grid sees ~4x fewer atomics.  Per corner the weight product and
+// the scaled mass w * 2^F cost two FP64 multiplies and the conversion.
 constexpr int DTI = 8, DTJ = 16, DTK = 32, DH = 2;
 constexpr int DRI = DTI + 2 * DH, DRJ = DTJ + 2 * DH, DRK = DTK + 2 * DH;
 constexpr int DCELLS = DRI * DRJ * DRK;
@@ -172,16 +174,16 @@ __global__ void __launch_bounds__(256) k_deposit_tracers_tiled(Dims d, const dou
         cic_offset(i, ox[c], i0, fx);
         cic_offset(j, oy[c], j0, fy);
         cic_offset(k, oz[c], k0, fz);
-        const double m = w[c];
+        const double msc = w[c] * scale;
         const int bi = i0 - ti + DH, bj = j0 - tj + DH, bk = k0 - tk + DH;
         const bool local = bi >= 0 && bi + 1 < DRI && bj >= 0 && bj + 1 < DRJ && bk >= 0 && bk + 1 < DRK;
         for (int di = 0; di < 2; ++di) {
             const double wx = di ? fx : 1.0 - fx;
             for (int dj = 0; dj < 2; ++dj) {
-                const double wy = dj ? fy : 1.0 - fy;
+                const double wxy = wx * (dj ? fy : 1.0 - fy);
                 for (int dk = 0; dk < 2; ++dk) {
                     const double wz = dk ? fz : 1.0 - fz;
-                    const unsigned long long qv = (unsigned long long)llrint(m * (wx * wy * wz) * scale);
+                    const unsigned long long qv = (unsigned long long)llrint(msc * (wxy * wz));
                     if (local)
                         atomicAdd(&acc[((bi + di) * DRJ + (bj + dj)) * DRK + (bk + dk)], qv);
                     else
