@@ -312,8 +312,18 @@ void vcycle(Handle* H, MG<T>& g, int l, T* u, const T* f, bool zero_u) {
         streamed = launch_resid_restrict_stream(L, H->lv[l + 1], cur, f, g.c[l], g.f[l + 1], H->st);
     if (!streamed) launch_resid_restrict<T>(L, H->lv[l + 1], cur, f, g.c[l], g.f[l + 1], H->st);
     vcycle<T>(H, g, l + 1, g.u[l + 1], g.f[l + 1], true);
-    launch_prolong_add<T>(L, H->lv[l + 1], g.u[l + 1], cur, H->st);
-    smooth_sweeps<T>(H, l, H->p.nu2, &cur, &oth, f, g.c[l], false);
+    int nu2 = H->p.nu2;
+    bool folded = false;
+    if constexpr (sizeof(T) == sizeof(float)) {
+        // the coarse correction folded into the first post-smoothing sweep
+        if (nu2 >= 1 && launch_rbgs_prolong(L, H->lv[l + 1], g.u[l + 1], cur, oth, f, g.c[l], H->st)) {
+            std::swap(cur, oth);
+            nu2 -= 1;
+            folded = true;
+        }
+    }
+    if (!folded) launch_prolong_add<T>(L, H->lv[l + 1], g.u[l + 1], cur, H->st);
+    smooth_sweeps<T>(H, l, nu2, &cur, &oth, f, g.c[l], false);
     if (cur != u)
         cudaMemcpyAsync(u, cur, sizeof(T) * L.d.cells, cudaMemcpyDeviceToDevice, H->st);
 }

@@ -114,6 +114,14 @@ void launch_rbgs_sweep(const Level& L, T* u, const T* f, const T* a, cudaStream_
 int launch_resid_restrict_stream(const Level& fine, const Level& coarse, const float* u,
                                  const float* f, const float* a, float* out, cudaStream_t st);
 
+// The first post-smoothing sweep of an FP32 level with the V-cycle's
+// coarse-grid correction folded in (u_new <- RBGS(u_old + P(uc))) where the
+// level fits the streaming sweep and every axis is halved; returns 1, or 0
+// with nothing launched (then prolongate and sweep separately).
+bool rbgs_prolong_fits(const Level& fine);
+int launch_rbgs_prolong(const Level& fine, const Level& coarse, const float* uc, const float* u_old,
+                        float* u_new, const float* f, const float* a, cudaStream_t st);
+
 template <typename T>
 int launch_rbgs_fused(const Level& L, const T* u_old, T* u_new, const T* f, const T* a,
                       int nsweeps, cudaStream_t st);

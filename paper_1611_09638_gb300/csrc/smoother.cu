@@ -50,12 +50,19 @@ static_assert(NR == 330 && (TJ + 2) * 32 == 320, "red task split");
 // carries the same factor hh = h^-2 / 2: the update sums the face sums
 // c + a_n and applies hh once, u = (sum (c + a_n) u_n - f / hh) / sum (c + a_n)
 // (1 / hh is a power of two); otherwise each face is scaled by its axis.
-template <bool ISO, int CI>
+// PRO: the sweep also applies the coarse-grid correction of the V-cycle
+// first: u_old + P(uc) is swept, P the trilinear prolongation from the
+// coarse level dc (every axis halved).  Each thread loads its 4-node chunk of
+// u into registers with the 12 coarse values the chunk's interpolation needs
+// and stores the sum to shared memory at the end of the iteration, so the
+// loads overlap that iteration's updates.
+template <bool ISO, int CI, bool PRO>
 __global__ void __launch_bounds__(NT) k_rbgs_stream(Dims d, float hx, float hy, float hz,
                                                     const float* __restrict__ u_old,
                                                     float* __restrict__ u_new,
                                                     const float* __restrict__ f,
-                                                    const float* __restrict__ a) {
+                                                    const float* __restrict__ a,
+                                                    const float* __restrict__ uc, Dims dc) {
     extern __shared__ float4 smem_f4[];
     float* su = reinterpret_cast<float*>(smem_f4);
     float* sa = su + SU * PL;
@@ -138,10 +145,49 @@ __global__ void __launch_bounds__(NT) k_rbgs_stream(Dims d, float hx, float hy, 
     auto fetch_ua = [&](int q, int slot) {
         if (ua_s >= 0) {
             const int so = slot + ua_s, g = pbase(q) + ua_g;
-            if (u_old) cp_async16(su + so, u_old + g);
-            else *reinterpret_cast<float4*>(su + so) = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (!PRO) {
+                if (u_old) cp_async16(su + so, u_old + g);
+                else *reinterpret_cast<float4*>(su + so) = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
             cp_async16(sa + so, a + g);
         }
+    };
+    // PRO: coarse indices of this thread's chunk (fine row gj, fine columns
+    // gk .. gk + 3 with gk a multiple of 4): rows J0, J1 with weights wj0, wj1
+    // and columns K0, K0 + 1, K0 + 2.
+    int pj0 = 0, pj1 = 0, pk0 = 0, pk1 = 0, pk2 = 0;
+    float wj0 = 1.f, wj1 = 0.f;
+    if (PRO && ua_s >= 0) {
+        const int gj = (ua_g >> d.s2) & (d.n1 - 1), gk = ua_g & (d.n2 - 1);
+        const int J0 = gj >> 1, oj = gj & 1;
+        pj0 = J0 << dc.s2, pj1 = ((J0 + oj) & (dc.n1 - 1)) << dc.s2;
+        wj0 = oj ? 0.5f : 1.f, wj1 = oj ? 0.5f : 0.f;
+        const int K0 = gk >> 1;
+        pk0 = K0, pk1 = (K0 + 1) & (dc.n2 - 1), pk2 = (K0 + 2) & (dc.n2 - 1);
+    }
+    const int cplane = dc.n1 * dc.n2;
+    // u_old + P(uc) for this thread's chunk of plane q
+    auto pro_value = [&](int q) -> float4 {
+        if (!PRO || ua_s < 0) return make_float4(0.f, 0.f, 0.f, 0.f);
+        const int gi = q & (d.n0 - 1);
+        const int I0 = gi >> 1, oi = gi & 1;
+        const float wi0 = oi ? 0.5f : 1.f, wi1 = oi ? 0.5f : 0.f;
+        const float* c0 = uc + I0 * cplane;
+        const float* c1 = uc + ((I0 + oi) & (dc.n0 - 1)) * cplane;
+        float ck[3];
+        const int kk[3] = {pk0, pk1, pk2};
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            const float x0 = fmaf(wj1, __ldg(c0 + pj1 + kk[m]), wj0 * __ldg(c0 + pj0 + kk[m]));
+            const float x1 = fmaf(wj1, __ldg(c1 + pj1 + kk[m]), wj0 * __ldg(c1 + pj0 + kk[m]));
+            ck[m] = fmaf(wi1, x1, wi0 * x0);
+        }
+        const float4 u = __ldg(reinterpret_cast<const float4*>(u_old + pbase(q) + ua_g));
+        return make_float4(u.x + ck[0], u.y + 0.5f * (ck[0] + ck[1]), u.z + ck[1],
+                           u.w + 0.5f * (ck[1] + ck[2]));
+    };
+    auto pro_store = [&](int slot, const float4& v) {
+        if (PRO && ua_s >= 0) *reinterpret_cast<float4*>(su + slot + ua_s) = v;
     };
     auto fetch_f = [&](int q, int slot) {
         if (f_s >= 0) cp_async16(sf + slot + f_s, f + pbase(q) + f_g);
@@ -178,6 +224,12 @@ __global__ void __launch_bounds__(NT) k_rbgs_stream(Dims d, float hx, float hy, 
     fetch_ua(i0, 2 * PL);
     fetch_f(i0 - 1, 1 * PL);
     cp_commit();
+    if (PRO) {
+        pro_store(0 * PL, pro_value(i0 - 2));
+        pro_store(1 * PL, pro_value(i0 - 1));
+        pro_store(2 * PL, pro_value(i0));
+        pro_store(3 * PL, pro_value(i0 + 1));
+    }
     cp_wait_all();
     __syncthreads();
     fetch_ua(i0 + 1, 3 * PL);
@@ -187,7 +239,9 @@ __global__ void __launch_bounds__(NT) k_rbgs_stream(Dims d, float hx, float hy, 
 #pragma unroll
     for (int it = 0; it < CI + 2; ++it) {
         const int q = i0 - 1 + it;  // plane of the red update
+        float4 pend;                // PRO: u + P(uc) of plane q + 3, stored below
         if (it < CI) {
+            if (PRO) pend = pro_value(q + 3);
             fetch_ua(q + 3, ((it + 4) % SU) * PL);
             fetch_f(q + 2, ((it + 3) % SF) * PL);
         }
@@ -215,10 +269,40 @@ __global__ void __launch_bounds__(NT) k_rbgs_stream(Dims d, float hx, float hy, 
 #pragma unroll
             for (int m = 0; m < 2; ++m) u_new[gb + out_g[m]] = su[cu + out_s[m]];
         }
+        // the slot of plane q + 3 was last read in the previous iteration
+        if (PRO && it < CI) pro_store(((it + 4) % SU) * PL, pend);
         cp_wait_prior();
         __syncthreads();
     }
 }
+
+constexpr int CIS = 16;  // planes streamed per block
+
+template <bool PRO>
+void launch_sweep(const Level& L, const float* u_old, float* u_new, const float* f, const float* a,
+                  const float* uc, const Dims& dc, cudaStream_t st) {
+    static bool configured = false;
+    if (!configured) {
+        cudaFuncSetAttribute(k_rbgs_stream<true, CIS, PRO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             SMEM);
+        cudaFuncSetAttribute(k_rbgs_stream<false, CIS, PRO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             SMEM);
+        configured = true;
+    }
+    const Dims& d = L.d;
+    dim3 grid(d.n2 / TK, d.n1 / TJ, d.n0 / CIS);
+    launch_counter()++;
+    if (L.h2i[0] == L.h2i[1] && L.h2i[1] == L.h2i[2]) {
+        const float hh = (float)(0.5 * L.h2i[0]);  // 2^-(2l+1): exact
+        k_rbgs_stream<true, CIS, PRO><<<grid, NT, SMEM, st>>>(d, hh, hh, hh, u_old, u_new, f, a, uc, dc);
+    } else {
+        k_rbgs_stream<false, CIS, PRO><<<grid, NT, SMEM, st>>>(d, (float)L.h2i[0], (float)L.h2i[1],
+                                                               (float)L.h2i[2], u_old, u_new, f, a,
+                                                               uc, dc);
+    }
+}
+
+bool stream_fits(const Dims& d) { return d.n2 % TK == 0 && d.n1 % TJ == 0 && d.n0 % CIS == 0; }
 
 }  // namespace
 
@@ -227,24 +311,21 @@ __global__ void __launch_bounds__(NT) k_rbgs_stream(Dims d, float hx, float hy, 
 template <>
 int launch_rbgs_fused<float>(const Level& L, const float* u_old, float* u_new, const float* f,
                              const float* a, int nsweeps, cudaStream_t st) {
-    constexpr int CI = 16;
-    const Dims& d = L.d;
-    if (nsweeps < 1 || d.n2 % TK || d.n1 % TJ || d.n0 % CI) return 0;
-    static bool configured = false;
-    if (!configured) {
-        cudaFuncSetAttribute(k_rbgs_stream<true, CI>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
-        cudaFuncSetAttribute(k_rbgs_stream<false, CI>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
-        configured = true;
-    }
-    dim3 grid(d.n2 / TK, d.n1 / TJ, d.n0 / CI);
-    launch_counter()++;
-    if (L.h2i[0] == L.h2i[1] && L.h2i[1] == L.h2i[2]) {
-        const float hh = (float)(0.5 * L.h2i[0]);  // 2^-(2l+1): exact
-        k_rbgs_stream<true, CI><<<grid, NT, SMEM, st>>>(d, hh, hh, hh, u_old, u_new, f, a);
-    } else {
-        k_rbgs_stream<false, CI><<<grid, NT, SMEM, st>>>(d, (float)L.h2i[0], (float)L.h2i[1],
-                                                         (float)L.h2i[2], u_old, u_new, f, a);
-    }
+    if (nsweeps < 1 || !stream_fits(L.d)) return 0;
+    launch_sweep<false>(L, u_old, u_new, f, a, nullptr, L.d, st);
+    return 1;
+}
+
+bool rbgs_prolong_fits(const Level& fine) {
+    return fine.coarsen[0] && fine.coarsen[1] && fine.coarsen[2] && stream_fits(fine.d);
+}
+
+// The first post-smoothing sweep with the coarse correction folded in:
+// u_new <- RBGS(u_old + P(uc)); returns 1, or 0 with nothing launched.
+int launch_rbgs_prolong(const Level& fine, const Level& coarse, const float* uc, const float* u_old,
+                        float* u_new, const float* f, const float* a, cudaStream_t st) {
+    if (!rbgs_prolong_fits(fine) || !u_old) return 0;
+    launch_sweep<true>(fine, u_old, u_new, f, a, uc, coarse.d, st);
     return 1;
 }
 
