@@ -40,6 +40,8 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--inner-vcycles", type=int, default=None,
+                    help="FP32 V-cycles per FP64 defect correction (library default if unset)")
     ap.add_argument("--k-max", type=int, default=40,
                     help="steps per solve (40 is the workload; fewer only for profiling)")
     return ap.parse_args()
@@ -183,7 +185,8 @@ def run_gb300(a):
         torch.cuda.synchronize()
 
     def timed(precision, steps, warmup, profile=False):
-        R = Recon((n, n, n), box=W.box, precision=precision, profile=int(profile), k_max=a.k_max)
+        kw = {} if a.inner_vcycles is None or precision != "mixed" else {"inner_vcycles": a.inner_vcycles}
+        R = Recon((n, n, n), box=W.box, precision=precision, profile=int(profile), k_max=a.k_max, **kw)
         R.deposit_particles(pos_dev)
         for _ in range(warmup):
             R.solve(record=False)

@@ -96,12 +96,18 @@ __global__ void k_rbgs_colour64_unit(Dims d, int colour, double* __restrict__ u,
 // undifferenced form is ~8 eps D |u|, i.e. ~1e-12 relative to |f| even for
 // the smoothest mode of a 512^3 grid, far below the stopping tolerance.
 // Optionally also writes r in FP32 (the next V-cycle's right-hand side);
-// always the per-block partial sums of r^2.
+// always the per-block partial sums of r^2.  With the FP32 copy (mixed mode)
+// r^2 is summed from it on the FP32 pipe, one FP64 instruction fewer per
+// node.  The norm only decides the multigrid stopping test: each thread's
+// FP32 sum covers cells / (kRedBlocks * kRedThreads) nodes (54 at 256^3, 431
+// at 512^3), so its relative error stays below ~3e-5, and the block sums
+// are FP64.
 __global__ void k_residual64_to32(Dims d, const double* __restrict__ u,
                                   const double* __restrict__ f, const double* __restrict__ F,
                                   const double* __restrict__ D, float* __restrict__ r32,
                                   double* __restrict__ partials) {
     double acc = 0.0;
+    float acc32 = 0.f;
     const size_t n = (size_t)d.cells;
     const double* __restrict__ Fx = F;
     const double* __restrict__ Fy = F + n;
@@ -119,9 +125,15 @@ __global__ void k_residual64_to32(Dims d, const double* __restrict__ u,
         r = fma(-Fy[n3], u[n3], r);
         r = fma(-Fz[c], u[n4], r);
         r = fma(-Fz[n5], u[n5], r);
-        if (r32) r32[c] = (float)r;
-        acc = fma(r, r, acc);
+        if (r32) {
+            const float rf = (float)r;
+            r32[c] = rf;
+            acc32 = fmaf(rf, rf, acc32);
+        } else {
+            acc = fma(r, r, acc);
+        }
     }
+    acc += (double)acc32;
     acc = block_reduce<OpSum>(acc);
     if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }

@@ -186,16 +186,9 @@ void prof_mark(Handle* H) {
     else cudaEventRecord(e, H->st);
 }
 
-// nu red-black sweeps of level l on the field held in *cur (zero_first: it is
-// 0 on entry and need not be read or cleared).  Where the level fits the
-// streaming kernel (FP32 levels) the sweeps run out of place, ping-ponging
-// between *cur and *oth, and the two pointers are swapped so that *cur holds
-// the result; elsewhere the two colour passes run in place.
 template <typename T>
-void smooth_sweeps(Handle* H, int l, int nu, T** cur, T** oth, const T* f, const T* c,
-                   bool zero_first) {
-    const bool prof = H->p.profile && l == 0 && nu > 0;
-    if (prof) prof_mark(H);
+void sweeps_unprofiled(Handle* H, int l, int nu, T** cur, T** oth, const T* f, const T* c,
+                       bool zero_first) {
     bool zero = zero_first;
     for (int s = 0; s < nu;) {
         const int k = launch_rbgs_fused<T>(H->lv[l], zero ? nullptr : *cur, *oth, f, c, nu - s, H->st);
@@ -218,10 +211,32 @@ void smooth_sweeps(Handle* H, int l, int nu, T** cur, T** oth, const T* f, const
         zero = false;
     }
     if (zero) cudaMemsetAsync(*cur, 0, sizeof(T) * H->lv[l].d.cells, H->st);  // nu == 0
-    if (prof) {
-        prof_mark(H);
-        H->prof_sweeps += nu;
+}
+
+// nu red-black sweeps of level l on the field held in *cur (zero_first: it is
+// 0 on entry and need not be read or cleared).  Where the level fits the
+// streaming kernel (FP32 levels) the sweeps run out of place, ping-ponging
+// between *cur and *oth, and the two pointers are swapped so that *cur holds
+// the result; elsewhere the two colour passes run in place.  With
+// params.profile the finest level's full sweeps (read u, a, f; write u) are
+// bracketed with events; a sweep from u = 0 reads no u and is left out.
+template <typename T>
+void smooth_sweeps(Handle* H, int l, int nu, T** cur, T** oth, const T* f, const T* c,
+                   bool zero_first) {
+    if (!(H->p.profile && l == 0)) {
+        sweeps_unprofiled<T>(H, l, nu, cur, oth, f, c, zero_first);
+        return;
     }
+    if (zero_first) {
+        const int first = nu > 0 ? 1 : 0;
+        sweeps_unprofiled<T>(H, l, first, cur, oth, f, c, true);
+        nu -= first;
+    }
+    if (nu <= 0) return;
+    prof_mark(H);
+    sweeps_unprofiled<T>(H, l, nu, cur, oth, f, c, false);
+    prof_mark(H);
+    H->prof_sweeps += nu;
 }
 
 bool pow2_ge(int v, int lo) { return v >= lo && (v & (v - 1)) == 0; }
@@ -295,14 +310,18 @@ struct MG {
 // level's residual buffer doubles as the ping-pong partner of the streaming
 // smoother; with even sweep counts the result is back in u, otherwise it is
 // copied there.
+// correct_into (mixed mode, finest level): if not null, the V-cycle's
+// result is also added to this FP64 field, by the last sweep where it can be;
+// returns whether it was.
 template <typename T>
-void vcycle(Handle* H, MG<T>& g, int l, T* u, const T* f, bool zero_u) {
+bool vcycle(Handle* H, MG<T>& g, int l, T* u, const T* f, bool zero_u,
+            double* correct_into = nullptr) {
     const int last = (int)H->lv.size() - 1;
     const Level& L = H->lv[l];
-    if (l == H->l0 && launch_coarse_vcycle<T>(H->cs, f, u, H->minv, zero_u, H->st)) return;
+    if (l == H->l0 && launch_coarse_vcycle<T>(H->cs, f, u, H->minv, zero_u, H->st)) return false;
     if (l == last) {
         launch_coarse_solve<T>(H->minv, f, u, H->st);
-        return;
+        return false;
     }
     T* cur = u;
     T* oth = g.r[l];
@@ -323,9 +342,24 @@ void vcycle(Handle* H, MG<T>& g, int l, T* u, const T* f, bool zero_u) {
         }
     }
     if (!folded) launch_prolong_add<T>(L, H->lv[l + 1], g.u[l + 1], cur, H->st);
+    bool corrected = false;
+    if constexpr (sizeof(T) == sizeof(float)) {
+        // the defect correction folded into the last sweep
+        if (correct_into && nu2 >= 1) {
+            smooth_sweeps<T>(H, l, nu2 - 1, &cur, &oth, f, g.c[l], false);
+            if (launch_rbgs_correct(L, cur, oth, f, g.c[l], correct_into, H->st)) {
+                std::swap(cur, oth);
+                corrected = true;
+            } else {
+                smooth_sweeps<T>(H, l, 1, &cur, &oth, f, g.c[l], false);
+            }
+            nu2 = 0;
+        }
+    }
     smooth_sweeps<T>(H, l, nu2, &cur, &oth, f, g.c[l], false);
     if (cur != u)
         cudaMemcpyAsync(u, cur, sizeof(T) * L.d.cells, cudaMemcpyDeviceToDevice, H->st);
+    return corrected;
 }
 
 template <typename T>
@@ -408,9 +442,12 @@ void mg_iter(Handle* H, const CtlHandles& h) {
         launch_residual_norm64(L0, H->phidot, H->s, H->F64, H->D64, H->part[0], H->st);
     } else {
         MG<float> g{H->u32, H->f32, H->c32, H->r32};
-        for (int v = 0; v < H->p.inner_vcycles; ++v)
-            vcycle<float>(H, g, 0, H->u32[0], H->f32[0], v == 0);
-        launch_correct(H->cells, H->phidot, H->u32[0], H->st);
+        bool corrected = false;
+        for (int v = 0; v < H->p.inner_vcycles; ++v) {
+            const bool last = v + 1 == H->p.inner_vcycles;
+            corrected = vcycle<float>(H, g, 0, H->u32[0], H->f32[0], v == 0, last ? H->phidot : nullptr);
+        }
+        if (!corrected) launch_correct(H->cells, H->phidot, H->u32[0], H->st);
         launch_residual64_to32(L0, H->phidot, H->s, H->F64, H->D64, H->f32[0], H->part[0], H->st);
     }
     finish_reduce(H->part[0], 0, H->scal, SC_RES2, H->st);

@@ -122,6 +122,11 @@ bool rbgs_prolong_fits(const Level& fine);
 int launch_rbgs_prolong(const Level& fine, const Level& coarse, const float* uc, const float* u_old,
                         float* u_new, const float* f, const float* a, cudaStream_t st);
 
+// A streaming FP32 sweep that also adds its result to an FP64 field
+// (u_new <- RBGS(u_old), u64 += u_new); returns 1, or 0 with nothing launched.
+int launch_rbgs_correct(const Level& L, const float* u_old, float* u_new, const float* f,
+                        const float* a, double* u64, cudaStream_t st);
+
 template <typename T>
 int launch_rbgs_fused(const Level& L, const T* u_old, T* u_new, const T* f, const T* a,
                       int nsweeps, cudaStream_t st);

@@ -56,13 +56,16 @@ static_assert(NR == 330 && (TJ + 2) * 32 == 320, "red task split");
 // u into registers with the 12 coarse values the chunk's interpolation needs
 // and stores the sum to shared memory at the end of the iteration, so the
 // loads overlap that iteration's updates.
-template <bool ISO, int CI, bool PRO>
+// COR: the swept values are also added to the FP64 field u64 (the defect
+// correction phidot += e of the mixed-precision solve) as they are written.
+template <bool ISO, int CI, bool PRO, bool COR>
 __global__ void __launch_bounds__(NT) k_rbgs_stream(Dims d, float hx, float hy, float hz,
                                                     const float* __restrict__ u_old,
                                                     float* __restrict__ u_new,
                                                     const float* __restrict__ f,
                                                     const float* __restrict__ a,
-                                                    const float* __restrict__ uc, Dims dc) {
+                                                    const float* __restrict__ uc, Dims dc,
+                                                    double* __restrict__ u64) {
     extern __shared__ float4 smem_f4[];
     float* su = reinterpret_cast<float*>(smem_f4);
     float* sa = su + SU * PL;
@@ -267,7 +270,11 @@ __global__ void __launch_bounds__(NT) k_rbgs_stream(Dims d, float hx, float hy, 
             __syncthreads();
             const int gb = pbase(q - 1);
 #pragma unroll
-            for (int m = 0; m < 2; ++m) u_new[gb + out_g[m]] = su[cu + out_s[m]];
+            for (int m = 0; m < 2; ++m) {
+                const float v = su[cu + out_s[m]];
+                u_new[gb + out_g[m]] = v;
+                if (COR) u64[gb + out_g[m]] += (double)v;
+            }
         }
         // the slot of plane q + 3 was last read in the previous iteration
         if (PRO && it < CI) pro_store(((it + 4) % SU) * PL, pend);
@@ -278,15 +285,15 @@ __global__ void __launch_bounds__(NT) k_rbgs_stream(Dims d, float hx, float hy, 
 
 constexpr int CIS = 16;  // planes streamed per block
 
-template <bool PRO>
+template <bool PRO, bool COR>
 void launch_sweep(const Level& L, const float* u_old, float* u_new, const float* f, const float* a,
-                  const float* uc, const Dims& dc, cudaStream_t st) {
+                  const float* uc, const Dims& dc, double* u64, cudaStream_t st) {
     static bool configured = false;
     if (!configured) {
-        cudaFuncSetAttribute(k_rbgs_stream<true, CIS, PRO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             SMEM);
-        cudaFuncSetAttribute(k_rbgs_stream<false, CIS, PRO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             SMEM);
+        cudaFuncSetAttribute(k_rbgs_stream<true, CIS, PRO, COR>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        cudaFuncSetAttribute(k_rbgs_stream<false, CIS, PRO, COR>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
         configured = true;
     }
     const Dims& d = L.d;
@@ -294,11 +301,11 @@ void launch_sweep(const Level& L, const float* u_old, float* u_new, const float*
     launch_counter()++;
     if (L.h2i[0] == L.h2i[1] && L.h2i[1] == L.h2i[2]) {
         const float hh = (float)(0.5 * L.h2i[0]);  // 2^-(2l+1): exact
-        k_rbgs_stream<true, CIS, PRO><<<grid, NT, SMEM, st>>>(d, hh, hh, hh, u_old, u_new, f, a, uc, dc);
+        k_rbgs_stream<true, CIS, PRO, COR><<<grid, NT, SMEM, st>>>(d, hh, hh, hh, u_old, u_new, f, a, uc,
+                                                                   dc, u64);
     } else {
-        k_rbgs_stream<false, CIS, PRO><<<grid, NT, SMEM, st>>>(d, (float)L.h2i[0], (float)L.h2i[1],
-                                                               (float)L.h2i[2], u_old, u_new, f, a,
-                                                               uc, dc);
+        k_rbgs_stream<false, CIS, PRO, COR><<<grid, NT, SMEM, st>>>(
+            d, (float)L.h2i[0], (float)L.h2i[1], (float)L.h2i[2], u_old, u_new, f, a, uc, dc, u64);
     }
 }
 
@@ -312,7 +319,7 @@ template <>
 int launch_rbgs_fused<float>(const Level& L, const float* u_old, float* u_new, const float* f,
                              const float* a, int nsweeps, cudaStream_t st) {
     if (nsweeps < 1 || !stream_fits(L.d)) return 0;
-    launch_sweep<false>(L, u_old, u_new, f, a, nullptr, L.d, st);
+    launch_sweep<false, false>(L, u_old, u_new, f, a, nullptr, L.d, nullptr, st);
     return 1;
 }
 
@@ -325,7 +332,16 @@ bool rbgs_prolong_fits(const Level& fine) {
 int launch_rbgs_prolong(const Level& fine, const Level& coarse, const float* uc, const float* u_old,
                         float* u_new, const float* f, const float* a, cudaStream_t st) {
     if (!rbgs_prolong_fits(fine) || !u_old) return 0;
-    launch_sweep<true>(fine, u_old, u_new, f, a, uc, coarse.d, st);
+    launch_sweep<true, false>(fine, u_old, u_new, f, a, uc, coarse.d, nullptr, st);
+    return 1;
+}
+
+// A sweep that also adds its result to the FP64 field u64:
+// u_new <- RBGS(u_old), u64 += u_new; returns 1, or 0 with nothing launched.
+int launch_rbgs_correct(const Level& L, const float* u_old, float* u_new, const float* f,
+                        const float* a, double* u64, cudaStream_t st) {
+    if (!stream_fits(L.d) || !u_old) return 0;
+    launch_sweep<false, true>(L, u_old, u_new, f, a, nullptr, L.d, u64, st);
     return 1;
 }
 

@@ -677,10 +677,19 @@ __global__ void k_geometry_out(Dims d, const double* __restrict__ phi, double* _
         cell_coords(d, c, i, j, k);
         Sym3 e = hessian(d, phi, i, j, k);
         e.xx += 1.0, e.yy += 1.0, e.zz += 1.0;
-        const double g = det3(e), l = min_eig_sym3(e);
+        const double g = det3(e);
         if (det) det[c] = g;
-        if (lam) lam[c] = l;
-        md = fmin(md, g), ml = fmin(ml, l);
+        md = fmin(md, g);
+        // lambda0 >= the Gershgorin bound, so without a per-node output the
+        // eigenvalue is needed only where that bound is below the running min
+        const double gersh =
+            fmin(fmin(e.xx - fabs(e.xy) - fabs(e.xz), e.yy - fabs(e.xy) - fabs(e.yz)),
+                 e.zz - fabs(e.xz) - fabs(e.yz));
+        if (lam || gersh < ml) {
+            const double l = min_eig_sym3(e);
+            if (lam) lam[c] = l;
+            ml = fmin(ml, l);
+        }
     }
     md = block_reduce<OpMin>(md);
     if (threadIdx.x == 0) pdet[blockIdx.x] = md;
