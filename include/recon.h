@@ -49,14 +49,17 @@ extern "C" {
 #define RECON_E_CUDA (-3)     /* a CUDA runtime call failed               */
 #define RECON_E_NONFINITE (-4) /* NaN/Inf or negative input               */
 #define RECON_E_LIMITER (-5)  /* reserved (a limiter stall is RECON_STALLED) */
-#define RECON_E_TIMEOUT (-6)  /* a bounded device wait expired             */
+#define RECON_E_TIMEOUT (-6)  /* reserved: no call waits on the device without
+                                 a bound (the solve's loops are graph nodes) */
 #define RECON_E_STATE (-7)    /* call out of order (e.g. solve before deposit) */
-#define RECON_E_UNSUPPORTED (-8) /* feature not available in this build    */
+#define RECON_E_UNSUPPORTED (-8) /* reserved: every declared call is built  */
 
 /* arithmetic of the solve */
 #define RECON_FP64 0  /* every step in FP64                                   */
 #define RECON_MIXED 1 /* FP32 smoothing / restriction / prolongation inside an
-                         FP64 defect correction; residual, phi, mesh, limiter FP64 */
+                         FP64 defect correction; residual, phi, mesh, limiter FP64
+                         (the multigrid stopping test's norm of the FP64 residual
+                         is summed from its FP32 copy)                           */
 
 /* readings of the printed compression limiter C(phi) of App. A */
 #define RECON_CLIM_SOFT 0    /* C = 4 max(0, xi_m/lambda0 - 1)^2            */
@@ -97,8 +100,9 @@ typedef struct {
     int profile;         /* nonzero: time the finest-level smoothing sweeps with
                             CUDA events (reported in recon_stats.smooth_ms)    */
     int inner_vcycles;   /* RECON_MIXED: FP32 V-cycles per FP64 defect
-                            correction (1..8); the FP64 residual is formed once
-                            per group, so the stopping test sees multiples of it */
+                            correction (1..8, default 3); the FP64 residual is
+                            formed once per group, so the stopping test sees
+                            multiples of it                                     */
     int density_update;  /* 0: CIC re-deposit of the tracers on the deformed mesh
                             every step (default); 1: App. A's linear update
                             m += alpha d_mu(m e^-1 d dphi) of the mass per cell  */
@@ -160,7 +164,11 @@ int recon_deposit(void* h, int mode, const double* data, const double* mass, int
  * (Sec. II; App. A).  Returns RECON_OK when rms(s) <= tol_out,
  * RECON_NOT_CONVERGED after k_max steps, RECON_STALLED when the step limiter
  * admits no alpha >= alpha_min (results valid in all three), or an error.
- * stats may be NULL. */
+ * stats may be NULL; with stats, the end-of-solve minima of det and lambda0
+ * and the maximum of delta_r are computed as well.  With device_loop = 1 the
+ * first call on a handle records the iteration as a CUDA graph (on private
+ * streams) and every call launches it on the handle's stream; later deposits
+ * on the handle reuse it.  The call returns when the stream has finished. */
 int recon_solve(void* h, recon_stats* stats);
 
 /* recon_solve_batch: solves count independent problems (for example many

@@ -374,12 +374,7 @@ void launch_prolong_add(const Level& fine, const Level& coarse, const T* uc, T* 
 
 template <typename T>
 void launch_coarse_invert(const Level& L, const T* a, double* minv, cudaStream_t st) {
-    static bool configured = false;
-    if (!configured) {
-        cudaFuncSetAttribute(k_coarse_invert<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kInvSmem);
-        configured = true;
-    }
+    allow_smem((const void*)k_coarse_invert<T>, (int)kInvSmem);
     launch_counter()++;
     k_coarse_invert<T><<<1, kInvThreads, kInvSmem, st>>>(L.d, L.h2i[0], L.h2i[1], L.h2i[2], a,
                                                          minv);
@@ -581,12 +576,7 @@ bool launch_coarse_vcycle(const CoarseSet& cs, const T* f_top, T* u_top, const d
     for (int l = 0; l < cs.nlev; ++l) cells += cs.lv[l].d.cells;
     const size_t sm = 4 * cells * sizeof(T);
     if (cs.nlev < 1 || cs.nlev > kCoarseMaxLevels || sm > kCoarseMaxSmem) return false;
-    static bool configured = false;
-    if (!configured) {
-        cudaFuncSetAttribute(k_coarse_vcycle<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kCoarseMaxSmem);
-        configured = true;
-    }
+    allow_smem((const void*)k_coarse_vcycle<T>, (int)kCoarseMaxSmem);
     launch_counter()++;
     k_coarse_vcycle<T><<<1, 1024, sm, st>>>(cs, f_top, u_top, minv, zero_u ? 1 : 0);
     return true;

@@ -980,7 +980,7 @@ int recon_default_params(recon_params* p, int n0, int n1, int n2) {
     p->lambda_floor = 0.01;
     p->replay_alpha = nullptr;
     p->profile = 0;
-    p->inner_vcycles = 2;
+    p->inner_vcycles = 3;
     p->density_update = 0;
     p->device_loop = 1;
     p->checkpoint = 0;

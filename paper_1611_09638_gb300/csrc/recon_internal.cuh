@@ -6,6 +6,9 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <mutex>
+#include <set>
+#include <utility>
 
 namespace recon {
 
@@ -13,6 +16,18 @@ namespace recon {
 inline std::atomic<long long>& launch_counter() {
     static std::atomic<long long> c{0};
     return c;
+}
+
+// Allows kernel fn up to `bytes` of dynamic shared memory on the current
+// device; the attribute is set once per kernel and device.
+inline void allow_smem(const void* fn, int bytes) {
+    static std::mutex mu;
+    static std::set<std::pair<const void*, int>> done;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.insert(std::make_pair(fn, dev)).second)
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 // Periodic power-of-two grid: n0 x n1 x n2 nodes, last axis fastest.

@@ -288,14 +288,8 @@ constexpr int CIS = 16;  // planes streamed per block
 template <bool PRO, bool COR>
 void launch_sweep(const Level& L, const float* u_old, float* u_new, const float* f, const float* a,
                   const float* uc, const Dims& dc, double* u64, cudaStream_t st) {
-    static bool configured = false;
-    if (!configured) {
-        cudaFuncSetAttribute(k_rbgs_stream<true, CIS, PRO, COR>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
-        cudaFuncSetAttribute(k_rbgs_stream<false, CIS, PRO, COR>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
-        configured = true;
-    }
+    allow_smem((const void*)k_rbgs_stream<true, CIS, PRO, COR>, SMEM);
+    allow_smem((const void*)k_rbgs_stream<false, CIS, PRO, COR>, SMEM);
     const Dims& d = L.d;
     dim3 grid(d.n2 / TK, d.n1 / TJ, d.n0 / CIS);
     launch_counter()++;

@@ -21,6 +21,12 @@ __device__ inline bool pd_above(Sym3 M, double floor) {
     return M.xx > 0.0 && (M.xx * M.yy - M.xy * M.xy) > 0.0 && det3(M) > 0.0;
 }
 
+// 1 / n for a power of two n (< 2^1023), exactly, from the exponent bits
+// (integer work only; x * inv_pow2(n) equals x / n bit for bit).
+__device__ inline double inv_pow2(int n) {
+    return __longlong_as_double((long long)(1023 - (__ffs(n) - 1)) << 52);
+}
+
 __device__ inline void cic_abs(double x, int n, int& i0, double& f) {
     const double u = x - (double)n * floor(x / (double)n);
     const double fl = floor(u);
@@ -144,11 +150,11 @@ __global__ void k_deposit_tracers(Dims d, const double* __restrict__ ox,
 // a block takes the tracers whose home nodes form a DTI x DTJ x DTK tile and
 // adds each corner weight into a copy of the tile plus DH nodes on every side
 // held in shared memory, then adds the non-zero cells of that copy to the
-// grid.  A tracer
-// whose stencil leaves the copy adds to the grid directly.  The fixed-point
-// sums are integers, so the result is bit-identical to k_deposit_tracers
-// while the grid sees ~4x fewer atomics.  Per corner the weight product and
-// the scaled mass w * 2^F cost two FP64 multiplies and the conversion.
+// grid.  A tracer whose stencil leaves the copy adds to the grid directly.
+// The fixed-point sums are integers, so the result is bit-identical to
+// k_deposit_tracers while the grid sees ~4x fewer atomics.  Per corner the
+// weight product and the scaled mass w * 2^F cost two FP64 multiplies and
+// the conversion.
 constexpr int DTI = 8, DTJ = 16, DTK = 32, DH = 2;
 constexpr int DRI = DTI + 2 * DH, DRJ = DTJ + 2 * DH, DRK = DTK + 2 * DH;
 constexpr int DCELLS = DRI * DRJ * DRK;
@@ -492,8 +498,8 @@ __global__ void k_limiter(Dims d, LimiterParams lp, const double* __restrict__ e
 }
 
 // V = e^-1 G at every node: e = I + Hess phi (before the step; stored by
-// k_geometry_source), G the central-difference gradient of dphi; solved by
-// Cramer's rule.
+// k_geometry_source), G the central-difference gradient of dphi; e^-1 from
+// the adjugate of the symmetric e.
 __global__ void k_node_velocity(Dims d, const double* __restrict__ e6,
                                 const double* __restrict__ dphi, double* __restrict__ vx,
                                 double* __restrict__ vy, double* __restrict__ vz) {
@@ -505,18 +511,18 @@ __global__ void k_node_velocity(Dims d, const double* __restrict__ e6,
     Sym3 e;
     e.xx = e6[c], e.yy = e6[n + c], e.zz = e6[2 * n + c];
     e.xy = e6[3 * n + c], e.xz = e6[4 * n + c], e.yz = e6[5 * n + c];
-    const double gx = 0.5 * (dphi[cell_index(d, i + 1, j, k)] - dphi[cell_index(d, i - 1, j, k)]);
-    const double gy = 0.5 * (dphi[cell_index(d, i, j + 1, k)] - dphi[cell_index(d, i, j - 1, k)]);
-    const double gz = 0.5 * (dphi[cell_index(d, i, j, k + 1)] - dphi[cell_index(d, i, j, k - 1)]);
-    const double inv = 1.0 / det3(e);
-    // columns of e replaced by G in turn
-    const double dx = gx * (e.yy * e.zz - e.yz * e.yz) - e.xy * (gy * e.zz - e.yz * gz) +
-                      e.xz * (gy * e.yz - e.yy * gz);
-    const double dy = e.xx * (gy * e.zz - gz * e.yz) - gx * (e.xy * e.zz - e.yz * e.xz) +
-                      e.xz * (e.xy * gz - gy * e.xz);
-    const double dz = e.xx * (e.yy * gz - e.yz * gy) - e.xy * (e.xy * gz - gy * e.xz) +
-                      gx * (e.xy * e.yz - e.yy * e.xz);
-    vx[c] = dx * inv, vy[c] = dy * inv, vz[c] = dz * inv;
+    // twice the central-difference gradient of dphi (the 1/2 goes with 1/det)
+    const double gx = dphi[cell_index(d, i + 1, j, k)] - dphi[cell_index(d, i - 1, j, k)];
+    const double gy = dphi[cell_index(d, i, j + 1, k)] - dphi[cell_index(d, i, j - 1, k)];
+    const double gz = dphi[cell_index(d, i, j, k + 1)] - dphi[cell_index(d, i, j, k - 1)];
+    // e^-1 = adj(e) / det e with the six cofactors of the symmetric e
+    const double Axx = e.yy * e.zz - e.yz * e.yz, Ayy = e.xx * e.zz - e.xz * e.xz;
+    const double Azz = e.xx * e.yy - e.xy * e.xy, Axy = e.xz * e.yz - e.xy * e.zz;
+    const double Axz = e.xy * e.yz - e.yy * e.xz, Ayz = e.xy * e.xz - e.xx * e.yz;
+    const double hinv = 0.5 / (e.xx * Axx + e.xy * Axy + e.xz * Axz);
+    vx[c] = (Axx * gx + Axy * gy + Axz * gz) * hinv;
+    vy[c] = (Axy * gx + Ayy * gy + Ayz * gz) * hinv;
+    vz[c] = (Axz * gx + Ayz * gy + Azz * gz) * hinv;
 }
 
 // App. A's linear density update (the variant that carries m instead of
@@ -599,7 +605,7 @@ __global__ void k_phi_advance(int cells, const double* __restrict__ alpha_p,
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= cells) return;
     const double alpha = *alpha_p;
-    const double mean = *sum_dphi / (double)cells;
+    const double mean = *sum_dphi * inv_pow2(cells);
     const double pn = phi[c] + alpha * (dphi[c] - mean);
     phi[c] = pn;
     phi32[c] = (float)pn;
@@ -635,7 +641,7 @@ __global__ void k_advance(Dims d, const double* __restrict__ vx, const double* _
         }
     }
     ox[c] = px - alpha * ux, oy[c] = py - alpha * uy, oz[c] = pz - alpha * uz;
-    const double mean = *sum_dphi / (double)d.cells;
+    const double mean = *sum_dphi * inv_pow2(d.cells);
     const double pn = phi[c] + alpha * (dphi[c] - mean);
     phi[c] = pn;
     phi32[c] = (float)pn;
@@ -756,12 +762,7 @@ void launch_deposit_tracers(const Dims& d, const double* ox, const double* oy, c
                             cudaStream_t st) {
     launch_counter()++;
     if (d.n0 % DTI == 0 && d.n1 % DTJ == 0 && d.n2 % DTK == 0) {
-        static bool configured = false;
-        if (!configured) {
-            cudaFuncSetAttribute(k_deposit_tracers_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kDepSmem);
-            configured = true;
-        }
+        allow_smem((const void*)k_deposit_tracers_tiled, (int)kDepSmem);
         dim3 grid(d.n2 / DTK, d.n1 / DTJ, d.n0 / DTI);
         k_deposit_tracers_tiled<<<grid, 256, kDepSmem, st>>>(d, ox, oy, oz, w, scale, mfix);
         return;

@@ -169,17 +169,15 @@ __global__ void __launch_bounds__(RT) k_resid_restrict_stream(Dims df, Dims dc, 
     }
 }
 
-int g_resident = 0;  // blocks of the kernel resident on the device at once
+// Blocks of the kernel resident at once on each device (0: not yet asked).
+constexpr int kMaxDevices = 64;
+int g_resident[kMaxDevices] = {};
+std::mutex g_resident_mu;
 
 template <bool ISO, int CIc>
 void launch_rr(dim3 grid, const Dims& df, const Dims& dc, float hx, float hy, float hz,
                const float* u, const float* f, const float* a, float* out, cudaStream_t st) {
-    static bool configured = false;
-    if (!configured) {
-        cudaFuncSetAttribute(k_resid_restrict_stream<ISO, CIc>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, RSMEM);
-        configured = true;
-    }
+    allow_smem((const void*)k_resid_restrict_stream<ISO, CIc>, RSMEM);
     k_resid_restrict_stream<ISO, CIc><<<grid, RT, RSMEM, st>>>(df, dc, hx, hy, hz, u, f, a, out);
 }
 
@@ -202,14 +200,21 @@ int launch_resid_restrict_stream(const Level& fine, const Level& coarse, const f
     const Dims& df = fine.d;
     if (!fine.coarsen[0] || !fine.coarsen[1] || !fine.coarsen[2]) return 0;
     if (df.n2 % FK || df.n1 % FJ || df.n0 < 4) return 0;
-    if (!g_resident) {
-        cudaFuncSetAttribute(k_resid_restrict_stream<true, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             RSMEM);
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_resid_restrict_stream<true, 8>, RT, RSMEM);
-        g_resident = sms * per_sm > 0 ? sms * per_sm : 1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int resident = 0;
+    {
+        std::lock_guard<std::mutex> lock(g_resident_mu);
+        int& r = g_resident[(dev >= 0 && dev < kMaxDevices) ? dev : 0];
+        if (!r) {
+            allow_smem((const void*)k_resid_restrict_stream<true, 8>, RSMEM);
+            int sms = 0, per_sm = 0;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_resid_restrict_stream<true, 8>, RT,
+                                                          RSMEM);
+            r = sms * per_sm > 0 ? sms * per_sm : 1;
+        }
+        resident = r;
     }
     // coarse planes per block: fewest rounds of resident blocks times the
     // planes each block streams (2 CIc + 1 residual planes and a start-up)
@@ -220,7 +225,7 @@ int launch_resid_restrict_stream(const Level& fine, const Level& coarse, const f
     for (int ci = 1; ci <= 16 && ci <= n0c; ci *= 2) {
         if (n0c % ci) continue;
         const long long blocks = tiles * (n0c / ci);
-        const long long cost = ((blocks + g_resident - 1) / g_resident) * (2 * ci + 2);
+        const long long cost = ((blocks + resident - 1) / resident) * (2 * ci + 2);
         if (!best || cost < best_cost) best = ci, best_cost = cost;
     }
     dim3 grid(df.n2 / FK, df.n1 / FJ, n0c / best);
