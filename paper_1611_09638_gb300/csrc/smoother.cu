@@ -52,10 +52,11 @@ static_assert(NR == 330 && (TJ + 2) * 32 == 320, "red task split");
 // (1 / hh is a power of two); otherwise each face is scaled by its axis.
 // PRO: the sweep also applies the coarse-grid correction of the V-cycle
 // first: u_old + P(uc) is swept, P the trilinear prolongation from the
-// coarse level dc (every axis halved).  Each thread loads its 4-node chunk of
-// u into registers with the 12 coarse values the chunk's interpolation needs
-// and stores the sum to shared memory at the end of the iteration, so the
-// loads overlap that iteration's updates.
+// coarse level dc (every axis halved).  Each thread issues the loads of its
+// 4-node chunk of u and of the 6 or 12 coarse values the chunk's
+// interpolation needs at the start of an iteration and combines and stores
+// them to shared memory at its end, so the loads overlap the iteration's
+// updates.
 // COR: the swept values are also added to the FP64 field u64 (the defect
 // correction phidot += e of the mixed-precision solve) as they are written.
 template <bool ISO, int CI, bool PRO, bool COR>
@@ -155,39 +156,59 @@ __global__ void __launch_bounds__(NT) k_rbgs_stream(Dims d, float hx, float hy, 
             cp_async16(sa + so, a + g);
         }
     };
-    // PRO: coarse indices of this thread's chunk (fine row gj, fine columns
-    // gk .. gk + 3 with gk a multiple of 4): rows J0, J1 with weights wj0, wj1
-    // and columns K0, K0 + 1, K0 + 2.
-    int pj0 = 0, pj1 = 0, pk0 = 0, pk1 = 0, pk2 = 0;
+    // PRO: coarse offsets of this thread's chunk (fine row gj, fine columns
+    // gk .. gk + 3 with gk a multiple of 4): rows J0, J1 (weights wj0, wj1)
+    // and columns K0, K0 + 1 (an aligned pair: K0 is even) and K0 + 2.
+    int o0 = 0, o1 = 0, o02 = 0, o12 = 0;
     float wj0 = 1.f, wj1 = 0.f;
     if (PRO && ua_s >= 0) {
         const int gj = (ua_g >> d.s2) & (d.n1 - 1), gk = ua_g & (d.n2 - 1);
         const int J0 = gj >> 1, oj = gj & 1;
-        pj0 = J0 << dc.s2, pj1 = ((J0 + oj) & (dc.n1 - 1)) << dc.s2;
+        const int r0 = J0 << dc.s2, r1 = ((J0 + oj) & (dc.n1 - 1)) << dc.s2;
         wj0 = oj ? 0.5f : 1.f, wj1 = oj ? 0.5f : 0.f;
-        const int K0 = gk >> 1;
-        pk0 = K0, pk1 = (K0 + 1) & (dc.n2 - 1), pk2 = (K0 + 2) & (dc.n2 - 1);
+        const int K0 = gk >> 1, K2 = (K0 + 2) & (dc.n2 - 1);
+        o0 = r0 + K0, o1 = r1 + K0, o02 = r0 + K2, o12 = r1 + K2;
     }
     const int cplane = dc.n1 * dc.n2;
-    // u_old + P(uc) for this thread's chunk of plane q
-    auto pro_value = [&](int q) -> float4 {
-        if (!PRO || ua_s < 0) return make_float4(0.f, 0.f, 0.f, 0.f);
+    // The raw values one chunk's u + P(uc) needs: u itself and, per coarse
+    // plane (one for an even fine plane, two for an odd one), the pairs at
+    // (J0 | J1, K0..K0+1) and the values at K0 + 2.  pro_load issues the loads;
+    // pro_value combines them later, so the loads stay in flight meanwhile.
+    struct ProRaw {
+        float4 u;
+        float2 a, b, c, e;
+        float a2, b2, c2, e2;
+        bool odd;
+    };
+    auto pro_load = [&](int q) -> ProRaw {
+        ProRaw r{};
+        if (!PRO || ua_s < 0) return r;
         const int gi = q & (d.n0 - 1);
-        const int I0 = gi >> 1, oi = gi & 1;
-        const float wi0 = oi ? 0.5f : 1.f, wi1 = oi ? 0.5f : 0.f;
-        const float* c0 = uc + I0 * cplane;
-        const float* c1 = uc + ((I0 + oi) & (dc.n0 - 1)) * cplane;
-        float ck[3];
-        const int kk[3] = {pk0, pk1, pk2};
-#pragma unroll
-        for (int m = 0; m < 3; ++m) {
-            const float x0 = fmaf(wj1, __ldg(c0 + pj1 + kk[m]), wj0 * __ldg(c0 + pj0 + kk[m]));
-            const float x1 = fmaf(wj1, __ldg(c1 + pj1 + kk[m]), wj0 * __ldg(c1 + pj0 + kk[m]));
-            ck[m] = fmaf(wi1, x1, wi0 * x0);
+        const int I0 = gi >> 1;
+        const float* p0 = uc + I0 * cplane;
+        r.a = __ldg(reinterpret_cast<const float2*>(p0 + o0));
+        r.b = __ldg(reinterpret_cast<const float2*>(p0 + o1));
+        r.a2 = __ldg(p0 + o02), r.b2 = __ldg(p0 + o12);
+        r.odd = gi & 1;
+        if (r.odd) {  // odd fine plane: coarse planes I0 and I0 + 1
+            const float* p1 = uc + ((I0 + 1) & (dc.n0 - 1)) * cplane;
+            r.c = __ldg(reinterpret_cast<const float2*>(p1 + o0));
+            r.e = __ldg(reinterpret_cast<const float2*>(p1 + o1));
+            r.c2 = __ldg(p1 + o02), r.e2 = __ldg(p1 + o12);
         }
-        const float4 u = __ldg(reinterpret_cast<const float4*>(u_old + pbase(q) + ua_g));
-        return make_float4(u.x + ck[0], u.y + 0.5f * (ck[0] + ck[1]), u.z + ck[1],
-                           u.w + 0.5f * (ck[1] + ck[2]));
+        r.u = __ldg(reinterpret_cast<const float4*>(u_old + pbase(q) + ua_g));
+        return r;
+    };
+    auto pro_value = [&](const ProRaw& r) -> float4 {
+        float k0v = fmaf(wj1, r.b.x, wj0 * r.a.x), k1v = fmaf(wj1, r.b.y, wj0 * r.a.y);
+        float k2v = fmaf(wj1, r.b2, wj0 * r.a2);
+        if (r.odd) {
+            k0v = 0.5f * (k0v + fmaf(wj1, r.e.x, wj0 * r.c.x));
+            k1v = 0.5f * (k1v + fmaf(wj1, r.e.y, wj0 * r.c.y));
+            k2v = 0.5f * (k2v + fmaf(wj1, r.e2, wj0 * r.c2));
+        }
+        return make_float4(r.u.x + k0v, r.u.y + 0.5f * (k0v + k1v), r.u.z + k1v,
+                           r.u.w + 0.5f * (k1v + k2v));
     };
     auto pro_store = [&](int slot, const float4& v) {
         if (PRO && ua_s >= 0) *reinterpret_cast<float4*>(su + slot + ua_s) = v;
@@ -228,10 +249,10 @@ __global__ void __launch_bounds__(NT) k_rbgs_stream(Dims d, float hx, float hy, 
     fetch_f(i0 - 1, 1 * PL);
     cp_commit();
     if (PRO) {
-        pro_store(0 * PL, pro_value(i0 - 2));
-        pro_store(1 * PL, pro_value(i0 - 1));
-        pro_store(2 * PL, pro_value(i0));
-        pro_store(3 * PL, pro_value(i0 + 1));
+        pro_store(0 * PL, pro_value(pro_load(i0 - 2)));
+        pro_store(1 * PL, pro_value(pro_load(i0 - 1)));
+        pro_store(2 * PL, pro_value(pro_load(i0)));
+        pro_store(3 * PL, pro_value(pro_load(i0 + 1)));
     }
     cp_wait_all();
     __syncthreads();
@@ -242,9 +263,9 @@ __global__ void __launch_bounds__(NT) k_rbgs_stream(Dims d, float hx, float hy, 
 #pragma unroll
     for (int it = 0; it < CI + 2; ++it) {
         const int q = i0 - 1 + it;  // plane of the red update
-        float4 pend;                // PRO: u + P(uc) of plane q + 3, stored below
+        ProRaw pend;                // PRO: raw values of plane q + 3, stored below
         if (it < CI) {
-            if (PRO) pend = pro_value(q + 3);
+            if (PRO) pend = pro_load(q + 3);
             fetch_ua(q + 3, ((it + 4) % SU) * PL);
             fetch_f(q + 2, ((it + 3) % SF) * PL);
         }
@@ -277,7 +298,7 @@ __global__ void __launch_bounds__(NT) k_rbgs_stream(Dims d, float hx, float hy, 
             }
         }
         // the slot of plane q + 3 was last read in the previous iteration
-        if (PRO && it < CI) pro_store(((it + 4) % SU) * PL, pend);
+        if (PRO && it < CI) pro_store(((it + 4) % SU) * PL, pro_value(pend));
         cp_wait_prior();
         __syncthreads();
     }
