@@ -58,7 +58,8 @@ static_assert(NR == 330 && (TJ + 2) * 32 == 320, "red task split");
 // them to shared memory at its end, so the loads overlap the iteration's
 // updates.
 // COR: the swept values are also added to the FP64 field u64 (the defect
-// correction phidot += e of the mixed-precision solve) as they are written.
+// correction phidot += e of the mixed-precision solve) as they are written;
+// the u64 values are loaded at the start of the iteration that writes them.
 template <bool ISO, int CI, bool PRO, bool COR>
 __global__ void __launch_bounds__(NT) k_rbgs_stream(Dims d, float hx, float hy, float hz,
                                                     const float* __restrict__ u_old,
@@ -264,6 +265,12 @@ __global__ void __launch_bounds__(NT) k_rbgs_stream(Dims d, float hx, float hy, 
     for (int it = 0; it < CI + 2; ++it) {
         const int q = i0 - 1 + it;  // plane of the red update
         ProRaw pend;                // PRO: raw values of plane q + 3, stored below
+        double cor[2] = {0.0, 0.0}; // COR: u64 at this thread's outputs of plane q - 1
+        if (COR && it >= 2) {
+            const int gb = pbase(q - 1);
+#pragma unroll
+            for (int m = 0; m < 2; ++m) cor[m] = u64[gb + out_g[m]];
+        }
         if (it < CI) {
             if (PRO) pend = pro_load(q + 3);
             fetch_ua(q + 3, ((it + 4) % SU) * PL);
@@ -294,7 +301,7 @@ __global__ void __launch_bounds__(NT) k_rbgs_stream(Dims d, float hx, float hy, 
             for (int m = 0; m < 2; ++m) {
                 const float v = su[cu + out_s[m]];
                 u_new[gb + out_g[m]] = v;
-                if (COR) u64[gb + out_g[m]] += (double)v;
+                if (COR) u64[gb + out_g[m]] = cor[m] + (double)v;
             }
         }
         // the slot of plane q + 3 was last read in the previous iteration
