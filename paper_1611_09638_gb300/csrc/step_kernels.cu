@@ -213,15 +213,26 @@ __global__ void k_mass_coef(int cells, unsigned long long* __restrict__ mfix, do
                             double a_min, double* __restrict__ m, double* __restrict__ a64,
                             float* __restrict__ a32, double* __restrict__ part) {
     double s = 0.0;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cells; c += gridDim.x * blockDim.x) {
-        const double v = (double)(long long)mfix[c] * inv_scale;
+    const int stride = gridDim.x * blockDim.x;
+    auto one = [&](int c, long long q) {
+        const double v = (double)q * inv_scale;
         mfix[c] = 0ull;
         m[c] = v;
         const double a = v > a_min ? v : a_min;
         a64[c] = a;
         if (a32) a32[c] = (float)a;
         s += v;
+    };
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    // four loads in flight per thread; the nodes are summed in the same order
+    for (; c + 3 * stride < cells; c += 4 * stride) {
+        long long q[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) q[u] = (long long)mfix[c + u * stride];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) one(c + u * stride, q[u]);
     }
+    for (; c < cells; c += stride) one(c, (long long)mfix[c]);
     s = block_reduce<OpSum>(s);
     if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
