@@ -4,23 +4,38 @@
 // single pass over memory.
 //
 // Each block owns a TJ x TK tile of the (j, k) plane and streams CI planes
-// along i.  At iteration q the red update of plane q runs on the tile plus a
-// one-node ring (it reads old black values on a two-node ring), then the black
-// update of plane q - 1 runs on the tile from those red values, and plane q - 1
-// of the tile is written out.  u is read from u_old and written to u_new
-// (another buffer), so halos read by a block are never values another block
-// has already updated: the result equals the in-place sweep node for node.
-// Shared memory holds rings of six u and a planes (tile + two-node ring in j,
-// four-node in k so that every row is whole 16-byte chunks) and four f
-// planes; while planes q and q - 1 are updated, the 16-byte cp.async copies
-// of plane q + 3 (u, a) and q + 2 (f) are issued and those of the plane
-// before them complete.  DRAM traffic is one read of u, a, f and one write
-// of u.  With u_old == nullptr the sweep starts from u = 0 and u is not read.
+// along i.  Every thread owns two adjacent columns (k, k + 1) of one row of
+// the tile for the whole stream.  In a plane exactly one of the two is red,
+// and the red column of plane q is the black column of plane q - 1, so at
+// iteration q a thread updates the red node of plane q and then the black
+// node of plane q - 1 in the same column.  Along i every value a thread needs
+// is its own: u, a and f of its two columns are read once per plane as one
+// 8-byte shared load each and carried in registers, the red value of plane q
+// is the black update's i + 1 neighbour and the red value of plane q - 2 its
+// i - 1 neighbour.  Only the in-plane neighbours (rows j +- 1 and the column
+// across the pair boundary) come from shared memory: 6 shared loads per
+// update instead of 14.  Black values never go to shared memory: a plane's
+// two outputs leave the thread as one 8-byte store.
+//
+// The red update also runs on a one-node ring around the tile (rows -1 and
+// TJ, columns -1 and TK), from old black values on a two-node ring; the
+// black update of the tile's edge nodes reads those ring values.  u is read
+// from u_old and written to u_new (another buffer), so halos read by a block
+// are never values another block has already updated: the result equals the
+// in-place sweep node for node.  Shared memory holds rings of SU planes of u,
+// a and f (u and a: tile + two-node ring in j, four-node in k so that every
+// row is whole 16-byte chunks; f: tile + one-node ring), all fetched with
+// 16-byte cp.async copies PD planes ahead of the one waited for (loading f
+// straight into registers instead left the warps waiting on those loads).
+// The stages of an iteration touch disjoint data (red writes red nodes of
+// plane q and reads black ones, black reads red nodes of plane q - 1), so one
+// block-wide barrier per plane suffices.  DRAM traffic is one read of u, a, f
+// and one write of u.  With u_old == nullptr the sweep starts from u = 0 and
+// u is not read.
 //
 // Every shared-memory and global offset a thread uses is computed once per
-// block, and the plane loop is unrolled so that the ring slots are
-// compile-time constants: the per-plane work is the cp.async issue, the
-// stencil arithmetic and the stores.
+// block, and the plane loop is unrolled so that ring slots and register
+// indices are compile-time constants.
 #include "async_copy.cuh"
 #include "recon_internal.cuh"
 
@@ -35,21 +50,45 @@ constexpr int RJ = TJ + 2 * H;         // 12 rows held per plane
 constexpr int RK = TK + 2 * KO;        // 72 columns held per plane
 constexpr int PL = RJ * RK;            // floats per plane
 constexpr int CH = RK / 4;             // 16-byte chunks per row
-constexpr int SU = 6, SF = 4;          // ring slots of u / a and of f (two planes ahead)
-constexpr int SMEM = (int)sizeof(float) * PL * (2 * SU + SF);
+constexpr int PD = 2;                  // planes of copies in flight ahead of the one waited for
+constexpr int SU = 3 + PD;             // ring slots of u, a and f
+constexpr int SMEM = (int)sizeof(float) * PL * 3 * SU;
 constexpr int NUA = RJ * CH;           // chunks of one u (or a) plane: 216
 constexpr int NF = (TJ + 2) * CH;      // chunks of one f plane (rows of the red ring): 180
-constexpr int NR = (TJ + 2) * ((TK + 2) / 2);  // red nodes on tile + ring: 330
-constexpr int NB = TJ * (TK / 2);      // black nodes on the tile: 256
-constexpr int NO = TJ * TK;            // outputs per plane: 512
-static_assert(NUA <= NT && NF <= NT && NB == NT && NO == 2 * NT && NR <= 2 * NT, "tile");
-static_assert(TJ % 2 == 0 && RK % 2 == 0 && TK == 64, "row-pair colour mapping");
-static_assert(NR == 330 && (TJ + 2) * 32 == 320, "red task split");
+constexpr int NRING = 2 * (TK / 2 + 1) + TJ;  // red ring nodes per plane: 74
+static_assert(NUA <= NT && NRING <= NT, "tile");
+static_assert(TJ * TK == 2 * NT && TK == 64 && TJ % 2 == 0, "two columns per thread, row pairs per warp");
+static_assert(RK % 32 == 8 && ((TJ + 1) * RK) % 32 == 8, "bank parity of the row pairs");
 
+// The Gauss-Seidel value of a node from its coefficient c, the neighbours'
+// coefficients and values (x: i, y: j, z: k; p: +1, m: -1) and f.
 // ISO: the level has one spacing on every axis, so every face coefficient
 // carries the same factor hh = h^-2 / 2: the update sums the face sums
 // c + a_n and applies hh once, u = (sum (c + a_n) u_n - f / hh) / sum (c + a_n)
-// (1 / hh is a power of two); otherwise each face is scaled by its axis.
+// (1 / hh is a power of two, passed as s0); otherwise each face is scaled by
+// its axis (s0, s1, s2 = h_i^-2, h_j^-2, h_k^-2).
+template <bool ISO>
+__device__ __forceinline__ float gs_node(float c, float apx, float amx, float apy, float amy, float apz,
+                                         float amz, float upx, float umx, float upy, float umy,
+                                         float upz, float umz, float f, float s0, float s1, float s2) {
+    if (ISO) {
+        const float px = c + apx, mx = c + amx, py = c + apy, my = c + amy, pz = c + apz, mz = c + amz;
+        const float diag = (px + mx) + (py + my) + (pz + mz);
+        const float off = (px * upx + mx * umx) + (py * upy + my * umy) + (pz * upz + mz * umz);
+        return __fdividef(fmaf(-s0, f, off), diag);
+    }
+    const float px = 0.5f * (c + apx) * s0, mx = 0.5f * (c + amx) * s0;
+    const float py = 0.5f * (c + apy) * s1, my = 0.5f * (c + amy) * s1;
+    const float pz = 0.5f * (c + apz) * s2, mz = 0.5f * (c + amz) * s2;
+    const float diag = (px + mx) + (py + my) + (pz + mz);
+    const float off = (px * upx + mx * umx) + (py * upy + my * umy) + (pz * upz + mz * umz);
+    return __fdividef(off - f, diag);
+}
+
+// the value of column z (0: k, 1: k + 1) of a pair, and of the other column
+__device__ __forceinline__ float pick(float2 v, int z) { return z ? v.y : v.x; }
+__device__ __forceinline__ float other(float2 v, int z) { return z ? v.x : v.y; }
+
 // PRO: the sweep also applies the coarse-grid correction of the V-cycle
 // first: u_old + P(uc) is swept, P the trilinear prolongation from the
 // coarse level dc (every axis halved).  Each thread issues the loads of its
@@ -59,7 +98,7 @@ static_assert(NR == 330 && (TJ + 2) * 32 == 320, "red task split");
 // updates.
 // COR: the swept values are also added to the FP64 field u64 (the defect
 // correction phidot += e of the mixed-precision solve) as they are written;
-// the u64 values are loaded at the start of the iteration that writes them.
+// the u64 values are loaded one iteration before the one that writes them.
 template <bool ISO, int CI, bool PRO, bool COR>
 __global__ void __launch_bounds__(NT) k_rbgs_stream(Dims d, float hx, float hy, float hz,
                                                     const float* __restrict__ u_old,
@@ -74,78 +113,71 @@ __global__ void __launch_bounds__(NT) k_rbgs_stream(Dims d, float hx, float hy, 
     float* sf = sa + SU * PL;
     const int t = threadIdx.x;
     const int k0 = blockIdx.x * TK, j0 = blockIdx.y * TJ, i0 = blockIdx.z * CI;
-    static_assert(CI % 2 == 0, "the plane parity of iteration it is (it + 1) & 1");
+    static_assert(CI % 2 == 0, "the parity of plane i0 - 1 + it is (it + 1) & 1");
     const int plane = d.n1 * d.n2;
+    const float s0 = ISO ? 1.0f / hx : hx;  // ISO: hx holds hh, a power of two
 
     // ---- offsets fixed for the whole block -------------------------------
-    // fetch: this thread's chunk of a u/a plane and of an f plane
-    int ua_s = -1, ua_g = 0, f_s = -1, f_g = 0;
+    // fetch: this thread's 16-byte chunk of a u/a plane and of an f plane
+    int ua_s = -1, ua_g = 0;
     if (t < NUA) {
         const int r = t / CH, ch = t - r * CH;
         ua_s = r * RK + ch * 4;
         ua_g = (((j0 + r - H) & (d.n1 - 1)) << d.s2) + ((k0 - KO + ch * 4) & (d.n2 - 1));
     }
+    int f_s = -1, f_g = 0;
     if (t < NF) {
         const int r = t / CH, ch = t - r * CH;
         f_s = (r + 1) * RK + ch * 4;
         f_g = (((j0 + r - 1) & (d.n1 - 1)) << d.s2) + ((k0 - KO + ch * 4) & (d.n2 - 1));
     }
-    // Colour nodes are assigned so that each warp takes 16 nodes of a row and
-    // the 16 nodes below them in the next row: the colours alternate from row
-    // to row and RK is even, so the two half-warps read opposite bank parities
-    // and the stride-2 access is free of bank conflicts.
-    // Red tasks r = t and t + NT cover the 33 red nodes c = 0 .. 32 of each of
-    // the ring rows jj = -1 .. TJ: r < 320 takes c = 1 .. 32 by row pairs, and
-    // r = 320 .. 329 takes c = 0 of the ten rows.  Stored: smem offset of the
-    // node with zero parity shift and the row's parity (the shift is
-    // (q + j0 + jj + k0 - 1) & 1, i.e. the plane parity xor the row's).
-    int red_e[2], red_p[2];
+    // Columns: warp w takes rows 2 (w / 2) and 2 (w / 2) + 1 (one per half
+    // warp) and column pairs 16 (w & 1) .. + 15.  The red column of a pair in
+    // plane q is k = q + j (mod 2) (red: i + j + k even), so the two half
+    // warps use opposite bank parities (RK = 8 mod 32) and the stride-2
+    // accesses are free of bank conflicts.  z[m]: the offset (0 or 1) in the
+    // pair of the column updated at iterations of parity m (plane
+    // q = i0 - 1 + it has the parity of it + 1).
+    const int w = t >> 5, lane = t & 31;
+    const int jj = 2 * (w >> 1) + (lane >> 4), pr = 16 * (w & 1) + (lane & 15);
+    const int jg = j0 + jj;
+    int z[2], ez[2], en[2];
 #pragma unroll
     for (int m = 0; m < 2; ++m) {
-        const int r = t + m * NT;
-        int jj = 0, c = -1;
-        if (r < 320) {
-            const int wt = r >> 5, lane = r & 31;
-            jj = 2 * (wt >> 1) + (lane >> 4) - 1;
-            c = 1 + 16 * (wt & 1) + (lane & 15);
-        } else if (r < NR) {
-            jj = r - 320 - 1;
-            c = 0;
-        }
-        if (c >= 0) {
-            red_e[m] = (jj + H) * RK + (2 * c - 1 + KO);
-            red_p[m] = (j0 + jj + k0 - 1) & 1;
-        } else {
-            red_e[m] = -1, red_p[m] = 0;
-        }
+        z[m] = (m + 1 + jg) & 1;
+        ez[m] = (jj + H) * RK + KO + 2 * pr + z[m];
+        en[m] = ez[m] + (z[m] ? 1 : -1);  // the k neighbour in the adjacent pair
     }
-    // black node t on the tile: 4 row pairs x 2 chunks of 16 of the 32 black
-    // nodes per row; shift (p + j0 + jj + k0 + 1) & 1
-    const int bw = t >> 5, blane = t & 31;
-    const int blk_row = 2 * (bw >> 1) + (blane >> 4), blk_c = 16 * (bw & 1) + (blane & 15);
-    const int blk_e = (blk_row + H) * RK + (2 * blk_c + KO);
-    const int blk_p = (j0 + blk_row + k0 + 1) & 1;
-    // the node offsets for an even and an odd plane
-    int red0[2], red1[2];
+    const int ep = (jj + H) * RK + KO + 2 * pr;  // the pair in a plane buffer (8-byte aligned)
+    const int gp = (jg << d.s2) + k0 + 2 * pr;   // the pair in a global plane
+    // Ring tasks (threads t < NRING): the red node of row -1 or TJ (t < 66:
+    // the 33 red nodes of each row) or of column -1 or TK of tile row t - 66.
+    // ring_e: smem offset of the node in a plane of even and of odd q - i0.
+    int ring_e[2] = {-1, -1};
+    if (t < NRING) {
 #pragma unroll
-    for (int m = 0; m < 2; ++m) red0[m] = red_e[m] + red_p[m], red1[m] = red_e[m] + (1 ^ red_p[m]);
-    const int blk0 = blk_e + blk_p, blk1 = blk_e + (1 ^ blk_p);
-    // outputs t and t + NT
-    int out_s[2], out_g[2];
-#pragma unroll
-    for (int m = 0; m < 2; ++m) {
-        const int e = t + m * NT;
-        const int jj = e / TK, kk = e - jj * TK;
-        out_s[m] = (jj + H) * RK + (kk + KO);
-        out_g[m] = ((j0 + jj) << d.s2) + k0 + kk;
+        for (int m = 0; m < 2; ++m) {
+            int rj, kc;
+            if (t < 64) {  // half warps: rows -1 and TJ (opposite bank parities), nodes 0 .. 31
+                rj = (t & 16) ? TJ : -1;
+                const int c = 16 * (t >> 5) + (t & 15);
+                kc = 2 * c - 1 + ((m + j0 + rj + k0 - 1) & 1);
+            } else if (t < 66) {  // node 32 of rows -1 and TJ
+                rj = t == 64 ? -1 : TJ;
+                kc = 2 * 32 - 1 + ((m + j0 + rj + k0 - 1) & 1);
+            } else {              // the red one of columns -1 and TK
+                rj = t - 66;
+                kc = ((m + j0 + rj + k0 - 1) & 1) ? TK : -1;
+            }
+            ring_e[m] = (rj + H) * RK + KO + kc;
+        }
     }
 
-    // Plane x is held in ring slot (x - (i0 - 2)) mod SU of u and a and
-    // (x - (i0 - 2)) mod SF of f.  The plane loop is unrolled, so with
-    // q = i0 - 1 + it every slot offset below is a compile-time constant.
-    // Copies run two planes ahead: iteration it issues u, a of plane q + 3
-    // and f of plane q + 2 and then waits only for the previous iteration's
-    // copies, so one group is always in flight while a plane is updated.
+    // Plane x is held in ring slot (x - (i0 - 2)) mod SU of u, a and f.  The
+    // plane loop is unrolled, so with q = i0 - 1 + it every slot offset below
+    // is a compile-time constant.  Iteration it issues the copies of plane
+    // q + 1 + PD and, before its barrier, waits for those the next iteration
+    // reads.
     auto pbase = [&](int q) { return (q & (d.n0 - 1)) * plane; };
     auto fetch_ua = [&](int q, int slot) {
         if (ua_s >= 0) {
@@ -156,6 +188,10 @@ __global__ void __launch_bounds__(NT) k_rbgs_stream(Dims d, float hx, float hy, 
             }
             cp_async16(sa + so, a + g);
         }
+    };
+    // f is read for the planes of the red updates, i0 - 1 .. i0 + CI
+    auto fetch_f = [&](int q, int slot) {
+        if (f_s >= 0) cp_async16(sf + slot + f_s, f + pbase(q) + f_g);
     };
     // PRO: coarse offsets of this thread's chunk (fine row gj, fine columns
     // gk .. gk + 3 with gk a multiple of 4): rows J0, J1 (weights wj0, wj1)
@@ -214,99 +250,105 @@ __global__ void __launch_bounds__(NT) k_rbgs_stream(Dims d, float hx, float hy, 
     auto pro_store = [&](int slot, const float4& v) {
         if (PRO && ua_s >= 0) *reinterpret_cast<float4*>(su + slot + ua_s) = v;
     };
-    auto fetch_f = [&](int q, int slot) {
-        if (f_s >= 0) cp_async16(sf + slot + f_s, f + pbase(q) + f_g);
-    };
-    // Gauss-Seidel value at smem offset e of the plane in slots (cu, mu, pu)
-    // of u and a (current, previous, next plane) and cf of f.
-    const float ihh = 1.0f / hx;  // ISO: hx holds hh, a power of two
-    auto gs = [&](int cu, int mu, int pu, int cf, int e) -> float {
-        const float* ac = sa + cu;
-        const float* uc = su + cu;
-        const float c = ac[e];
-        if (ISO) {
-            const float px = c + sa[pu + e], mx = c + sa[mu + e];
-            const float py = c + ac[e + RK], my = c + ac[e - RK];
-            const float pz = c + ac[e + 1], mz = c + ac[e - 1];
-            const float diag = (px + mx) + (py + my) + (pz + mz);
-            const float off = (px * su[pu + e] + mx * su[mu + e]) + (py * uc[e + RK] + my * uc[e - RK]) +
-                              (pz * uc[e + 1] + mz * uc[e - 1]);
-            return __fdividef(fmaf(-ihh, sf[cf + e], off), diag);
-        }
-        const float apx = 0.5f * (c + sa[pu + e]) * hx, amx = 0.5f * (c + sa[mu + e]) * hx;
-        const float apy = 0.5f * (c + ac[e + RK]) * hy, amy = 0.5f * (c + ac[e - RK]) * hy;
-        const float apz = 0.5f * (c + ac[e + 1]) * hz, amz = 0.5f * (c + ac[e - 1]) * hz;
-        const float diag = (apx + amx) + (apy + amy) + (apz + amz);
-        const float off = (apx * su[pu + e] + amx * su[mu + e]) + (apy * uc[e + RK] + amy * uc[e - RK]) +
-                          (apz * uc[e + 1] + amz * uc[e - 1]);
-        return __fdividef(off - sf[cf + e], diag);
-    };
+    auto own = [&](const float* buf, int slot) { return *reinterpret_cast<const float2*>(buf + slot + ep); };
 
-    // prologue: u, a of planes i0-2 .. i0 and f of plane i0-1 (waited for);
-    // u, a of plane i0+1 and f of plane i0 (left in flight)
+    // Registers, indexed by plane x as (x - (i0 - 2)) & 3 (plane q: (it + 1) & 3):
+    // U, A: old u and a of the pair (planes q - 1 .. q + 1 and q - 2 .. q + 1);
+    // F: f of the pair (q - 1 .. q); R: the red value of the column updated
+    // for that plane (q - 2 .. q).
+    float2 U[4], A[4], F[4];
+    float R[4];
+    double2 cor = make_double2(0.0, 0.0);  // COR: u64 at the pair of the plane written next
+
+    // prologue: u, a of planes i0-2 .. i0 (waited for); with PD = 2 also
+    // plane i0+1 (left in flight)
     fetch_ua(i0 - 2, 0 * PL);
     fetch_ua(i0 - 1, 1 * PL);
     fetch_ua(i0, 2 * PL);
     fetch_f(i0 - 1, 1 * PL);
+    fetch_f(i0, 2 * PL);
     cp_commit();
     if (PRO) {
         pro_store(0 * PL, pro_value(pro_load(i0 - 2)));
         pro_store(1 * PL, pro_value(pro_load(i0 - 1)));
         pro_store(2 * PL, pro_value(pro_load(i0)));
-        pro_store(3 * PL, pro_value(pro_load(i0 + 1)));
+        if (PD == 2) pro_store(3 * PL, pro_value(pro_load(i0 + 1)));
     }
     cp_wait_all();
     __syncthreads();
-    fetch_ua(i0 + 1, 3 * PL);
-    fetch_f(i0, 2 * PL);
-    cp_commit();
+    if (PD == 2) {
+        fetch_ua(i0 + 1, 3 * PL);
+        fetch_f(i0 + 1, 3 * PL);
+        cp_commit();
+    }
+    U[0] = own(su, 0 * PL), U[1] = own(su, 1 * PL);
+    A[0] = own(sa, 0 * PL), A[1] = own(sa, 1 * PL);
 
 #pragma unroll
     for (int it = 0; it < CI + 2; ++it) {
-        const int q = i0 - 1 + it;  // plane of the red update
-        ProRaw pend;                // PRO: raw values of plane q + 3, stored below
-        double cor[2] = {0.0, 0.0}; // COR: u64 at this thread's outputs of plane q - 1
-        if (COR && it >= 2) {
-            const int gb = pbase(q - 1);
-#pragma unroll
-            for (int m = 0; m < 2; ++m) cor[m] = u64[gb + out_g[m]];
-        }
-        if (it < CI) {
-            if (PRO) pend = pro_load(q + 3);
-            fetch_ua(q + 3, ((it + 4) % SU) * PL);
-            fetch_f(q + 2, ((it + 3) % SF) * PL);
+        const int q = i0 - 1 + it;                 // plane of the red update
+        const int iq = (it + 1) & 3;               // register index of plane q
+        const int im1 = it & 3, ip1 = (it + 2) & 3, im2 = (it + 3) & 3;  // q - 1, q + 1, q - 2
+        const int cu = ((it + 1) % SU) * PL, mu = (it % SU) * PL, pu = ((it + 2) % SU) * PL;
+        const int zz = z[it & 1], e = ez[it & 1], en_ = en[it & 1];
+        const bool fetch = it <= CI + 1 - PD;
+        ProRaw pend;                               // PRO: raw values of plane q + 1 + PD
+        if (fetch) {
+            if (PRO) pend = pro_load(q + 1 + PD);
+            fetch_ua(q + 1 + PD, ((it + 2 + PD) % SU) * PL);
+            if (it + PD <= CI) fetch_f(q + 1 + PD, ((it + 2 + PD) % SU) * PL);
         }
         cp_commit();
-        // red update of plane q on the tile + 1-node ring (reads old black)
+        const double2 cor_now = cor;
+        if (COR && it >= 1 && it <= CI) cor = *reinterpret_cast<const double2*>(u64 + pbase(q) + gp);
+        U[ip1] = own(su, pu);
+        A[ip1] = own(sa, pu);
+        F[iq] = own(sf, cu);
+
+        // red update of plane q at this thread's column
         {
-            const int cu = ((it + 1) % SU) * PL, mu = (it % SU) * PL, pu = ((it + 2) % SU) * PL;
-            const int cf = ((it + 1) % SF) * PL;
-#pragma unroll
-            for (int m = 0; m < 2; ++m)
-                if (red_e[m] >= 0) {
-                    const int e = ((it + 1) & 1) ? red1[m] : red0[m];
-                    su[cu + e] = gs(cu, mu, pu, cf, e);
-                }
+            const float* ap = sa + cu;
+            const float* up = su + cu;
+            const float aN = ap[en_], uN = up[en_];
+            const float aW = other(A[iq], zz), uW = other(U[iq], zz);
+            const float r = gs_node<ISO>(pick(A[iq], zz), pick(A[ip1], zz), pick(A[im1], zz), ap[e + RK],
+                                         ap[e - RK], zz ? aN : aW, zz ? aW : aN, pick(U[ip1], zz),
+                                         pick(U[im1], zz), up[e + RK], up[e - RK], zz ? uN : uW,
+                                         zz ? uW : uN, pick(F[iq], zz), s0, hy, hz);
+            R[iq] = r;
+            if (it >= 1 && it <= CI) su[cu + e] = r;  // the black update of plane q reads it
         }
-        __syncthreads();
-        // black update of plane p = q - 1 on the tile, then write the tile
+        // red update of plane q at the ring node (the black updates read
+        // planes i0 .. i0 + CI - 1 only)
+        if (it >= 1 && it <= CI && t < NRING) {
+            const int r = ring_e[(it + 1) & 1];
+            const float* ac = sa + cu;
+            const float* uq = su + cu;
+            su[cu + r] = gs_node<ISO>(ac[r], sa[pu + r], sa[mu + r], ac[r + RK], ac[r - RK], ac[r + 1],
+                                      ac[r - 1], su[pu + r], su[mu + r], uq[r + RK], uq[r - RK],
+                                      uq[r + 1], uq[r - 1], sf[cu + r], s0, hy, hz);
+        }
+        // black update of plane q - 1 at the same column; write plane q - 1
         if (it >= 2) {
-            const int cu = (it % SU) * PL, mu = ((it - 1) % SU) * PL, pu = ((it + 1) % SU) * PL;
-            const int cf = (it % SF) * PL;
-            const int e = (it & 1) ? blk1 : blk0;
-            su[cu + e] = gs(cu, mu, pu, cf, e);
-            __syncthreads();
-            const int gb = pbase(q - 1);
-#pragma unroll
-            for (int m = 0; m < 2; ++m) {
-                const float v = su[cu + out_s[m]];
-                u_new[gb + out_g[m]] = v;
-                if (COR) u64[gb + out_g[m]] = cor[m] + (double)v;
-            }
+            const float* ap = sa + mu;
+            const float* up = su + mu;
+            const float aN = ap[en_], uN = up[en_];
+            const float aW = other(A[im1], zz), uW = R[im1];
+            const float b = gs_node<ISO>(pick(A[im1], zz), pick(A[iq], zz), pick(A[im2], zz), ap[e + RK],
+                                         ap[e - RK], zz ? aN : aW, zz ? aW : aN, R[iq], R[im2],
+                                         up[e + RK], up[e - RK], zz ? uN : uW, zz ? uW : uN,
+                                         pick(F[im1], zz), s0, hy, hz);
+            const float2 v = zz ? make_float2(R[im1], b) : make_float2(b, R[im1]);
+            const int g = pbase(q - 1) + gp;
+            *reinterpret_cast<float2*>(u_new + g) = v;
+            if (COR)
+                *reinterpret_cast<double2*>(u64 + g) =
+                    make_double2(cor_now.x + (double)v.x, cor_now.y + (double)v.y);
         }
-        // the slot of plane q + 3 was last read in the previous iteration
-        if (PRO && it < CI) pro_store(((it + 4) % SU) * PL, pro_value(pend));
-        cp_wait_prior();
+        // the slot of plane q + 1 + PD was last read in the previous iteration
+        if (PRO && fetch) pro_store(((it + 2 + PD) % SU) * PL, pro_value(pend));
+        if (PD == 1) cp_wait_all();
+        else cp_wait_prior();
         __syncthreads();
     }
 }
