@@ -162,7 +162,7 @@ def _workload(name):
 def run_gb300(a):
     import torch
 
-    from paper_1611_09638_gb300 import Recon
+    from paper_1611_09638_gb300 import Recon, resolved_params
 
     rank, world, local = _dist()
     torch.cuda.set_device(local)
@@ -184,8 +184,10 @@ def run_gb300(a):
             dist.barrier()
         torch.cuda.synchronize()
 
+    mg_kw = {} if a.inner_vcycles is None else {"inner_vcycles": a.inner_vcycles}
+
     def timed(precision, steps, warmup, profile=False):
-        kw = {} if a.inner_vcycles is None or precision != "mixed" else {"inner_vcycles": a.inner_vcycles}
+        kw = mg_kw if precision == "mixed" else {}
         R = Recon((n, n, n), box=W.box, precision=precision, profile=int(profile), k_max=a.k_max, **kw)
         R.deposit_particles(pos_dev)
         for _ in range(warmup):
@@ -220,6 +222,7 @@ def run_gb300(a):
         value_fp64 = whole_job_mcells(cells, world, ms_fp64)
         fp64 = {"value": value_fp64, "unit": "Mcells/s", "ms_per_step": ms_fp64,
                 "steps": a.fp64_steps, "vcycles_per_solve": st_fp64[0].vcycles,
+                "multigrid": _mg_settings(resolved_params((n, n, n), precision="fp64")),
                 "mixed_over_fp64": value / value_fp64}
 
     # roofline of the dominant kernel: the finest-level FP32 red-black sweep
@@ -267,7 +270,8 @@ def run_gb300(a):
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        cpu = cpu_baseline(W, st_mixed[0])
+        cpu = (cpu_baseline(W, st_fp64[0], "FP64") if st_fp64 else
+               cpu_baseline(W, st_mixed[0], "mixed"))
 
     s0 = st_mixed[0]
     line = {
@@ -278,6 +282,7 @@ def run_gb300(a):
                    "displacement": "2LPT" if W.order == 2 else "ZA", "seed": W.seed,
                    "precision": "mixed", "k_max": a.k_max, "tol_in": 1e-8, "tol_out": 1e-3,
                    "steps_per_solve": s0.steps, "vcycles_per_solve": s0.vcycles,
+                   "multigrid": _mg_settings(resolved_params((n, n, n), precision="mixed", **mg_kw)),
                    "l2": "inputs larger than L2 (working set ~1.7 GB per solve)",
                    "control": "device loop: one CUDA graph per solve (conditional nodes)",
                    "parallelism": f"replicas x{world}"},
@@ -446,10 +451,17 @@ def run_batch(a):
         print(json.dumps(line))
 
 
-def cpu_baseline(W, st):
+def _mg_settings(p):
+    """The multigrid settings a solve resolved to."""
+    return {"nu1": p.nu1, "nu2": p.nu2, "inner_vcycles": p.inner_vcycles if p.precision else None,
+            "max_vcycles": p.max_vcycles}
+
+
+def cpu_baseline(W, st, which):
     """The CPU oracle as it stands (single thread) on a bounded sample of the
     same workload: one V-cycle and one each of the per-step passes on the full
-    grid, scaled by the GPU solve's own step and V-cycle counts to one solve."""
+    grid, scaled to one solve by the step and V-cycle counts of a GPU solve
+    (the FP64 one where it ran: its V(2, 2) cycles are the oracle's)."""
     import oracle as O
 
     n = W.n
@@ -483,7 +495,7 @@ def cpu_baseline(W, st):
     solve_s = st.steps * per_step + st.vcycles * t["vcycle"] + t["deposit"]
     return {"value": n ** 3 / solve_s / 1e6, "unit": "Mcells/s", "cores": 1, "kind": "oracle",
             "sample": (f"{n}^3 grid: one oracle V-cycle ({t['vcycle']:.1f} s) and one of each "
-                       f"per-step pass ({per_step:.1f} s), scaled to the GPU solve's "
+                       f"per-step pass ({per_step:.1f} s), scaled to the {which} GPU solve's "
                        f"{st.steps} steps and {st.vcycles} V-cycles"),
             "sample_seconds": sum(t.values()), "est_solve_seconds": solve_s}
 

@@ -88,9 +88,12 @@ typedef struct {
     double a_min;        /* floor of the operator coefficient in voids, 0.01   */
     int climiter;        /* RECON_CLIM_*                                       */
     double s_side;       /* smoothing S: per-axis side weight of the 3x3x3 mean, 1/4 */
-    int nu1, nu2;        /* pre / post red-black Gauss-Seidel sweeps, 2 / 2    */
+    int nu1, nu2;        /* pre / post red-black Gauss-Seidel sweeps per level;
+                            -1 (default): 2 / 2 in RECON_FP64, 1 / 1 in
+                            RECON_MIXED (see recon_resolve_params)            */
     double tol_in;       /* stop the linear solve at ||s - L phidot|| <= tol_in ||s|| */
-    int max_vcycles;     /* V-cycle cap per step                               */
+    int max_vcycles;     /* V-cycle cap per step; -1 (default): 50 in
+                            RECON_FP64, 100 in RECON_MIXED                      */
     double tol_out;      /* stop the iteration when rms(s) <= tol_out          */
     int k_max;           /* step cap                                           */
     double d_max;        /* step limiter: max |alpha grad dphi| in cells       */
@@ -100,9 +103,9 @@ typedef struct {
     int profile;         /* nonzero: time the finest-level smoothing sweeps with
                             CUDA events (reported in recon_stats.smooth_ms)    */
     int inner_vcycles;   /* RECON_MIXED: FP32 V-cycles per FP64 defect
-                            correction (1..8, default 3); the FP64 residual is
-                            formed once per group, so the stopping test sees
-                            multiples of it                                     */
+                            correction (1..16; -1, the default: 6); the FP64
+                            residual is formed once per group, so the stopping
+                            test sees multiples of it                           */
     int density_update;  /* 0: CIC re-deposit of the tracers on the deformed mesh
                             every step (default); 1: App. A's linear update
                             m += alpha d_mu(m e^-1 d dphi) of the mass per cell  */
@@ -141,8 +144,19 @@ typedef struct {
 } recon_stats;
 
 /* Fill *p with the defaults above for an n0 x n1 x n2 grid (grid units,
- * FP64).  Always succeeds for a non-NULL p. */
+ * FP64).  The multigrid settings nu1, nu2, inner_vcycles and max_vcycles are
+ * left at -1, which recon_create resolves by p->precision.  Always succeeds
+ * for a non-NULL p. */
 int recon_default_params(recon_params* p, int n0, int n1, int n2);
+
+/* Replace, in place, every multigrid setting of *p left at -1 by the value
+ * recon_create uses for p->precision (nu1 = nu2 = 2 and max_vcycles = 50 in
+ * RECON_FP64; nu1 = nu2 = 1, inner_vcycles = 6 and max_vcycles = 100 in
+ * RECON_MIXED).  The paper leaves the cycle shape open; these are the
+ * settings that reach the stopping residual in the least time on the 256^3
+ * workload.  Other fields are not touched or checked.  RECON_E_INVALID for
+ * a NULL p. */
+int recon_resolve_params(recon_params* p);
 
 /* Create a solver (Sec. II, App. A): validates p (dims powers of two >= 8,
  * cubic cells, 0 < xi_m < 1, v_m > 1, ...), allocates every device buffer of

@@ -17,7 +17,7 @@ from . import _abi
 from ._abi import (RECON_FP64, RECON_MIXED, RECON_OK, RECON_NOT_CONVERGED, ReconError,  # noqa: F401
                    FIELDS)
 
-__all__ = ["Recon", "SolveStats", "default_params", "solve_batch", "reconstruct", "RECON_FP64", "RECON_MIXED", "ReconError"]
+__all__ = ["Recon", "SolveStats", "default_params", "resolved_params", "solve_batch", "reconstruct", "RECON_FP64", "RECON_MIXED", "ReconError"]
 
 
 def default_params(n, box=None, precision="fp64", **overrides):
@@ -36,6 +36,14 @@ def default_params(n, box=None, precision="fp64", **overrides):
         if not hasattr(p, k):
             raise KeyError(k)
         setattr(p, k, v)
+    return p
+
+
+def resolved_params(n, box=None, precision="fp64", **overrides):
+    """default_params with the multigrid settings left at -1 replaced by the
+    values recon_create uses for the precision (recon_resolve_params)."""
+    p = default_params(n, box=box, precision=precision, **overrides)
+    _abi.check(_abi.load().recon_resolve_params(C.byref(p)), "recon_resolve_params")
     return p
 
 

@@ -19,6 +19,7 @@ _I = C.POINTER(C.c_int)
 # Every function the header declares, with (restype, argtypes).
 SYMBOLS = {
     "recon_default_params": (C.c_int, None),
+    "recon_resolve_params": (C.c_int, None),
     "recon_create": (C.c_int, None),
     "recon_deposit": (C.c_int, None),
     "recon_solve": (C.c_int, None),
@@ -73,6 +74,8 @@ def load(build_if_missing: bool = True):
     lib = C.CDLL(path)
     lib.recon_default_params.restype = C.c_int
     lib.recon_default_params.argtypes = [C.POINTER(recon_params), C.c_int, C.c_int, C.c_int]
+    lib.recon_resolve_params.restype = C.c_int
+    lib.recon_resolve_params.argtypes = [C.POINTER(recon_params)]
     lib.recon_create.restype = C.c_int
     lib.recon_create.argtypes = [C.POINTER(C.c_void_p), C.POINTER(recon_params), C.c_void_p]
     lib.recon_deposit.restype = C.c_int

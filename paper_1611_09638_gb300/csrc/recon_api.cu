@@ -241,6 +241,19 @@ void smooth_sweeps(Handle* H, int l, int nu, T** cur, T** oth, const T* f, const
 
 bool pow2_ge(int v, int lo) { return v >= lo && (v & (v - 1)) == 0; }
 
+// The multigrid settings left at -1 take the precision's defaults: V(2, 2)
+// cycles and at most 50 per step in FP64; in mixed precision V(1, 1) FP32
+// cycles, 6 per FP64 defect correction and at most 100 per step (the FP64
+// residual of a correction costs as much as several FP32 sweeps, so cheaper
+// cycles in longer groups reach the same residual sooner).
+void resolve_params(recon_params* p) {
+    const bool mixed = p->precision == RECON_MIXED;
+    if (p->nu1 == -1) p->nu1 = mixed ? 1 : 2;
+    if (p->nu2 == -1) p->nu2 = mixed ? 1 : 2;
+    if (p->inner_vcycles == -1) p->inner_vcycles = 6;
+    if (p->max_vcycles == -1) p->max_vcycles = mixed ? 100 : 50;
+}
+
 int check_params(const recon_params* p) {
     if (!p) return fail(RECON_E_INVALID, "params is NULL");
     for (int a = 0; a < 3; ++a)
@@ -272,7 +285,7 @@ int check_params(const recon_params* p) {
     if (!(p->d_max > 0.0)) return fail(RECON_E_INVALID, "need d_max > 0");
     if (!(p->alpha_min > 0.0 && p->alpha_min <= 1.0)) return fail(RECON_E_INVALID, "need 0 < alpha_min <= 1");
     if (!(p->lambda_floor >= 0.0 && p->lambda_floor < 1.0)) return fail(RECON_E_INVALID, "need 0 <= lambda_floor < 1");
-    if (p->inner_vcycles < 1 || p->inner_vcycles > 8) return fail(RECON_E_INVALID, "need 1 <= inner_vcycles <= 8");
+    if (p->inner_vcycles < 1 || p->inner_vcycles > 16) return fail(RECON_E_INVALID, "need 1 <= inner_vcycles <= 16");
     if (p->density_update != 0 && p->density_update != 1) return fail(RECON_E_INVALID, "density_update must be 0 or 1");
     if (p->device_loop != 0 && p->device_loop != 1) return fail(RECON_E_INVALID, "device_loop must be 0 or 1");
     if (p->checkpoint != 0 && p->checkpoint != 1) return fail(RECON_E_INVALID, "checkpoint must be 0 or 1");
@@ -970,9 +983,9 @@ int recon_default_params(recon_params* p, int n0, int n1, int n2) {
     p->a_min = 0.01;
     p->climiter = RECON_CLIM_SOFT;
     p->s_side = 0.25;
-    p->nu1 = 2, p->nu2 = 2;
+    p->nu1 = -1, p->nu2 = -1;  // by precision (resolve_params)
     p->tol_in = 1e-8;
-    p->max_vcycles = 50;
+    p->max_vcycles = -1;
     p->tol_out = 1e-3;
     p->k_max = 40;
     p->d_max = 0.5;
@@ -980,17 +993,28 @@ int recon_default_params(recon_params* p, int n0, int n1, int n2) {
     p->lambda_floor = 0.01;
     p->replay_alpha = nullptr;
     p->profile = 0;
-    p->inner_vcycles = 3;
+    p->inner_vcycles = -1;
     p->density_update = 0;
     p->device_loop = 1;
     p->checkpoint = 0;
     return RECON_OK;
 }
 
-int recon_create(void** out, const recon_params* p, void* cuda_stream) {
+int recon_resolve_params(recon_params* p) {
+    g_err[0] = 0;
+    if (!p) return fail(RECON_E_INVALID, "params is NULL");
+    resolve_params(p);
+    return RECON_OK;
+}
+
+int recon_create(void** out, const recon_params* p_in, void* cuda_stream) {
     g_err[0] = 0;
     if (!out) return fail(RECON_E_INVALID, "out is NULL");
     *out = nullptr;
+    if (!p_in) return fail(RECON_E_INVALID, "params is NULL");
+    recon_params resolved = *p_in;
+    resolve_params(&resolved);
+    const recon_params* p = &resolved;
     int rc = check_params(p);
     if (rc) return rc;
     Handle* H = new Handle();

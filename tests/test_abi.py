@@ -27,15 +27,32 @@ def test_library_builds_and_exports_every_declared_symbol():
 
 
 def test_default_params_match_the_paper_and_the_oracle():
-    from paper_1611_09638_gb300 import default_params
+    """The FP64 defaults are the oracle's; the multigrid settings are left at
+    -1 and resolved by precision (FP64: V(2, 2), 50 cycles per step)."""
+    from paper_1611_09638_gb300 import default_params, resolved_params
     import oracle as O
 
     p = default_params((32, 16, 8))
+    assert (p.nu1, p.nu2, p.inner_vcycles, p.max_vcycles) == (-1, -1, -1, -1)
+    p = resolved_params((32, 16, 8))
     q = O.OracleParams()
     assert list(p.n) == [32, 16, 8]
     for f in ("xi_m", "v_m", "a_min", "climiter", "s_side", "nu1", "nu2", "tol_in", "max_vcycles",
               "tol_out", "k_max", "d_max", "alpha_min", "lambda_floor", "density_update"):
         assert getattr(p, f) == getattr(q, f), f
+
+
+def test_mixed_precision_defaults_and_explicit_settings_resolve():
+    """Mixed precision resolves to V(1, 1) FP32 cycles, 6 per FP64 defect
+    correction and 100 per step; explicit values are kept."""
+    from paper_1611_09638_gb300 import resolved_params
+
+    p = resolved_params((16, 16, 16), precision="mixed")
+    assert (p.nu1, p.nu2, p.inner_vcycles, p.max_vcycles) == (1, 1, 6, 100)
+    p = resolved_params((16, 16, 16), precision="mixed", nu1=2, nu2=3, inner_vcycles=4, max_vcycles=7)
+    assert (p.nu1, p.nu2, p.inner_vcycles, p.max_vcycles) == (2, 3, 4, 7)
+    p = resolved_params((16, 16, 16), precision="fp64", nu1=1)
+    assert (p.nu1, p.nu2) == (1, 2)
 
 
 def test_struct_layout_matches_header(tmp_path):
@@ -80,6 +97,7 @@ def test_create_rejects_bad_params_before_touching_the_device():
     h = C.c_void_p()
     for bad in ({"xi_m": 1.5}, {"v_m": 0.5}, {"nu1": 0, "nu2": 0}, {"s_side": 0.3},
                 {"device_loop": 2}, {"density_update": 3}, {"inner_vcycles": 0},
+                {"inner_vcycles": 17}, {"nu1": -2}, {"max_vcycles": 0},
                 {"checkpoint": 2}, {"checkpoint": 1, "density_update": 1}):
         p = default_params((16, 16, 16), **bad)
         assert lib.recon_create(C.byref(h), C.byref(p), None) == _abi.RECON_E_INVALID
