@@ -345,20 +345,23 @@ bool vcycle(Handle* H, MG<T>& g, int l, T* u, const T* f, bool zero_u,
     if (!streamed) launch_resid_restrict<T>(L, H->lv[l + 1], cur, f, g.c[l], g.f[l + 1], H->st);
     vcycle<T>(H, g, l + 1, g.u[l + 1], g.f[l + 1], true);
     int nu2 = H->p.nu2;
-    bool folded = false;
+    bool folded = false, corrected = false;
     if constexpr (sizeof(T) == sizeof(float)) {
-        // the coarse correction folded into the first post-smoothing sweep
-        if (nu2 >= 1 && launch_rbgs_prolong(L, H->lv[l + 1], g.u[l + 1], cur, oth, f, g.c[l], H->st)) {
+        // the coarse correction folded into the first post-smoothing sweep,
+        // and the defect correction too where that sweep is the last
+        double* c64 = nu2 == 1 ? correct_into : nullptr;
+        if (nu2 >= 1 &&
+            launch_rbgs_prolong(L, H->lv[l + 1], g.u[l + 1], cur, oth, f, g.c[l], H->st, c64)) {
             std::swap(cur, oth);
             nu2 -= 1;
             folded = true;
+            corrected = c64 != nullptr;
         }
     }
     if (!folded) launch_prolong_add<T>(L, H->lv[l + 1], g.u[l + 1], cur, H->st);
-    bool corrected = false;
     if constexpr (sizeof(T) == sizeof(float)) {
         // the defect correction folded into the last sweep
-        if (correct_into && nu2 >= 1) {
+        if (correct_into && !corrected && nu2 >= 1) {
             smooth_sweeps<T>(H, l, nu2 - 1, &cur, &oth, f, g.c[l], false);
             if (launch_rbgs_correct(L, cur, oth, f, g.c[l], correct_into, H->st)) {
                 std::swap(cur, oth);

@@ -131,11 +131,14 @@ int launch_resid_restrict_stream(const Level& fine, const Level& coarse, const f
 
 // The first post-smoothing sweep of an FP32 level with the V-cycle's
 // coarse-grid correction folded in (u_new <- RBGS(u_old + P(uc))) where the
-// level fits the streaming sweep and every axis is halved; returns 1, or 0
-// with nothing launched (then prolongate and sweep separately).
+// level fits the streaming sweep and every axis is halved; with u64 also
+// u64 += u_new (the defect correction, when this is the level's only
+// post-smoothing sweep).  Returns 1, or 0 with nothing launched (then
+// prolongate and sweep separately).
 bool rbgs_prolong_fits(const Level& fine);
 int launch_rbgs_prolong(const Level& fine, const Level& coarse, const float* uc, const float* u_old,
-                        float* u_new, const float* f, const float* a, cudaStream_t st);
+                        float* u_new, const float* f, const float* a, cudaStream_t st,
+                        double* u64 = nullptr);
 
 // A streaming FP32 sweep that also adds its result to an FP64 field
 // (u_new <- RBGS(u_old), u64 += u_new); returns 1, or 0 with nothing launched.

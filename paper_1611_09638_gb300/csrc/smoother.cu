@@ -99,8 +99,9 @@ __device__ __forceinline__ float other(float2 v, int z) { return z ? v.x : v.y; 
 // COR: the swept values are also added to the FP64 field u64 (the defect
 // correction phidot += e of the mixed-precision solve) as they are written;
 // the u64 values are loaded one iteration before the one that writes them.
+// Registers are capped so that 4 blocks (3 with PRO) stay resident per SM.
 template <bool ISO, int CI, bool PRO, bool COR>
-__global__ void __launch_bounds__(NT) k_rbgs_stream(Dims d, float hx, float hy, float hz,
+__global__ void __launch_bounds__(NT, PRO ? 3 : 4) k_rbgs_stream(Dims d, float hx, float hy, float hz,
                                                     const float* __restrict__ u_old,
                                                     float* __restrict__ u_new,
                                                     const float* __restrict__ f,
@@ -392,11 +393,15 @@ bool rbgs_prolong_fits(const Level& fine) {
 }
 
 // The first post-smoothing sweep with the coarse correction folded in:
-// u_new <- RBGS(u_old + P(uc)); returns 1, or 0 with nothing launched.
+// u_new <- RBGS(u_old + P(uc)), and with u64 also u64 += u_new; returns 1,
+// or 0 with nothing launched.
 int launch_rbgs_prolong(const Level& fine, const Level& coarse, const float* uc, const float* u_old,
-                        float* u_new, const float* f, const float* a, cudaStream_t st) {
+                        float* u_new, const float* f, const float* a, cudaStream_t st, double* u64) {
     if (!rbgs_prolong_fits(fine) || !u_old) return 0;
-    launch_sweep<true, false>(fine, u_old, u_new, f, a, uc, coarse.d, nullptr, st);
+    if (u64)
+        launch_sweep<true, true>(fine, u_old, u_new, f, a, uc, coarse.d, u64, st);
+    else
+        launch_sweep<true, false>(fine, u_old, u_new, f, a, uc, coarse.d, nullptr, st);
     return 1;
 }
 

@@ -7,14 +7,23 @@
 // The per-coarse-node kernel in mg_kernels.cu evaluates the 27 fine residuals
 // of each coarse node's stencil, so every fine residual is computed 27/8
 // times.  Here a block owns a 8 x 32 tile of the coarse (J, K) plane, i.e. a
-// 16 x 64 tile of the fine plane, and streams fine planes along i: the
-// residual of fine plane p is computed once per node on the tile plus its
-// low-side ring (17 x 65 nodes) into shared memory, weighted in j and k there,
-// and the i weights are applied in registers (an odd plane 2I+1 closes coarse
-// plane I and opens I+1).  u and a are held for four planes (p-1 .. p+1 and
-// the one being fetched), f for two; each plane is fetched with 16-byte
-// cp.async copies.  DRAM traffic is one read of u, a, f and one write of the
-// coarse plane.
+// 16 x 64 tile of the fine plane, and streams fine planes along i.  Each
+// thread owns one coarse node and the 2 x 2 fine columns (2J, 2J+1) x (2K,
+// 2K+1) under it for the whole stream: u and a of its columns for planes
+// p - 1 .. p + 1 and f of plane p are carried in registers (one 8-byte shared
+// load per row and plane), so the residual of its four nodes reads from
+// shared memory only the rows above and below (8-byte loads) and takes the
+// columns left and right from the neighbouring lanes by warp shuffles.  The
+// block's low-side ring of residuals (row -1 and column -1, 81 nodes) is
+// computed from shared memory by three warps.  Every thread stores the
+// residuals of its lower fine row; after the plane's barrier the next
+// iteration weights plane p in j and k (the row above from shared memory,
+// the column to the left by shuffles) and applies the i weights in registers
+// (an odd plane 2I+1 closes coarse plane I and opens I+1).  The residuals
+// alternate between two buffers, so one block-wide barrier per plane
+// suffices.  u and a are held for four planes (p-1 .. p+1 and the one being
+// fetched), f for two; each plane is fetched with 16-byte cp.async copies.
+// DRAM traffic is one read of u, a, f and one write of the coarse plane.
 #include "async_copy.cuh"
 #include "recon_internal.cuh"
 
@@ -22,7 +31,7 @@ namespace recon {
 
 namespace {
 
-constexpr int RT = 256;                 // threads
+constexpr int RT = 256;                 // threads: one per coarse node of the tile
 constexpr int FJ = 16, FK = 64;         // fine tile rows (j) and columns (k)
 constexpr int RH = 2, RKO = 4;          // halo rows / columns held
 constexpr int RRJ = FJ + 2 * RH;        // 20 rows per plane
@@ -31,15 +40,35 @@ constexpr int RPL = RRJ * RRK;          // floats per plane
 constexpr int RCH = RRK / 4;            // 16-byte chunks per row
 constexpr int NUA = RRJ * RCH;          // chunks of a u (or a) plane: 360
 constexpr int NFC = (FJ + 1) * RCH;     // chunks of an f plane (rows -1 .. FJ-1): 306
-constexpr int NRES = (FJ + 1) * (FK + 1);  // residual nodes (rows and columns -1 .. F-1): 1105
-constexpr int RES_T = (NRES + RT - 1) / RT;  // residual nodes per thread: 5
+constexpr int NRING = (FK + 1) + FJ;    // low-side ring residuals: row -1 and column -1: 81
 constexpr int SUA = 4, SFF = 2;         // ring slots of u / a and of f
-constexpr int RSMEM = (int)sizeof(float) * RPL * (2 * SUA + SFF + 1);
-static_assert(NUA <= 2 * RT && NFC <= 2 * RT, "fetch rounds");
-static_assert((FJ / 2) * (FK / 2) == RT, "one coarse node per thread");
+constexpr int RSMEM = (int)sizeof(float) * RPL * (2 * SUA + SFF + 2);
+static_assert(NUA <= 2 * RT && NFC <= 2 * RT && NRING <= RT, "fetch rounds");
+static_assert((FJ / 2) * (FK / 2) == RT && FK / 2 == 32, "one coarse node per thread, a coarse row per warp");
 
-// ISO: one spacing on every axis; hx then holds hh = h^-2 / 2, applied once
-// to the sums of the face sums c + a_n (see k_rbgs_stream).
+// The residual f - L u at a node from its coefficient c, the neighbours'
+// coefficients and values (x: i, y: j, z: k; p: +1, m: -1), u at the node
+// and f.  ISO: one spacing on every axis; hx then holds hh = h^-2 / 2,
+// applied once to the sums of the face sums c + a_n (see k_rbgs_stream).
+template <bool ISO>
+__device__ __forceinline__ float resid_node(float c, float apx, float amx, float apy, float amy, float apz,
+                                            float amz, float upx, float umx, float upy, float umy,
+                                            float upz, float umz, float uc, float f, float hx, float hy,
+                                            float hz) {
+    if (ISO) {
+        const float px = c + apx, mx = c + amx, py = c + apy, my = c + amy, pz = c + apz, mz = c + amz;
+        const float diag = (px + mx) + (py + my) + (pz + mz);
+        const float off = (px * upx + mx * umx) + (py * upy + my * umy) + (pz * upz + mz * umz);
+        return fmaf(-hx, fmaf(-diag, uc, off), f);
+    }
+    const float px = 0.5f * (c + apx) * hx, mx = 0.5f * (c + amx) * hx;
+    const float py = 0.5f * (c + apy) * hy, my = 0.5f * (c + amy) * hy;
+    const float pz = 0.5f * (c + apz) * hz, mz = 0.5f * (c + amz) * hz;
+    const float diag = (px + mx) + (py + my) + (pz + mz);
+    const float off = (px * upx + mx * umx) + (py * upy + my * umy) + (pz * upz + mz * umz);
+    return f - (off - diag * uc);
+}
+
 template <bool ISO, int CIc>
 __global__ void __launch_bounds__(RT) k_resid_restrict_stream(Dims df, Dims dc, float hx, float hy,
                                                               float hz,
@@ -51,7 +80,7 @@ __global__ void __launch_bounds__(RT) k_resid_restrict_stream(Dims df, Dims dc, 
     float* su = reinterpret_cast<float*>(smem_f4);
     float* sa = su + SUA * RPL;
     float* sf = sa + SUA * RPL;
-    float* sr = sf + SFF * RPL;
+    float* sr = sf + SFF * RPL;  // two residual planes
     const int t = threadIdx.x;
     const int K0c = blockIdx.x * (FK / 2), J0c = blockIdx.y * (FJ / 2), I0c = blockIdx.z * CIc;
     const int k0 = 2 * K0c, j0 = 2 * J0c;
@@ -72,20 +101,19 @@ __global__ void __launch_bounds__(RT) k_resid_restrict_stream(Dims df, Dims dc, 
         f_s[m] = e < NFC ? (r + 1) * RRK + ch * 4 : -1;  // fine row r - 1
         f_g[m] = (((j0 + r - 1) & (df.n1 - 1)) << df.s2) + gk;
     }
-    int res_e[RES_T];
-#pragma unroll
-    for (int m = 0; m < RES_T; ++m) {
-        const int e = t + m * RT;
-        const int r = e / (FK + 1), c = e - r * (FK + 1);  // fine row r - 1, column c - 1
-        res_e[m] = e < NRES ? (r + 1) * RRK + c + RKO - 1 : -1;
-    }
+    // warp jc = coarse row, lane kc = coarse column: fine rows 2 jc, 2 jc + 1
+    // (offsets e0, e1 of the column pair 2 kc, 2 kc + 1)
     const int jc = t >> 5, kc = t & 31;
-    const int rc_e = (2 * jc + RH) * RRK + 2 * kc + RKO;
+    const int e0 = (2 * jc + RH) * RRK + 2 * kc + RKO, e1 = e0 + RRK;
     const int out_o = ((J0c + jc) << dc.s2) + K0c + kc;
+    // ring residual of thread t < NRING: row -1 (columns -1 .. FK-1) or
+    // column -1 (rows 0 .. FJ-1)
+    const int ring_e = t < FK + 1 ? (RH - 1) * RRK + RKO + t - 1
+                                  : (t < NRING ? (t - (FK + 1) + RH) * RRK + RKO - 1 : -1);
 
     // Plane p is held in u / a slot (p - pS + 1) mod SUA and f slot
     // (p - pS) mod SFF; the plane loop is unrolled (p = pS + it), so every
-    // slot offset is a compile-time constant.
+    // slot offset and register index is a compile-time constant.
     auto gplane = [&](int p) { return (p & (df.n0 - 1)) * plane; };
     auto fetch_ua = [&](int p, int so) {
         const int g = gplane(p);
@@ -102,6 +130,13 @@ __global__ void __launch_bounds__(RT) k_resid_restrict_stream(Dims df, Dims dc, 
         for (int m = 0; m < 2; ++m)
             if (f_s[m] >= 0) cp_async16(sf + so + f_s[m], f + g + f_g[m]);
     };
+    auto ld2 = [](const float* p) { return *reinterpret_cast<const float2*>(p); };
+    const unsigned full = 0xffffffffu;
+
+    // U, A: the thread's u and a (rows 0 and 1 of its quad) for plane x at
+    // index (x - pS + 1) & 3; Rp: its residuals of the previous plane.
+    float2 U[4][2], A[4][2];
+    float Rp[4] = {0.f, 0.f, 0.f, 0.f};
 
     fetch_ua(pS - 1, 0 * RPL);
     fetch_ua(pS, 1 * RPL);
@@ -110,59 +145,86 @@ __global__ void __launch_bounds__(RT) k_resid_restrict_stream(Dims df, Dims dc, 
     cp_commit();
     cp_wait_all();
     __syncthreads();
+#pragma unroll
+    for (int x = 0; x < 2; ++x) {
+        U[x][0] = ld2(su + x * RPL + e0), U[x][1] = ld2(su + x * RPL + e1);
+        A[x][0] = ld2(sa + x * RPL + e0), A[x][1] = ld2(sa + x * RPL + e1);
+    }
 
     float acc = 0.f;
 #pragma unroll
-    for (int it = 0; it <= 2 * CIc; ++it) {
+    for (int it = 0; it <= 2 * CIc + 1; ++it) {
         const int p = pS + it;
         if (it < 2 * CIc) {
             fetch_ua(p + 2, ((it + 3) % SUA) * RPL);
             fetch_f(p + 1, ((it + 1) % SFF) * RPL);
         }
         cp_commit();
-        // residual r = f - L u of plane p on the tile and its low-side ring
-        {
-            const int cu = ((it + 1) % SUA) * RPL, mu = (it % SUA) * RPL;
-            const int pu = ((it + 2) % SUA) * RPL, cf = (it % SFF) * RPL;
-            const float* ac = sa + cu;
-            const float* uc = su + cu;
-#pragma unroll
-            for (int m = 0; m < RES_T; ++m) {
-                const int e = res_e[m];
-                if (e < 0) continue;
-                const float c = ac[e];
-                if (ISO) {
-                    const float px = c + sa[pu + e], mx = c + sa[mu + e];
-                    const float py = c + ac[e + RRK], my = c + ac[e - RRK];
-                    const float pz = c + ac[e + 1], mz = c + ac[e - 1];
-                    const float diag = (px + mx) + (py + my) + (pz + mz);
-                    const float off = (px * su[pu + e] + mx * su[mu + e]) +
-                                      (py * uc[e + RRK] + my * uc[e - RRK]) +
-                                      (pz * uc[e + 1] + mz * uc[e - 1]);
-                    sr[e] = fmaf(-hx, fmaf(-diag, uc[e], off), sf[cf + e]);
-                } else {
-                    const float apx = 0.5f * (c + sa[pu + e]) * hx, amx = 0.5f * (c + sa[mu + e]) * hx;
-                    const float apy = 0.5f * (c + ac[e + RRK]) * hy, amy = 0.5f * (c + ac[e - RRK]) * hy;
-                    const float apz = 0.5f * (c + ac[e + 1]) * hz, amz = 0.5f * (c + ac[e - 1]) * hz;
-                    const float diag = (apx + amx) + (apy + amy) + (apz + amz);
-                    const float off = (apx * su[pu + e] + amx * su[mu + e]) +
-                                      (apy * uc[e + RRK] + amy * uc[e - RRK]) +
-                                      (apz * uc[e + 1] + amz * uc[e - 1]);
-                    sr[e] = sf[cf + e] - (off - diag * uc[e]);
-                }
+        // (1/4, 1/2, 1/4) weights in j and k around fine node (2 jc, 2 kc) of
+        // plane p - 1, whose residuals were stored before the last barrier
+        if (it >= 1) {
+            const float* rb = sr + ((it - 1) & 1) * RPL;
+            const float2 up = ld2(rb + e0 - RRK);  // row 2 jc - 1
+            float la = __shfl_up_sync(full, up.y, 1);
+            float l0 = __shfl_up_sync(full, Rp[1], 1), l1 = __shfl_up_sync(full, Rp[3], 1);
+            if (kc == 0) la = rb[e0 - RRK - 1], l0 = rb[e0 - 1], l1 = rb[e1 - 1];
+            const float s = 0.25f * (0.25f * la + 0.5f * up.x + 0.25f * up.y) +
+                            0.5f * (0.25f * l0 + 0.5f * Rp[0] + 0.25f * Rp[1]) +
+                            0.25f * (0.25f * l1 + 0.5f * Rp[2] + 0.25f * Rp[3]);
+            if ((it - 1) & 1) {
+                acc += 0.5f * s;
+            } else {  // p - 1 = 2I + 1 (odd) closes coarse plane I and opens I + 1
+                if (it > 1)
+                    out[((I0c - 1 + ((it - 1) >> 1)) << (dc.s1 + dc.s2)) + out_o] = acc + 0.25f * s;
+                acc = 0.25f * s;
             }
         }
-        __syncthreads();
-        // (1/4, 1/2, 1/4) weights in j and k around fine node (2 jc, 2 kc)
-        const float* R = sr + rc_e;
-        const float s = 0.25f * (0.25f * R[-RRK - 1] + 0.5f * R[-RRK] + 0.25f * R[-RRK + 1]) +
-                        0.5f * (0.25f * R[-1] + 0.5f * R[0] + 0.25f * R[1]) +
-                        0.25f * (0.25f * R[RRK - 1] + 0.5f * R[RRK] + 0.25f * R[RRK + 1]);
-        if (!(it & 1)) {  // p = 2I + 1 (odd) closes coarse plane I and opens I + 1
-            if (it > 0) out[((I0c - 1 + (it >> 1)) << (dc.s1 + dc.s2)) + out_o] = acc + 0.25f * s;
-            acc = 0.25f * s;
-        } else {
-            acc += 0.5f * s;
+        if (it == 2 * CIc + 1) break;
+        // residual r = f - L u of plane p at the thread's four nodes
+        const int iq = (it + 1) & 3, im1 = it & 3, ip1 = (it + 2) & 3;
+        const int cu = ((it + 1) % SUA) * RPL, mu = (it % SUA) * RPL;
+        const int pu = ((it + 2) % SUA) * RPL, cf = (it % SFF) * RPL;
+        U[ip1][0] = ld2(su + pu + e0), U[ip1][1] = ld2(su + pu + e1);
+        A[ip1][0] = ld2(sa + pu + e0), A[ip1][1] = ld2(sa + pu + e1);
+        const float2 f0 = ld2(sf + cf + e0), f1 = ld2(sf + cf + e1);
+        const float2 ua = ld2(su + cu + e0 - RRK), ub = ld2(su + cu + e1 + RRK);  // rows 2jc-1, 2jc+2
+        const float2 aa = ld2(sa + cu + e0 - RRK), ab = ld2(sa + cu + e1 + RRK);
+        const float2 u0 = U[iq][0], u1 = U[iq][1], a0 = A[iq][0], a1 = A[iq][1];
+        // columns 2 kc - 1 and 2 kc + 2 from the neighbouring lanes (the tile's
+        // edge columns from shared memory)
+        float ul0 = __shfl_up_sync(full, u0.y, 1), ul1 = __shfl_up_sync(full, u1.y, 1);
+        float al0 = __shfl_up_sync(full, a0.y, 1), al1 = __shfl_up_sync(full, a1.y, 1);
+        float ur0 = __shfl_down_sync(full, u0.x, 1), ur1 = __shfl_down_sync(full, u1.x, 1);
+        float ar0 = __shfl_down_sync(full, a0.x, 1), ar1 = __shfl_down_sync(full, a1.x, 1);
+        if (kc == 0) {
+            ul0 = su[cu + e0 - 1], ul1 = su[cu + e1 - 1];
+            al0 = sa[cu + e0 - 1], al1 = sa[cu + e1 - 1];
+        }
+        if (kc == 31) {
+            ur0 = su[cu + e0 + 2], ur1 = su[cu + e1 + 2];
+            ar0 = sa[cu + e0 + 2], ar1 = sa[cu + e1 + 2];
+        }
+        const float2 up0 = U[ip1][0], up1 = U[ip1][1], um0 = U[im1][0], um1 = U[im1][1];
+        const float2 ap0 = A[ip1][0], ap1 = A[ip1][1], am0 = A[im1][0], am1 = A[im1][1];
+        const float r00 = resid_node<ISO>(a0.x, ap0.x, am0.x, a1.x, aa.x, a0.y, al0, up0.x, um0.x, u1.x, ua.x,
+                                          u0.y, ul0, u0.x, f0.x, hx, hy, hz);
+        const float r01 = resid_node<ISO>(a0.y, ap0.y, am0.y, a1.y, aa.y, ar0, a0.x, up0.y, um0.y, u1.y, ua.y,
+                                          ur0, u0.x, u0.y, f0.y, hx, hy, hz);
+        const float r10 = resid_node<ISO>(a1.x, ap1.x, am1.x, ab.x, a0.x, a1.y, al1, up1.x, um1.x, ub.x, u0.x,
+                                          u1.y, ul1, u1.x, f1.x, hx, hy, hz);
+        const float r11 = resid_node<ISO>(a1.y, ap1.y, am1.y, ab.y, a0.y, ar1, a1.x, up1.y, um1.y, ub.y, u0.y,
+                                          ur1, u1.x, u1.y, f1.y, hx, hy, hz);
+        float* rw = sr + (it & 1) * RPL;
+        *reinterpret_cast<float2*>(rw + e1) = make_float2(r10, r11);  // read by the coarse row below
+        Rp[0] = r00, Rp[1] = r01, Rp[2] = r10, Rp[3] = r11;
+        // the low-side ring from shared memory
+        if (ring_e >= 0) {
+            const int e = ring_e;
+            const float* ac = sa + cu;
+            const float* uq = su + cu;
+            rw[e] = resid_node<ISO>(ac[e], sa[pu + e], sa[mu + e], ac[e + RRK], ac[e - RRK], ac[e + 1], ac[e - 1],
+                                    su[pu + e], su[mu + e], uq[e + RRK], uq[e - RRK], uq[e + 1], uq[e - 1], uq[e],
+                                    sf[cf + e], hx, hy, hz);
         }
         cp_wait_all();
         __syncthreads();
