@@ -9,7 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librecon.so")
-SOURCES = ["recon_api.cu", "mg_kernels.cu", "step_kernels.cu", "smoother.cu", "transfer.cu", "control.cu", "adjoint.cu", "noalloc.cu"]
+SOURCES = ["recon_api.cu", "mg_kernels.cu", "step_kernels.cu", "smoother.cu", "transfer.cu", "control.cu", "adjoint.cu", "noalloc.cu", "coarse_cluster.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr"]

@@ -5,6 +5,7 @@
 // full-weighting restriction, trilinear prolongation, and a dense solve of the
 // 4^3 coarsest level with the mean constraint.  Templated on float (mixed mode)
 // and double.
+#include "mg_stencil.cuh"
 #include "recon_internal.cuh"
 #include "reduce.cuh"
 
@@ -15,30 +16,6 @@ namespace {
 constexpr int kThreads = 256;
 
 inline int nblocks(long long work) { return (int)((work + kThreads - 1) / kThreads); }
-
-// Seven-point operator pieces at node c of level L: diagonal D and
-// off-diagonal sum O, so that (L u)_c = O - D u_c.
-template <typename T>
-struct Stencil7 {
-    T diag, off;
-};
-
-template <typename T>
-__device__ inline Stencil7<T> stencil7(const Dims& d, T hx, T hy, T hz, int i, int j, int k, int c,
-                                       const T* __restrict__ u, const T* __restrict__ a) {
-    const int xp = cell_index(d, i + 1, j, k), xm = cell_index(d, i - 1, j, k);
-    const int yp = cell_index(d, i, j + 1, k), ym = cell_index(d, i, j - 1, k);
-    const int zp = cell_index(d, i, j, k + 1), zm = cell_index(d, i, j, k - 1);
-    const T ac = a[c];
-    const T h = T(0.5);
-    T apx = h * (ac + a[xp]) * hx, amx = h * (ac + a[xm]) * hx;
-    T apy = h * (ac + a[yp]) * hy, amy = h * (ac + a[ym]) * hy;
-    T apz = h * (ac + a[zp]) * hz, amz = h * (ac + a[zm]) * hz;
-    Stencil7<T> s;
-    s.diag = (apx + amx) + (apy + amy) + (apz + amz);
-    s.off = (apx * u[xp] + amx * u[xm]) + (apy * u[yp] + amy * u[ym]) + (apz * u[zp] + amz * u[zm]);
-    return s;
-}
 
 // One colour of a red-black Gauss-Seidel sweep; thread t owns the t-th node
 // of that colour (nodes of a colour alternate along the fastest axis).
@@ -247,7 +224,6 @@ __global__ void k_prolong_add(Dims df, Dims dc, int cx, int cy, int cz, const T*
 // the bordered system [L 1; 1^T 0] (65 x 65), in FP64, by one block working
 // on the augmented matrix [M | I] (65 x 130) in shared memory; the result is
 // written to global memory in the same layout.
-constexpr int kNc = 64, kNb = 65, kW = 130;
 constexpr int kInvThreads = 1024;
 constexpr size_t kInvSmem = sizeof(double) * kNb * kW;
 

@@ -79,6 +79,8 @@ struct Handle {
     double* minv = nullptr;
     int l0 = -1;        // first level of the single-block coarse V-cycle
     CoarseSet cs{};     // those levels and their coefficients
+    int lc = -1;        // the 32^3 level whose V-cycle runs as one cluster launch
+    CoarseSet cc{};     // the levels from it down
     double* part[4] = {nullptr, nullptr, nullptr, nullptr};
     double* scal = nullptr;   // device scalars
     double* hscal = nullptr;  // pinned host copy
@@ -331,6 +333,7 @@ bool vcycle(Handle* H, MG<T>& g, int l, T* u, const T* f, bool zero_u,
             double* correct_into = nullptr) {
     const int last = (int)H->lv.size() - 1;
     const Level& L = H->lv[l];
+    if (l == H->lc && launch_coarse_cluster<T>(H->cc, f, u, H->minv, zero_u, H->st)) return false;
     if (l == H->l0 && launch_coarse_vcycle<T>(H->cs, f, u, H->minv, zero_u, H->st)) return false;
     if (l == last) {
         launch_coarse_solve<T>(H->minv, f, u, H->st);
@@ -1107,6 +1110,18 @@ int recon_create(void** out, const recon_params* p_in, void* cuda_stream) {
             H->l0 = l;
             break;
         }
+    // a 32^3 level with 16^3, 8^3 and 4^3 below it runs in one cluster launch
+    if (nl >= 4) {
+        CoarseSet& cc = H->cc;
+        cc.nlev = 4;
+        cc.nu1 = p->nu1, cc.nu2 = p->nu2;
+        for (int l = 0; l < 4; ++l) {
+            cc.lv[l] = H->lv[nl - 4 + l];
+            cc.a[l] = H->mixed ? (const void*)H->c32[nl - 4 + l] : (const void*)H->c64[nl - 4 + l];
+        }
+        // (not the finest FP64 level, which sweeps with its stored faces)
+        if (coarse_cluster_fits(cc) && (H->mixed || nl > 4)) H->lc = nl - 4;
+    }
     if (H->l0 >= 0) {
         H->cs.nlev = nl - H->l0;
         H->cs.nu1 = p->nu1, H->cs.nu2 = p->nu2;

@@ -112,6 +112,14 @@ struct CoarseSet {
     const void* a[kCoarseMaxLevels];       // coefficient of each level (T*)
 };
 
+// The coarse end from a 32^3 level (32^3, 16^3, 8^3, 4^3, every axis halved)
+// in one launch of one thread-block cluster (coarse_cluster.cu); false with
+// nothing launched when cs is not that set.
+bool coarse_cluster_fits(const CoarseSet& cs);
+template <typename T>
+bool launch_coarse_cluster(const CoarseSet& cs, const T* f, T* u, const double* minv, bool zero_u,
+                           cudaStream_t st);
+
 // ---- reductions -----------------------------------------------------------
 // op: 0 = sum, 1 = min, 2 = max.  Finishes kRedBlocks partials into slot.
 void finish_reduce(const double* partials, int op, double* scalars, int slot, cudaStream_t st);
