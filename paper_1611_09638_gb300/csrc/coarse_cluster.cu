@@ -30,40 +30,40 @@ constexpr int kCR = 8;      // blocks of the cluster (portable cluster size)
 constexpr int kCT = 1024;   // threads per block
 constexpr int kCN = 32;     // edge of the top level
 
-// One level's four arrays (u, f, a, r) in a block's shared memory: the block
-// holds global planes [rank P, rank P + P) of an n^3 level; planes are owned
-// by block gi / P.
+// One level's four arrays (u, f, a, r) in a block's shared memory.  The
+// level functions take its edge N and planes per block P as template
+// arguments: the block holds global planes [rank P, rank P + P) of the N^3
+// level, and plane gi is owned by block gi / P.
 template <typename T>
 struct CLev {
     T *u, *f, *a, *r;
-    int n, lg, P;     // edge, log2 edge, planes per block
     T hx, hy, hz;
 };
 
-template <typename T>
-__device__ inline T* plane_of(const CLev<T>& L, T* X, int gi, int self) {
-    gi &= L.n - 1;
-    const int owner = gi / L.P;
+template <typename T, int N, int P>
+__device__ inline T* plane_of(T* X, int gi, int self) {
+    gi &= N - 1;
+    const int owner = gi / P;
     T* base = owner == self ? X : cg::this_cluster().map_shared_rank(X, owner);
-    return base + (gi - owner * L.P) * (L.n * L.n);
+    return base + (gi - owner * P) * (N * N);
 }
 
 // One colour of a red-black sweep on the block's planes (colour: (i + j + k)
 // parity; in-plane neighbours wrap periodically).
-template <typename T>
+template <typename T, int N, int P>
 __device__ void cl_sweep(const CLev<T>& L, int colour, int self) {
-    const int n = L.n, nn = n * n, hn = n >> 1, m = n - 1;
-    const int half = L.P * nn / 2;
+    constexpr int n = N, nn = n * n, hn = n >> 1, m = n - 1;
+    constexpr int half = P * nn / 2;
     for (int t = threadIdx.x; t < half; t += blockDim.x) {
         const int lp = t / (nn / 2), rem = t - lp * (nn / 2);
         const int j = rem / hn, kk = rem - j * hn;
-        const int gi = self * L.P + lp;
+        const int gi = self * P + lp;
         const int k = 2 * kk + ((gi + j + colour) & 1);
         const int o = j * n + k, c = lp * nn + o;
-        const T* up = plane_of(L, L.u, gi + 1, self);
-        const T* um = plane_of(L, L.u, gi - 1, self);
-        const T* ap = plane_of(L, L.a, gi + 1, self);
-        const T* am = plane_of(L, L.a, gi - 1, self);
+        const T* up = plane_of<T, N, P>(L.u, gi + 1, self);
+        const T* um = plane_of<T, N, P>(L.u, gi - 1, self);
+        const T* ap = plane_of<T, N, P>(L.a, gi + 1, self);
+        const T* am = plane_of<T, N, P>(L.a, gi - 1, self);
         const T* uc = L.u + lp * nn;
         const T* ac = L.a + lp * nn;
         const int yp = ((j + 1) & m) * n + k, ym = ((j - 1) & m) * n + k;
@@ -75,17 +75,17 @@ __device__ void cl_sweep(const CLev<T>& L, int colour, int self) {
 }
 
 // r = f - L u on the block's planes.
-template <typename T>
+template <typename T, int N, int P>
 __device__ void cl_resid(const CLev<T>& L, int self) {
-    const int n = L.n, nn = n * n, m = n - 1;
-    for (int c = threadIdx.x; c < L.P * nn; c += blockDim.x) {
+    constexpr int n = N, nn = n * n, m = n - 1;
+    for (int c = threadIdx.x; c < P * nn; c += blockDim.x) {
         const int lp = c / nn, o = c - lp * nn;
-        const int j = o >> L.lg, k = o & m;
-        const int gi = self * L.P + lp;
-        const T* up = plane_of(L, L.u, gi + 1, self);
-        const T* um = plane_of(L, L.u, gi - 1, self);
-        const T* ap = plane_of(L, L.a, gi + 1, self);
-        const T* am = plane_of(L, L.a, gi - 1, self);
+        const int j = o / n, k = o & m;
+        const int gi = self * P + lp;
+        const T* up = plane_of<T, N, P>(L.u, gi + 1, self);
+        const T* um = plane_of<T, N, P>(L.u, gi - 1, self);
+        const T* ap = plane_of<T, N, P>(L.a, gi + 1, self);
+        const T* am = plane_of<T, N, P>(L.a, gi - 1, self);
         const T* uc = L.u + lp * nn;
         const T* ac = L.a + lp * nn;
         const int yp = ((j + 1) & m) * n + k, ym = ((j - 1) & m) * n + k;
@@ -97,20 +97,20 @@ __device__ void cl_resid(const CLev<T>& L, int self) {
 }
 
 // Full weighting of the fine residual into the coarse right-hand side on the
-// coarse planes the block holds (all of them when C.P == C.n); u = 0 there.
+// coarse planes the block holds (all of them when PC == NC); u = 0 there.
 // self: the calling block (fine planes are read from whichever block holds
-// them); C's planes start at plane cself * C.P.
-template <typename T>
+// them); the coarse planes start at plane cself * PC.
+template <typename T, int NF, int PF, int NC, int PC>
 __device__ void cl_restrict(const CLev<T>& F, const CLev<T>& C, int self, int cself) {
-    const int n = C.n, nn = n * n, m = n - 1, fn = F.n, fm = fn - 1;
-    for (int c = threadIdx.x; c < C.P * nn; c += blockDim.x) {
+    constexpr int n = NC, nn = n * n, m = n - 1, fn = NF, fm = fn - 1;
+    for (int c = threadIdx.x; c < PC * nn; c += blockDim.x) {
         const int lp = c / nn, o = c - lp * nn;
-        const int J = o >> C.lg, K = o & m;
-        const int I = cself * C.P + lp;
+        const int J = o / n, K = o & m;
+        const int I = cself * PC + lp;
         T acc = T(0);
         for (int oi = -1; oi <= 1; ++oi) {
             const T wi = oi == 0 ? T(0.5) : T(0.25);
-            const T* rp = plane_of(F, F.r, 2 * I + oi, self);
+            const T* rp = plane_of<T, NF, PF>(F.r, 2 * I + oi, self);
             for (int oj = -1; oj <= 1; ++oj) {
                 const T wj = oj == 0 ? T(0.5) : T(0.25);
                 const int row = ((2 * J + oj) & fm) * fn;
@@ -127,13 +127,13 @@ __device__ void cl_restrict(const CLev<T>& F, const CLev<T>& C, int self, int cs
 
 // Trilinear prolongation of the coarse field, added on the fine planes the
 // block holds (coarse planes are read from whichever block holds them).
-template <typename T>
+template <typename T, int NC, int PC, int NF, int PF>
 __device__ void cl_prolong(const CLev<T>& C, const CLev<T>& F, int self) {
-    const int n = F.n, nn = n * n, m = n - 1, cn = C.n, cm = cn - 1;
-    for (int c = threadIdx.x; c < F.P * nn; c += blockDim.x) {
+    constexpr int n = NF, nn = n * n, m = n - 1, cn = NC, cm = cn - 1;
+    for (int c = threadIdx.x; c < PF * nn; c += blockDim.x) {
         const int lp = c / nn, o = c - lp * nn;
-        const int j = o >> F.lg, k = o & m;
-        const int i = self * F.P + lp;
+        const int j = o / n, k = o & m;
+        const int i = self * PF + lp;
         int ii[2], jj[2], kk[2];
         T wi[2], wj[2], wk[2];
         int ni, nj, nk;
@@ -145,10 +145,10 @@ __device__ void cl_prolong(const CLev<T>& C, const CLev<T>& F, int self) {
         else { kk[0] = k >> 1; kk[1] = (k >> 1) + 1; wk[0] = wk[1] = T(0.5); nk = 2; }
         T acc = T(0);
         for (int p = 0; p < ni; ++p) {
-            const T* cp = plane_of(C, C.u, ii[p], self);
+            const T* cp = plane_of<T, NC, PC>(C.u, ii[p], self);
             for (int q = 0; q < nj; ++q)
                 for (int r = 0; r < nk; ++r)
-                    acc += wi[p] * wj[q] * wk[r] * cp[((jj[q] & cm) << C.lg) + (kk[r] & cm)];
+                    acc += wi[p] * wj[q] * wk[r] * cp[(jj[q] & cm) * cn + (kk[r] & cm)];
         }
         F.u[c] += acc;
     }
@@ -156,6 +156,10 @@ __device__ void cl_prolong(const CLev<T>& C, const CLev<T>& F, int self) {
 
 // Levels: 0 = 32^3 and 1 = 16^3 spread over the cluster; 2 = 8^3 and
 // 3 = 4^3 held by block 0 alone.
+constexpr int N0 = kCN, P0 = N0 / kCR, N1 = kCN / 2, P1 = N1 / kCR, N2 = kCN / 4, P2 = N2,
+              N3 = kCN / 8, P3 = N3;
+static_assert(P0 >= 1 && P1 >= 1 && N3 * N3 * N3 == kNc, "level split");
+
 template <typename T>
 __global__ void __cluster_dims__(kCR, 1, 1) __launch_bounds__(kCT)
     k_coarse_cluster(CoarseSet cs, const T* __restrict__ f_top, T* __restrict__ u_top,
@@ -165,14 +169,11 @@ __global__ void __cluster_dims__(kCR, 1, 1) __launch_bounds__(kCT)
     extern __shared__ unsigned char smem_raw[];
     T* q = reinterpret_cast<T*>(smem_raw);
     CLev<T> L[4];
+    const int sz[4] = {P0 * N0 * N0, P1 * N1 * N1, P2 * N2 * N2, P3 * N3 * N3};
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
-        const int n = kCN >> l;
-        const int P = l == 0 ? n / kCR : (l == 1 ? n / kCR : n);
-        const int sz = P * n * n;
-        L[l].u = q, L[l].f = q + sz, L[l].a = q + 2 * sz, L[l].r = q + 3 * sz;
-        q += 4 * sz;
-        L[l].n = n, L[l].lg = 5 - l, L[l].P = P;
+        L[l].u = q, L[l].f = q + sz[l], L[l].a = q + 2 * sz[l], L[l].r = q + 3 * sz[l];
+        q += 4 * sz[l];
         L[l].hx = (T)cs.lv[l].h2i[0], L[l].hy = (T)cs.lv[l].h2i[1], L[l].hz = (T)cs.lv[l].h2i[2];
     }
     // the block's planes of a, f and u; block 0 also the whole 8^3 and 4^3 a
@@ -180,86 +181,89 @@ __global__ void __cluster_dims__(kCR, 1, 1) __launch_bounds__(kCT)
     for (int l = 0; l < 4; ++l) {
         if (l >= 2 && self != 0) continue;
         const T* ag = reinterpret_cast<const T*>(cs.a[l]);
-        const int base = (l >= 2 ? 0 : self * L[l].P) * L[l].n * L[l].n;
-        for (int c = threadIdx.x; c < L[l].P * L[l].n * L[l].n; c += blockDim.x) L[l].a[c] = ag[base + c];
+        const int base = l >= 2 ? 0 : self * sz[l];
+        for (int c = threadIdx.x; c < sz[l]; c += blockDim.x) L[l].a[c] = ag[base + c];
     }
-    {
-        const int base = self * L[0].P * kCN * kCN;
-        for (int c = threadIdx.x; c < L[0].P * kCN * kCN; c += blockDim.x) {
-            L[0].f[c] = f_top[base + c];
-            L[0].u[c] = zero_u ? T(0) : u_top[base + c];
-        }
+    for (int c = threadIdx.x; c < sz[0]; c += blockDim.x) {
+        L[0].f[c] = f_top[self * sz[0] + c];
+        L[0].u[c] = zero_u ? T(0) : u_top[self * sz[0] + c];
     }
+    // block 0: the 4^3 inverse (its kNc x kNc block of the augmented matrix),
+    // read once here so that the exact solve later runs from shared memory
+    double* minv = reinterpret_cast<double*>(q);
+    if (self == 0)
+        for (int e = threadIdx.x; e < kNc * kNc; e += blockDim.x)
+            minv[e] = aug[(e / kNc) * kW + kNb + (e % kNc)];
     cluster.sync();
     // down: the two distributed levels
-#pragma unroll
-    for (int l = 0; l < 2; ++l) {
-        for (int s = 0; s < cs.nu1; ++s)
-            for (int colour = 0; colour < 2; ++colour) {
-                cl_sweep<T>(L[l], colour, self);
-                cluster.sync();
-            }
-        cl_resid<T>(L[l], self);
-        cluster.sync();
-        if (l == 0) {
-            cl_restrict<T>(L[0], L[1], self, self);
+    for (int s = 0; s < cs.nu1; ++s)
+        for (int colour = 0; colour < 2; ++colour) {
+            cl_sweep<T, N0, P0>(L[0], colour, self);
             cluster.sync();
         }
-    }
+    cl_resid<T, N0, P0>(L[0], self);
+    cluster.sync();
+    cl_restrict<T, N0, P0, N1, P1>(L[0], L[1], self, self);
+    cluster.sync();
+    for (int s = 0; s < cs.nu1; ++s)
+        for (int colour = 0; colour < 2; ++colour) {
+            cl_sweep<T, N1, P1>(L[1], colour, self);
+            cluster.sync();
+        }
+    cl_resid<T, N1, P1>(L[1], self);
+    cluster.sync();
     // block 0: the 8^3 and 4^3 levels and the exact 4^3 solve
     if (self == 0) {
-        cl_restrict<T>(L[1], L[2], 0, 0);
+        cl_restrict<T, N1, P1, N2, P2>(L[1], L[2], 0, 0);
         __syncthreads();
         for (int s = 0; s < cs.nu1; ++s)
             for (int colour = 0; colour < 2; ++colour) {
-                cl_sweep<T>(L[2], colour, 0);
+                cl_sweep<T, N2, P2>(L[2], colour, 0);
                 __syncthreads();
             }
-        cl_resid<T>(L[2], 0);
+        cl_resid<T, N2, P2>(L[2], 0);
         __syncthreads();
-        cl_restrict<T>(L[2], L[3], 0, 0);
+        cl_restrict<T, N2, P2, N3, P3>(L[2], L[3], 0, 0);
         __syncthreads();
         if (threadIdx.x < kNc) {
             double acc = 0.0;
-            for (int c = 0; c < kNc; ++c) acc += aug[threadIdx.x * kW + kNb + c] * (double)L[3].f[c];
+            for (int c = 0; c < kNc; ++c) acc += minv[threadIdx.x * kNc + c] * (double)L[3].f[c];
             L[3].u[threadIdx.x] = (T)acc;
         }
         __syncthreads();
-        cl_prolong<T>(L[3], L[2], 0);
+        cl_prolong<T, N3, P3, N2, P2>(L[3], L[2], 0);
         __syncthreads();
         for (int s = 0; s < cs.nu2; ++s)
             for (int colour = 0; colour < 2; ++colour) {
-                cl_sweep<T>(L[2], colour, 0);
+                cl_sweep<T, N2, P2>(L[2], colour, 0);
                 __syncthreads();
             }
     }
     cluster.sync();
     // up: the two distributed levels (the 8^3 field is read from block 0)
-#pragma unroll
-    for (int l = 1; l >= 0; --l) {
-        cl_prolong<T>(L[l + 1], L[l], self);
-        cluster.sync();
-        for (int s = 0; s < cs.nu2; ++s)
-            for (int colour = 0; colour < 2; ++colour) {
-                cl_sweep<T>(L[l], colour, self);
-                cluster.sync();
-            }
-    }
-    {
-        const int base = self * L[0].P * kCN * kCN;
-        for (int c = threadIdx.x; c < L[0].P * kCN * kCN; c += blockDim.x) u_top[base + c] = L[0].u[c];
-    }
+    cl_prolong<T, N2, P2, N1, P1>(L[2], L[1], self);
+    cluster.sync();
+    for (int s = 0; s < cs.nu2; ++s)
+        for (int colour = 0; colour < 2; ++colour) {
+            cl_sweep<T, N1, P1>(L[1], colour, self);
+            cluster.sync();
+        }
+    cl_prolong<T, N1, P1, N0, P0>(L[1], L[0], self);
+    cluster.sync();
+    for (int s = 0; s < cs.nu2; ++s)
+        for (int colour = 0; colour < 2; ++colour) {
+            cl_sweep<T, N0, P0>(L[0], colour, self);
+            cluster.sync();
+        }
+    for (int c = threadIdx.x; c < sz[0]; c += blockDim.x) u_top[self * sz[0] + c] = L[0].u[c];
 }
 
 template <typename T>
 constexpr int cluster_smem() {
-    int floats = 0;
-    for (int l = 0; l < 4; ++l) {
-        const int n = kCN >> l;
-        const int P = l <= 1 ? n / kCR : n;
-        floats += 4 * P * n * n;
-    }
-    return floats * (int)sizeof(T);
+    // the four levels' arrays, then the 4^3 inverse (8-byte aligned: every
+    // level's arrays are a multiple of 8 bytes long)
+    return 4 * (P0 * N0 * N0 + P1 * N1 * N1 + P2 * N2 * N2 + P3 * N3 * N3) * (int)sizeof(T) +
+           kNc * kNc * (int)sizeof(double);
 }
 
 }  // namespace

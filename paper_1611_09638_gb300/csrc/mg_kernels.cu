@@ -467,6 +467,10 @@ __global__ void __launch_bounds__(1024) k_coarse_vcycle(CoarseSet cs, const T* _
         f[0][c] = f_top[c];
         u[0][c] = zero_u ? T(0) : u_top[c];
     }
+    // the 4^3 inverse (its kNc x kNc block of the augmented matrix) in shared
+    // memory, after the levels (8-byte aligned: 4 arrays of whole levels)
+    double* minv = reinterpret_cast<double*>(u[cs.nlev - 1] + 4 * cs.lv[cs.nlev - 1].d.cells);
+    for (int e = threadIdx.x; e < kNc * kNc; e += blockDim.x) minv[e] = aug[(e / kNc) * kW + kNb + (e % kNc)];
     __syncthreads();
     const int last = cs.nlev - 1;
     // down
@@ -506,7 +510,7 @@ __global__ void __launch_bounds__(1024) k_coarse_vcycle(CoarseSet cs, const T* _
     // coarsest: u = M^-1 [f; 0]
     if (threadIdx.x < kNc) {
         double acc = 0.0;
-        for (int c = 0; c < kNc; ++c) acc += aug[threadIdx.x * kW + kNb + c] * (double)f[last][c];
+        for (int c = 0; c < kNc; ++c) acc += minv[threadIdx.x * kNc + c] * (double)f[last][c];
         u[last][threadIdx.x] = (T)acc;
     }
     __syncthreads();
@@ -550,7 +554,7 @@ bool launch_coarse_vcycle(const CoarseSet& cs, const T* f_top, T* u_top, const d
                           bool zero_u, cudaStream_t st) {
     size_t cells = 0;
     for (int l = 0; l < cs.nlev; ++l) cells += cs.lv[l].d.cells;
-    const size_t sm = 4 * cells * sizeof(T);
+    const size_t sm = 4 * cells * sizeof(T) + kNc * kNc * sizeof(double);
     if (cs.nlev < 1 || cs.nlev > kCoarseMaxLevels || sm > kCoarseMaxSmem) return false;
     allow_smem((const void*)k_coarse_vcycle<T>, (int)kCoarseMaxSmem);
     launch_counter()++;
