@@ -36,6 +36,8 @@
 // Every shared-memory and global offset a thread uses is computed once per
 // block, and the plane loop is unrolled so that ring slots and register
 // indices are compile-time constants.
+#include <mutex>
+
 #include "async_copy.cuh"
 #include "recon_internal.cuh"
 
@@ -354,27 +356,69 @@ __global__ void __launch_bounds__(NT, PRO ? 3 : 4) k_rbgs_stream(Dims d, float h
     }
 }
 
-constexpr int CIS = 16;  // planes streamed per block
+// Planes streamed per block: 16 where the level gives enough blocks (a
+// round of resident blocks per SM streams fewer halo planes), 8 or 4 on
+// small levels, where fewer planes per block put more blocks to work.  The
+// choice minimises rounds of resident blocks times (planes + prologue).
+constexpr int kCIs[3] = {4, 8, 16};
+constexpr int kMaxDevices = 64;
+
+template <bool ISO, int CI, bool PRO, bool COR>
+void launch_ci(dim3 grid, const Level& L, float hx, float hy, float hz, const float* u_old, float* u_new,
+               const float* f, const float* a, const float* uc, const Dims& dc, double* u64, cudaStream_t st) {
+    allow_smem((const void*)k_rbgs_stream<ISO, CI, PRO, COR>, SMEM);
+    k_rbgs_stream<ISO, CI, PRO, COR><<<grid, NT, SMEM, st>>>(L.d, hx, hy, hz, u_old, u_new, f, a, uc, dc, u64);
+}
+
+// Blocks of the PRO (or plain) variant resident at once on the current device.
+template <bool PRO>
+int resident_blocks() {
+    static int cache[kMaxDevices] = {};
+    static std::mutex mu;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    int& r = cache[(dev >= 0 && dev < kMaxDevices) ? dev : 0];
+    if (!r) {
+        allow_smem((const void*)k_rbgs_stream<true, 16, PRO, false>, SMEM);
+        int sms = 0, per_sm = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rbgs_stream<true, 16, PRO, false>, NT, SMEM);
+        r = sms * per_sm > 0 ? sms * per_sm : 1;
+    }
+    return r;
+}
 
 template <bool PRO, bool COR>
 void launch_sweep(const Level& L, const float* u_old, float* u_new, const float* f, const float* a,
                   const float* uc, const Dims& dc, double* u64, cudaStream_t st) {
-    allow_smem((const void*)k_rbgs_stream<true, CIS, PRO, COR>, SMEM);
-    allow_smem((const void*)k_rbgs_stream<false, CIS, PRO, COR>, SMEM);
     const Dims& d = L.d;
-    dim3 grid(d.n2 / TK, d.n1 / TJ, d.n0 / CIS);
-    launch_counter()++;
-    if (L.h2i[0] == L.h2i[1] && L.h2i[1] == L.h2i[2]) {
-        const float hh = (float)(0.5 * L.h2i[0]);  // 2^-(2l+1): exact
-        k_rbgs_stream<true, CIS, PRO, COR><<<grid, NT, SMEM, st>>>(d, hh, hh, hh, u_old, u_new, f, a, uc,
-                                                                   dc, u64);
-    } else {
-        k_rbgs_stream<false, CIS, PRO, COR><<<grid, NT, SMEM, st>>>(
-            d, (float)L.h2i[0], (float)L.h2i[1], (float)L.h2i[2], u_old, u_new, f, a, uc, dc, u64);
+    const long long tiles = (long long)(d.n2 / TK) * (d.n1 / TJ);
+    const int resident = resident_blocks<PRO>();
+    int ci = 0;
+    long long best = 0;
+    for (int ci_try : kCIs) {
+        if (d.n0 % ci_try) continue;
+        const long long blocks = tiles * (d.n0 / ci_try);
+        const long long cost = ((blocks + resident - 1) / resident) * (ci_try + 4);
+        if (!ci || cost < best) ci = ci_try, best = cost;
     }
+    dim3 grid(d.n2 / TK, d.n1 / TJ, d.n0 / ci);
+    launch_counter()++;
+    const bool iso = L.h2i[0] == L.h2i[1] && L.h2i[1] == L.h2i[2];
+    // ISO: hh = 2^-(2l+1), exact in FP32
+    const float hx = iso ? (float)(0.5 * L.h2i[0]) : (float)L.h2i[0];
+    const float hy = iso ? hx : (float)L.h2i[1], hz = iso ? hx : (float)L.h2i[2];
+#define RECON_SWEEP_CI(CI)                                                                          \
+    (iso ? launch_ci<true, CI, PRO, COR>(grid, L, hx, hy, hz, u_old, u_new, f, a, uc, dc, u64, st)   \
+         : launch_ci<false, CI, PRO, COR>(grid, L, hx, hy, hz, u_old, u_new, f, a, uc, dc, u64, st))
+    if (ci == 4) RECON_SWEEP_CI(4);
+    else if (ci == 8) RECON_SWEEP_CI(8);
+    else RECON_SWEEP_CI(16);
+#undef RECON_SWEEP_CI
 }
 
-bool stream_fits(const Dims& d) { return d.n2 % TK == 0 && d.n1 % TJ == 0 && d.n0 % CIS == 0; }
+bool stream_fits(const Dims& d) { return d.n2 % TK == 0 && d.n1 % TJ == 0 && d.n0 % kCIs[0] == 0; }
 
 }  // namespace
 
