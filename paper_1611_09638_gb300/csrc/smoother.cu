@@ -53,6 +53,7 @@ constexpr int RK = TK + 2 * KO;        // 72 columns held per plane
 constexpr int PL = RJ * RK;            // floats per plane
 constexpr int CH = RK / 4;             // 16-byte chunks per row
 constexpr int PD = 2;                  // planes of copies in flight ahead of the one waited for
+static_assert(PD >= 2, "the prolongation is applied one iteration before a plane is read");
 constexpr int SU = 3 + PD;             // ring slots of u, a and f
 constexpr int SMEM = (int)sizeof(float) * PL * 3 * SU;
 constexpr int NUA = RJ * CH;           // chunks of one u (or a) plane: 216
@@ -93,11 +94,12 @@ __device__ __forceinline__ float other(float2 v, int z) { return z ? v.x : v.y; 
 
 // PRO: the sweep also applies the coarse-grid correction of the V-cycle
 // first: u_old + P(uc) is swept, P the trilinear prolongation from the
-// coarse level dc (every axis halved).  Each thread issues the loads of its
-// 4-node chunk of u and of the 6 or 12 coarse values the chunk's
-// interpolation needs at the start of an iteration and combines and stores
-// them to shared memory at its end, so the loads overlap the iteration's
-// updates.
+// coarse level dc (every axis halved).  u_old arrives by the same cp.async
+// copies as in the plain sweep; a plane's copies are waited for at the end of
+// the iteration before the one that first reads it, and there each thread
+// adds P(uc) to its own 4-node chunk in shared memory, from the 6 or 12
+// coarse values (an L2-resident level) it loaded at the start of that
+// iteration.
 // COR: the swept values are also added to the FP64 field u64 (the defect
 // correction phidot += e of the mixed-precision solve) as they are written;
 // the u64 values are loaded one iteration before the one that writes them.
@@ -185,10 +187,8 @@ __global__ void __launch_bounds__(NT, PRO ? 3 : 4) k_rbgs_stream(Dims d, float h
     auto fetch_ua = [&](int q, int slot) {
         if (ua_s >= 0) {
             const int so = slot + ua_s, g = pbase(q) + ua_g;
-            if (!PRO) {
-                if (u_old) cp_async16(su + so, u_old + g);
-                else *reinterpret_cast<float4*>(su + so) = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
+            if (u_old) cp_async16(su + so, u_old + g);
+            else *reinterpret_cast<float4*>(su + so) = make_float4(0.f, 0.f, 0.f, 0.f);
             cp_async16(sa + so, a + g);
         }
     };
@@ -210,12 +210,11 @@ __global__ void __launch_bounds__(NT, PRO ? 3 : 4) k_rbgs_stream(Dims d, float h
         o0 = r0 + K0, o1 = r1 + K0, o02 = r0 + K2, o12 = r1 + K2;
     }
     const int cplane = dc.n1 * dc.n2;
-    // The raw values one chunk's u + P(uc) needs: u itself and, per coarse
-    // plane (one for an even fine plane, two for an odd one), the pairs at
-    // (J0 | J1, K0..K0+1) and the values at K0 + 2.  pro_load issues the loads;
-    // pro_value combines them later, so the loads stay in flight meanwhile.
+    // The coarse values one chunk's P(uc) needs: per coarse plane (one for an
+    // even fine plane, two for an odd one), the pairs at (J0 | J1, K0..K0+1)
+    // and the values at K0 + 2.  pro_load issues the loads; pro_value combines
+    // them with the chunk of u later, so the loads stay in flight meanwhile.
     struct ProRaw {
-        float4 u;
         float2 a, b, c, e;
         float a2, b2, c2, e2;
         bool odd;
@@ -236,10 +235,9 @@ __global__ void __launch_bounds__(NT, PRO ? 3 : 4) k_rbgs_stream(Dims d, float h
             r.e = __ldg(reinterpret_cast<const float2*>(p1 + o1));
             r.c2 = __ldg(p1 + o02), r.e2 = __ldg(p1 + o12);
         }
-        r.u = __ldg(reinterpret_cast<const float4*>(u_old + pbase(q) + ua_g));
         return r;
     };
-    auto pro_value = [&](const ProRaw& r) -> float4 {
+    auto pro_value = [&](const ProRaw& r, const float4& u) -> float4 {
         float k0v = fmaf(wj1, r.b.x, wj0 * r.a.x), k1v = fmaf(wj1, r.b.y, wj0 * r.a.y);
         float k2v = fmaf(wj1, r.b2, wj0 * r.a2);
         if (r.odd) {
@@ -247,11 +245,15 @@ __global__ void __launch_bounds__(NT, PRO ? 3 : 4) k_rbgs_stream(Dims d, float h
             k1v = 0.5f * (k1v + fmaf(wj1, r.e.y, wj0 * r.c.y));
             k2v = 0.5f * (k2v + fmaf(wj1, r.e2, wj0 * r.c2));
         }
-        return make_float4(r.u.x + k0v, r.u.y + 0.5f * (k0v + k1v), r.u.z + k1v,
-                           r.u.w + 0.5f * (k1v + k2v));
+        return make_float4(u.x + k0v, u.y + 0.5f * (k0v + k1v), u.z + k1v, u.w + 0.5f * (k1v + k2v));
     };
-    auto pro_store = [&](int slot, const float4& v) {
-        if (PRO && ua_s >= 0) *reinterpret_cast<float4*>(su + slot + ua_s) = v;
+    // u + P(uc) in place on this thread's chunk of the plane in ring slot
+    // `slot` (its own copies of that plane have completed)
+    auto pro_apply = [&](int slot, const ProRaw& r) {
+        if (PRO && ua_s >= 0) {
+            float4* p = reinterpret_cast<float4*>(su + slot + ua_s);
+            *p = pro_value(r, *p);
+        }
     };
     auto own = [&](const float* buf, int slot) { return *reinterpret_cast<const float2*>(buf + slot + ep); };
 
@@ -271,11 +273,12 @@ __global__ void __launch_bounds__(NT, PRO ? 3 : 4) k_rbgs_stream(Dims d, float h
     fetch_f(i0 - 1, 1 * PL);
     fetch_f(i0, 2 * PL);
     cp_commit();
-    if (PRO) {
-        pro_store(0 * PL, pro_value(pro_load(i0 - 2)));
-        pro_store(1 * PL, pro_value(pro_load(i0 - 1)));
-        pro_store(2 * PL, pro_value(pro_load(i0)));
-        if (PD == 2) pro_store(3 * PL, pro_value(pro_load(i0 + 1)));
+    if (PRO) {  // the three planes read first: their coarse values, then u + P(uc)
+        const ProRaw r0 = pro_load(i0 - 2), r1 = pro_load(i0 - 1), r2 = pro_load(i0);
+        cp_wait_all();
+        pro_apply(0 * PL, r0);
+        pro_apply(1 * PL, r1);
+        pro_apply(2 * PL, r2);
     }
     cp_wait_all();
     __syncthreads();
@@ -295,9 +298,12 @@ __global__ void __launch_bounds__(NT, PRO ? 3 : 4) k_rbgs_stream(Dims d, float h
         const int cu = ((it + 1) % SU) * PL, mu = (it % SU) * PL, pu = ((it + 2) % SU) * PL;
         const int zz = z[it & 1], e = ez[it & 1], en_ = en[it & 1];
         const bool fetch = it <= CI + 1 - PD;
-        ProRaw pend;                               // PRO: raw values of plane q + 1 + PD
+        // PRO: plane q + PD (copied in the previous iteration, first read in
+        // the next one) gets u + P(uc) at the end of this iteration
+        const bool prolong = PRO && it <= CI + 2 - PD;
+        ProRaw pend;
+        if (prolong) pend = pro_load(q + PD);
         if (fetch) {
-            if (PRO) pend = pro_load(q + 1 + PD);
             fetch_ua(q + 1 + PD, ((it + 2 + PD) % SU) * PL);
             if (it + PD <= CI) fetch_f(q + 1 + PD, ((it + 2 + PD) % SU) * PL);
         }
@@ -348,10 +354,11 @@ __global__ void __launch_bounds__(NT, PRO ? 3 : 4) k_rbgs_stream(Dims d, float h
                 *reinterpret_cast<double2*>(u64 + g) =
                     make_double2(cor_now.x + (double)v.x, cor_now.y + (double)v.y);
         }
-        // the slot of plane q + 1 + PD was last read in the previous iteration
-        if (PRO && fetch) pro_store(((it + 2 + PD) % SU) * PL, pro_value(pend));
         if (PD == 1) cp_wait_all();
         else cp_wait_prior();
+        // this thread's copies of plane q + PD are complete; no one reads that
+        // slot before the barrier
+        if (prolong) pro_apply(((it + 1 + PD) % SU) * PL, pend);
         __syncthreads();
     }
 }
