@@ -6,9 +6,9 @@
 // sweep, residual and restriction, prolongation) leaves it bound by launch
 // gaps.  Here a cluster of kCR blocks holds the 32^3 and 16^3 levels in
 // distributed shared memory, four (two) consecutive i-planes per block, and
-// every phase ends with the cluster's hardware barrier.  A node
-// whose i-neighbour lives in another block reads it from that block's shared
-// memory (cluster.map_shared_rank).  Block 0 then gathers the 16^3 residual,
+// every phase ends with the cluster's hardware barrier.  A node whose
+// i-neighbour lives in another block reads it from that block's shared memory
+// (cluster.map_shared_rank).  Block 0 then gathers the 16^3 residual,
 // runs the 8^3 and 4^3 levels alone (block barriers), and solves the 4^3
 // level exactly with the stored inverse of the bordered system; the other
 // blocks read the 8^3 correction back from it.  The per-node arithmetic is
@@ -40,6 +40,8 @@ struct CLev {
     T hx, hy, hz;
 };
 
+// Plane gi (periodic) of array X of an N^3 level: this block's own shared
+// memory, or the owner's through the cluster's distributed shared memory.
 template <typename T, int N, int P>
 __device__ inline T* plane_of(T* X, int gi, int self) {
     gi &= N - 1;
