@@ -70,9 +70,11 @@ def _peak_hbm():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-def _traffic(kernel_tag):
+def _traffic(kernel_tag, cells):
     """DRAM bytes per launch of the dominant kernel from the committed ncu
-    summary, if it was taken on the current kernel source."""
+    summary, if it was taken on the current kernel source: (bytes, note).
+    The sweep moves each node's bytes once, so a capture on another grid is
+    scaled by the cell count, and the note says so."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
@@ -81,10 +83,13 @@ def _traffic(kernel_tag):
         with open(src, "rb") as fh:
             digest = hashlib.sha256(fh.read()).hexdigest()
         if rec.get("kernel") == kernel_tag and rec.get("sha256") == digest:
-            return float(rec["bytes_per_sweep_full_size"])
+            got, at = float(rec["bytes_per_sweep_full_size"]), int(rec["cells_captured"])
+            if at == cells:
+                return got, None
+            return got * cells / at, f"scaled by cells from the capture on {at} cells"
     except Exception:
         pass
-    return None
+    return None, None
 
 
 class Clocks:
@@ -230,13 +235,16 @@ def run_gb300(a):
     sweeps = sum(s.smooth_sweeps for s in st_prof)
     sweep_bytes = st_prof[0].smooth_bytes
     peak, peak_kind = _peak_hbm()
+    traffic, traffic_note = _traffic("rbgs_f32", cells)
     achieved = sweep_bytes / (sm_ms * 1e-3 / sweeps) / 1e9 if sweeps else None
     roof = {"bound": "hbm", "kernel": "rbgs_f32 finest-level sweep (red + black)",
             "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak if achieved else None, "peak_source": peak_kind,
-            "traffic": _traffic("rbgs_f32"), "algorithmic_bytes_per_sweep": sweep_bytes,
+            "traffic": traffic, "algorithmic_bytes_per_sweep": sweep_bytes,
             "sweeps_timed": sweeps, "share_of_solve": sm_ms / st_prof[0].ms,
             "timed_in": "one extra solve with CUDA events around each finest-level sweep"}
+    if traffic_note:
+        roof["traffic_note"] = traffic_note
 
     e2e = None
     if not a.no_e2e:
@@ -283,7 +291,7 @@ def run_gb300(a):
                    "precision": "mixed", "k_max": a.k_max, "tol_in": 1e-8, "tol_out": 1e-3,
                    "steps_per_solve": s0.steps, "vcycles_per_solve": s0.vcycles,
                    "multigrid": _mg_settings(resolved_params((n, n, n), precision="mixed", **mg_kw)),
-                   "l2": "inputs larger than L2 (working set ~1.7 GB per solve)",
+                   "l2": f"inputs larger than L2 (working set ~{cells * 235 / 1e9:.1f} GB per solve)",
                    "control": "device loop: one CUDA graph per solve (conditional nodes)",
                    "parallelism": f"replicas x{world}"},
         "fp64_gpu": fp64,
