@@ -70,6 +70,23 @@ def _peak_hbm():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+def _kernel_source_hash(rec):
+    """sha256 of what decides the captured kernel's code: its source file up to
+    the line that ends the kernel's part (rec["source_end"]), followed by the
+    helper headers it includes (rec["headers"]); host-side launch code after
+    that line does not change the kernel."""
+    csrc = os.path.join(ROOT, "paper_1611_09638_gb300", "csrc")
+    with open(os.path.join(csrc, rec["source"])) as fh:
+        text = fh.read()
+    end = rec.get("source_end")
+    if end:
+        text = text[:text.index(end)]
+    for h in rec.get("headers", []):
+        with open(os.path.join(csrc, h)) as fh:
+            text += fh.read()
+    return hashlib.sha256(text.encode()).hexdigest()
+
+
 def _traffic(kernel_tag, cells):
     """DRAM bytes per launch of the dominant kernel from the committed ncu
     summary, if it was taken on the current kernel source: (bytes, note).
@@ -79,10 +96,7 @@ def _traffic(kernel_tag, cells):
     try:
         with open(path) as fh:
             rec = json.load(fh)
-        src = os.path.join(ROOT, "paper_1611_09638_gb300", "csrc", rec["source"])
-        with open(src, "rb") as fh:
-            digest = hashlib.sha256(fh.read()).hexdigest()
-        if rec.get("kernel") == kernel_tag and rec.get("sha256") == digest:
+        if rec.get("kernel") == kernel_tag and rec.get("sha256") == _kernel_source_hash(rec):
             got, at = float(rec["bytes_per_sweep_full_size"]), int(rec["cells_captured"])
             if at == cells:
                 return got, None

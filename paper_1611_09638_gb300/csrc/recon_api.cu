@@ -1104,6 +1104,21 @@ int recon_create(void** out, const recon_params* p_in, void* cuda_stream) {
         }
     }
 #undef AL
+    // planes per block of the streaming FP32 kernels, measured per level on
+    // the level's own buffers (every choice computes the same values)
+    if (H->mixed) {
+        for (int l = 0; l + 1 < nl; ++l) {
+            tune_sweep_level(H->lv[l], &H->lv[l + 1], H->u32[l + 1], H->u32[l], H->r32[l], H->f32[l],
+                             H->c32[l], H->st);
+            tune_resid_restrict_level(H->lv[l], H->lv[l + 1], H->u32[l], H->f32[l], H->c32[l],
+                                      H->f32[l + 1], H->st);
+        }
+        if (cudaGetLastError() != cudaSuccess) {
+            free_all(H);
+            delete H;
+            return fail(RECON_E_CUDA, "tuning the streaming kernels failed");
+        }
+    }
     // the levels from the first one of at most 16^3 nodes down run in one block
     for (int l = 0; l < nl; ++l)
         if (H->lv[l].d.cells <= 4096 && nl - l <= kCoarseMaxLevels) {

@@ -90,7 +90,30 @@ struct Level {
     Dims d;
     double h2i[3];
     int coarsen[3];  // axis halved on the way to the next level
+    // planes per block measured fastest at create (tune_streaming_level) for
+    // the plain sweep, the sweep with the prolongation folded in and the
+    // residual restriction; 0: the occupancy cost model decides
+    int tune[3];
 };
+
+// Mean device time (ms) of `reps` launches issued by launch() on st, after
+// one untimed launch.
+template <typename F>
+float time_launches(cudaStream_t st, int reps, F&& launch) {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    launch();
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < reps; ++r) launch();
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ms / reps;
+}
 
 struct SourceParams {
     double xi_m, v_m;
@@ -134,6 +157,15 @@ void launch_rbgs_sweep(const Level& L, T* u, const T* f, const T* a, cudaStream_
 // Residual and full-weighting restriction of an FP32 level in one streaming
 // pass; returns 1, or 0 with nothing launched where the level does not fit
 // its tiles (then launch_resid_restrict does the work).
+// Tuning of an FP32 level at create: every planes-per-block choice of the
+// streaming sweep (plain and, with a coarse level, with the prolongation) and
+// of the streaming residual restriction is timed on the level's own buffers
+// (their contents do not matter: every choice computes the same values) and
+// the fastest is stored in L.tune.  No-op where the kernels do not apply.
+void tune_sweep_level(Level& L, const Level* coarse, const float* uc, float* u, float* w,
+                      const float* f, const float* a, cudaStream_t st);
+void tune_resid_restrict_level(Level& fine, const Level& coarse, const float* u, const float* f,
+                               const float* a, float* out, cudaStream_t st);
 int launch_resid_restrict_stream(const Level& fine, const Level& coarse, const float* u,
                                  const float* f, const float* a, float* out, cudaStream_t st);
 

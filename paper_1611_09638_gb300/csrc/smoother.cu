@@ -396,10 +396,9 @@ int resident_blocks() {
     return r;
 }
 
-template <bool PRO, bool COR>
-void launch_sweep(const Level& L, const float* u_old, float* u_new, const float* f, const float* a,
-                  const float* uc, const Dims& dc, double* u64, cudaStream_t st) {
-    const Dims& d = L.d;
+// The cost model's choice of planes per block.
+template <bool PRO>
+int model_ci(const Dims& d) {
     const long long tiles = (long long)(d.n2 / TK) * (d.n1 / TJ);
     const int resident = resident_blocks<PRO>();
     int ci = 0;
@@ -410,6 +409,16 @@ void launch_sweep(const Level& L, const float* u_old, float* u_new, const float*
         const long long cost = ((blocks + resident - 1) / resident) * (ci_try + 4);
         if (!ci || cost < best) ci = ci_try, best = cost;
     }
+    return ci;
+}
+
+// ci: planes per block (0: the level's tuned value, else the cost model's).
+template <bool PRO, bool COR>
+void launch_sweep(const Level& L, const float* u_old, float* u_new, const float* f, const float* a,
+                  const float* uc, const Dims& dc, double* u64, cudaStream_t st, int ci = 0) {
+    const Dims& d = L.d;
+    if (!ci) ci = L.tune[PRO ? 1 : 0];
+    if (!ci || d.n0 % ci) ci = model_ci<PRO>(d);
     dim3 grid(d.n2 / TK, d.n1 / TJ, d.n0 / ci);
     launch_counter()++;
     const bool iso = L.h2i[0] == L.h2i[1] && L.h2i[1] == L.h2i[2];
@@ -463,6 +472,27 @@ int launch_rbgs_correct(const Level& L, const float* u_old, float* u_new, const 
     if (!stream_fits(L.d) || !u_old) return 0;
     launch_sweep<false, true>(L, u_old, u_new, f, a, nullptr, L.d, u64, st);
     return 1;
+}
+
+void tune_sweep_level(Level& L, const Level* coarse, const float* uc, float* u, float* w,
+                      const float* f, const float* a, cudaStream_t st) {
+    if (!stream_fits(L.d)) return;
+    for (int pro = 0; pro < 2; ++pro) {
+        if (pro && !(coarse && uc && rbgs_prolong_fits(L))) continue;
+        float best_ms = 0.f;
+        int best = 0;
+        for (int ci : kCIs) {
+            if (L.d.n0 % ci) continue;
+            const float ms = time_launches(st, 3, [&] {
+                if (pro)
+                    launch_sweep<true, false>(L, u, w, f, a, uc, coarse->d, nullptr, st, ci);
+                else
+                    launch_sweep<false, false>(L, u, w, f, a, nullptr, L.d, nullptr, st, ci);
+            });
+            if (!best || ms < best_ms) best = ci, best_ms = ms;
+        }
+        L.tune[pro] = best;
+    }
 }
 
 // FP64 levels are bound by the FP64 issue rate, not by memory: the ring nodes

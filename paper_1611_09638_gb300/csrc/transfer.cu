@@ -257,11 +257,13 @@ void launch_rr_ci(int ci, dim3 grid, const Dims& df, const Dims& dc, float hx, f
 
 }  // namespace
 
-int launch_resid_restrict_stream(const Level& fine, const Level& coarse, const float* u,
-                                 const float* f, const float* a, float* out, cudaStream_t st) {
+namespace {
+
+// Coarse planes per block from the cost model: fewest rounds of resident
+// blocks times the planes each block streams (2 CIc + 1 residual planes and a
+// start-up).
+int model_rr_ci(const Level& fine, const Level& coarse) {
     const Dims& df = fine.d;
-    if (!fine.coarsen[0] || !fine.coarsen[1] || !fine.coarsen[2]) return 0;
-    if (df.n2 % FK || df.n1 % FJ || df.n0 < 4) return 0;
     int dev = 0;
     cudaGetDevice(&dev);
     int resident = 0;
@@ -278,8 +280,6 @@ int launch_resid_restrict_stream(const Level& fine, const Level& coarse, const f
         }
         resident = r;
     }
-    // coarse planes per block: fewest rounds of resident blocks times the
-    // planes each block streams (2 CIc + 1 residual planes and a start-up)
     const long long tiles = (long long)(df.n2 / FK) * (df.n1 / FJ);
     const int n0c = coarse.d.n0;
     int best = 0;
@@ -290,16 +290,52 @@ int launch_resid_restrict_stream(const Level& fine, const Level& coarse, const f
         const long long cost = ((blocks + resident - 1) / resident) * (2 * ci + 2);
         if (!best || cost < best_cost) best = ci, best_cost = cost;
     }
-    dim3 grid(df.n2 / FK, df.n1 / FJ, n0c / best);
+    return best;
+}
+
+bool rr_fits(const Level& fine) {
+    const Dims& df = fine.d;
+    return fine.coarsen[0] && fine.coarsen[1] && fine.coarsen[2] && df.n2 % FK == 0 && df.n1 % FJ == 0 &&
+           df.n0 >= 4;
+}
+
+void launch_rr_level(const Level& fine, const Level& coarse, int ci, const float* u, const float* f,
+                     const float* a, float* out, cudaStream_t st) {
+    const Dims& df = fine.d;
+    dim3 grid(df.n2 / FK, df.n1 / FJ, coarse.d.n0 / ci);
     launch_counter()++;
     if (fine.h2i[0] == fine.h2i[1] && fine.h2i[1] == fine.h2i[2]) {
         const float hh = (float)(0.5 * fine.h2i[0]);  // 2^-(2l+1): exact
-        launch_rr_ci<true>(best, grid, df, coarse.d, hh, hh, hh, u, f, a, out, st);
+        launch_rr_ci<true>(ci, grid, df, coarse.d, hh, hh, hh, u, f, a, out, st);
     } else {
-        launch_rr_ci<false>(best, grid, df, coarse.d, (float)fine.h2i[0], (float)fine.h2i[1],
+        launch_rr_ci<false>(ci, grid, df, coarse.d, (float)fine.h2i[0], (float)fine.h2i[1],
                             (float)fine.h2i[2], u, f, a, out, st);
     }
+}
+
+}  // namespace
+
+// Coarse planes per block: the level's tuned value, else the cost model's.
+int launch_resid_restrict_stream(const Level& fine, const Level& coarse, const float* u,
+                                 const float* f, const float* a, float* out, cudaStream_t st) {
+    if (!rr_fits(fine)) return 0;
+    int ci = fine.tune[2];
+    if (!ci || coarse.d.n0 % ci) ci = model_rr_ci(fine, coarse);
+    launch_rr_level(fine, coarse, ci, u, f, a, out, st);
     return 1;
+}
+
+void tune_resid_restrict_level(Level& fine, const Level& coarse, const float* u, const float* f,
+                               const float* a, float* out, cudaStream_t st) {
+    if (!rr_fits(fine)) return;
+    float best_ms = 0.f;
+    int best = 0;
+    for (int ci = 1; ci <= 16 && ci <= coarse.d.n0; ci *= 2) {
+        if (coarse.d.n0 % ci) continue;
+        const float ms = time_launches(st, 3, [&] { launch_rr_level(fine, coarse, ci, u, f, a, out, st); });
+        if (!best || ms < best_ms) best = ci, best_ms = ms;
+    }
+    fine.tune[2] = best;
 }
 
 }  // namespace recon
