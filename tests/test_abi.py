@@ -137,3 +137,20 @@ def test_package_has_no_cpu_fallback():
         pytest.skip("GPU present")
     with pytest.raises(RuntimeError):
         R.Recon((16, 16, 16))
+
+
+def test_resolve_params_touches_only_the_multigrid_settings():
+    """recon_resolve_params replaces only the -1 multigrid entries and rejects
+    a NULL pointer with a status and a message."""
+    from paper_1611_09638_gb300 import _abi, default_params
+
+    lib = _abi.load()
+    p = default_params((16, 32, 64), box=(1.0, 2.0, 4.0), precision="mixed", k_max=7, tol_in=1e-6)
+    skip = ("nu1", "nu2", "inner_vcycles", "max_vcycles", "n", "box", "replay_alpha")
+    before = {f: getattr(p, f) for f, _ in _abi.recon_params._fields_ if f not in skip}
+    assert lib.recon_resolve_params(C.byref(p)) == _abi.RECON_OK
+    after = {f: getattr(p, f) for f in before}
+    assert after == before and list(p.n) == [16, 32, 64] and list(p.box) == [1.0, 2.0, 4.0]
+    assert not p.replay_alpha  # still NULL
+    assert lib.recon_resolve_params(None) == _abi.RECON_E_INVALID
+    assert b"NULL" in lib.recon_last_error()
