@@ -17,7 +17,7 @@ __all__ = [
     "OracleParams", "CLIM_SOFT", "CLIM_LITERAL", "CLIM_STEP", "cic_deposit", "apply_L",
     "rbgs_sweep", "restrict", "prolong_add", "apply_S", "vcycle", "mg_solve", "geometry",
     "source", "step_limiter", "advance", "solve", "delta_r", "mesh_x", "min_eig_sym3", "mass_change",
-    "coarse_dims", "levels", "adjoint",
+    "coarse_dims", "levels", "adjoint", "set_threads",
 ]
 
 CLIM_SOFT, CLIM_LITERAL, CLIM_STEP = 0, 1, 2
@@ -58,7 +58,7 @@ class OracleParams:
     tol_in: float = 1e-8
     max_vcycles: int = 50
     tol_out: float = 1e-3
-    k_max: int = 40
+    k_max: int = 200
     d_max: float = 0.5
     alpha_min: float = 2.0 ** -20
     lambda_floor: float = 0.01
@@ -75,16 +75,30 @@ class OracleParams:
 
 
 def _load():
+    """Load (building if needed) the oracle library.  It runs one thread unless
+    ORACLE_THREADS or set_threads() asks for more; idle threads sleep instead
+    of spinning, so a busy host is not slowed further."""
     global _lib
     if _lib is None:
+        import os
+
+        os.environ.setdefault("OMP_WAIT_POLICY", "PASSIVE")
         _lib = C.CDLL(build())
+        _lib.orc_set_threads(C.c_int(int(os.environ.get("ORACLE_THREADS", "1"))))
         for name in ("orc_cic_deposit", "orc_apply_L", "orc_rbgs_sweep", "orc_restrict",
                      "orc_prolong_add", "orc_apply_S", "orc_vcycle", "orc_mg_solve",
                      "orc_geometry", "orc_source", "orc_step_limiter", "orc_advance",
                      "orc_solve", "orc_delta_r", "orc_mesh_x", "orc_mass_change", "orc_adjoint"):
             getattr(_lib, name).restype = C.c_int
         _lib.orc_min_eig_sym3.restype = C.c_double
+        _lib.orc_set_threads.restype = C.c_int
     return _lib
+
+
+def set_threads(nthreads=0):
+    """Threads of the plane-split loops (OpenMP build; the results do not
+    depend on it).  nthreads > 0 sets the count; returns the count in use."""
+    return int(_load().orc_set_threads(C.c_int(int(nthreads))))
 
 
 def _dp(a: Optional[np.ndarray]):

@@ -3,10 +3,16 @@
  * of "Nonlinear reconstruction" (Zhu et al. 2016, arXiv:1611.09638).
  *
  * TEST INFRASTRUCTURE ONLY: the slow, obviously-correct reference the CUDA
- * library is checked against.  Single-threaded, FP64, plain loops in
- * ascending index order, no blocking, no fusion.  Only tests, the smoke check
- * and the benchmark's CPU-baseline leg may load it.  It shares no code with
- * the CUDA library.
+ * library is checked against.  FP64, plain loops in ascending index order, no
+ * blocking, no fusion.  Only tests, the smoke check and the benchmark's
+ * CPU-baseline leg may load it.  It shares no code with the CUDA library.
+ *
+ * Threads: built with OpenMP, the loops whose iterations write disjoint
+ * outputs and read nothing another iteration writes (stencils, one colour of
+ * a red-black sweep, transfers, per-node geometry, per-tracer moves) are split
+ * over threads by their outermost index (ORC_FOR_PLANES).  Every sum, and the
+ * CIC scatter, stays one serial loop in ascending order, so the results are
+ * bit for bit those of the single-threaded build for any thread count.
  *
  * The method, step by step (Sec. II moving-mesh iteration; App. A):
  *   init  rho_bar = mean(rho); tracer c has mass w_c = rho_c / rho_bar at
@@ -41,6 +47,13 @@
 #include <stdlib.h>
 #include <string.h>
 
+#ifdef _OPENMP
+#include <omp.h>
+#define ORC_FOR_PLANES _Pragma("omp parallel for schedule(static)")
+#else
+#define ORC_FOR_PLANES
+#endif
+
 #define ORC_E_INVALID (-1)
 #define ORC_E_NOMEM (-2)
 #define ORC_E_LIMITER (-5)
@@ -63,6 +76,18 @@ static int is_pow2_ge(int v, int lo) { return v >= lo && (v & (v - 1)) == 0; }
 
 static int dims_ok(const int n[3], int lo) {
     return is_pow2_ge(n[0], lo) && is_pow2_ge(n[1], lo) && is_pow2_ge(n[2], lo);
+}
+
+/* ---------------------------------------------------------------- threads */
+
+int orc_set_threads(int nthreads) {
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+    return omp_get_max_threads();
+#else
+    (void)nthreads;
+    return 1;
+#endif
 }
 
 /* ------------------------------------------------------------ CIC deposit */
@@ -104,6 +129,7 @@ int orc_cic_deposit(const int n[3], const double* x, const double* w, int64_t np
 int orc_apply_L(const int n[3], const double h[3], const double* a, const double* u,
                 double* out) {
     if (!n || !h || !a || !u || !out) return ORC_E_INVALID;
+    ORC_FOR_PLANES
     for (long i = 0; i < n[0]; ++i)
         for (long j = 0; j < n[1]; ++j)
             for (long k = 0; k < n[2]; ++k) {
@@ -125,7 +151,10 @@ int orc_apply_L(const int n[3], const double h[3], const double* a, const double
 int orc_rbgs_sweep(const int n[3], const double h[3], const double* a, const double* f,
                    double* u) {
     if (!n || !h || !a || !f || !u) return ORC_E_INVALID;
-    for (int colour = 0; colour < 2; ++colour)
+    /* nodes of one colour read only nodes of the other colour (even dims,
+     * periodic), so each colour's updates are independent of each other */
+    for (int colour = 0; colour < 2; ++colour) {
+        ORC_FOR_PLANES
         for (long i = 0; i < n[0]; ++i)
             for (long j = 0; j < n[1]; ++j)
                 for (long k = 0; k < n[2]; ++k) {
@@ -144,6 +173,7 @@ int orc_rbgs_sweep(const int n[3], const double h[3], const double* a, const dou
                     /* L u = off - diag u = f at this node */
                     u[c] = (off - f[c]) / diag;
                 }
+    }
     return 0;
 }
 
@@ -156,6 +186,7 @@ int orc_restrict(const int n[3], const double* fine, double* coarse) {
     int nc[3];
     coarse_dims(n, nc);
     int cz[3] = {n[0] > 4, n[1] > 4, n[2] > 4};
+    ORC_FOR_PLANES
     for (long I = 0; I < nc[0]; ++I)
         for (long J = 0; J < nc[1]; ++J)
             for (long K = 0; K < nc[2]; ++K) {
@@ -200,6 +231,7 @@ int orc_prolong_add(const int n[3], const double* coarse, double* fine) {
     if (!n || !coarse || !fine) return ORC_E_INVALID;
     int nc[3];
     coarse_dims(n, nc);
+    ORC_FOR_PLANES
     for (long i = 0; i < n[0]; ++i)
         for (long j = 0; j < n[1]; ++j)
             for (long k = 0; k < n[2]; ++k) {
@@ -223,6 +255,7 @@ int orc_apply_S(const int n[3], double s_side, const double* u, double* out) {
     /* weights (s_side, 1 - 2 s_side, s_side) along every axis: a weighted mean
      * over the 3x3x3 block of nearest neighbours */
     double w[3] = {s_side, 1.0 - 2.0 * s_side, s_side};
+    ORC_FOR_PLANES
     for (long i = 0; i < n[0]; ++i)
         for (long j = 0; j < n[1]; ++j)
             for (long k = 0; k < n[2]; ++k) {
@@ -480,6 +513,7 @@ double orc_min_eig_sym3(const double A[3][3]) {
 
 int orc_geometry(const int n[3], const double* phi, double* sqrt_g, double* lambda0) {
     if (!n || !phi || !dims_ok(n, 1)) return ORC_E_INVALID;
+    ORC_FOR_PLANES
     for (long i = 0; i < n[0]; ++i)
         for (long j = 0; j < n[1]; ++j)
             for (long k = 0; k < n[2]; ++k) {
@@ -522,6 +556,7 @@ int orc_source(const orc_params* p, const double* phi, const double* m, double* 
         return ORC_E_NOMEM;
     }
     orc_geometry(n, phi, g, lam);
+    ORC_FOR_PLANES
     for (size_t c = 0; c < len; ++c) {
         double Sigma = 1.0 - m[c];                          /* deviation density */
         double C = climit(p->climiter, p->xi_m, lam[c]);    /* compression limiter */
@@ -560,17 +595,34 @@ int orc_step_limiter(const orc_params* p, const double* phi, const double* dphi,
                      double* alpha) {
     if (!p || !phi || !dphi || !alpha || !dims_ok(p->n, 1)) return ORC_E_INVALID;
     const int* n = p->n;
-    double gmax = 0.0;
-    for (long i = 0; i < n[0]; ++i)
+    /* per-plane results (max |grad dphi|, "every node admissible"), combined
+     * after the plane loop: a max and an AND do not depend on the order */
+    double* gplane = (double*)malloc((size_t)n[0] * sizeof(double));
+    int* okplane = (int*)malloc((size_t)n[0] * sizeof(int));
+    if (!gplane || !okplane) {
+        free(gplane), free(okplane);
+        return ORC_E_NOMEM;
+    }
+    ORC_FOR_PLANES
+    for (long i = 0; i < n[0]; ++i) {
+        double gm = 0.0;
         for (long j = 0; j < n[1]; ++j)
             for (long k = 0; k < n[2]; ++k)
                 for (int ax = 0; ax < 3; ++ax) {
                     double g = fabs(cgrad(n, dphi, i, j, k, ax));
-                    if (g > gmax) gmax = g;
+                    if (g > gm) gm = g;
                 }
+        gplane[i] = gm;
+    }
+    double gmax = 0.0;
+    for (long i = 0; i < n[0]; ++i)
+        if (gplane[i] > gmax) gmax = gplane[i];
+    int rc = ORC_E_LIMITER;
     for (double al = 1.0; al >= p->alpha_min; al *= 0.5) {
-        int ok = al * gmax <= p->d_max;
-        for (long i = 0; ok && i < n[0]; ++i)
+        if (!(al * gmax <= p->d_max)) continue;
+        ORC_FOR_PLANES
+        for (long i = 0; i < n[0]; ++i) {
+            int ok = 1;
             for (long j = 0; ok && j < n[1]; ++j)
                 for (long k = 0; ok && k < n[2]; ++k) {
                     double H0[3][3], H1[3][3], M[3][3];
@@ -581,12 +633,18 @@ int orc_step_limiter(const orc_params* p, const double* phi, const double* dphi,
                             M[a][b] = (a == b ? 1.0 : 0.0) + H0[a][b] + al * H1[a][b];
                     ok = pd_sylvester(M, p->lambda_floor);
                 }
+            okplane[i] = ok;
+        }
+        int ok = 1;
+        for (long i = 0; i < n[0]; ++i) ok = ok && okplane[i];
         if (ok) {
             *alpha = al;
-            return 0;
+            rc = 0;
+            break;
         }
     }
-    return ORC_E_LIMITER;
+    free(gplane), free(okplane);
+    return rc;
 }
 
 /* -------------------------------------------------------------- advance */
@@ -602,6 +660,7 @@ int orc_advance(const int n[3], double alpha, const double* dphi, double* phi, d
      * gradient of dphi; phi is read before its own update. */
     double* V = (double*)malloc(3 * len * sizeof(double));
     if (!V) return ORC_E_NOMEM;
+    ORC_FOR_PLANES
     for (long i = 0; i < n[0]; ++i)
         for (long j = 0; j < n[1]; ++j)
             for (long k = 0; k < n[2]; ++k) {
@@ -622,6 +681,7 @@ int orc_advance(const int n[3], double alpha, const double* dphi, double* phi, d
                 }
             }
     for (size_t c = 0; c < len; ++c) phi[c] += alpha * dphi[c];
+    ORC_FOR_PLANES
     for (int64_t t = 0; t < np; ++t) {
         long i0[3];
         double f[3], v[3] = {0.0, 0.0, 0.0};
@@ -701,6 +761,7 @@ int orc_mass_change(const int n[3], const double* phi, const double* m, const do
 
 int orc_delta_r(const int n[3], const double* phi, double* out) {
     if (!n || !phi || !out || !dims_ok(n, 1)) return ORC_E_INVALID;
+    ORC_FOR_PLANES
     for (long i = 0; i < n[0]; ++i)
         for (long j = 0; j < n[1]; ++j)
             for (long k = 0; k < n[2]; ++k) {
@@ -713,6 +774,7 @@ int orc_delta_r(const int n[3], const double* phi, double* out) {
 
 int orc_mesh_x(const int n[3], const double* phi, double* out) {
     if (!n || !phi || !out || !dims_ok(n, 1)) return ORC_E_INVALID;
+    ORC_FOR_PLANES
     for (long i = 0; i < n[0]; ++i)
         for (long j = 0; j < n[1]; ++j)
             for (long k = 0; k < n[2]; ++k) {

@@ -61,6 +61,11 @@ typedef struct {
     double* mass;       /* sum of the deposited mass m at step start             */
 } orc_trace;
 
+/* Threads for the loops that split over planes (OpenMP builds; results do
+ * not depend on the count).  nthreads > 0 sets the count; returns the count
+ * in use (1 in a build without OpenMP). */
+int orc_set_threads(int nthreads);
+
 /* CIC deposit (Sec. III density gridding; Sec. IV "assign particles to a
  * uniform grid"): out[j] = sum_p w_p prod_a max(0, 1 - |d_a|), d = x_p - j wrapped
  * periodically.  x in grid units, w == NULL means unit masses. */

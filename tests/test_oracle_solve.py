@@ -221,3 +221,25 @@ def test_paper_literal_density_update():
     assert np.array_equal(a.phi, b.phi)
     u = O.solve(O.OracleParams(n=(16, 8, 8), density_update=1), np.full((16, 8, 8), 2.0))
     assert u.status == 0 and u.steps == 0
+
+
+def test_thread_count_does_not_change_a_bit():
+    """The OpenMP build splits only loops with independent iterations over
+    threads and keeps every sum serial, so 1 and 4 threads give the same bits
+    (a whole solve with the limiter active, and the operators on their own)."""
+    n, box = 16, 50.0
+    pos, _ = lpt_particles(n, box, 3, order=2)
+    rho = O.cic_deposit((n, n, n), pos / (box / n))
+    p = O.OracleParams(n=(n, n, n), k_max=6)
+    old = O.set_threads()
+    try:
+        outs = []
+        for t in (1, 4):
+            O.set_threads(t)
+            r = O.solve(p, rho)
+            outs.append((r.phi, r.xi, r.alpha, r.ncycles, O.geometry(r.phi)[1],
+                         O.apply_S(r.phi), O.delta_r(r.phi)))
+        for a, b in zip(*outs):
+            assert np.array_equal(a, b)
+    finally:
+        O.set_threads(old)
