@@ -18,11 +18,12 @@
  *     >= 8), C order with the last axis fastest: idx = (i*n1 + j)*n2 + k.
  *   - Cells are cubes of side h = box[a] / n[a] (all three equal).  With
  *     box = {0,0,0} the grid unit is used (h = 1).
- *   - Every array argument is a plain pointer to host OR device memory (the
- *     library tells them apart through unified addressing); device pointers
- *     must be on the device that was current at recon_create.  Inputs are
- *     borrowed for the duration of the call only; the handle owns all of its
- *     device state.
+ *   - Every array argument of the handle calls is a plain pointer to host OR
+ *     device memory (the library tells them apart through unified
+ *     addressing); host memory and another device's memory are copied to the
+ *     handle's device (the device current at recon_create) before a kernel
+ *     reads them.  Inputs are borrowed for the duration of the call only; the
+ *     handle owns all of its device state.
  *   - Every call returns a status (RECON_OK = 0, errors < 0, RECON_NOT_CONVERGED
  *     = 1 is a warning with valid results) and never traps or aborts; the
  *     thread-local text of the last error is returned by recon_last_error().
@@ -95,7 +96,8 @@ typedef struct {
     int max_vcycles;     /* V-cycle cap per step; -1 (default): 50 in
                             RECON_FP64, 100 in RECON_MIXED                      */
     double tol_out;      /* stop the iteration when rms(s) <= tol_out          */
-    int k_max;           /* step cap                                           */
+    int k_max;           /* step cap, 200: the iteration runs to its own end
+                            (rms(s) <= tol_out, or no admissible step)         */
     double d_max;        /* step limiter: max |alpha grad dphi| in cells       */
     double alpha_min;    /* step limiter: smallest admissible alpha            */
     double lambda_floor; /* step limiter: lambda_min(I + Hess phi) must exceed it */
@@ -118,6 +120,17 @@ typedef struct {
                             phidot_k on the device for recon_adjoint
                             (5 x 8 bytes x cells x k_max, allocated at create);
                             needs density_update = 0.  Default 0.               */
+    int stream_planes;   /* RECON_MIXED: i-planes per block of the streaming FP32
+                            red-black sweep on every level it runs on.  0 (the
+                            default): the fastest of 4, 8 and 16, timed per level
+                            at create; 4, 8 or 16: that value wherever the level's
+                            first dimension is a multiple of it.  Every choice
+                            computes the same bits.                            */
+    int restrict_planes; /* RECON_MIXED: coarse i-planes per block of the
+                            streaming residual + full-weighting restriction.  0
+                            (the default): timed per level at create; 1, 2, 4, 8
+                            or 16: that value wherever it divides the coarse
+                            level.  Every choice computes the same bits.         */
 } recon_params;
 
 /* Per-solve record.  The per-step arrays are optional caller-owned host
@@ -229,24 +242,26 @@ const char* recon_last_error(void);
 
 /* CIC deposit of particles without any device allocation.  The paper has no
  * counterpart: this is the deposit of recon_deposit(RECON_PARTICLES) for
- * callers that cannot call cudaMalloc where they need it -- e.g. while a CUDA
- * graph is being captured, under an external allocator that owns all device
- * memory, or in a loop where an allocation would stall the device.
+ * callers that cannot call cudaMalloc where they need it -- e.g. code whose
+ * device memory is owned by another allocator that must account for every
+ * byte, or a loop where an allocation would synchronise the device.
  *   n0, n1, n2  grid dims, powers of two; n0*n1*n2 <= 2^21 (128^3) cells
  *   cell        cell side in the units of pos (positions wrap periodically)
  *   pos         device array of np x 3 doubles; mass: device array of np
  *               doubles, or NULL for unit masses
  *   rho         device array of n0*n1*n2 doubles, receives the mass per cell
  *   cuda_stream stream for the work (cudaStream_t, NULL = legacy stream)
- * The accumulators live in one fixed 16 MiB device array of the library
- * (allocated when the library is loaded, on every GPU that loads it, until
- * exit).  The first call on a device looks up that array's device address;
- * make that first call before any stream capture.  Every call reuses the same
- * array, so calls that overlap on the GPU (other streams or threads) race.
- * The call synchronises the stream once to check the inputs.  Larger grids,
- * host pointers, NaN/Inf or negative inputs and zero total mass are rejected
- * with a status (RECON_E_INVALID / RECON_E_NONFINITE); nothing is allocated
- * or freed. */
+ * pos, mass and rho must be memory of the current device (or managed).  The
+ * accumulators live in one fixed 16 MiB device array of the library (resident
+ * on every GPU that loads the library, until exit).  The first call on a
+ * device looks up that array's device address; after a cudaDeviceReset of the
+ * device the call must not be used there again in the same process.  Every
+ * call reuses the same array, so calls that overlap on the GPU (other streams
+ * or threads) race.  The call synchronises its stream once to check the
+ * inputs on the host, so it cannot be used while the stream is being captured
+ * into a CUDA graph.  Larger grids, host or other-device pointers, NaN/Inf or
+ * negative inputs and zero total mass are rejected with a status
+ * (RECON_E_INVALID / RECON_E_NONFINITE); nothing is allocated or freed. */
 int recon_deposit_cic_noalloc(int n0, int n1, int n2, double cell, const double* pos,
                               const double* mass, int64_t np, double* rho, void* cuda_stream);
 

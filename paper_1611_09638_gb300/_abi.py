@@ -41,7 +41,7 @@ class recon_params(C.Structure):
         ("k_max", C.c_int), ("d_max", C.c_double), ("alpha_min", C.c_double),
         ("lambda_floor", C.c_double), ("replay_alpha", _D), ("profile", C.c_int),
         ("inner_vcycles", C.c_int), ("density_update", C.c_int), ("device_loop", C.c_int),
-        ("checkpoint", C.c_int),
+        ("checkpoint", C.c_int), ("stream_planes", C.c_int), ("restrict_planes", C.c_int),
     ]
 
 

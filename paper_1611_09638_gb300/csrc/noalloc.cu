@@ -3,13 +3,15 @@
 //
 // recon_deposit accumulates particle masses in a 64-bit fixed-point grid and
 // reduces partial sums in buffers that the handle allocates.  Some callers
-// cannot allocate at the point where they need a deposit: code running while a
-// CUDA graph is being captured (cudaMalloc is not allowed then), code whose
-// device memory is owned by another allocator that must see every byte, or
-// latency-critical loops where an allocation would synchronise the device.
-// For them this file keeps the scratch in a file-scope device array of fixed
-// size, resident on every GPU that loads the library until the process exits.
-// The caller still passes the inputs and the output.
+// cannot allocate at the point where they need a deposit: code whose device
+// memory is owned by another allocator that must account for every byte (a
+// framework's caching allocator, a fixed memory pool), or loops where a
+// cudaMalloc / cudaFree would synchronise the device.  For them this file
+// keeps the scratch in a file-scope device array of fixed size, resident on
+// every GPU that loads the library until the process exits.  The caller still
+// passes the inputs and the output.  The call checks its inputs on the host
+// after one synchronisation of its stream, so it cannot run inside a stream
+// capture.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -45,7 +47,9 @@ std::mutex g_setup_mutex;
 NoallocScratch* g_scratch_addr[kMaxDevices] = {};
 
 // Device address of the scratch on the current device, looked up once per
-// device (the first call on a device does this set-up).
+// device (the first call on a device does this set-up).  A cudaDeviceReset of
+// that device ends the context the address belongs to; the entry point must
+// not be used on that device afterwards in the same process.
 int scratch_on_current_device(NoallocScratch** out) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
@@ -71,13 +75,20 @@ int scratch_on_current_device(NoallocScratch** out) {
     return RECON_OK;
 }
 
+// Device memory of the current device, or managed memory.
 bool on_device(const void* p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 bool pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
@@ -101,7 +112,7 @@ extern "C" int recon_deposit_cic_noalloc(int n0, int n1, int n2, double cell, co
     if (!(cell > 0.0) || !std::isfinite(cell)) return recon::set_last_error(RECON_E_INVALID, "cell size must be positive");
     if (np <= 0 || !pos || !rho) return recon::set_last_error(RECON_E_INVALID, "need particles, positions and an output");
     if (!on_device(pos) || !on_device(rho) || (mass && !on_device(mass)))
-        return recon::set_last_error(RECON_E_INVALID, "pos, mass and rho must be device memory");
+        return recon::set_last_error(RECON_E_INVALID, "pos, mass and rho must be device memory of the current device");
     NoallocScratch* S = nullptr;
     int rc = scratch_on_current_device(&S);
     if (rc) return rc;

@@ -293,6 +293,10 @@ int check_params(const recon_params* p) {
     if (p->checkpoint != 0 && p->checkpoint != 1) return fail(RECON_E_INVALID, "checkpoint must be 0 or 1");
     if (p->checkpoint && p->density_update != 0)
         return fail(RECON_E_INVALID, "checkpoint (the adjoint) needs density_update = 0");
+    if (p->stream_planes != 0 && p->stream_planes != 4 && p->stream_planes != 8 && p->stream_planes != 16)
+        return fail(RECON_E_INVALID, "stream_planes must be 0, 4, 8 or 16");
+    if (p->restrict_planes < 0 || p->restrict_planes > 16 || (p->restrict_planes & (p->restrict_planes - 1)))
+        return fail(RECON_E_INVALID, "restrict_planes must be 0, 1, 2, 4, 8 or 16");
     return RECON_OK;
 }
 
@@ -957,13 +961,16 @@ int adjoint(Handle* H, const double* gbar, double* grad) {
     return RECON_OK;
 }
 
-bool is_device_ptr(const void* p) {
+// Memory a kernel on `device` may read directly: device memory of that device,
+// or managed memory.  Host memory and other devices' memory are staged.
+bool is_local_device_ptr(const void* p, int device) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == device;
 }
 
 }  // namespace
@@ -993,7 +1000,7 @@ int recon_default_params(recon_params* p, int n0, int n1, int n2) {
     p->tol_in = 1e-8;
     p->max_vcycles = -1;
     p->tol_out = 1e-3;
-    p->k_max = 40;
+    p->k_max = 200;
     p->d_max = 0.5;
     p->alpha_min = std::ldexp(1.0, -20);
     p->lambda_floor = 0.01;
@@ -1003,6 +1010,8 @@ int recon_default_params(recon_params* p, int n0, int n1, int n2) {
     p->density_update = 0;
     p->device_loop = 1;
     p->checkpoint = 0;
+    p->stream_planes = 0;
+    p->restrict_planes = 0;
     return RECON_OK;
 }
 
@@ -1105,13 +1114,21 @@ int recon_create(void** out, const recon_params* p_in, void* cuda_stream) {
     }
 #undef AL
     // planes per block of the streaming FP32 kernels, measured per level on
-    // the level's own buffers (every choice computes the same values)
+    // the level's own buffers unless the parameters fix them (every choice
+    // computes the same values; a fixed choice the level does not divide
+    // falls back to the occupancy cost model at launch)
     if (H->mixed) {
         for (int l = 0; l + 1 < nl; ++l) {
-            tune_sweep_level(H->lv[l], &H->lv[l + 1], H->u32[l + 1], H->u32[l], H->r32[l], H->f32[l],
-                             H->c32[l], H->st);
-            tune_resid_restrict_level(H->lv[l], H->lv[l + 1], H->u32[l], H->f32[l], H->c32[l],
-                                      H->f32[l + 1], H->st);
+            if (p->stream_planes)
+                H->lv[l].tune[0] = H->lv[l].tune[1] = p->stream_planes;
+            else
+                tune_sweep_level(H->lv[l], &H->lv[l + 1], H->u32[l + 1], H->u32[l], H->r32[l],
+                                 H->f32[l], H->c32[l], H->st);
+            if (p->restrict_planes)
+                H->lv[l].tune[2] = p->restrict_planes;
+            else
+                tune_resid_restrict_level(H->lv[l], H->lv[l + 1], H->u32[l], H->f32[l], H->c32[l],
+                                          H->f32[l + 1], H->st);
         }
         if (cudaGetLastError() != cudaSuccess) {
             free_all(H);
@@ -1188,11 +1205,13 @@ int recon_deposit(void* hp, int mode, const double* data, const double* mass, in
         launch_validate_grid(n, H->rho, H->part[0], H->part[1], H->st);
     } else if (mode == RECON_PARTICLES) {
         if (np <= 0) return fail(RECON_E_INVALID, "no particles");
-        // host inputs are staged through a temporary device buffer
+        // host inputs (and another device's) are staged through a temporary
+        // device buffer
         const double* dpos = data;
         const double* dmass = mass;
         void* stage = nullptr;
-        bool host_pos = !is_device_ptr(data), host_mass = mass && !is_device_ptr(mass);
+        bool host_pos = !is_local_device_ptr(data, H->device),
+             host_mass = mass && !is_local_device_ptr(mass, H->device);
         size_t bytes = (host_pos ? 3 * sizeof(double) * np : 0) + (host_mass ? sizeof(double) * np : 0);
         if (bytes) {
             cudaError_t e = cudaMallocAsync(&stage, bytes, H->st);
@@ -1202,12 +1221,12 @@ int recon_deposit(void* hp, int mode, const double* data, const double* mass, in
             }
             char* q = (char*)stage;
             if (host_pos) {
-                CK(cudaMemcpyAsync(q, data, 3 * sizeof(double) * np, cudaMemcpyHostToDevice, H->st));
+                CK(cudaMemcpyAsync(q, data, 3 * sizeof(double) * np, cudaMemcpyDefault, H->st));
                 dpos = (const double*)q;
                 q += 3 * sizeof(double) * np;
             }
             if (host_mass) {
-                CK(cudaMemcpyAsync(q, mass, sizeof(double) * np, cudaMemcpyHostToDevice, H->st));
+                CK(cudaMemcpyAsync(q, mass, sizeof(double) * np, cudaMemcpyDefault, H->st));
                 dmass = (const double*)q;
             }
         }

@@ -66,8 +66,8 @@ def test_device_loop_stall_replay_and_edge_cases():
     _same(a, b, pa, pb)
     # replayed alpha sequence
     ra = np.r_[a.alpha, np.full(40 - len(a.alpha), 0.5)]
-    Ra, a, pa = _run(rho, "mixed", 0, replay_alpha=ra)
-    Rb, b, pb = _run(rho, "mixed", 1, replay_alpha=ra)
+    Ra, a, pa = _run(rho, "mixed", 0, replay_alpha=ra, k_max=40)
+    Rb, b, pb = _run(rho, "mixed", 1, replay_alpha=ra, k_max=40)
     _same(a, b, pa, pb)
     assert np.array_equal(b.alpha, ra[:b.steps])
     # no steps at all, and a stop at the first step start
