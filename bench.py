@@ -1,14 +1,17 @@
 """Benchmark of the reconstruction solve on GB300.
 
 One step = one whole recon_solve (every step of the moving-mesh iteration,
-Sec. II / App. A of Zhu et al. 2016) on the 256^3 / 400 Mpc/h 2LPT workload
-(BBKS, Gamma 0.2, n_s 1, sigma_8 0.8, seed 1001), from phi = 0 on the
-density already resident in HBM, in mixed precision; the plain FP64 form of
-the same solve is timed beside it.  Metric: Mcells/s per full reconstruction
-solve at fixed residual = ncells / solve time / 1e6 (whole job: summed over
-ranks, which solve independent copies of the workload).
+Sec. II / App. A of Zhu et al. 2016) on the 512^3 / 800 Mpc/h 2LPT workload
+(BBKS, Gamma 0.2, n_s 1, sigma_8 0.8, seed 1002), from phi = 0 on the
+density already resident in HBM, in mixed precision, run to the iteration's
+own end (rms(s) <= tol_out, or the step limiter admits no step; at most
+--k-max steps); the plain FP64 form of the same solve is timed beside it.
+Metric: Mcells/s per full reconstruction solve at fixed residual = ncells /
+solve time / 1e6 (whole job: summed over ranks, which solve independent
+copies of the workload).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload lpt256]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload lpt512]
+    python bench.py --workload lpt256       # the 256^3 / 400 Mpc/h workload
     python bench.py --workload mocks96      # 96 mocks of 32^3..128^3, batched solve
     python bench.py --impl reference ...   # the CPU FP64 oracle, bounded sample
 """
@@ -28,6 +31,17 @@ sys.path.insert(0, ROOT)
 METRIC = "Mcells/s per full reconstruction solve at fixed residual, mixed vs FP64 GPU"
 FALLBACK_HBM_GBS = 6800.0
 
+# Steps and V(2,2) cycles of one FP64 solve of each workload (the oracle's
+# cycle and stopping residual), as the plain FP64 GPU form measured them on
+# GB300 with the default parameters.  The CPU oracle baseline (cpu_baseline
+# and the reference arm) is one model: (deposit + geometry/source + S + limiter
+# + advance) x steps + V-cycle x cycles + one deposit, each pass timed on the
+# full grid by the oracle, with these counts.
+ORACLE_SOLVE_COUNTS = {
+    "lpt512": (27, 532),
+    "lpt256": (56, 1003),
+}
+
 
 def _args():
     ap = argparse.ArgumentParser()
@@ -35,15 +49,19 @@ def _args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="lpt256")
-    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--workload", default="lpt512")
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--fp64-warmup", type=int, default=0,
+                    help="untimed FP64 solves first (one FP64 solve at 512^3 takes ~30 s)")
+    ap.add_argument("--cpu-threads", type=int, default=0,
+                    help="oracle threads for the CPU baseline (0: every host core)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--inner-vcycles", type=int, default=None,
                     help="FP32 V-cycles per FP64 defect correction (library default if unset)")
-    ap.add_argument("--k-max", type=int, default=40,
-                    help="steps per solve (40 is the workload; fewer only for profiling)")
+    ap.add_argument("--k-max", type=int, default=200,
+                    help="step cap per solve; the default lets the solve run to its own end")
     return ap.parse_args()
 
 
@@ -231,18 +249,28 @@ def run_gb300(a):
     _, st_prof, _ = timed("mixed", 1, 0, profile=True)
     ms_fp64, st_fp64 = None, None
     if a.fp64_steps > 0:
-        ms_fp64, st_fp64, _ = timed("fp64", a.fp64_steps, 1)
+        ms_fp64, st_fp64, _ = timed("fp64", a.fp64_steps, a.fp64_warmup)
 
     ms_mixed = max_over_ranks(ms_mixed, world, "cuda")
     value = whole_job_mcells(cells, world, ms_mixed)
+    s0 = st_mixed[0]
     fp64 = None
     if ms_fp64 is not None:
         ms_fp64 = max_over_ranks(ms_fp64, world, "cuda")
         value_fp64 = whole_job_mcells(cells, world, ms_fp64)
+        f0 = st_fp64[0]
+        # the two forms take their own step lengths, so a solve can end at a
+        # different step; per step the comparison holds either way
+        per_step = (ms_fp64 / max(f0.steps, 1)) / (ms_mixed / max(s0.steps, 1))
         fp64 = {"value": value_fp64, "unit": "Mcells/s", "ms_per_step": ms_fp64,
-                "steps": a.fp64_steps, "vcycles_per_solve": st_fp64[0].vcycles,
+                "timed_solves": a.fp64_steps, "warmup_solves": a.fp64_warmup,
+                "status": _status_name(f0.status), "steps_per_solve": f0.steps,
+                "vcycles_per_solve": f0.vcycles, "R_end": f0.R,
                 "multigrid": _mg_settings(resolved_params((n, n, n), precision="fp64")),
-                "mixed_over_fp64": value / value_fp64}
+                "same_steps_as_mixed": f0.steps == s0.steps,
+                "mixed_over_fp64_per_solve": value / value_fp64,
+                "mixed_over_fp64_per_step": per_step,
+                "mixed_over_fp64": value / value_fp64 if f0.steps == s0.steps else per_step}
 
     # roofline of the dominant kernel: the finest-level FP32 red-black sweep
     sm_ms = sum(s.smooth_ms for s in st_prof)
@@ -292,22 +320,19 @@ def run_gb300(a):
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        cpu = (cpu_baseline(W, st_fp64[0], "FP64") if st_fp64 else
-               cpu_baseline(W, st_mixed[0], "mixed"))
+        cpu = cpu_baseline(a, W)
 
-    s0 = st_mixed[0]
     line = {
         "metric": METRIC, "value": value, "unit": "Mcells/s", "n_gpus": world,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_mixed, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": W.name, "grid": [n, n, n], "box_mpc_h": W.box,
-                   "displacement": "2LPT" if W.order == 2 else "ZA", "seed": W.seed,
-                   "precision": "mixed", "k_max": a.k_max, "tol_in": 1e-8, "tol_out": 1e-3,
-                   "steps_per_solve": s0.steps, "vcycles_per_solve": s0.vcycles,
-                   "multigrid": _mg_settings(resolved_params((n, n, n), precision="mixed", **mg_kw)),
-                   "l2": f"inputs larger than L2 (working set ~{cells * 235 / 1e9:.1f} GB per solve)",
-                   "control": "device loop: one CUDA graph per solve (conditional nodes)",
-                   "parallelism": f"replicas x{world}"},
+        "config": _config(a, W),
+        "solve": {"precision": "mixed", "status": _status_name(s0.status),
+                  "steps_per_solve": s0.steps, "vcycles_per_solve": s0.vcycles,
+                  "R0": s0.R0, "R_end": s0.R, "min_lambda0": s0.min_lambda0,
+                  "max_delta_r": s0.max_delta_r,
+                  "multigrid": _mg_settings(resolved_params((n, n, n), precision="mixed", **mg_kw)),
+                  "control": "device loop: one CUDA graph per solve (conditional nodes)"},
         "fp64_gpu": fp64,
         "roofline": roof,
         "cpu_baseline": cpu,
@@ -337,7 +362,8 @@ def adjoint_timing(a, stream, barrier, steps=3):
     W = WORKLOADS["za128"]
     n = W.n
     pos, _ = W.particles()
-    R = Recon((n, n, n), box=W.box, precision="mixed", checkpoint=1, k_max=a.k_max)
+    K = min(a.k_max, 40)
+    R = Recon((n, n, n), box=W.box, precision="mixed", checkpoint=1, k_max=K)
     R.deposit_particles(torch.from_numpy(pos).cuda())
     st = R.solve()
     g = torch.from_numpy(np.random.default_rng(1004).standard_normal((n, n, n))).cuda()
@@ -360,7 +386,7 @@ def adjoint_timing(a, stream, barrier, steps=3):
     return {"workload": W.name, "precision": "mixed", "steps_per_solve": st.steps,
             "forward_ms": fwd, "adjoint_ms": bwd, "adjoint_over_forward": bwd / fwd,
             "adjoint_mcells_s": n ** 3 / (bwd * 1e-3) / 1e6,
-            "checkpoint_bytes": 5 * 8 * n ** 3 * a.k_max}
+            "k_max": K, "checkpoint_bytes": 5 * 8 * n ** 3 * K}
 
 
 def run_batch(a):
@@ -473,96 +499,157 @@ def run_batch(a):
         print(json.dumps(line))
 
 
+def _config(a, W):
+    """The workload, the same in both arms."""
+    n = W.n
+    return {"workload": W.name, "grid": [n, n, n], "box_mpc_h": W.box,
+            "displacement": "2LPT" if W.order == 2 else "ZA", "seed": W.seed,
+            "k_max": a.k_max, "tol_in": 1e-8, "tol_out": 1e-3,
+            "l2": f"inputs larger than L2 (working set ~{n ** 3 * 235 / 1e9:.1f} GB per solve)",
+            "parallelism": f"replicas x{_dist()[1]}"}
+
+
 def _mg_settings(p):
     """The multigrid settings a solve resolved to."""
     return {"nu1": p.nu1, "nu2": p.nu2, "inner_vcycles": p.inner_vcycles if p.precision else None,
             "max_vcycles": p.max_vcycles}
 
 
-def cpu_baseline(W, st, which):
-    """The CPU oracle as it stands (single thread) on a bounded sample of the
-    same workload: one V-cycle and one each of the per-step passes on the full
-    grid, scaled to one solve by the step and V-cycle counts of a GPU solve
-    (the FP64 one where it ran: its V(2, 2) cycles are the oracle's)."""
-    import oracle as O
+def _status_name(code):
+    return {0: "converged (rms(s) <= tol_out)", 1: "k_max reached",
+            2: "stalled (step limiter admits no step)"}.get(int(code), str(code))
 
-    n = W.n
-    pos, _ = W.particles()
-    x = pos / W.cell
-    rho = O.cic_deposit((n, n, n), x)
-    m = rho / rho.mean()
-    p = O.OracleParams(n=(n, n, n))
-    t = {}
+
+def _host_cpu():
+    """nproc and the host CPU model (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() == "Model name":
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as fh:
+                for ln in fh:
+                    if ln.lower().startswith(("model name", "cpu part")):
+                        model = ln.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            pass
+    return {"nproc": os.cpu_count(), "model": model}
+
+
+class OracleModel:
+    """The CPU oracle's solve time on a workload, from a bounded sample: each
+    pass of one step (deposit, geometry + source, S, limiter, advance) timed
+    once on the full grid, and V-cycles timed on the full grid; a solve is
+    steps x passes + cycles x V-cycle + one deposit, with the FP64 solve's
+    counts (ORACLE_SOLVE_COUNTS)."""
+
+    def __init__(self, W, threads):
+        import oracle as O
+
+        self.O, self.W = O, W
+        n = W.n
+        self.threads = O.set_threads(threads if threads > 0 else (os.cpu_count() or 1))
+        pos, _ = W.particles()
+        self.x = pos / W.cell
+        rho = O.cic_deposit((n, n, n), self.x)
+        self.m = rho / rho.mean()
+        self.p = O.OracleParams(n=(n, n, n))
+        self.s, _ = O.source(self.p, np.zeros((n, n, n)), self.m)
+        self.a = np.maximum(self.m, self.p.a_min)
+        self.steps, self.cycles = ORACLE_SOLVE_COUNTS[W_key(W)]
+
+    def passes(self):
+        O, n = self.O, self.W.n
+        t = {}
+        t0 = time.perf_counter()
+        O.cic_deposit((n, n, n), self.x, self.m.ravel())
+        t["deposit"] = time.perf_counter() - t0
+        phi = np.zeros((n, n, n))
+        t0 = time.perf_counter()
+        O.source(self.p, phi, self.m)
+        t["source"] = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        d = O.apply_S(self.s)
+        t["smooth"] = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        O.step_limiter(self.p, phi, d * 1e-3)
+        t["limiter"] = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        O.advance(1.0, d * 1e-3, phi, self.x)
+        t["advance"] = time.perf_counter() - t0
+        self.t_passes = t
+        return t
+
+    def vcycle(self):
+        t0 = time.perf_counter()
+        self.O.vcycle(self.p, self.a, self.s, np.zeros_like(self.s))
+        return time.perf_counter() - t0
+
+    def solve_seconds(self, t_vcycle):
+        t = self.t_passes
+        per_step = t["deposit"] + t["source"] + t["smooth"] + t["limiter"] + t["advance"]
+        return self.steps * per_step + self.cycles * t_vcycle + t["deposit"]
+
+    def sample(self, nv):
+        return (f"{self.W.n}^3 grid: each pass of one step once and {nv} V(2,2) cycle(s) on the "
+                f"full grid, scaled to the FP64 solve's {self.steps} steps and {self.cycles} "
+                f"V-cycles, {self.threads} oracle thread(s)")
+
+
+def W_key(W):
+    from paper_1611_09638_gb300.inputs import WORKLOADS
+
+    return next(k for k, v in WORKLOADS.items() if v == W)
+
+
+def cpu_baseline(a, W):
+    """The CPU oracle as it stands on a bounded sample of the same workload
+    (OracleModel), on every host core unless --cpu-threads says otherwise."""
+    M = OracleModel(W, a.cpu_threads)
     t0 = time.perf_counter()
-    O.cic_deposit((n, n, n), x, m.ravel())
-    t["deposit"] = time.perf_counter() - t0
-    phi = np.zeros((n, n, n))
-    t0 = time.perf_counter()
-    s, _ = O.source(p, phi, m)
-    t["source"] = time.perf_counter() - t0
-    a_ = np.maximum(m, p.a_min)
-    t0 = time.perf_counter()
-    u = O.vcycle(p, a_, s, np.zeros_like(s))
-    t["vcycle"] = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    d = O.apply_S(u)
-    t["smooth"] = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    O.step_limiter(p, phi, d * 1e-3)
-    t["limiter"] = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    O.advance(1.0, d * 1e-3, phi, x)
-    t["advance"] = time.perf_counter() - t0
-    per_step = t["deposit"] + t["source"] + t["smooth"] + t["limiter"] + t["advance"]
-    solve_s = st.steps * per_step + st.vcycles * t["vcycle"] + t["deposit"]
-    return {"value": n ** 3 / solve_s / 1e6, "unit": "Mcells/s", "cores": 1, "kind": "oracle",
-            "sample": (f"{n}^3 grid: one oracle V-cycle ({t['vcycle']:.1f} s) and one of each "
-                       f"per-step pass ({per_step:.1f} s), scaled to the {which} GPU solve's "
-                       f"{st.steps} steps and {st.vcycles} V-cycles"),
-            "sample_seconds": sum(t.values()), "est_solve_seconds": solve_s}
+    M.passes()
+    tv = M.vcycle()
+    solve_s = M.solve_seconds(tv)
+    return {"value": W.n ** 3 / solve_s / 1e6, "unit": "Mcells/s", "cores": M.threads,
+            "kind": "oracle", "sample": M.sample(1), "host": _host_cpu(),
+            "sample_seconds": time.perf_counter() - t0, "vcycle_s": tv,
+            "passes_s": M.t_passes, "est_solve_seconds": solve_s}
 
 
 def run_reference(a):
+    """The reference arm: the CPU FP64 oracle (OracleModel, every host core);
+    each timed step is one oracle V-cycle on the full grid, the per-step passes
+    are timed once before the warm-up."""
     rank, world, _ = _dist()
     if rank != 0:
         return
-    import oracle as O
-
     W = _workload(a.workload)
     n = W.n
-    pos, _ = W.particles()
-    x = pos / W.cell
-    rho = O.cic_deposit((n, n, n), x)
-    m = rho / rho.mean()
-    p = O.OracleParams(n=(n, n, n))
-    s, _ = O.source(p, np.zeros((n, n, n)), m)
-    a_ = np.maximum(m, p.a_min)
-    # one step of this arm = one oracle V-cycle on the full grid; the solve
-    # time is that times the V-cycles of a solve plus the per-step passes
-    # measured once
-    t0 = time.perf_counter()
-    O.cic_deposit((n, n, n), x, m.ravel())
-    O.source(p, np.zeros((n, n, n)), m)
-    per_step_fixed = time.perf_counter() - t0
-    steps_per_solve, vc_per_solve = 40, 40 * 17
+    M = OracleModel(W, a.cpu_threads)
+    M.passes()
     for _ in range(a.warmup):
-        O.vcycle(p, a_, s, np.zeros_like(s))
+        M.vcycle()
     t0 = time.perf_counter()
     for _ in range(a.steps):
-        O.vcycle(p, a_, s, np.zeros_like(s))
+        M.vcycle()
     tv = (time.perf_counter() - t0) / a.steps
-    solve_s = steps_per_solve * per_step_fixed + vc_per_solve * tv
+    solve_s = M.solve_seconds(tv)
     value = n ** 3 / solve_s / 1e6
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mcells/s",
             "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": tv * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": W.name, "grid": [n, n, n], "box_mpc_h": W.box,
-                       "precision": "fp64 (CPU oracle)"},
-            "cpu_baseline": {"value": value, "unit": "Mcells/s", "cores": 1, "kind": "oracle",
-                             "sample": (f"each step one oracle V-cycle on the {n}^3 grid; solve "
-                                        f"time = {vc_per_solve} V-cycles + {steps_per_solve} x "
-                                        f"deposit and source passes")},
+            "data": "synthetic", "config": _config(a, W),
+            "solve": {"precision": "fp64, CPU oracle (V(2,2) cycles)"},
+            "cpu_baseline": {"value": value, "unit": "Mcells/s", "cores": M.threads,
+                             "kind": "oracle", "sample": M.sample(a.steps), "host": _host_cpu(),
+                             "passes_s": M.t_passes, "est_solve_seconds": solve_s},
             "e2e": {"value": value, "unit": "Mcells/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
