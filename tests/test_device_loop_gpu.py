@@ -112,6 +112,31 @@ def test_batch_of_mixed_sizes_equals_single_solves():
         R.close()
 
 
+def test_batch_matches_the_oracle():
+    """A batch of mocks of three sizes (ZA, 3.125 Mpc/h cells, seeds 2000 + i)
+    solved together in mixed precision: every mock against the oracle's solve
+    of it, 10 steps at the default tolerances -- the same step lengths,
+    status and step count, and phi within 1e-4."""
+    specs = [(16, 50.0), (32, 100.0), (64, 200.0), (16, 50.0), (32, 100.0)]
+    K = 10
+    rhos = [_density(n, box, 2000 + i) for i, (n, box) in enumerate(specs)]
+    recons = []
+    for rho in rhos:
+        R = Recon(rho.shape, precision="mixed", k_max=K, stream=torch.cuda.Stream())
+        torch.cuda.synchronize()
+        R.deposit_grid(torch.from_numpy(np.ascontiguousarray(rho)).cuda())
+        recons.append(R)
+    torch.cuda.synchronize()
+    out = solve_batch(recons)
+    for R, st, rho in zip(recons, out, rhos):
+        ref = O.solve(O.OracleParams(n=rho.shape, k_max=K), rho)
+        assert st.status == ref.status and st.steps == ref.steps
+        np.testing.assert_array_equal(st.alpha, ref.alpha)
+        phi = R.field("phi").cpu().numpy()
+        assert np.linalg.norm(phi - ref.phi) <= 1e-4 * np.linalg.norm(ref.phi)
+        R.close()
+
+
 def test_limiter_parameter_sweep_runs_every_setting():
     """The App. B sweep driver on the 32^3 workload: every (xi_m, v_m) setting
     gives a valid map and an r(k) record; the settings share the input."""
