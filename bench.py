@@ -58,10 +58,17 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-mocks", action="store_true",
+                    help="skip the brief batched-mocks timing in the headline line")
     ap.add_argument("--inner-vcycles", type=int, default=None,
                     help="FP32 V-cycles per FP64 defect correction (library default if unset)")
     ap.add_argument("--k-max", type=int, default=200,
                     help="step cap per solve; the default lets the solve run to its own end")
+    ap.add_argument("--launch-list", action="store_true",
+                    help="only one solve on the host-driven loop (every kernel its own launch), "
+                         "for a profiler's launch list; prints its record")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
+                    help="precision of the --launch-list solve")
     return ap.parse_args()
 
 
@@ -317,6 +324,7 @@ def run_gb300(a):
                "path": "recon_deposit(host pinned particles) + recon_solve + recon_field(delta_r -> host pinned)"}
 
     adj = None if a.no_adjoint else adjoint_timing(a, stream, barrier)
+    mocks = None if a.no_mocks else mocks_timing(a, stream, barrier)
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -338,6 +346,7 @@ def run_gb300(a):
         "cpu_baseline": cpu,
         "e2e": e2e,
         "adjoint": adj,
+        "batched_mocks": mocks,
         "gpu_launches": int(sum(s.launches for s in st_mixed)),
         "clocks": clocks,
     }
@@ -387,6 +396,55 @@ def adjoint_timing(a, stream, barrier, steps=3):
             "forward_ms": fwd, "adjoint_ms": bwd, "adjoint_over_forward": bwd / fwd,
             "adjoint_mcells_s": n ** 3 / (bwd * 1e-3) / 1e6,
             "k_max": K, "checkpoint_bytes": 5 * 8 * n ** 3 * K}
+
+
+def mocks_timing(a, stream, barrier, steps=2):
+    """The batched-mocks configuration (96 ZA mocks of 32^3 / 64^3 / 128^3,
+    seeds 2000 + i, mixed precision, each solve to its own end) in brief:
+    one untimed batch, then `steps` batched solves (recon_solve_batch, every
+    mock on its own stream) timed with CUDA events, and the same solves one
+    after another."""
+    import torch
+
+    from paper_1611_09638_gb300 import Recon, solve_batch
+    from paper_1611_09638_gb300.inputs import mock_batch
+
+    mocks = mock_batch()
+    cells = sum(W.n ** 3 for W in mocks)
+    recons = []
+    for W in mocks:
+        R = Recon((W.n,) * 3, box=W.box, precision="mixed", stream=torch.cuda.Stream(),
+                  k_max=a.k_max)
+        torch.cuda.synchronize()
+        R.deposit_particles(torch.from_numpy(W.particles()[0]).cuda())
+        recons.append(R)
+    solve_batch(recons, record=False)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        stats = solve_batch(recons, record=False)
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1) / steps
+    e0.record(stream)
+    for R in recons:
+        R.solve(record=False)
+    e1.record(stream)
+    barrier()
+    ms_seq = e0.elapsed_time(e1)
+    by_size = {}
+    for W, st in zip(mocks, stats):
+        d = by_size.setdefault(f"{W.n}^3", {"mocks": 0, "steps": 0, "vcycles": 0})
+        d["mocks"] += 1
+        d["steps"] += st.steps
+        d["vcycles"] += st.vcycles
+    for R in recons:
+        R.close()
+    return {"workload": "96 ZA mocks: 32 x 32^3/100, 32 x 64^3/200, 32 x 128^3/400 Mpc/h",
+            "value": cells / (ms * 1e-3) / 1e6, "unit": "Mcells/s", "ms_per_batch": ms,
+            "timed_batches": steps, "sequential_value": cells / (ms_seq * 1e-3) / 1e6,
+            "per_size": by_size, "control": "recon_solve_batch: 96 solve graphs on 96 streams"}
 
 
 def run_batch(a):
@@ -655,9 +713,28 @@ def run_reference(a):
     print(json.dumps(line))
 
 
+def run_launch_list(a):
+    """One solve of the workload on the host-driven loop, nothing else."""
+    import torch
+
+    from paper_1611_09638_gb300 import Recon
+
+    W = _workload(a.workload)
+    n = W.n
+    pos, _ = W.particles()
+    with Recon((n, n, n), box=W.box, precision=a.precision, k_max=a.k_max, device_loop=0) as R:
+        R.deposit_particles(torch.from_numpy(pos).cuda())
+        st = R.solve()
+    print(json.dumps({"workload": W.name, "precision": a.precision, "k_max": a.k_max,
+                      "steps": st.steps, "vcycles": st.vcycles, "launches": st.launches,
+                      "ms": st.ms, "status": _status_name(st.status)}))
+
+
 if __name__ == "__main__":
     args = _args()
-    if args.impl == "reference":
+    if args.launch_list:
+        run_launch_list(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "mocks96":
         run_batch(args)
