@@ -62,13 +62,16 @@ def _args():
                     help="skip the brief batched-mocks timing in the headline line")
     ap.add_argument("--inner-vcycles", type=int, default=None,
                     help="FP32 V-cycles per FP64 defect correction (library default if unset)")
-    ap.add_argument("--k-max", type=int, default=200,
-                    help="step cap per solve; the default lets the solve run to its own end")
+    ap.add_argument("--k-max", type=int, default=None,
+                    help="step cap per solve (default: 200, so that a solve of the 2LPT "
+                         "workloads runs to its own end; 40 for the mocks)")
     ap.add_argument("--launch-list", action="store_true",
                     help="only one solve on the host-driven loop (every kernel its own launch), "
                          "for a profiler's launch list; prints its record")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
                     help="precision of the --launch-list solve")
+    ap.add_argument("--coarse-faces", type=int, default=None,
+                    help="mixed precision's coarse-level coefficients (library default if unset)")
     return ap.parse_args()
 
 
@@ -229,6 +232,8 @@ def run_gb300(a):
         torch.cuda.synchronize()
 
     mg_kw = {} if a.inner_vcycles is None else {"inner_vcycles": a.inner_vcycles}
+    if a.coarse_faces is not None:
+        mg_kw["coarse_faces"] = a.coarse_faces
 
     def timed(precision, steps, warmup, profile=False):
         kw = mg_kw if precision == "mixed" else {}
@@ -398,12 +403,12 @@ def adjoint_timing(a, stream, barrier, steps=3):
             "k_max": K, "checkpoint_bytes": 5 * 8 * n ** 3 * K}
 
 
-def mocks_timing(a, stream, barrier, steps=2):
+def mocks_timing(a, stream, barrier, steps=2, k_max=40):
     """The batched-mocks configuration (96 ZA mocks of 32^3 / 64^3 / 128^3,
-    seeds 2000 + i, mixed precision, each solve to its own end) in brief:
-    one untimed batch, then `steps` batched solves (recon_solve_batch, every
-    mock on its own stream) timed with CUDA events, and the same solves one
-    after another."""
+    seeds 2000 + i, mixed precision, 40 steps each: the small mocks' solves do
+    not end by themselves within 200 steps) in brief: one untimed batch, then
+    `steps` batched solves (recon_solve_batch, every mock on its own stream)
+    timed with CUDA events, and the same solves one after another."""
     import torch
 
     from paper_1611_09638_gb300 import Recon, solve_batch
@@ -414,7 +419,7 @@ def mocks_timing(a, stream, barrier, steps=2):
     recons = []
     for W in mocks:
         R = Recon((W.n,) * 3, box=W.box, precision="mixed", stream=torch.cuda.Stream(),
-                  k_max=a.k_max)
+                  k_max=k_max)
         torch.cuda.synchronize()
         R.deposit_particles(torch.from_numpy(W.particles()[0]).cuda())
         recons.append(R)
@@ -443,7 +448,8 @@ def mocks_timing(a, stream, barrier, steps=2):
         R.close()
     return {"workload": "96 ZA mocks: 32 x 32^3/100, 32 x 64^3/200, 32 x 128^3/400 Mpc/h",
             "value": cells / (ms * 1e-3) / 1e6, "unit": "Mcells/s", "ms_per_batch": ms,
-            "timed_batches": steps, "sequential_value": cells / (ms_seq * 1e-3) / 1e6,
+            "timed_batches": steps, "k_max": k_max,
+            "sequential_value": cells / (ms_seq * 1e-3) / 1e6,
             "per_size": by_size, "control": "recon_solve_batch: 96 solve graphs on 96 streams"}
 
 
@@ -722,7 +728,12 @@ def run_launch_list(a):
     W = _workload(a.workload)
     n = W.n
     pos, _ = W.particles()
-    with Recon((n, n, n), box=W.box, precision=a.precision, k_max=a.k_max, device_loop=0) as R:
+    kw = {}
+    if a.precision == "mixed" and a.inner_vcycles is not None:
+        kw["inner_vcycles"] = a.inner_vcycles
+    if a.precision == "mixed" and a.coarse_faces is not None:
+        kw["coarse_faces"] = a.coarse_faces
+    with Recon((n, n, n), box=W.box, precision=a.precision, k_max=a.k_max, device_loop=0, **kw) as R:
         R.deposit_particles(torch.from_numpy(pos).cuda())
         st = R.solve()
     print(json.dumps({"workload": W.name, "precision": a.precision, "k_max": a.k_max,
@@ -732,6 +743,8 @@ def run_launch_list(a):
 
 if __name__ == "__main__":
     args = _args()
+    if args.k_max is None:
+        args.k_max = 40 if args.workload == "mocks96" else 200
     if args.launch_list:
         run_launch_list(args)
     elif args.impl == "reference":

@@ -105,9 +105,10 @@ typedef struct {
     int profile;         /* nonzero: time the finest-level smoothing sweeps with
                             CUDA events (reported in recon_stats.smooth_ms)    */
     int inner_vcycles;   /* RECON_MIXED: FP32 V-cycles per FP64 defect
-                            correction (1..16; -1, the default: 6); the FP64
-                            residual is formed once per group, so the stopping
-                            test sees multiples of it                           */
+                            correction (1..16; -1, the default: 4 with per-face
+                            coarse coefficients, else 6); the FP64 residual is
+                            formed once per group, so the stopping test sees
+                            multiples of it                                     */
     int density_update;  /* 0: CIC re-deposit of the tracers on the deformed mesh
                             every step (default); 1: App. A's linear update
                             m += alpha d_mu(m e^-1 d dphi) of the mass per cell  */
@@ -131,6 +132,18 @@ typedef struct {
                             (the default): timed per level at create; 1, 2, 4, 8
                             or 16: that value wherever it divides the coarse
                             level.  Every choice computes the same bits.         */
+    int coarse_faces;    /* RECON_MIXED, cubic grids: how the FP32 V-cycle's
+                            coarse levels carry the coefficient.  0: a nodal
+                            coefficient restricted by full weighting, faces its
+                            two-node means (the re-discretised operator of
+                            RECON_FP64); 1: per-face coefficients, each the
+                            full-weighted mean over the fine lines beneath it of
+                            the series (harmonic) combination of the two fine
+                            faces it spans.  Either way the solve stops at the
+                            same FP64 residual; 1 takes fewer V-cycles where the
+                            coefficient jumps.  1 needs RECON_MIXED and a cubic
+                            grid of at least 64^3.  -1 (default): 1 where that
+                            holds, else 0.                                     */
 } recon_params;
 
 /* Per-solve record.  The per-step arrays are optional caller-owned host
@@ -163,9 +176,10 @@ typedef struct {
 int recon_default_params(recon_params* p, int n0, int n1, int n2);
 
 /* Replace, in place, every multigrid setting of *p left at -1 by the value
- * recon_create uses for p->precision (nu1 = nu2 = 2 and max_vcycles = 50 in
- * RECON_FP64; nu1 = nu2 = 1, inner_vcycles = 6 and max_vcycles = 100 in
- * RECON_MIXED).  The paper leaves the cycle shape open; these are the
+ * recon_create uses for p->precision and p->n (nu1 = nu2 = 2, max_vcycles =
+ * 50 and coarse_faces = 0 in RECON_FP64; in RECON_MIXED nu1 = nu2 = 1,
+ * max_vcycles = 100, coarse_faces = 1 on cubic grids of at least 64^3 (else
+ * 0), and inner_vcycles = 4 with coarse_faces = 1, else 6).  The paper leaves the cycle shape open; these are the
  * settings that reach the stopping residual in the least time on the 256^3
  * workload.  Other fields are not touched or checked.  RECON_E_INVALID for
  * a NULL p. */

@@ -14,7 +14,9 @@
 // blocks read the 8^3 correction back from it.  The per-node arithmetic is
 // that of mg_stencil.cuh and the loop orders are those of the per-phase
 // kernels (k_rbgs_colour, k_resid_restrict, k_prolong_add) and of the
-// single-block coarse V-cycle, so the result is the same bit for bit.
+// single-block coarse V-cycle, so the result is the same bit for bit.  With
+// coarse levels given by face sums (Level::face) the same phases read the
+// x face sums where they read a, and the y and z sums of their own planes.
 #include <cooperative_groups.h>
 
 #include "mg_stencil.cuh"
@@ -37,6 +39,7 @@ constexpr int kCN = 32;     // edge of the top level
 template <typename T>
 struct CLev {
     T *u, *f, *a, *r;
+    T *gy, *gz;  // face-sum levels: a holds the x face sums, these the y and z ones
     T hx, hy, hz;
 };
 
@@ -52,7 +55,7 @@ __device__ inline T* plane_of(T* X, int gi, int self) {
 
 // One colour of a red-black sweep on the block's planes (colour: (i + j + k)
 // parity; in-plane neighbours wrap periodically).
-template <typename T, int N, int P>
+template <typename T, int N, int P, bool FACE>
 __device__ void cl_sweep(const CLev<T>& L, int colour, int self) {
     constexpr int n = N, nn = n * n, hn = n >> 1, m = n - 1;
     constexpr int half = P * nn / 2;
@@ -70,14 +73,22 @@ __device__ void cl_sweep(const CLev<T>& L, int colour, int self) {
         const T* ac = L.a + lp * nn;
         const int yp = ((j + 1) & m) * n + k, ym = ((j - 1) & m) * n + k;
         const int zp = j * n + ((k + 1) & m), zm = j * n + ((k - 1) & m);
-        const Stencil7<T> s = stencil7v<T>(L.hx, L.hy, L.hz, ac[o], ap[o], am[o], ac[yp], ac[ym], ac[zp], ac[zm],
-                                           up[o], um[o], uc[yp], uc[ym], uc[zp], uc[zm]);
+        Stencil7<T> s;
+        if constexpr (FACE) {
+            const T* gy = L.gy + lp * nn;
+            const T* gz = L.gz + lp * nn;
+            s = stencil7g<T>(L.hx, L.hy, L.hz, ac[o], am[o], gy[o], gy[ym], gz[o], gz[zm], up[o], um[o],
+                             uc[yp], uc[ym], uc[zp], uc[zm]);
+        } else {
+            s = stencil7v<T>(L.hx, L.hy, L.hz, ac[o], ap[o], am[o], ac[yp], ac[ym], ac[zp], ac[zm], up[o], um[o],
+                             uc[yp], uc[ym], uc[zp], uc[zm]);
+        }
         L.u[c] = (s.off - L.f[c]) / s.diag;
     }
 }
 
 // r = f - L u on the block's planes.
-template <typename T, int N, int P>
+template <typename T, int N, int P, bool FACE>
 __device__ void cl_resid(const CLev<T>& L, int self) {
     constexpr int n = N, nn = n * n, m = n - 1;
     for (int c = threadIdx.x; c < P * nn; c += blockDim.x) {
@@ -92,8 +103,16 @@ __device__ void cl_resid(const CLev<T>& L, int self) {
         const T* ac = L.a + lp * nn;
         const int yp = ((j + 1) & m) * n + k, ym = ((j - 1) & m) * n + k;
         const int zp = j * n + ((k + 1) & m), zm = j * n + ((k - 1) & m);
-        const Stencil7<T> s = stencil7v<T>(L.hx, L.hy, L.hz, ac[o], ap[o], am[o], ac[yp], ac[ym], ac[zp], ac[zm],
-                                           up[o], um[o], uc[yp], uc[ym], uc[zp], uc[zm]);
+        Stencil7<T> s;
+        if constexpr (FACE) {
+            const T* gy = L.gy + lp * nn;
+            const T* gz = L.gz + lp * nn;
+            s = stencil7g<T>(L.hx, L.hy, L.hz, ac[o], am[o], gy[o], gy[ym], gz[o], gz[zm], up[o], um[o],
+                             uc[yp], uc[ym], uc[zp], uc[zm]);
+        } else {
+            s = stencil7v<T>(L.hx, L.hy, L.hz, ac[o], ap[o], am[o], ac[yp], ac[ym], ac[zp], ac[zm], up[o], um[o],
+                             uc[yp], uc[ym], uc[zp], uc[zm]);
+        }
         L.r[c] = L.f[c] - (s.off - s.diag * uc[o]);
     }
 }
@@ -162,7 +181,7 @@ constexpr int N0 = kCN, P0 = N0 / kCR, N1 = kCN / 2, P1 = N1 / kCR, N2 = kCN / 4
               N3 = kCN / 8, P3 = N3;
 static_assert(P0 >= 1 && P1 >= 1 && N3 * N3 * N3 == kNc, "level split");
 
-template <typename T>
+template <typename T, bool FACE>
 __global__ void __cluster_dims__(kCR, 1, 1) __launch_bounds__(kCT)
     k_coarse_cluster(CoarseSet cs, const T* __restrict__ f_top, T* __restrict__ u_top,
                      const double* __restrict__ aug, int zero_u) {
@@ -176,15 +195,27 @@ __global__ void __cluster_dims__(kCR, 1, 1) __launch_bounds__(kCT)
     for (int l = 0; l < 4; ++l) {
         L[l].u = q, L[l].f = q + sz[l], L[l].a = q + 2 * sz[l], L[l].r = q + 3 * sz[l];
         q += 4 * sz[l];
+        if (FACE) {
+            L[l].gy = q, L[l].gz = q + sz[l];
+            q += 2 * sz[l];
+        }
         L[l].hx = (T)cs.lv[l].h2i[0], L[l].hy = (T)cs.lv[l].h2i[1], L[l].hz = (T)cs.lv[l].h2i[2];
     }
-    // the block's planes of a, f and u; block 0 also the whole 8^3 and 4^3 a
+    // the block's planes of a (or of the three face sums), f and u; block 0
+    // also the whole 8^3 and 4^3 coefficients
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
         if (l >= 2 && self != 0) continue;
         const T* ag = reinterpret_cast<const T*>(cs.a[l]);
         const int base = l >= 2 ? 0 : self * sz[l];
         for (int c = threadIdx.x; c < sz[l]; c += blockDim.x) L[l].a[c] = ag[base + c];
+        if (FACE) {
+            const int cells = cs.lv[l].d.cells;
+            for (int c = threadIdx.x; c < sz[l]; c += blockDim.x) {
+                L[l].gy[c] = ag[cells + base + c];
+                L[l].gz[c] = ag[2 * cells + base + c];
+            }
+        }
     }
     for (int c = threadIdx.x; c < sz[0]; c += blockDim.x) {
         L[0].f[c] = f_top[self * sz[0] + c];
@@ -200,19 +231,19 @@ __global__ void __cluster_dims__(kCR, 1, 1) __launch_bounds__(kCT)
     // down: the two distributed levels
     for (int s = 0; s < cs.nu1; ++s)
         for (int colour = 0; colour < 2; ++colour) {
-            cl_sweep<T, N0, P0>(L[0], colour, self);
+            cl_sweep<T, N0, P0, FACE>(L[0], colour, self);
             cluster.sync();
         }
-    cl_resid<T, N0, P0>(L[0], self);
+    cl_resid<T, N0, P0, FACE>(L[0], self);
     cluster.sync();
     cl_restrict<T, N0, P0, N1, P1>(L[0], L[1], self, self);
     cluster.sync();
     for (int s = 0; s < cs.nu1; ++s)
         for (int colour = 0; colour < 2; ++colour) {
-            cl_sweep<T, N1, P1>(L[1], colour, self);
+            cl_sweep<T, N1, P1, FACE>(L[1], colour, self);
             cluster.sync();
         }
-    cl_resid<T, N1, P1>(L[1], self);
+    cl_resid<T, N1, P1, FACE>(L[1], self);
     cluster.sync();
     // block 0: the 8^3 and 4^3 levels and the exact 4^3 solve
     if (self == 0) {
@@ -220,10 +251,10 @@ __global__ void __cluster_dims__(kCR, 1, 1) __launch_bounds__(kCT)
         __syncthreads();
         for (int s = 0; s < cs.nu1; ++s)
             for (int colour = 0; colour < 2; ++colour) {
-                cl_sweep<T, N2, P2>(L[2], colour, 0);
+                cl_sweep<T, N2, P2, FACE>(L[2], colour, 0);
                 __syncthreads();
             }
-        cl_resid<T, N2, P2>(L[2], 0);
+        cl_resid<T, N2, P2, FACE>(L[2], 0);
         __syncthreads();
         cl_restrict<T, N2, P2, N3, P3>(L[2], L[3], 0, 0);
         __syncthreads();
@@ -237,7 +268,7 @@ __global__ void __cluster_dims__(kCR, 1, 1) __launch_bounds__(kCT)
         __syncthreads();
         for (int s = 0; s < cs.nu2; ++s)
             for (int colour = 0; colour < 2; ++colour) {
-                cl_sweep<T, N2, P2>(L[2], colour, 0);
+                cl_sweep<T, N2, P2, FACE>(L[2], colour, 0);
                 __syncthreads();
             }
     }
@@ -247,24 +278,25 @@ __global__ void __cluster_dims__(kCR, 1, 1) __launch_bounds__(kCT)
     cluster.sync();
     for (int s = 0; s < cs.nu2; ++s)
         for (int colour = 0; colour < 2; ++colour) {
-            cl_sweep<T, N1, P1>(L[1], colour, self);
+            cl_sweep<T, N1, P1, FACE>(L[1], colour, self);
             cluster.sync();
         }
     cl_prolong<T, N1, P1, N0, P0>(L[1], L[0], self);
     cluster.sync();
     for (int s = 0; s < cs.nu2; ++s)
         for (int colour = 0; colour < 2; ++colour) {
-            cl_sweep<T, N0, P0>(L[0], colour, self);
+            cl_sweep<T, N0, P0, FACE>(L[0], colour, self);
             cluster.sync();
         }
     for (int c = threadIdx.x; c < sz[0]; c += blockDim.x) u_top[self * sz[0] + c] = L[0].u[c];
 }
 
-template <typename T>
+template <typename T, bool FACE>
 constexpr int cluster_smem() {
-    // the four levels' arrays, then the 4^3 inverse (8-byte aligned: every
-    // level's arrays are a multiple of 8 bytes long)
-    return 4 * (P0 * N0 * N0 + P1 * N1 * N1 + P2 * N2 * N2 + P3 * N3 * N3) * (int)sizeof(T) +
+    // the four levels' arrays (u, f, r and a or the three face sums), then the
+    // 4^3 inverse (8-byte aligned: every level's arrays are a multiple of 8
+    // bytes long)
+    return (FACE ? 6 : 4) * (P0 * N0 * N0 + P1 * N1 * N1 + P2 * N2 * N2 + P3 * N3 * N3) * (int)sizeof(T) +
            kNc * kNc * (int)sizeof(double);
 }
 
@@ -274,6 +306,7 @@ bool coarse_cluster_fits(const CoarseSet& cs) {
     if (cs.nlev != 4) return false;
     for (int l = 0; l < 4; ++l) {
         const Dims& d = cs.lv[l].d;
+        if (cs.lv[l].face != cs.lv[0].face) return false;  // one form for the whole set
         const int n = kCN >> l;
         if (d.n0 != n || d.n1 != n || d.n2 != n) return false;
         if (l < 3 && !(cs.lv[l].coarsen[0] && cs.lv[l].coarsen[1] && cs.lv[l].coarsen[2])) return false;
@@ -285,10 +318,18 @@ template <typename T>
 bool launch_coarse_cluster(const CoarseSet& cs, const T* f, T* u, const double* minv, bool zero_u,
                            cudaStream_t st) {
     if (!coarse_cluster_fits(cs)) return false;
-    constexpr int smem = cluster_smem<T>();
-    allow_smem((const void*)k_coarse_cluster<T>, smem);
     launch_counter()++;
-    k_coarse_cluster<T><<<kCR, kCT, smem, st>>>(cs, f, u, minv, zero_u ? 1 : 0);
+    if constexpr (sizeof(T) == sizeof(float)) {
+        if (cs.lv[0].face) {
+            constexpr int smem = cluster_smem<T, true>();
+            allow_smem((const void*)k_coarse_cluster<T, true>, smem);
+            k_coarse_cluster<T, true><<<kCR, kCT, smem, st>>>(cs, f, u, minv, zero_u ? 1 : 0);
+            return true;
+        }
+    }
+    constexpr int smem = cluster_smem<T, false>();
+    allow_smem((const void*)k_coarse_cluster<T, false>, smem);
+    k_coarse_cluster<T, false><<<kCR, kCT, smem, st>>>(cs, f, u, minv, zero_u ? 1 : 0);
     return true;
 }
 

@@ -21,7 +21,7 @@ inline int nblocks(long long work) { return (int)((work + kThreads - 1) / kThrea
 // of that colour (nodes of a colour alternate along the fastest axis).
 template <typename T>
 __global__ void k_rbgs_colour(Dims d, T hx, T hy, T hz, int colour, T* __restrict__ u,
-                              const T* __restrict__ f, const T* __restrict__ a) {
+                              const T* __restrict__ f, const T* __restrict__ a, int face) {
     const int half = d.cells >> 1;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= half) return;
@@ -31,7 +31,7 @@ __global__ void k_rbgs_colour(Dims d, T hx, T hy, T hz, int colour, T* __restric
     const int i = t >> (d.s1 + hs2);
     const int k = 2 * kk + ((i + j + colour) & 1);
     const int c = cell_index(d, i, j, k);
-    Stencil7<T> s = stencil7<T>(d, hx, hy, hz, i, j, k, c, u, a);
+    Stencil7<T> s = stencil7_any<T>(d, hx, hy, hz, i, j, k, c, u, a, face);
     u[c] = (s.off - f[c]) / s.diag;
 }
 
@@ -167,7 +167,7 @@ __global__ void k_restrict(Dims df, Dims dc, int cx, int cy, int cz, const T* __
 template <typename T>
 __global__ void k_resid_restrict(Dims df, Dims dc, int cx, int cy, int cz, T hx, T hy, T hz,
                                  const T* __restrict__ u, const T* __restrict__ f,
-                                 const T* __restrict__ a, T* __restrict__ out) {
+                                 const T* __restrict__ a, int face, T* __restrict__ out) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= dc.cells) return;
     int I, J, K;
@@ -183,13 +183,58 @@ __global__ void k_resid_restrict(Dims df, Dims dc, int cx, int cy, int cz, T hx,
                 const int i = (fi + oi) & (df.n0 - 1), j = (fj + oj) & (df.n1 - 1),
                           k = (fk + ok) & (df.n2 - 1);
                 const int n = cell_index(df, i, j, k);
-                Stencil7<T> s = stencil7<T>(df, hx, hy, hz, i, j, k, n, u, a);
+                Stencil7<T> s = stencil7_any<T>(df, hx, hy, hz, i, j, k, n, u, a, face);
                 const T r = f[n] - (s.off - s.diag * u[n]);
                 acc += wi * wj * wk * r;
             }
         }
     }
     out[c] = acc;
+}
+
+// Face sums of the coarse level (every axis halved) from the fine level's
+// nodal coefficient a (face sum a_c + a_n) or its face sums (fine_face).  A
+// coarse face between coarse nodes I and I + 1 along an axis spans the two
+// fine faces 2I|2I+1 and 2I+1|2I+2 of each fine line along that axis: in
+// series they conduct as the harmonic mean of the two, and the 3 x 3 lines
+// around the coarse line are weighted (1/4, 1/2, 1/4) in both transverse
+// axes.  For a constant coefficient this is the re-discretised face; where
+// the coefficient jumps it keeps the flux a fine-grid path can carry, which
+// full weighting of a nodal coefficient does not.
+__global__ void k_faces_line(Dims df, Dims dc, const float* __restrict__ in, int fine_face,
+                             float* __restrict__ out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= dc.cells) return;
+    int I, J, K;
+    cell_coords(dc, c, I, J, K);
+    const int f0[3] = {2 * I, 2 * J, 2 * K};
+    const float w[3] = {0.25f, 0.5f, 0.25f};
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        const int t1 = ax == 0 ? 1 : 0, t2 = ax == 2 ? 1 : 2;  // transverse axes
+        float acc = 0.f;
+        for (int o1 = -1; o1 <= 1; ++o1)
+            for (int o2 = -1; o2 <= 1; ++o2) {
+                int p[3];
+                p[ax] = f0[ax];
+                p[t1] = f0[t1] + o1;
+                p[t2] = f0[t2] + o2;
+                const int e0 = cell_index(df, p[0], p[1], p[2]);
+                p[ax] += 1;
+                const int e1 = cell_index(df, p[0], p[1], p[2]);
+                p[ax] += 1;
+                const int e2 = cell_index(df, p[0], p[1], p[2]);
+                float g1, g2;
+                if (fine_face) {
+                    const float* g = in + (size_t)ax * df.cells;
+                    g1 = g[e0], g2 = g[e1];
+                } else {
+                    g1 = in[e0] + in[e1], g2 = in[e1] + in[e2];
+                }
+                acc += w[o1 + 1] * w[o2 + 1] * __fdividef(2.f * g1 * g2, g1 + g2);
+            }
+        out[(size_t)ax * dc.cells + c] = acc;
+    }
 }
 
 // Trilinear prolongation of the coarse correction, added to the fine field.
@@ -230,7 +275,7 @@ constexpr size_t kInvSmem = sizeof(double) * kNb * kW;
 template <typename T>
 __global__ void __launch_bounds__(kInvThreads) k_coarse_invert(Dims d, double hx, double hy,
                                                               double hz, const T* __restrict__ a,
-                                                              double* __restrict__ out) {
+                                                              int face, double* __restrict__ out) {
     extern __shared__ double aug[];
     __shared__ double fac[kNb];
     __shared__ int piv_row;
@@ -247,7 +292,11 @@ __global__ void __launch_bounds__(kInvThreads) k_coarse_invert(Dims d, double hx
         const double hh[3] = {hx, hy, hz};
         double diag = 0.0;
         for (int q = 0; q < 6; ++q) {
-            double w = 0.5 * ((double)a[c] + (double)a[nb[q]]) * hh[q >> 1];
+            // face sum of face q: the +1 face of node c, or the +1 face of
+            // its -1 neighbour
+            const double g = face ? (double)a[(size_t)(q >> 1) * d.cells + ((q & 1) ? nb[q] : c)]
+                                  : (double)a[c] + (double)a[nb[q]];
+            double w = 0.5 * g * hh[q >> 1];
             diag += w;
             aug[c * kW + nb[q]] += w;  // row c of L; distinct neighbours on 4^3
         }
@@ -322,7 +371,7 @@ void launch_rbgs_sweep(const Level& L, T* u, const T* f, const T* a, cudaStream_
     launch_counter() += 2;
     for (int colour = 0; colour < 2; ++colour)
         k_rbgs_colour<T><<<nblocks(half), kThreads, 0, st>>>(L.d, (T)L.h2i[0], (T)L.h2i[1],
-                                                             (T)L.h2i[2], colour, u, f, a);
+                                                             (T)L.h2i[2], colour, u, f, a, L.face);
 }
 
 template <typename T>
@@ -338,7 +387,13 @@ void launch_resid_restrict(const Level& fine, const Level& coarse, const T* u, c
     launch_counter()++;
     k_resid_restrict<T><<<nblocks(coarse.d.cells), kThreads, 0, st>>>(
         fine.d, coarse.d, fine.coarsen[0], fine.coarsen[1], fine.coarsen[2], (T)fine.h2i[0],
-        (T)fine.h2i[1], (T)fine.h2i[2], u, f, a, out);
+        (T)fine.h2i[1], (T)fine.h2i[2], u, f, a, fine.face, out);
+}
+
+void launch_faces_line(const Level& fine, const Level& coarse, const float* in, float* out,
+                       cudaStream_t st) {
+    launch_counter()++;
+    k_faces_line<<<nblocks(coarse.d.cells), kThreads, 0, st>>>(fine.d, coarse.d, in, fine.face, out);
 }
 
 template <typename T>
@@ -353,7 +408,7 @@ void launch_coarse_invert(const Level& L, const T* a, double* minv, cudaStream_t
     allow_smem((const void*)k_coarse_invert<T>, (int)kInvSmem);
     launch_counter()++;
     k_coarse_invert<T><<<1, kInvThreads, kInvSmem, st>>>(L.d, L.h2i[0], L.h2i[1], L.h2i[2], a,
-                                                         minv);
+                                                         L.face, minv);
 }
 
 template <typename T>

@@ -243,6 +243,12 @@ void smooth_sweeps(Handle* H, int l, int nu, T** cur, T** oth, const T* f, const
 
 bool pow2_ge(int v, int lo) { return v >= lo && (v & (v - 1)) == 0; }
 
+// Per-face coarse coefficients: cubic grids of at least 64^3 (every level
+// halves every axis, and the levels from 32^3 down form one cluster launch).
+bool faces_apply(const recon_params* p) {
+    return p->n[0] == p->n[1] && p->n[1] == p->n[2] && p->n[0] >= 64;
+}
+
 // The multigrid settings left at -1 take the precision's defaults: V(2, 2)
 // cycles and at most 50 per step in FP64; in mixed precision V(1, 1) FP32
 // cycles, 6 per FP64 defect correction and at most 100 per step (the FP64
@@ -250,9 +256,12 @@ bool pow2_ge(int v, int lo) { return v >= lo && (v & (v - 1)) == 0; }
 // cycles in longer groups reach the same residual sooner).
 void resolve_params(recon_params* p) {
     const bool mixed = p->precision == RECON_MIXED;
+    if (p->coarse_faces == -1) p->coarse_faces = mixed && faces_apply(p) ? 1 : 0;
     if (p->nu1 == -1) p->nu1 = mixed ? 1 : 2;
     if (p->nu2 == -1) p->nu2 = mixed ? 1 : 2;
-    if (p->inner_vcycles == -1) p->inner_vcycles = 6;
+    // with per-face coarse coefficients a V-cycle contracts more, so the FP64
+    // residual is worth forming after fewer of them
+    if (p->inner_vcycles == -1) p->inner_vcycles = p->coarse_faces == 1 ? 4 : 6;
     if (p->max_vcycles == -1) p->max_vcycles = mixed ? 100 : 50;
 }
 
@@ -297,6 +306,9 @@ int check_params(const recon_params* p) {
         return fail(RECON_E_INVALID, "stream_planes must be 0, 4, 8 or 16");
     if (p->restrict_planes < 0 || p->restrict_planes > 16 || (p->restrict_planes & (p->restrict_planes - 1)))
         return fail(RECON_E_INVALID, "restrict_planes must be 0, 1, 2, 4, 8 or 16");
+    if (p->coarse_faces != 0 && p->coarse_faces != 1) return fail(RECON_E_INVALID, "coarse_faces must be 0 or 1");
+    if (p->coarse_faces == 1 && (p->precision != RECON_MIXED || !faces_apply(p)))
+        return fail(RECON_E_INVALID, "coarse_faces = 1 needs RECON_MIXED on a cubic grid of at least 64^3");
     return RECON_OK;
 }
 
@@ -388,8 +400,15 @@ bool vcycle(Handle* H, MG<T>& g, int l, T* u, const T* f, bool zero_u,
 template <typename T>
 void build_hierarchy(Handle* H, std::vector<T*>& c) {
     launch_faces64(H->lv[0], H->a64, H->F64, H->D64, H->inv64, H->st);
-    for (size_t l = 0; l + 1 < H->lv.size(); ++l)
+    for (size_t l = 0; l + 1 < H->lv.size(); ++l) {
+        if constexpr (sizeof(T) == sizeof(float)) {
+            if (H->lv[l + 1].face) {
+                launch_faces_line(H->lv[l], H->lv[l + 1], c[l], c[l + 1], H->st);
+                continue;
+            }
+        }
         launch_restrict<T>(H->lv[l], H->lv[l + 1], c[l], c[l + 1], H->st);
+    }
     launch_coarse_invert<T>(H->lv.back(), c.back(), H->minv, H->st);
 }
 
@@ -1012,6 +1031,7 @@ int recon_default_params(recon_params* p, int n0, int n1, int n2) {
     p->checkpoint = 0;
     p->stream_planes = 0;
     p->restrict_planes = 0;
+    p->coarse_faces = -1;
     return RECON_OK;
 }
 
@@ -1107,9 +1127,13 @@ int recon_create(void** out, const recon_params* p_in, void* cuda_stream) {
     } else {
         H->u32.assign(nl, nullptr), H->f32.assign(nl, nullptr), H->c32.assign(nl, nullptr),
             H->r32.assign(nl, nullptr);
+        // per-face coefficients on the coarse levels of a cubic grid
+        const bool faces = p->coarse_faces == 1;
+        for (int l = 1; l < nl; ++l) H->lv[l].face = faces ? 1 : 0;
         for (int l = 0; l < nl; ++l) {
             size_t cl = H->lv[l].d.cells;
-            AL(H->u32[l], cl); AL(H->f32[l], cl); AL(H->c32[l], cl); AL(H->r32[l], cl);
+            AL(H->u32[l], cl); AL(H->f32[l], cl); AL(H->c32[l], H->lv[l].face ? 3 * cl : cl);
+            AL(H->r32[l], cl);
         }
     }
 #undef AL
@@ -1138,7 +1162,7 @@ int recon_create(void** out, const recon_params* p_in, void* cuda_stream) {
     }
     // the levels from the first one of at most 16^3 nodes down run in one block
     for (int l = 0; l < nl; ++l)
-        if (H->lv[l].d.cells <= 4096 && nl - l <= kCoarseMaxLevels) {
+        if (H->lv[l].d.cells <= 4096 && nl - l <= kCoarseMaxLevels && !H->lv[l].face) {
             H->l0 = l;
             break;
         }

@@ -94,6 +94,12 @@ struct Level {
     // the plain sweep, the sweep with the prolongation folded in and the
     // residual restriction; 0: the occupancy cost model decides
     int tune[3];
+    // 0: the operator's coefficient is nodal (a, faces (a_c + a_n) / 2);
+    // 1: it is given per face, as one array of 3 x cells face sums
+    // G = 2 x the face coefficient (x faces, then y, then z; entry c is the
+    // face between node c and its +1 neighbour), built from the level above
+    // by launch_faces_line
+    int face;
 };
 
 // Mean device time (ms) of `reps` launches issued by launch() on st, after
@@ -196,6 +202,12 @@ int launch_rbgs_fused<double>(const Level&, const double*, double*, const double
                               const double*, int, cudaStream_t);
 template <typename T>
 void launch_restrict(const Level& fine, const Level& coarse, const T* in, T* out, cudaStream_t st);
+// Face sums of a coarse level (every axis halved) from the level above
+// (nodal coefficient, or its face sums when fine.face): along each axis the
+// two fine faces a coarse face spans act in series (harmonic mean), and the
+// fine lines under it are averaged with the full-weighting weights across.
+void launch_faces_line(const Level& fine, const Level& coarse, const float* in, float* out,
+                       cudaStream_t st);
 // full-weighting restriction of the residual f - L u, without storing it
 template <typename T>
 void launch_resid_restrict(const Level& fine, const Level& coarse, const T* u, const T* f,

@@ -43,6 +43,9 @@ constexpr int NFC = (FJ + 1) * RCH;     // chunks of an f plane (rows -1 .. FJ-1
 constexpr int NRING = (FK + 1) + FJ;    // low-side ring residuals: row -1 and column -1: 81
 constexpr int SUA = 4, SFF = 2;         // ring slots of u / a and of f
 constexpr int RSMEM = (int)sizeof(float) * RPL * (2 * SUA + SFF + 2);
+// FACE: also the y and z face sums of a plane, two slots each (read for the
+// residual plane only)
+constexpr int RSMEM_FACE = RSMEM + (int)sizeof(float) * RPL * 2 * SFF;
 static_assert(NUA <= 2 * RT && NFC <= 2 * RT && NRING <= RT, "fetch rounds");
 static_assert((FJ / 2) * (FK / 2) == RT && FK / 2 == 32, "one coarse node per thread, a coarse row per warp");
 
@@ -69,7 +72,20 @@ __device__ __forceinline__ float resid_node(float c, float apx, float amx, float
     return f - (off - diag * uc);
 }
 
-template <bool ISO, int CIc>
+// The residual of an isotropic level given by face sums G of the node's six
+// faces (hx holds hh, as in resid_node).
+__device__ __forceinline__ float resid_face(float gpx, float gmx, float gpy, float gmy, float gpz, float gmz,
+                                            float upx, float umx, float upy, float umy, float upz,
+                                            float umz, float uc, float f, float hx) {
+    const float diag = (gpx + gmx) + (gpy + gmy) + (gpz + gmz);
+    const float off = (gpx * upx + gmx * umx) + (gpy * upy + gmy * umy) + (gpz * upz + gmz * umz);
+    return fmaf(-hx, fmaf(-diag, uc, off), f);
+}
+
+// FACE: the fine level is given by face sums (a points at its x, y and z
+// face-sum arrays): the x sums ride in the registers that hold a, the y and z
+// sums of the residual plane come from shared memory.
+template <bool ISO, int CIc, bool FACE>
 __global__ void __launch_bounds__(RT) k_resid_restrict_stream(Dims df, Dims dc, float hx, float hy,
                                                               float hz,
                                                               const float* __restrict__ u,
@@ -81,6 +97,11 @@ __global__ void __launch_bounds__(RT) k_resid_restrict_stream(Dims df, Dims dc, 
     float* sa = su + SUA * RPL;
     float* sf = sa + SUA * RPL;
     float* sr = sf + SFF * RPL;  // two residual planes
+    float* sy = sr + 2 * RPL;    // FACE: y and z face sums
+    float* sz = sy + SFF * RPL;
+    static_assert(!FACE || ISO, "face sums: isotropic levels");
+    const float* gyg = FACE ? a + df.cells : nullptr;
+    const float* gzg = FACE ? a + 2 * (size_t)df.cells : nullptr;
     const int t = threadIdx.x;
     const int K0c = blockIdx.x * (FK / 2), J0c = blockIdx.y * (FJ / 2), I0c = blockIdx.z * CIc;
     const int k0 = 2 * K0c, j0 = 2 * J0c;
@@ -129,6 +150,14 @@ __global__ void __launch_bounds__(RT) k_resid_restrict_stream(Dims df, Dims dc, 
 #pragma unroll
         for (int m = 0; m < 2; ++m)
             if (f_s[m] >= 0) cp_async16(sf + so + f_s[m], f + g + f_g[m]);
+        if (FACE) {
+#pragma unroll
+            for (int m = 0; m < 2; ++m)
+                if (ua_s[m] >= 0) {
+                    cp_async16(sy + so + ua_s[m], gyg + g + ua_g[m]);
+                    cp_async16(sz + so + ua_s[m], gzg + g + ua_g[m]);
+                }
+        }
     };
     auto ld2 = [](const float* p) { return *reinterpret_cast<const float2*>(p); };
     const unsigned full = 0xffffffffu;
@@ -206,14 +235,31 @@ __global__ void __launch_bounds__(RT) k_resid_restrict_stream(Dims df, Dims dc, 
         }
         const float2 up0 = U[ip1][0], up1 = U[ip1][1], um0 = U[im1][0], um1 = U[im1][1];
         const float2 ap0 = A[ip1][0], ap1 = A[ip1][1], am0 = A[im1][0], am1 = A[im1][1];
-        const float r00 = resid_node<ISO>(a0.x, ap0.x, am0.x, a1.x, aa.x, a0.y, al0, up0.x, um0.x, u1.x, ua.x,
-                                          u0.y, ul0, u0.x, f0.x, hx, hy, hz);
-        const float r01 = resid_node<ISO>(a0.y, ap0.y, am0.y, a1.y, aa.y, ar0, a0.x, up0.y, um0.y, u1.y, ua.y,
-                                          ur0, u0.x, u0.y, f0.y, hx, hy, hz);
-        const float r10 = resid_node<ISO>(a1.x, ap1.x, am1.x, ab.x, a0.x, a1.y, al1, up1.x, um1.x, ub.x, u0.x,
-                                          u1.y, ul1, u1.x, f1.x, hx, hy, hz);
-        const float r11 = resid_node<ISO>(a1.y, ap1.y, am1.y, ab.y, a0.y, ar1, a1.x, up1.y, um1.y, ub.y, u0.y,
-                                          ur1, u1.x, u1.y, f1.y, hx, hy, hz);
+        float r00, r01, r10, r11;
+        if constexpr (FACE) {
+            // x sums: a0/a1 (plane p), am0/am1 (plane p - 1); y sums of rows
+            // 2jc - 1 .. 2jc + 1 and z sums of columns 2kc - 1 .. 2kc + 1
+            const float2 gym = ld2(sy + cf + e0 - RRK), gy0 = ld2(sy + cf + e0), gy1 = ld2(sy + cf + e1);
+            const float2 gz0 = ld2(sz + cf + e0), gz1 = ld2(sz + cf + e1);
+            const float gzl0 = sz[cf + e0 - 1], gzl1 = sz[cf + e1 - 1];
+            r00 = resid_face(a0.x, am0.x, gy0.x, gym.x, gz0.x, gzl0, up0.x, um0.x, u1.x, ua.x, u0.y, ul0, u0.x,
+                             f0.x, hx);
+            r01 = resid_face(a0.y, am0.y, gy0.y, gym.y, gz0.y, gz0.x, up0.y, um0.y, u1.y, ua.y, ur0, u0.x, u0.y,
+                             f0.y, hx);
+            r10 = resid_face(a1.x, am1.x, gy1.x, gy0.x, gz1.x, gzl1, up1.x, um1.x, ub.x, u0.x, u1.y, ul1, u1.x,
+                             f1.x, hx);
+            r11 = resid_face(a1.y, am1.y, gy1.y, gy0.y, gz1.y, gz1.x, up1.y, um1.y, ub.y, u0.y, ur1, u1.x, u1.y,
+                             f1.y, hx);
+        } else {
+            r00 = resid_node<ISO>(a0.x, ap0.x, am0.x, a1.x, aa.x, a0.y, al0, up0.x, um0.x, u1.x, ua.x,
+                                  u0.y, ul0, u0.x, f0.x, hx, hy, hz);
+            r01 = resid_node<ISO>(a0.y, ap0.y, am0.y, a1.y, aa.y, ar0, a0.x, up0.y, um0.y, u1.y, ua.y,
+                                  ur0, u0.x, u0.y, f0.y, hx, hy, hz);
+            r10 = resid_node<ISO>(a1.x, ap1.x, am1.x, ab.x, a0.x, a1.y, al1, up1.x, um1.x, ub.x, u0.x,
+                                  u1.y, ul1, u1.x, f1.x, hx, hy, hz);
+            r11 = resid_node<ISO>(a1.y, ap1.y, am1.y, ab.y, a0.y, ar1, a1.x, up1.y, um1.y, ub.y, u0.y,
+                                  ur1, u1.x, u1.y, f1.y, hx, hy, hz);
+        }
         float* rw = sr + (it & 1) * RPL;
         *reinterpret_cast<float2*>(rw + e1) = make_float2(r10, r11);  // read by the coarse row below
         Rp[0] = r00, Rp[1] = r01, Rp[2] = r10, Rp[3] = r11;
@@ -222,9 +268,14 @@ __global__ void __launch_bounds__(RT) k_resid_restrict_stream(Dims df, Dims dc, 
             const int e = ring_e;
             const float* ac = sa + cu;
             const float* uq = su + cu;
-            rw[e] = resid_node<ISO>(ac[e], sa[pu + e], sa[mu + e], ac[e + RRK], ac[e - RRK], ac[e + 1], ac[e - 1],
-                                    su[pu + e], su[mu + e], uq[e + RRK], uq[e - RRK], uq[e + 1], uq[e - 1], uq[e],
-                                    sf[cf + e], hx, hy, hz);
+            if constexpr (FACE)
+                rw[e] = resid_face(ac[e], sa[mu + e], sy[cf + e], sy[cf + e - RRK], sz[cf + e], sz[cf + e - 1],
+                                   su[pu + e], su[mu + e], uq[e + RRK], uq[e - RRK], uq[e + 1], uq[e - 1], uq[e],
+                                   sf[cf + e], hx);
+            else
+                rw[e] = resid_node<ISO>(ac[e], sa[pu + e], sa[mu + e], ac[e + RRK], ac[e - RRK], ac[e + 1],
+                                        ac[e - 1], su[pu + e], su[mu + e], uq[e + RRK], uq[e - RRK], uq[e + 1],
+                                        uq[e - 1], uq[e], sf[cf + e], hx, hy, hz);
         }
         cp_wait_all();
         __syncthreads();
@@ -236,22 +287,23 @@ constexpr int kMaxDevices = 64;
 int g_resident[kMaxDevices] = {};
 std::mutex g_resident_mu;
 
-template <bool ISO, int CIc>
+template <bool ISO, int CIc, bool FACE>
 void launch_rr(dim3 grid, const Dims& df, const Dims& dc, float hx, float hy, float hz,
                const float* u, const float* f, const float* a, float* out, cudaStream_t st) {
-    allow_smem((const void*)k_resid_restrict_stream<ISO, CIc>, RSMEM);
-    k_resid_restrict_stream<ISO, CIc><<<grid, RT, RSMEM, st>>>(df, dc, hx, hy, hz, u, f, a, out);
+    constexpr int smem = FACE ? RSMEM_FACE : RSMEM;
+    allow_smem((const void*)k_resid_restrict_stream<ISO, CIc, FACE>, smem);
+    k_resid_restrict_stream<ISO, CIc, FACE><<<grid, RT, smem, st>>>(df, dc, hx, hy, hz, u, f, a, out);
 }
 
-template <bool ISO>
+template <bool ISO, bool FACE = false>
 void launch_rr_ci(int ci, dim3 grid, const Dims& df, const Dims& dc, float hx, float hy, float hz,
                   const float* u, const float* f, const float* a, float* out, cudaStream_t st) {
     switch (ci) {
-        case 1: launch_rr<ISO, 1>(grid, df, dc, hx, hy, hz, u, f, a, out, st); break;
-        case 2: launch_rr<ISO, 2>(grid, df, dc, hx, hy, hz, u, f, a, out, st); break;
-        case 4: launch_rr<ISO, 4>(grid, df, dc, hx, hy, hz, u, f, a, out, st); break;
-        case 8: launch_rr<ISO, 8>(grid, df, dc, hx, hy, hz, u, f, a, out, st); break;
-        default: launch_rr<ISO, 16>(grid, df, dc, hx, hy, hz, u, f, a, out, st); break;
+        case 1: launch_rr<ISO, 1, FACE>(grid, df, dc, hx, hy, hz, u, f, a, out, st); break;
+        case 2: launch_rr<ISO, 2, FACE>(grid, df, dc, hx, hy, hz, u, f, a, out, st); break;
+        case 4: launch_rr<ISO, 4, FACE>(grid, df, dc, hx, hy, hz, u, f, a, out, st); break;
+        case 8: launch_rr<ISO, 8, FACE>(grid, df, dc, hx, hy, hz, u, f, a, out, st); break;
+        default: launch_rr<ISO, 16, FACE>(grid, df, dc, hx, hy, hz, u, f, a, out, st); break;
     }
 }
 
@@ -271,11 +323,11 @@ int model_rr_ci(const Level& fine, const Level& coarse) {
         std::lock_guard<std::mutex> lock(g_resident_mu);
         int& r = g_resident[(dev >= 0 && dev < kMaxDevices) ? dev : 0];
         if (!r) {
-            allow_smem((const void*)k_resid_restrict_stream<true, 8>, RSMEM);
+            allow_smem((const void*)k_resid_restrict_stream<true, 8, false>, RSMEM);
             int sms = 0, per_sm = 0;
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_resid_restrict_stream<true, 8>, RT,
-                                                          RSMEM);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_resid_restrict_stream<true, 8, false>,
+                                                          RT, RSMEM);
             r = sms * per_sm > 0 ? sms * per_sm : 1;
         }
         resident = r;
@@ -293,6 +345,8 @@ int model_rr_ci(const Level& fine, const Level& coarse) {
     return best;
 }
 
+bool iso(const Level& L) { return L.h2i[0] == L.h2i[1] && L.h2i[1] == L.h2i[2]; }
+
 bool rr_fits(const Level& fine) {
     const Dims& df = fine.d;
     return fine.coarsen[0] && fine.coarsen[1] && fine.coarsen[2] && df.n2 % FK == 0 && df.n1 % FJ == 0 &&
@@ -306,7 +360,10 @@ void launch_rr_level(const Level& fine, const Level& coarse, int ci, const float
     launch_counter()++;
     if (fine.h2i[0] == fine.h2i[1] && fine.h2i[1] == fine.h2i[2]) {
         const float hh = (float)(0.5 * fine.h2i[0]);  // 2^-(2l+1): exact
-        launch_rr_ci<true>(ci, grid, df, coarse.d, hh, hh, hh, u, f, a, out, st);
+        if (fine.face)
+            launch_rr_ci<true, true>(ci, grid, df, coarse.d, hh, hh, hh, u, f, a, out, st);
+        else
+            launch_rr_ci<true>(ci, grid, df, coarse.d, hh, hh, hh, u, f, a, out, st);
     } else {
         launch_rr_ci<false>(ci, grid, df, coarse.d, (float)fine.h2i[0], (float)fine.h2i[1],
                             (float)fine.h2i[2], u, f, a, out, st);
@@ -318,7 +375,7 @@ void launch_rr_level(const Level& fine, const Level& coarse, int ci, const float
 // Coarse planes per block: the level's tuned value, else the cost model's.
 int launch_resid_restrict_stream(const Level& fine, const Level& coarse, const float* u,
                                  const float* f, const float* a, float* out, cudaStream_t st) {
-    if (!rr_fits(fine)) return 0;
+    if (!rr_fits(fine) || (fine.face && !iso(fine))) return 0;
     int ci = fine.tune[2];
     if (!ci || coarse.d.n0 % ci) ci = model_rr_ci(fine, coarse);
     launch_rr_level(fine, coarse, ci, u, f, a, out, st);
@@ -327,14 +384,16 @@ int launch_resid_restrict_stream(const Level& fine, const Level& coarse, const f
 
 void tune_resid_restrict_level(Level& fine, const Level& coarse, const float* u, const float* f,
                                const float* a, float* out, cudaStream_t st) {
-    if (!rr_fits(fine)) return;
+    if (!rr_fits(fine) || (fine.face && !iso(fine))) return;
     float best_ms = 0.f;
     int best = 0;
-    for (int ci = 1; ci <= 16 && ci <= coarse.d.n0; ci *= 2) {
-        if (coarse.d.n0 % ci) continue;
-        const float ms = time_launches(st, 3, [&] { launch_rr_level(fine, coarse, ci, u, f, a, out, st); });
-        if (!best || ms < best_ms) best = ci, best_ms = ms;
-    }
+    // two rounds, the first only bringing the clocks up
+    for (int round = 0; round < 2; ++round)
+        for (int ci = 1; ci <= 16 && ci <= coarse.d.n0; ci *= 2) {
+            if (coarse.d.n0 % ci) continue;
+            const float ms = time_launches(st, 5, [&] { launch_rr_level(fine, coarse, ci, u, f, a, out, st); });
+            if (round == 1 && (!best || ms < best_ms)) best = ci, best_ms = ms;
+        }
     fine.tune[2] = best;
 }
 

@@ -48,7 +48,15 @@ def test_mixed_precision_defaults_and_explicit_settings_resolve():
     from paper_1611_09638_gb300 import resolved_params
 
     p = resolved_params((16, 16, 16), precision="mixed")
-    assert (p.nu1, p.nu2, p.inner_vcycles, p.max_vcycles) == (1, 1, 6, 100)
+    assert (p.nu1, p.nu2, p.inner_vcycles, p.max_vcycles, p.coarse_faces) == (1, 1, 6, 100, 0)
+    # per-face coarse coefficients on cubic grids of at least 64^3, with
+    # shorter groups of V-cycles; not in FP64, not on other grids
+    p = resolved_params((64, 64, 64), precision="mixed")
+    assert (p.inner_vcycles, p.coarse_faces) == (4, 1)
+    assert resolved_params((64, 64, 64), precision="fp64").coarse_faces == 0
+    assert resolved_params((128, 64, 64), precision="mixed").coarse_faces == 0
+    p = resolved_params((64, 64, 64), precision="mixed", coarse_faces=0)
+    assert (p.inner_vcycles, p.coarse_faces) == (6, 0)
     p = resolved_params((16, 16, 16), precision="mixed", nu1=2, nu2=3, inner_vcycles=4, max_vcycles=7)
     assert (p.nu1, p.nu2, p.inner_vcycles, p.max_vcycles) == (2, 3, 4, 7)
     p = resolved_params((16, 16, 16), precision="fp64", nu1=1)
@@ -146,7 +154,7 @@ def test_resolve_params_touches_only_the_multigrid_settings():
 
     lib = _abi.load()
     p = default_params((16, 32, 64), box=(1.0, 2.0, 4.0), precision="mixed", k_max=7, tol_in=1e-6)
-    skip = ("nu1", "nu2", "inner_vcycles", "max_vcycles", "n", "box", "replay_alpha")
+    skip = ("nu1", "nu2", "inner_vcycles", "max_vcycles", "coarse_faces", "n", "box", "replay_alpha")
     before = {f: getattr(p, f) for f, _ in _abi.recon_params._fields_ if f not in skip}
     assert lib.recon_resolve_params(C.byref(p)) == _abi.RECON_OK
     after = {f: getattr(p, f) for f in before}
