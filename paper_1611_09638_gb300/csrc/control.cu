@@ -46,14 +46,13 @@ __global__ void k_ctl_step_begin(Ctl* c, const double* scal, CtlArrays a, double
     }
 }
 
-// Multigrid start: in mixed mode the first FP64 defect (phidot = 0) is
-// already reduced into scal[SC_RES2].
+// Multigrid start: phidot = 0, so the defect is s and its relative size 1.
 __global__ void k_ctl_mg_begin(Ctl* c, const double* scal, CtlArrays a, int mixed, double tol_in,
                                int max_vcycles, CtlHandles h) {
     const int k = c->k;
     c->n_cont += 1;
     c->ncyc = 0;
-    const double rel = mixed ? sqrt(scal[SC_RES2] / c->s2) : 1.0;
+    const double rel = 1.0;
     c->rel = rel;
     a.ncycles[k] = 0, a.relres[k] = rel;
     const int go = c->s2 > 0.0 && max_vcycles > 0 && !(mixed && rel <= tol_in);

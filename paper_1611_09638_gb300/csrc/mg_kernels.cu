@@ -358,6 +358,11 @@ __global__ void k_coarse_solve(const double* __restrict__ aug, const T* __restri
     u[r] = (T)acc;
 }
 
+__global__ void k_to_f32(int cells, const double* __restrict__ x, float* __restrict__ y) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < cells) y[c] = (float)x[c];
+}
+
 __global__ void k_correct(int cells, double* __restrict__ u, const float* __restrict__ e) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c < cells) u[c] += (double)e[c];
@@ -415,6 +420,11 @@ template <typename T>
 void launch_coarse_solve(const double* minv, const T* f, T* u, cudaStream_t st) {
     launch_counter()++;
     k_coarse_solve<T><<<1, kNc, 0, st>>>(minv, f, u);
+}
+
+void launch_to_f32(int cells, const double* x, float* y, cudaStream_t st) {
+    launch_counter()++;
+    k_to_f32<<<nblocks(cells), kThreads, 0, st>>>(cells, x, y);
 }
 
 void launch_residual64_to32(const Level& L, const double* u, const double* f, const double* F,

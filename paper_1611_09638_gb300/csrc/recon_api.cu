@@ -464,10 +464,9 @@ void mg_head(Handle* H, const CtlHandles& h) {
     if (H->mixed) build_hierarchy<float>(H, H->c32);
     else build_hierarchy<double>(H, H->c64);
     cudaMemsetAsync(H->phidot, 0, sizeof(double) * H->cells, H->st);
-    if (H->mixed) {
-        launch_residual64_to32(H->lv[0], H->phidot, H->s, H->F64, H->D64, H->f32[0], H->part[0], H->st);
-        finish_reduce(H->part[0], 0, H->scal, SC_RES2, H->st);
-    }
+    // with phidot = 0 the FP64 defect is s itself: its FP32 copy is the first
+    // right-hand side of the FP32 V-cycles
+    if (H->mixed) launch_to_f32(H->cells, H->s, H->f32[0], H->st);
     launch_ctl_mg_begin(H->ctl, H->scal, H->arr, H->mixed ? 1 : 0, H->p.tol_in, H->p.max_vcycles,
                         h, H->st);
 }

@@ -208,6 +208,8 @@ void launch_restrict(const Level& fine, const Level& coarse, const T* in, T* out
 // fine lines under it are averaged with the full-weighting weights across.
 void launch_faces_line(const Level& fine, const Level& coarse, const float* in, float* out,
                        cudaStream_t st);
+// y = (float) x, elementwise
+void launch_to_f32(int cells, const double* x, float* y, cudaStream_t st);
 // full-weighting restriction of the residual f - L u, without storing it
 template <typename T>
 void launch_resid_restrict(const Level& fine, const Level& coarse, const T* u, const T* f,
