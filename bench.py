@@ -72,6 +72,9 @@ def _args():
                     help="precision of the --launch-list solve")
     ap.add_argument("--coarse-faces", type=int, default=None,
                     help="mixed precision's coarse-level coefficients (library default if unset)")
+    ap.add_argument("--tune-inner", type=int, default=1,
+                    help="1: each mixed-precision handle picks its FP32 V-cycles per FP64 defect "
+                         "correction by timing on its first (untimed) solve")
     return ap.parse_args()
 
 
@@ -234,9 +237,14 @@ def run_gb300(a):
     mg_kw = {} if a.inner_vcycles is None else {"inner_vcycles": a.inner_vcycles}
     if a.coarse_faces is not None:
         mg_kw["coarse_faces"] = a.coarse_faces
+    if a.tune_inner and a.inner_vcycles is None:
+        mg_kw["tune_inner"] = 1
 
-    def timed(precision, steps, warmup, profile=False):
-        kw = mg_kw if precision == "mixed" else {}
+    def timed(precision, steps, warmup, profile=False, inner=None):
+        kw = dict(mg_kw) if precision == "mixed" else {}
+        if inner:  # the count the timed solves' handle chose
+            kw.pop("tune_inner", None)
+            kw["inner_vcycles"] = inner
         R = Recon((n, n, n), box=W.box, precision=precision, profile=int(profile), k_max=a.k_max, **kw)
         R.deposit_particles(pos_dev)
         for _ in range(warmup):
@@ -258,7 +266,7 @@ def run_gb300(a):
     ms_mixed, st_mixed, clocks = timed("mixed", a.steps, a.warmup)
     # one more solve on the host-driven loop with CUDA events around every
     # finest-level sweep, for the roofline of the dominant kernel
-    _, st_prof, _ = timed("mixed", 1, 0, profile=True)
+    _, st_prof, _ = timed("mixed", 1, 0, profile=True, inner=st_mixed[0].inner_vcycles)
     ms_fp64, st_fp64 = None, None
     if a.fp64_steps > 0:
         ms_fp64, st_fp64, _ = timed("fp64", a.fp64_steps, a.fp64_warmup)
@@ -302,7 +310,7 @@ def run_gb300(a):
 
     e2e = None
     if not a.no_e2e:
-        R = Recon((n, n, n), box=W.box, precision="mixed")
+        R = Recon((n, n, n), box=W.box, precision="mixed", k_max=a.k_max, **mg_kw)
         pin_pos = torch.from_numpy(pos_host).pin_memory()
         out = torch.empty((n, n, n), dtype=torch.float64).pin_memory()
         for _ in range(1):
@@ -342,6 +350,11 @@ def run_gb300(a):
         "config": _config(a, W),
         "solve": {"precision": "mixed", "status": _status_name(s0.status),
                   "steps_per_solve": s0.steps, "vcycles_per_solve": s0.vcycles,
+                  "inner_vcycles_used": s0.inner_vcycles,
+                  "coarse_levels": "per-face coefficients" if resolved_params(
+                      (n, n, n), precision="mixed", **{k: v for k, v in mg_kw.items()
+                                                        if k != "tune_inner"}).coarse_faces
+                  else "nodal (full-weighted a)",
                   "R0": s0.R0, "R_end": s0.R, "min_lambda0": s0.min_lambda0,
                   "max_delta_r": s0.max_delta_r,
                   "multigrid": _mg_settings(resolved_params((n, n, n), precision="mixed", **mg_kw)),
@@ -419,7 +432,7 @@ def mocks_timing(a, stream, barrier, steps=2, k_max=40):
     recons = []
     for W in mocks:
         R = Recon((W.n,) * 3, box=W.box, precision="mixed", stream=torch.cuda.Stream(),
-                  k_max=k_max)
+                  k_max=k_max, tune_inner=1 if a.tune_inner else 0)
         torch.cuda.synchronize()
         R.deposit_particles(torch.from_numpy(W.particles()[0]).cuda())
         recons.append(R)

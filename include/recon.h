@@ -105,7 +105,7 @@ typedef struct {
     int profile;         /* nonzero: time the finest-level smoothing sweeps with
                             CUDA events (reported in recon_stats.smooth_ms)    */
     int inner_vcycles;   /* RECON_MIXED: FP32 V-cycles per FP64 defect
-                            correction (1..16; -1, the default: 4 with per-face
+                            correction (1..16; -1, the default: 5 with per-face
                             coarse coefficients, else 6); the FP64 residual is
                             formed once per group, so the stopping test sees
                             multiples of it                                     */
@@ -144,6 +144,13 @@ typedef struct {
                             coefficient jumps.  1 needs RECON_MIXED and a cubic
                             grid of at least 64^3.  -1 (default): 1 where that
                             holds, else 0.                                     */
+    int tune_inner;      /* RECON_MIXED: 1: the first recon_solve on the handle
+                            times the first step's linear solve with 3, 4, 5, 6
+                            and 8 FP32 V-cycles per FP64 defect correction and
+                            keeps the fastest for this and later solves (the
+                            solution is the same to the stopping residual; the
+                            choice follows the timing).  Ignored with profile.
+                            0 (default): keep inner_vcycles.                    */
 } recon_params;
 
 /* Per-solve record.  The per-step arrays are optional caller-owned host
@@ -167,6 +174,8 @@ typedef struct {
     int smooth_sweeps;   /* with params.profile: number of those sweeps        */
     double smooth_bytes; /* algorithmic bytes of one such sweep (read u, a, f;
                             write u), for the roofline                          */
+    int inner_vcycles;   /* RECON_MIXED: FP32 V-cycles per FP64 defect correction
+                            the solve used (params.tune_inner may have chosen it) */
 } recon_stats;
 
 /* Fill *p with the defaults above for an n0 x n1 x n2 grid (grid units,
@@ -179,7 +188,7 @@ int recon_default_params(recon_params* p, int n0, int n1, int n2);
  * recon_create uses for p->precision and p->n (nu1 = nu2 = 2, max_vcycles =
  * 50 and coarse_faces = 0 in RECON_FP64; in RECON_MIXED nu1 = nu2 = 1,
  * max_vcycles = 100, coarse_faces = 1 on cubic grids of at least 64^3 (else
- * 0), and inner_vcycles = 4 with coarse_faces = 1, else 6).  The paper leaves the cycle shape open; these are the
+ * 0), and inner_vcycles = 5 with coarse_faces = 1, else 6).  The paper leaves the cycle shape open; these are the
  * settings that reach the stopping residual in the least time on the 256^3
  * workload.  Other fields are not touched or checked.  RECON_E_INVALID for
  * a NULL p. */

@@ -42,7 +42,7 @@ class recon_params(C.Structure):
         ("lambda_floor", C.c_double), ("replay_alpha", _D), ("profile", C.c_int),
         ("inner_vcycles", C.c_int), ("density_update", C.c_int), ("device_loop", C.c_int),
         ("checkpoint", C.c_int), ("stream_planes", C.c_int), ("restrict_planes", C.c_int),
-        ("coarse_faces", C.c_int),
+        ("coarse_faces", C.c_int), ("tune_inner", C.c_int),
     ]
 
 
@@ -53,7 +53,7 @@ class recon_stats(C.Structure):
         ("max_delta_r", C.c_double), ("mass_error", C.c_double), ("ms", C.c_double),
         ("alpha", _D), ("Rk", _D), ("ncycles", _I), ("relres", _D),
         ("launches", C.c_longlong), ("smooth_ms", C.c_double), ("smooth_sweeps", C.c_int),
-        ("smooth_bytes", C.c_double),
+        ("smooth_bytes", C.c_double), ("inner_vcycles", C.c_int),
     ]
 
 

@@ -97,6 +97,7 @@ struct Handle {
     cudaStream_t cap = nullptr;
     bool capturing = false;
     cudaGraphExec_t cyc_exec = nullptr;
+    bool inner_tuned = false;  // params.tune_inner: the first solve has chosen inner_vcycles
     long long cyc_kernels = 0;
     int cyc_sweeps = 0;
     std::vector<cudaEvent_t> cyc_ev;
@@ -261,7 +262,7 @@ void resolve_params(recon_params* p) {
     if (p->nu2 == -1) p->nu2 = mixed ? 1 : 2;
     // with per-face coarse coefficients a V-cycle contracts more, so the FP64
     // residual is worth forming after fewer of them
-    if (p->inner_vcycles == -1) p->inner_vcycles = p->coarse_faces == 1 ? 4 : 6;
+    if (p->inner_vcycles == -1) p->inner_vcycles = p->coarse_faces == 1 ? 5 : 6;
     if (p->max_vcycles == -1) p->max_vcycles = mixed ? 100 : 50;
 }
 
@@ -309,6 +310,7 @@ int check_params(const recon_params* p) {
     if (p->coarse_faces != 0 && p->coarse_faces != 1) return fail(RECON_E_INVALID, "coarse_faces must be 0 or 1");
     if (p->coarse_faces == 1 && (p->precision != RECON_MIXED || !faces_apply(p)))
         return fail(RECON_E_INVALID, "coarse_faces = 1 needs RECON_MIXED on a cubic grid of at least 64^3");
+    if (p->tune_inner != 0 && p->tune_inner != 1) return fail(RECON_E_INVALID, "tune_inner must be 0 or 1");
     return RECON_OK;
 }
 
@@ -600,6 +602,48 @@ int run_cycle(Handle* H) {
     return RECON_OK;
 }
 
+// params.tune_inner, on the first solve of a mixed-precision handle: the
+// first step's linear solve (from phidot = 0 on the step's own source and
+// coefficient) is run with 3, 4, 5, 6 and 8 FP32 V-cycles per FP64 defect
+// correction, twice over (the first round only brings the clocks up), timed
+// with CUDA events, and the fastest count is kept.  Every count stops at the
+// same FP64 residual; the solve that follows starts again from phi = 0.
+int tune_inner_vcycles(Handle* H) {
+    H->inner_tuned = true;
+    // (not with profile: the sweep timing events belong to the timed solve)
+    if (!H->mixed || !H->p.tune_inner || H->p.profile) return RECON_OK;
+    Range range("recon_tune_inner");
+    const CtlHandles none{};
+    solve_init(H);
+    step_head(H, none);
+    int rc = read_ctl(H);
+    if (rc) return rc;
+    if (!H->hctl->go_cont) return RECON_OK;  // nothing to solve at step 0
+    const int cand[5] = {3, 4, 5, 6, 8};
+    int best = H->p.inner_vcycles;
+    float best_ms = 0.f;
+    for (int round = 0; round < 2; ++round)
+        for (int n : cand) {
+            H->p.inner_vcycles = n;
+            if (H->cyc_exec) cudaGraphExecDestroy(H->cyc_exec);
+            H->cyc_exec = nullptr;
+            CK(cudaEventRecord(H->ev0, H->st));
+            mg_head(H, none);
+            if ((rc = read_ctl(H))) return rc;
+            while (H->hctl->go_mg)
+                if ((rc = run_cycle(H))) return rc;
+            CK(cudaEventRecord(H->ev1, H->st));
+            CK(cudaEventSynchronize(H->ev1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, H->ev0, H->ev1));
+            if (round == 1 && (best_ms == 0.f || ms < best_ms)) best = n, best_ms = ms;
+        }
+    H->p.inner_vcycles = best;
+    if (H->cyc_exec) cudaGraphExecDestroy(H->cyc_exec);
+    H->cyc_exec = nullptr;
+    return RECON_OK;
+}
+
 // The host-driven loop: each decision is read back from the control block.
 int solve_host(Handle* H) {
     const CtlHandles none{};
@@ -799,6 +843,7 @@ void fill_stats(Handle* H, recon_stats* stats, float ms, long long launches, boo
     stats->ms = ms;
     stats->mass_error = std::fabs(c.last_mass - (double)H->cells) / (double)H->cells;
     stats->launches = launches;
+    stats->inner_vcycles = H->mixed ? H->p.inner_vcycles : 0;
     const size_t km = (size_t)std::max(H->p.k_max, 1);
     const double* Rk = H->harr;
     const double* al = H->harr + km;
@@ -1031,6 +1076,7 @@ int recon_default_params(recon_params* p, int n0, int n1, int n2) {
     p->stream_planes = 0;
     p->restrict_planes = 0;
     p->coarse_faces = -1;
+    p->tune_inner = 0;
     return RECON_OK;
 }
 
@@ -1291,7 +1337,8 @@ int recon_solve(void* hp, recon_stats* stats) {
     Handle* H = (Handle*)hp;
     if (!H) return fail(RECON_E_INVALID, "handle is NULL");
     if (!H->have_density) return fail(RECON_E_STATE, "recon_deposit must succeed before recon_solve");
-    int rc = solve(H, stats);
+    int rc = H->inner_tuned ? RECON_OK : tune_inner_vcycles(H);
+    if (rc == RECON_OK) rc = solve(H, stats);
     if (rc < 0) {
         cudaStreamSynchronize(H->st);
         H->solved = false;
@@ -1318,7 +1365,11 @@ int recon_solve_batch(void* const* handles, int count, recon_stats* stats) {
     for (int b = 0; b < count; ++b) {
         Handle* H = (Handle*)handles[b];
         H->solved = false;
-        if (use_graph(H)) rc[b] = solve_launch(H, stats != nullptr);
+        if (!H->inner_tuned) rc[b] = tune_inner_vcycles(H);
+    }
+    for (int b = 0; b < count; ++b) {
+        Handle* H = (Handle*)handles[b];
+        if (rc[b] == RECON_OK && use_graph(H)) rc[b] = solve_launch(H, stats != nullptr);
     }
     int worst = RECON_OK;
     for (int b = 0; b < count; ++b) {

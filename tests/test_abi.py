@@ -52,7 +52,7 @@ def test_mixed_precision_defaults_and_explicit_settings_resolve():
     # per-face coarse coefficients on cubic grids of at least 64^3, with
     # shorter groups of V-cycles; not in FP64, not on other grids
     p = resolved_params((64, 64, 64), precision="mixed")
-    assert (p.inner_vcycles, p.coarse_faces) == (4, 1)
+    assert (p.inner_vcycles, p.coarse_faces) == (5, 1)
     assert resolved_params((64, 64, 64), precision="fp64").coarse_faces == 0
     assert resolved_params((128, 64, 64), precision="mixed").coarse_faces == 0
     p = resolved_params((64, 64, 64), precision="mixed", coarse_faces=0)

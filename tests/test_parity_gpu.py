@@ -264,6 +264,27 @@ def test_per_face_coarse_levels_match_the_oracle_in_fewer_vcycles():
         assert cycles[1] < cycles[0], cycles
 
 
+def test_schedule_autotuner_keeps_the_solution():
+    """tune_inner: the first solve times the first step's linear solve with
+    3, 4, 5, 6 and 8 FP32 V-cycles per FP64 defect correction and keeps the
+    fastest; the result matches the oracle like any fixed count, and later
+    solves reuse the choice (the same bits)."""
+    n, box = 64, 100.0
+    pos, _ = lpt_particles(n, box, 23, order=2)
+    rho = O.cic_deposit((n, n, n), pos / (box / n))
+    res = O.solve(O.OracleParams(n=(n, n, n), k_max=3), rho)
+    R, st = _gpu_solve((n, n, n), rho, precision="mixed", k_max=3, replay_alpha=res.alpha,
+                       tune_inner=1)
+    assert st.inner_vcycles in (3, 4, 5, 6, 8)
+    assert np.all(st.relres <= 1e-8)
+    phi = R.field("phi").cpu().numpy()
+    assert rel(phi, res.phi) <= 1e-4
+    st2 = R.solve()
+    assert st2.inner_vcycles == st.inner_vcycles and st2.vcycles == st.vcycles
+    assert np.array_equal(R.field("phi").cpu().numpy(), phi)
+    R.close()
+
+
 def test_paper_literal_density_update_matches_oracle():
     """App. A's variant (m += alpha D(dphi), no tracers) through the C ABI."""
     n, box = 16, 100.0
