@@ -47,7 +47,7 @@ __global__ void k_ctl_step_begin(Ctl* c, const double* scal, CtlArrays a, double
 }
 
 // Multigrid start: phidot = 0, so the defect is s and its relative size 1.
-__global__ void k_ctl_mg_begin(Ctl* c, const double* scal, CtlArrays a, int mixed, double tol_in,
+__global__ void k_ctl_mg_begin(Ctl* c, CtlArrays a, int mixed, double tol_in,
                                int max_vcycles, CtlHandles h) {
     const int k = c->k;
     c->n_cont += 1;
@@ -137,10 +137,10 @@ void launch_ctl_step_begin(Ctl* c, const double* scal, const CtlArrays& a, doubl
     launch_counter()++;
     k_ctl_step_begin<<<1, 1, 0, st>>>(c, scal, a, ncells, tol_out, h);
 }
-void launch_ctl_mg_begin(Ctl* c, const double* scal, const CtlArrays& a, int mixed, double tol_in,
+void launch_ctl_mg_begin(Ctl* c, const CtlArrays& a, int mixed, double tol_in,
                          int max_vcycles, const CtlHandles& h, cudaStream_t st) {
     launch_counter()++;
-    k_ctl_mg_begin<<<1, 1, 0, st>>>(c, scal, a, mixed, tol_in, max_vcycles, h);
+    k_ctl_mg_begin<<<1, 1, 0, st>>>(c, a, mixed, tol_in, max_vcycles, h);
 }
 void launch_ctl_mg_check(Ctl* c, const double* scal, const CtlArrays& a, int per_launch,
                          double tol_in, int max_vcycles, const CtlHandles& h, cudaStream_t st) {

@@ -469,7 +469,7 @@ void mg_head(Handle* H, const CtlHandles& h) {
     // with phidot = 0 the FP64 defect is s itself: its FP32 copy is the first
     // right-hand side of the FP32 V-cycles
     if (H->mixed) launch_to_f32(H->cells, H->s, H->f32[0], H->st);
-    launch_ctl_mg_begin(H->ctl, H->scal, H->arr, H->mixed ? 1 : 0, H->p.tol_in, H->p.max_vcycles,
+    launch_ctl_mg_begin(H->ctl, H->arr, H->mixed ? 1 : 0, H->p.tol_in, H->p.max_vcycles,
                         h, H->st);
 }
 

@@ -333,7 +333,7 @@ struct CtlHandles {
 void launch_ctl_init(Ctl* c, cudaStream_t st);
 void launch_ctl_step_begin(Ctl* c, const double* scal, const CtlArrays& a, double ncells,
                            double tol_out, const CtlHandles& h, cudaStream_t st);
-void launch_ctl_mg_begin(Ctl* c, const double* scal, const CtlArrays& a, int mixed, double tol_in,
+void launch_ctl_mg_begin(Ctl* c, const CtlArrays& a, int mixed, double tol_in,
                          int max_vcycles, const CtlHandles& h, cudaStream_t st);
 void launch_ctl_mg_check(Ctl* c, const double* scal, const CtlArrays& a, int per_launch,
                          double tol_in, int max_vcycles, const CtlHandles& h, cudaStream_t st);
