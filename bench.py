@@ -60,6 +60,8 @@ def _args():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-mocks", action="store_true",
                     help="skip the brief batched-mocks timing in the headline line")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the brief 256^3 timing in the 512^3 headline line")
     ap.add_argument("--inner-vcycles", type=int, default=None,
                     help="FP32 V-cycles per FP64 defect correction (library default if unset)")
     ap.add_argument("--k-max", type=int, default=None,
@@ -338,6 +340,9 @@ def run_gb300(a):
 
     adj = None if a.no_adjoint else adjoint_timing(a, stream, barrier)
     mocks = None if a.no_mocks else mocks_timing(a, stream, barrier)
+    second = None
+    if a.workload == "lpt512" and not a.no_secondary:
+        second = secondary_timing(a, stream, barrier, mg_kw)
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -365,6 +370,7 @@ def run_gb300(a):
         "e2e": e2e,
         "adjoint": adj,
         "batched_mocks": mocks,
+        "secondary": second,
         "gpu_launches": int(sum(s.launches for s in st_mixed)),
         "clocks": clocks,
     }
@@ -414,6 +420,41 @@ def adjoint_timing(a, stream, barrier, steps=3):
             "forward_ms": fwd, "adjoint_ms": bwd, "adjoint_over_forward": bwd / fwd,
             "adjoint_mcells_s": n ** 3 / (bwd * 1e-3) / 1e6,
             "k_max": K, "checkpoint_bytes": 5 * 8 * n ** 3 * K}
+
+
+def secondary_timing(a, stream, barrier, mg_kw, steps=3):
+    """The 256^3 / 400 Mpc/h 2LPT workload (seed 1001) in brief, beside the
+    512^3 headline: mixed precision (the headline's settings) and FP64, each
+    solved to its own end, one untimed solve then `steps` timed ones (one for
+    FP64)."""
+    import torch
+
+    from paper_1611_09638_gb300 import Recon
+
+    W = _workload("lpt256")
+    n = W.n
+    pos = torch.from_numpy(W.particles()[0]).cuda()
+    out = {"workload": W.name}
+    for prec, k in (("mixed", steps), ("fp64", 1)):
+        kw = mg_kw if prec == "mixed" else {}
+        with Recon((n, n, n), box=W.box, precision=prec, k_max=a.k_max, **kw) as R:
+            R.deposit_particles(pos)
+            R.solve(record=False)
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(k):
+                st = R.solve(record=False)
+            e1.record(stream)
+            barrier()
+            ms = e0.elapsed_time(e1) / k
+        out[prec] = {"value": n ** 3 / (ms * 1e-3) / 1e6, "unit": "Mcells/s", "ms_per_solve": ms,
+                     "timed_solves": k, "steps_per_solve": st.steps, "vcycles_per_solve": st.vcycles,
+                     "status": _status_name(st.status)}
+        if prec == "mixed":
+            out[prec]["inner_vcycles_used"] = st.inner_vcycles
+    out["mixed_over_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
+    return out
 
 
 def mocks_timing(a, stream, barrier, steps=2, k_max=40):
