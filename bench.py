@@ -64,6 +64,8 @@ def _args():
                     help="skip the brief 256^3 timing in the 512^3 headline line")
     ap.add_argument("--inner-vcycles", type=int, default=None,
                     help="FP32 V-cycles per FP64 defect correction (library default if unset)")
+    ap.add_argument("--group-max", type=int, default=None,
+                    help="most FP32 V-cycles per FP64 defect correction under grouped checks")
     ap.add_argument("--k-max", type=int, default=None,
                     help="step cap per solve (default: 200, so that a solve of the 2LPT "
                          "workloads runs to its own end; 40 for the mocks)")
@@ -241,6 +243,8 @@ def run_gb300(a):
         mg_kw["coarse_faces"] = a.coarse_faces
     if a.tune_inner and a.inner_vcycles is None:
         mg_kw["tune_inner"] = 1
+    if a.group_max is not None:
+        mg_kw["group_max"] = a.group_max
 
     def timed(precision, steps, warmup, profile=False, inner=None):
         kw = dict(mg_kw) if precision == "mixed" else {}

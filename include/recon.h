@@ -151,6 +151,15 @@ typedef struct {
                             solution is the same to the stopping residual; the
                             choice follows the timing).  Ignored with profile.
                             0 (default): keep inner_vcycles.                    */
+    int group_max;       /* RECON_MIXED: the most FP32 V-cycles one FP64 defect
+                            correction may run (inner_vcycles .. 64).  Above
+                            inner_vcycles the V-cycles run in blocks of
+                            inner_vcycles, and after each block the device
+                            decides, from the contraction per V-cycle the last
+                            FP64 residual showed, whether to form the next FP64
+                            residual now or to run another block first (fewer
+                            FP64 residuals per step).  -1 (default):
+                            inner_vcycles, one FP64 residual per group.         */
 } recon_params;
 
 /* Per-solve record.  The per-step arrays are optional caller-owned host
@@ -188,7 +197,8 @@ int recon_default_params(recon_params* p, int n0, int n1, int n2);
  * recon_create uses for p->precision and p->n (nu1 = nu2 = 2, max_vcycles =
  * 50 and coarse_faces = 0 in RECON_FP64; in RECON_MIXED nu1 = nu2 = 1,
  * max_vcycles = 100, coarse_faces = 1 on cubic grids of at least 64^3 (else
- * 0), and inner_vcycles = 5 with coarse_faces = 1, else 6).  The paper leaves the cycle shape open; these are the
+ * 0), and inner_vcycles = 5 with coarse_faces = 1, else 6; group_max =
+ * inner_vcycles).  The paper leaves the cycle shape open; these are the
  * settings that reach the stopping residual in the least time on the 256^3
  * workload.  Other fields are not touched or checked.  RECON_E_INVALID for
  * a NULL p. */

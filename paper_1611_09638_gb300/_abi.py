@@ -42,7 +42,7 @@ class recon_params(C.Structure):
         ("lambda_floor", C.c_double), ("replay_alpha", _D), ("profile", C.c_int),
         ("inner_vcycles", C.c_int), ("density_update", C.c_int), ("device_loop", C.c_int),
         ("checkpoint", C.c_int), ("stream_planes", C.c_int), ("restrict_planes", C.c_int),
-        ("coarse_faces", C.c_int), ("tune_inner", C.c_int),
+        ("coarse_faces", C.c_int), ("tune_inner", C.c_int), ("group_max", C.c_int),
     ]
 
 

@@ -22,7 +22,10 @@ __global__ void k_ctl_init(Ctl* c) {
     c->final_deposit = 1;
     c->n_step = c->n_cont = c->n_mg = c->n_adv = c->n_fin = 0;
     c->go_cont = c->go_mg = c->go_adv = c->go_step = 0;
+    c->gcyc = c->gtarget = c->chk = c->n_chk = 0;
+    c->fresh = 1;
     c->R0 = c->R = c->s2 = c->rel = c->alpha = c->last_mass = 0.0;
+    c->rel0 = 1.0;
 }
 
 // Step start: R_k from the sum of s^2; stop when R_k <= tol_out.
@@ -54,6 +57,8 @@ __global__ void k_ctl_mg_begin(Ctl* c, CtlArrays a, int mixed, double tol_in,
     c->ncyc = 0;
     const double rel = 1.0;
     c->rel = rel;
+    c->gcyc = 0, c->fresh = 1, c->rel0 = rel;
+    c->gtarget = 0;  // the first correction forms its residual after one block
     a.ncycles[k] = 0, a.relres[k] = rel;
     const int go = c->s2 > 0.0 && max_vcycles > 0 && !(mixed && rel <= tol_in);
     c->go_mg = go;
@@ -73,6 +78,61 @@ __global__ void k_ctl_mg_check(Ctl* c, const double* scal, CtlArrays a, int per_
     const int go = !(rel <= tol_in) && c->ncyc < max_vcycles;
     c->go_mg = go;
     set_cond(h, h.mg, go);
+}
+
+// After a block of FP32 V-cycles: the correction forms its FP64 residual when
+// it has run the cycles the last check asked for (or the step's cap is near).
+__global__ void k_ctl_block(Ctl* c, CtlArrays a, int block, int max_vcycles, CtlHandles h) {
+    const int k = c->k;
+    c->n_mg += 1;
+    c->gcyc += block;
+    c->ncyc += block;
+    c->vtot += block;
+    a.ncycles[k] = c->ncyc;
+    const int chk = c->gcyc >= c->gtarget || c->ncyc >= max_vcycles;
+    c->chk = chk;
+    c->fresh = 0;
+    set_cond(h, h.chk, chk);
+    if (!chk) {
+        c->go_mg = 1;
+        set_cond(h, h.mg, 1);
+    }
+}
+
+// After the FP64 residual that ends a defect correction: the stopping test,
+// then the length of the next correction, from the contraction per V-cycle
+// this one achieved, rho = (rel / rel0)^(1 / cycles): the cycles that take
+// rel below tol_in, in whole blocks, between one block and group_max.
+__global__ void k_ctl_group_check(Ctl* c, const double* scal, CtlArrays a, int block, int group_max,
+                                  double tol_in, int max_vcycles, CtlHandles h) {
+    const int k = c->k;
+    c->n_chk += 1;
+    const double rel = sqrt(scal[SC_RES2] / c->s2);
+    c->rel = rel;
+    a.relres[k] = rel;
+    const int go = !(rel <= tol_in) && c->ncyc < max_vcycles;
+    int need = block;
+    if (go && c->gcyc > 0 && rel > 0.0 && rel < c->rel0) {
+        const double rho = pow(rel / c->rel0, 1.0 / (double)c->gcyc);
+        if (rho > 0.0 && rho < 1.0) {
+            const double cyc = log(tol_in / rel) / log(rho);
+            need = cyc < (double)group_max ? (int)ceil(cyc) : group_max;
+            need = ((need + block - 1) / block) * block;
+            if (need > group_max) need = (group_max / block) * block;
+            if (need < block) need = block;
+        }
+    }
+    c->gtarget = need;
+    c->gcyc = 0;
+    c->fresh = 1;
+    c->rel0 = rel;
+    c->go_mg = go;
+    set_cond(h, h.mg, go);
+}
+
+__global__ void k_zero_if_fresh(const Ctl* __restrict__ c, float* __restrict__ u, int cells) {
+    if (!c->fresh) return;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < cells; e += gridDim.x * blockDim.x) u[e] = 0.f;
 }
 
 // Step length: the largest 2^-j the limiter certified, halved further while
@@ -147,6 +207,23 @@ void launch_ctl_mg_check(Ctl* c, const double* scal, const CtlArrays& a, int per
     launch_counter()++;
     k_ctl_mg_check<<<1, 1, 0, st>>>(c, scal, a, per_launch, tol_in, max_vcycles, h);
 }
+void launch_ctl_block(Ctl* c, const CtlArrays& a, int block, int max_vcycles, const CtlHandles& h,
+                      cudaStream_t st) {
+    launch_counter()++;
+    k_ctl_block<<<1, 1, 0, st>>>(c, a, block, max_vcycles, h);
+}
+
+void launch_ctl_group_check(Ctl* c, const double* scal, const CtlArrays& a, int block, int group_max,
+                            double tol_in, int max_vcycles, const CtlHandles& h, cudaStream_t st) {
+    launch_counter()++;
+    k_ctl_group_check<<<1, 1, 0, st>>>(c, scal, a, block, group_max, tol_in, max_vcycles, h);
+}
+
+void launch_zero_if_fresh(const Ctl* c, float* u, int cells, cudaStream_t st) {
+    launch_counter()++;
+    k_zero_if_fresh<<<kRedBlocks, kRedThreads, 0, st>>>(c, u, cells);
+}
+
 void launch_ctl_select_alpha(Ctl* c, double* scal, const CtlArrays& a, const double* replay,
                              int kmax_exp, double d_max, double alpha_min, const CtlHandles& h,
                              cudaStream_t st) {

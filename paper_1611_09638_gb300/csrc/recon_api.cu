@@ -48,7 +48,7 @@ struct Range {
 };
 
 struct GraphCounts {
-    long long init = 0, step = 0, cont = 0, mg = 0, adv = 0, fin = 0;
+    long long init = 0, step = 0, cont = 0, mg = 0, adv = 0, fin = 0, chk = 0;
 };
 
 struct Handle {
@@ -97,6 +97,9 @@ struct Handle {
     cudaStream_t cap = nullptr;
     bool capturing = false;
     cudaGraphExec_t cyc_exec = nullptr;
+    cudaGraphExec_t chk_exec = nullptr;  // grouped checks: the check body, host-driven loop
+    long long chk_kernels = 0;
+    bool adaptive = false;     // mixed precision with group_max > inner_vcycles
     bool inner_tuned = false;  // params.tune_inner: the first solve has chosen inner_vcycles
     long long cyc_kernels = 0;
     int cyc_sweeps = 0;
@@ -123,7 +126,7 @@ struct Handle {
     CtlArrays aarr{};
 
     // params.device_loop: the whole solve as one graph with conditional nodes
-    cudaStream_t gst[4] = {nullptr, nullptr, nullptr, nullptr};  // capture streams
+    cudaStream_t gst[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // capture streams
     cudaGraphExec_t solve_exec = nullptr;
     GraphCounts gn{};
 
@@ -156,13 +159,15 @@ void free_all(Handle* H) {
     H->prof_ev.clear();
     if (H->cyc_exec) cudaGraphExecDestroy(H->cyc_exec);
     H->cyc_exec = nullptr;
+    if (H->chk_exec) cudaGraphExecDestroy(H->chk_exec);
+    H->chk_exec = nullptr;
     for (cudaEvent_t e : H->cyc_ev) cudaEventDestroy(e);
     H->cyc_ev.clear();
     if (H->cap) cudaStreamDestroy(H->cap);
     H->cap = nullptr;
     if (H->solve_exec) cudaGraphExecDestroy(H->solve_exec);
     H->solve_exec = nullptr;
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < 5; ++q) {
         if (H->gst[q]) cudaStreamDestroy(H->gst[q]);
         H->gst[q] = nullptr;
     }
@@ -264,6 +269,7 @@ void resolve_params(recon_params* p) {
     // residual is worth forming after fewer of them
     if (p->inner_vcycles == -1) p->inner_vcycles = p->coarse_faces == 1 ? 5 : 6;
     if (p->max_vcycles == -1) p->max_vcycles = mixed ? 100 : 50;
+    if (p->group_max == -1) p->group_max = p->inner_vcycles;
 }
 
 int check_params(const recon_params* p) {
@@ -311,6 +317,8 @@ int check_params(const recon_params* p) {
     if (p->coarse_faces == 1 && (p->precision != RECON_MIXED || !faces_apply(p)))
         return fail(RECON_E_INVALID, "coarse_faces = 1 needs RECON_MIXED on a cubic grid of at least 64^3");
     if (p->tune_inner != 0 && p->tune_inner != 1) return fail(RECON_E_INVALID, "tune_inner must be 0 or 1");
+    if (p->group_max < p->inner_vcycles || p->group_max > 64)
+        return fail(RECON_E_INVALID, "need inner_vcycles <= group_max <= 64");
     return RECON_OK;
 }
 
@@ -473,12 +481,40 @@ void mg_head(Handle* H, const CtlHandles& h) {
                         h, H->st);
 }
 
+// Grouped FP64 checks (params.group_max > inner_vcycles): one block of
+// inner_vcycles FP32 V-cycles on the correction e (zeroed where a new defect
+// correction starts), then the control's decision whether the correction
+// ends after this block.
+void mg_block(Handle* H, const CtlHandles& h) {
+    MG<float> g{H->u32, H->f32, H->c32, H->r32};
+    launch_zero_if_fresh(H->ctl, H->u32[0], H->cells, H->st);
+    for (int v = 0; v < H->p.inner_vcycles; ++v)
+        vcycle<float>(H, g, 0, H->u32[0], H->f32[0], false, nullptr);
+    launch_ctl_block(H->ctl, H->arr, H->p.inner_vcycles, H->p.max_vcycles, h, H->st);
+}
+
+// The end of a defect correction under grouped checks: phidot += e, the FP64
+// residual (and its FP32 copy, the next right-hand side), the stopping test
+// and the length of the next correction.
+void mg_check_body(Handle* H, const CtlHandles& h) {
+    launch_correct(H->cells, H->phidot, H->u32[0], H->st);
+    launch_residual64_to32(H->lv[0], H->phidot, H->s, H->F64, H->D64, H->f32[0], H->part[0], H->st);
+    finish_reduce(H->part[0], 0, H->scal, SC_RES2, H->st);
+    launch_ctl_group_check(H->ctl, H->scal, H->arr, H->p.inner_vcycles, H->p.group_max, H->p.tol_in,
+                           H->p.max_vcycles, h, H->st);
+}
+
 // One multigrid iteration: the V-cycle (FP64 on phidot, or inner_vcycles FP32
 // V-cycles on the correction e followed by phidot += e), then the FP64
 // residual of L phidot = s (in mixed mode also the next FP32 right-hand side)
-// and its squared norm, and the stopping test.
+// and its squared norm, and the stopping test.  Under grouped checks only the
+// block (mg_block): the caller runs mg_check_body where the control asks.
 void mg_iter(Handle* H, const CtlHandles& h) {
     const Level& L0 = H->lv[0];
+    if (H->adaptive) {
+        mg_block(H, h);
+        return;
+    }
     if (!H->mixed) {
         MG<double> g{H->u64, H->f64, H->c64, H->r64};
         vcycle<double>(H, g, 0, H->phidot, H->s, false);
@@ -553,9 +589,11 @@ int read_ctl(Handle* H) {
     return RECON_OK;
 }
 
-// The multigrid iteration with the control block's readback, recorded once as
-// a CUDA graph on a private stream and replayed on the handle's stream.
-int record_cycle_graph(Handle* H) {
+// The multigrid iteration (or, under grouped checks, the check body) with the
+// control block's readback, recorded once as a CUDA graph on a private stream
+// and replayed on the handle's stream.
+template <typename F>
+int record_cycle_graph(Handle* H, cudaGraphExec_t* exec, long long* kernels, int* sweeps, F&& segment) {
     if (!H->cap) CK(cudaStreamCreateWithFlags(&H->cap, cudaStreamNonBlocking));
     cudaStream_t user = H->st;
     const long long c0 = launch_counter().load();
@@ -563,29 +601,44 @@ int record_cycle_graph(Handle* H) {
     CK(cudaStreamBeginCapture(H->cap, cudaStreamCaptureModeRelaxed));
     H->st = H->cap;
     H->capturing = true;
-    mg_iter(H, CtlHandles{});
+    segment();
     cudaMemcpyAsync(H->hctl, H->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, H->st);
     H->capturing = false;
     H->st = user;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(H->cap, &g);
-    H->cyc_kernels = launch_counter().load() - c0;
-    launch_counter() -= H->cyc_kernels;
-    H->cyc_sweeps = H->prof_sweeps - s0;
+    *kernels = launch_counter().load() - c0;
+    launch_counter() -= *kernels;
+    *sweeps = H->prof_sweeps - s0;
     H->prof_sweeps = s0;
     if (e != cudaSuccess) return fail(RECON_E_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&H->cyc_exec, g, 0);
+    e = cudaGraphInstantiate(exec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
-        H->cyc_exec = nullptr;
+        *exec = nullptr;
         return fail(RECON_E_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
     }
     return RECON_OK;
 }
 
+// The check body of grouped checks, when the block just run asked for it.
+int run_check(Handle* H) {
+    if (!H->chk_exec) {
+        int no_sweeps = 0;
+        int rc = record_cycle_graph(H, &H->chk_exec, &H->chk_kernels, &no_sweeps,
+                                    [&] { mg_check_body(H, CtlHandles{}); });
+        if (rc) return rc;
+    }
+    CK(cudaGraphLaunch(H->chk_exec, H->st));
+    CK(cudaStreamSynchronize(H->st));
+    launch_counter() += H->chk_kernels;
+    return RECON_OK;
+}
+
 int run_cycle(Handle* H) {
     if (!H->cyc_exec) {
-        int rc = record_cycle_graph(H);
+        int rc = record_cycle_graph(H, &H->cyc_exec, &H->cyc_kernels, &H->cyc_sweeps,
+                                    [&] { mg_iter(H, CtlHandles{}); });
         if (rc) return rc;
     }
     CK(cudaGraphLaunch(H->cyc_exec, H->st));
@@ -599,6 +652,7 @@ int run_cycle(Handle* H) {
         cudaGetLastError();
         H->prof_sweeps += H->cyc_sweeps;
     }
+    if (H->adaptive && H->hctl->chk) return run_check(H);
     return RECON_OK;
 }
 
@@ -624,9 +678,12 @@ int tune_inner_vcycles(Handle* H) {
     float best_ms = 0.f;
     for (int round = 0; round < 2; ++round)
         for (int n : cand) {
+            if (H->adaptive && n > H->p.group_max) continue;
             H->p.inner_vcycles = n;
             if (H->cyc_exec) cudaGraphExecDestroy(H->cyc_exec);
             H->cyc_exec = nullptr;
+            if (H->chk_exec) cudaGraphExecDestroy(H->chk_exec);
+            H->chk_exec = nullptr;
             CK(cudaEventRecord(H->ev0, H->st));
             mg_head(H, none);
             if ((rc = read_ctl(H))) return rc;
@@ -641,6 +698,9 @@ int tune_inner_vcycles(Handle* H) {
     H->p.inner_vcycles = best;
     if (H->cyc_exec) cudaGraphExecDestroy(H->cyc_exec);
     H->cyc_exec = nullptr;
+    if (H->chk_exec) cudaGraphExecDestroy(H->chk_exec);
+    H->chk_exec = nullptr;
+    H->adaptive = H->p.group_max > H->p.inner_vcycles;
     return RECON_OK;
 }
 
@@ -731,7 +791,7 @@ int capture_into(Handle* H, cudaStream_t s, cudaGraph_t g, long long* kernels, F
 }
 
 int build_solve_graph(Handle* H) {
-    for (int q = 0; q < 4; ++q)
+    for (int q = 0; q < 5; ++q)
         if (!H->gst[q]) CK(cudaStreamCreateWithFlags(&H->gst[q], cudaStreamNonBlocking));
     cudaGraph_t top = nullptr;
     CK(cudaGraphCreate(&top, 0));
@@ -761,8 +821,21 @@ int build_solve_graph(Handle* H) {
                     cudaGraph_t b_mg = nullptr, b_adv = nullptr;
                     if ((r2 = add_conditional(H->gst[2], h.mg, cudaGraphCondTypeWhile, &b_mg))) return r2;
                     r2 = capture_into(H, H->gst[3], b_mg, &n.mg, [&]() -> int {
-                        mg_iter(H, h);
-                        return RECON_OK;
+                        if (!H->adaptive) {
+                            mg_iter(H, h);
+                            return RECON_OK;
+                        }
+                        // grouped checks: the block, then the check body where
+                        // the block's control kernel asks for it
+                        int r3 = new_handle(H->gst[3], 0, &h.chk);
+                        if (r3) return r3;
+                        mg_block(H, h);
+                        cudaGraph_t b_chk = nullptr;
+                        if ((r3 = add_conditional(H->gst[3], h.chk, cudaGraphCondTypeIf, &b_chk))) return r3;
+                        return capture_into(H, H->gst[4], b_chk, &n.chk, [&]() -> int {
+                            mg_check_body(H, h);
+                            return RECON_OK;
+                        });
                     });
                     if (r2) return r2;
                     step_tail(H, h);
@@ -869,7 +942,7 @@ long long graph_launches(const Handle* H) {
     const Ctl& c = *H->hctl;
     const GraphCounts& n = H->gn;
     return n.init + c.n_step * n.step + c.n_cont * n.cont + (long long)c.n_mg * n.mg +
-           c.n_adv * n.adv + c.n_fin * n.fin;
+           c.n_adv * n.adv + c.n_fin * n.fin + (long long)c.n_chk * n.chk;
 }
 
 int solve_finish(Handle* H, recon_stats* stats) {
@@ -950,6 +1023,10 @@ int adjoint_mg(Handle* H) {
     while (!rc && H->hctl->go_mg) {
         mg_iter(H, none);
         rc = read_ctl(H);
+        if (!rc && H->adaptive && H->hctl->chk) {
+            mg_check_body(H, none);
+            rc = read_ctl(H);
+        }
     }
     return rc;
 }
@@ -1077,6 +1154,7 @@ int recon_default_params(recon_params* p, int n0, int n1, int n2) {
     p->restrict_planes = 0;
     p->coarse_faces = -1;
     p->tune_inner = 0;
+    p->group_max = -1;
     return RECON_OK;
 }
 
@@ -1103,6 +1181,7 @@ int recon_create(void** out, const recon_params* p_in, void* cuda_stream) {
     H->p.replay_alpha = nullptr;
     H->st = (cudaStream_t)cuda_stream;
     H->mixed = p->precision == RECON_MIXED;
+    H->adaptive = H->mixed && p->group_max > p->inner_vcycles;
     cudaGetDevice(&H->device);
     H->d = make_dims(p->n[0], p->n[1], p->n[2]);
     H->cells = H->d.cells;

@@ -312,8 +312,14 @@ struct Ctl {
     int final_deposit;  // the last map still needs its deposit
     int n_step, n_cont, n_mg, n_adv, n_fin;  // executions of each graph body
     int go_cont, go_mg, go_adv, go_step, go_fin;
+    // grouped FP64 checks (params.group_max): V-cycles in the current defect
+    // correction, the count at which it forms its FP64 residual, whether the
+    // next block starts a new correction, whether this block ends one, and
+    // executions of the check body
+    int gcyc, gtarget, fresh, chk, n_chk;
     int pad;
     double R0, R, s2, rel, alpha, last_mass;
+    double rel0;        // relative residual when the current correction began
 };
 
 // Per-step records on the device (k_max entries each).
@@ -327,7 +333,7 @@ struct CtlArrays {
 // Conditional nodes of the solve graph; active = 0 outside a graph.
 struct CtlHandles {
     int active;
-    cudaGraphConditionalHandle step, cont, mg, adv, fin;
+    cudaGraphConditionalHandle step, cont, mg, adv, fin, chk;
 };
 
 void launch_ctl_init(Ctl* c, cudaStream_t st);
@@ -335,6 +341,15 @@ void launch_ctl_step_begin(Ctl* c, const double* scal, const CtlArrays& a, doubl
                            double tol_out, const CtlHandles& h, cudaStream_t st);
 void launch_ctl_mg_begin(Ctl* c, const CtlArrays& a, int mixed, double tol_in,
                          int max_vcycles, const CtlHandles& h, cudaStream_t st);
+// Grouped FP64 checks: after a block of `block` FP32 V-cycles, whether the
+// defect correction ends here (its FP64 residual is formed next); and after
+// that residual, the stopping test and the length of the next correction.
+void launch_ctl_block(Ctl* c, const CtlArrays& a, int block, int max_vcycles, const CtlHandles& h,
+                      cudaStream_t st);
+void launch_ctl_group_check(Ctl* c, const double* scal, const CtlArrays& a, int block, int group_max,
+                            double tol_in, int max_vcycles, const CtlHandles& h, cudaStream_t st);
+// u = 0 where the control block says a new defect correction starts
+void launch_zero_if_fresh(const Ctl* c, float* u, int cells, cudaStream_t st);
 void launch_ctl_mg_check(Ctl* c, const double* scal, const CtlArrays& a, int per_launch,
                          double tol_in, int max_vcycles, const CtlHandles& h, cudaStream_t st);
 void launch_ctl_select_alpha(Ctl* c, double* scal, const CtlArrays& a, const double* replay,

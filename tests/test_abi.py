@@ -154,7 +154,8 @@ def test_resolve_params_touches_only_the_multigrid_settings():
 
     lib = _abi.load()
     p = default_params((16, 32, 64), box=(1.0, 2.0, 4.0), precision="mixed", k_max=7, tol_in=1e-6)
-    skip = ("nu1", "nu2", "inner_vcycles", "max_vcycles", "coarse_faces", "n", "box", "replay_alpha")
+    skip = ("nu1", "nu2", "inner_vcycles", "max_vcycles", "coarse_faces", "group_max", "n", "box",
+            "replay_alpha")
     before = {f: getattr(p, f) for f, _ in _abi.recon_params._fields_ if f not in skip}
     assert lib.recon_resolve_params(C.byref(p)) == _abi.RECON_OK
     after = {f: getattr(p, f) for f in before}

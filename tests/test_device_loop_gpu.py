@@ -44,11 +44,14 @@ def _same(a, b, pa, pb):
     assert np.array_equal(pa, pb)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_device_loop_equals_host_loop(precision):
+@pytest.mark.parametrize("precision,kw", [("fp64", {}), ("mixed", {}),
+                                          ("mixed", {"inner_vcycles": 3, "group_max": 12})])
+def test_device_loop_equals_host_loop(precision, kw):
+    """Both loops, also with grouped FP64 checks (the device decides after
+    each block of V-cycles whether to form the FP64 residual)."""
     rho = _density(32, 100.0, 1000)
-    Ra, a, pa = _run(rho, precision, 0)
-    Rb, b, pb = _run(rho, precision, 1)
+    Ra, a, pa = _run(rho, precision, 0, **kw)
+    Rb, b, pb = _run(rho, precision, 1, **kw)
     assert a.steps > 10
     _same(a, b, pa, pb)
     # a second solve on the same handle replays the recorded graph
