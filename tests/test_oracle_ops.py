@@ -320,6 +320,31 @@ def test_advance_closed_form():
         assert xi2[t, 1] == xi[t, 1] and xi2[t, 2] == xi[t, 2]
 
 
+def test_advance_off_node_closed_form():
+    """Tracers at fractional offsets on all three axes of an anisotropic grid.
+    With phi = x'Px/2 and dphi = x'Qx/2 + b'x (x = node - c) the central
+    differences are exact, so every node has e = I + P and G = Qx + b, the
+    node velocity e^-1 G is affine in position, CIC interpolation of it is
+    exact, and each tracer moves to xi - alpha (I + P)^-1 (Q (xi - c) + b).
+    A weight taken from the wrong axis, a swapped corner or a wrong column in
+    the solve for e^-1 G each move the result by far more than the tolerance."""
+    n = (16, 8, 32)
+    c = np.array([8.0, 4.0, 16.0])
+    P = np.array([[0.30, 0.05, -0.07], [0.05, -0.20, 0.11], [-0.07, 0.11, 0.15]])
+    Q = np.array([[0.40, -0.13, 0.09], [-0.13, 0.25, 0.06], [0.09, 0.06, -0.30]])
+    b = np.array([0.20, -0.35, 0.50])
+    alpha = 0.375
+    g = np.stack(np.meshgrid(*[np.arange(m, dtype=float) for m in n], indexing="ij"), axis=-1) - c
+    phi = 0.5 * np.einsum("...a,ab,...b->...", g, P, g)
+    dphi = 0.5 * np.einsum("...a,ab,...b->...", g, Q, g) + g @ b
+    # every stencil around these tracers stays clear of the periodic seam
+    xi = np.array([[7.25, 3.625, 15.875], [4.5, 2.125, 22.375], [10.875, 4.25, 9.0625]])
+    phi2, xi2 = O.advance(alpha, dphi, phi, xi)
+    assert np.max(np.abs(phi2 - (phi + alpha * dphi))) < 1e-13
+    want = xi - alpha * np.linalg.solve(np.eye(3) + P, (Q @ (xi - c).T + b[:, None])).T
+    assert np.max(np.abs(xi2 - want)) < 1e-12, (xi2, want)
+
+
 def test_paper_constants_are_the_defaults():
     with open(os.path.join(GOLDEN, "paper_constants.json")) as fh:
         g = json.load(fh)
