@@ -50,8 +50,9 @@ extern "C" {
 #define RECON_E_CUDA (-3)     /* a CUDA runtime call failed               */
 #define RECON_E_NONFINITE (-4) /* NaN/Inf or negative input               */
 #define RECON_E_LIMITER (-5)  /* reserved (a limiter stall is RECON_STALLED) */
-#define RECON_E_TIMEOUT (-6)  /* reserved: no call waits on the device without
-                                 a bound (the solve's loops are graph nodes) */
+#define RECON_E_TIMEOUT (-6)  /* a bounded wait on the device ran out (the
+                                 bulk-copy waits of the streaming sweep); no
+                                 call waits on the device without a bound  */
 #define RECON_E_STATE (-7)    /* call out of order (e.g. solve before deposit) */
 #define RECON_E_UNSUPPORTED (-8) /* reserved: every declared call is built  */
 
@@ -160,6 +161,13 @@ typedef struct {
                             residual now or to run another block first (fewer
                             FP64 residuals per step).  -1 (default):
                             inner_vcycles, one FP64 residual per group.         */
+    int tma;             /* RECON_MIXED: 1 (default): the streaming FP32 sweep
+                            stages the u, a and f planes of tiles clear of the
+                            periodic seams with bulk tensor copies (TMA) into
+                            shared memory; 0: every tile uses per-thread 16-byte
+                            copies.  Both compute the same bits.  A sweep whose
+                            wait for a copy runs out (~1 s) makes recon_solve
+                            return RECON_E_TIMEOUT.                            */
 } recon_params;
 
 /* Per-solve record.  The per-step arrays are optional caller-owned host

@@ -317,6 +317,7 @@ int check_params(const recon_params* p) {
     if (p->coarse_faces == 1 && (p->precision != RECON_MIXED || !faces_apply(p)))
         return fail(RECON_E_INVALID, "coarse_faces = 1 needs RECON_MIXED on a cubic grid of at least 64^3");
     if (p->tune_inner != 0 && p->tune_inner != 1) return fail(RECON_E_INVALID, "tune_inner must be 0 or 1");
+    if (p->tma != 0 && p->tma != 1) return fail(RECON_E_INVALID, "tma must be 0 or 1");
     if (p->group_max < p->inner_vcycles || p->group_max > 64)
         return fail(RECON_E_INVALID, "need inner_vcycles <= group_max <= 64");
     return RECON_OK;
@@ -1155,6 +1156,7 @@ int recon_default_params(recon_params* p, int n0, int n1, int n2) {
     p->coarse_faces = -1;
     p->tune_inner = 0;
     p->group_max = -1;
+    p->tma = 1;
     return RECON_OK;
 }
 
@@ -1254,6 +1256,7 @@ int recon_create(void** out, const recon_params* p_in, void* cuda_stream) {
         // per-face coefficients on the coarse levels of a cubic grid
         const bool faces = p->coarse_faces == 1;
         for (int l = 1; l < nl; ++l) H->lv[l].face = faces ? 1 : 0;
+        for (int l = 0; l < nl; ++l) H->lv[l].tma = p->tma;
         for (int l = 0; l < nl; ++l) {
             size_t cl = H->lv[l].d.cells;
             AL(H->u32[l], cl); AL(H->f32[l], cl); AL(H->c32[l], H->lv[l].face ? 3 * cl : cl);
@@ -1418,6 +1421,8 @@ int recon_solve(void* hp, recon_stats* stats) {
     if (!H->have_density) return fail(RECON_E_STATE, "recon_deposit must succeed before recon_solve");
     int rc = H->inner_tuned ? RECON_OK : tune_inner_vcycles(H);
     if (rc == RECON_OK) rc = solve(H, stats);
+    if (rc >= 0 && H->mixed && sweep_wait_failed())
+        rc = fail(RECON_E_TIMEOUT, "a streaming sweep gave up waiting for a bulk copy");
     if (rc < 0) {
         cudaStreamSynchronize(H->st);
         H->solved = false;
@@ -1463,6 +1468,8 @@ int recon_solve_batch(void* const* handles, int count, recon_stats* stats) {
             if (worst >= 0) worst = r;
         }
     }
+    if (worst >= 0 && sweep_wait_failed())
+        worst = fail(RECON_E_TIMEOUT, "a streaming sweep gave up waiting for a bulk copy");
     return worst;
 }
 

@@ -100,6 +100,9 @@ struct Level {
     // face between node c and its +1 neighbour), built from the level above
     // by launch_faces_line
     int face;
+    // 1: the streaming sweep stages the planes of tiles clear of the periodic
+    // seams with bulk tensor copies (same values as the per-thread copies)
+    int tma;
 };
 
 // Mean device time (ms) of `reps` launches issued by launch() on st, after
@@ -182,6 +185,9 @@ int launch_resid_restrict_stream(const Level& fine, const Level& coarse, const f
 // post-smoothing sweep).  Returns 1, or 0 with nothing launched (then
 // prolongate and sweep separately).
 bool rbgs_prolong_fits(const Level& fine);
+// Whether a streaming sweep gave up waiting for a bulk copy since the last
+// call (on the current device); clears the record.
+bool sweep_wait_failed();
 int launch_rbgs_prolong(const Level& fine, const Level& coarse, const float* uc, const float* u_old,
                         float* u_new, const float* f, const float* a, cudaStream_t st,
                         double* u64 = nullptr);

@@ -33,15 +33,30 @@
 // and one write of u.  With u_old == nullptr the sweep starts from u = 0 and
 // u is not read.
 //
+// Tiles clear of the periodic seams (the 12 x 72 window of a plane lies
+// inside the grid) stage their planes with the Tensor Memory Accelerator
+// instead: one thread copies each field's whole window of a plane (a 72 x 12
+// box of a rank-3 tensor map, which lands in exactly the ring slot's layout)
+// and the block waits on that slot's mbarrier; tiles on a seam keep the
+// per-thread 16-byte copies.  Both fill the slots with the same values.
+//
 // Every shared-memory and global offset a thread uses is computed once per
 // block, and the plane loop is unrolled so that ring slots and register
 // indices are compile-time constants.
+#include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 
 #include "async_copy.cuh"
 #include "recon_internal.cuh"
+#include "tma.cuh"
 
 namespace recon {
+
+// Set by a sweep whose wait for a bulk copy gave up (read and cleared by
+// sweep_wait_failed after a solve).
+__device__ int g_sweep_wait_fail;
 
 namespace {
 
@@ -55,9 +70,18 @@ constexpr int CH = RK / 4;             // 16-byte chunks per row
 constexpr int PD = 2;                  // planes of copies in flight ahead of the one waited for
 static_assert(PD >= 2, "the prolongation is applied one iteration before a plane is read");
 constexpr int SU = 3 + PD;             // ring slots of u, a and f
-constexpr int SMEM = (int)sizeof(float) * PL * 3 * SU;
+constexpr int MBAR = 8 * SU;           // one mbarrier per ring slot (bulk copies)
+constexpr int SMEM = (int)sizeof(float) * PL * 3 * SU + MBAR;
 // FACE: u, the three face-sum planes and f
-constexpr int SMEM_FACE = (int)sizeof(float) * PL * 5 * SU;
+constexpr int SMEM_FACE = (int)sizeof(float) * PL * 5 * SU + MBAR;
+static_assert((sizeof(float) * PL) % 128 == 0, "every ring slot starts on a 128-byte boundary");
+
+// Tensor maps of one sweep's inputs: u_old, a (or the x face sums), f, and
+// the y and z face sums of a FACE level; on = 0 where none apply.
+struct SweepMaps {
+    CUtensorMap m[5];
+    int on;
+};
 constexpr int NUA = RJ * CH;           // chunks of one u (or a) plane: 216
 constexpr int NF = (TJ + 2) * CH;      // chunks of one f plane (rows of the red ring): 180
 constexpr int NRING = 2 * (TK / 2 + 1) + TJ;  // red ring nodes per plane: 74
@@ -119,6 +143,8 @@ __device__ __forceinline__ float other(float2 v, int z) { return z ? v.x : v.y; 
 // z face-sum arrays, one after another): the x sums of the thread's columns
 // are carried in registers like a, the y and z sums of the plane come from
 // shared memory (isotropic levels only; two blocks per SM).
+// tm: tensor maps of u_old, a (or the x face sums), f and the y and z face
+// sums, each with a 72 x 12 x 1 box; tm.on = 0: every tile uses cp.async.
 // Registers are capped so that 4 blocks (3 with PRO) stay resident per SM.
 template <bool ISO, int CI, bool PRO, bool COR, bool FACE>
 __global__ void __launch_bounds__(NT, FACE ? 2 : (PRO ? 3 : 4)) k_rbgs_stream(Dims d, float hx, float hy, float hz,
@@ -127,8 +153,9 @@ __global__ void __launch_bounds__(NT, FACE ? 2 : (PRO ? 3 : 4)) k_rbgs_stream(Di
                                                     const float* __restrict__ f,
                                                     const float* __restrict__ a,
                                                     const float* __restrict__ uc, Dims dc,
-                                                    double* __restrict__ u64) {
-    extern __shared__ float4 smem_f4[];
+                                                    double* __restrict__ u64,
+                                                    const __grid_constant__ SweepMaps tm) {
+    extern __shared__ __align__(128) float4 smem_f4[];
     float* su = reinterpret_cast<float*>(smem_f4);
     float* sa = su + SU * PL;  // a, or (FACE) the x face sums
     float* sy = sa + SU * PL;  // FACE: y and z face sums
@@ -205,6 +232,34 @@ __global__ void __launch_bounds__(NT, FACE ? 2 : (PRO ? 3 : 4)) k_rbgs_stream(Di
     // q + 1 + PD and, before its barrier, waits for those the next iteration
     // reads.
     auto pbase = [&](int q) { return (q & (d.n0 - 1)) * plane; };
+    // Bulk copies: plane x sits in ring slot r % SU, r = x - (i0 - 2), and is
+    // that slot's (r / SU)-th fill, so it completes the phase of parity
+    // (r / SU) & 1 of the slot's mbarrier.  f is read on rows 1 .. TJ only;
+    // its box brings the same 12 rows as u's.
+    unsigned long long* mbar = reinterpret_cast<unsigned long long*>(sf + SU * PL);
+    const bool tma = tm.on && j0 >= H && j0 + TJ + H <= d.n1 && k0 >= KO && k0 + TK + KO <= d.n2;
+    auto tma_issue = [&](int x, bool with_f) {
+        const int r = x - (i0 - 2), slot = (r % SU) * PL;
+        unsigned long long* bar = mbar + r % SU;
+        const int kx = k0 - KO, jy = j0 - H, iz = x & (d.n0 - 1);
+        const unsigned nfield = (u_old ? 1u : 0u) + (FACE ? 3u : 1u) + (with_f ? 1u : 0u);
+        mbar_arrive_expect(bar, nfield * (unsigned)(sizeof(float) * PL));
+        if (u_old) tma_load_3d(su + slot, &tm.m[0], kx, jy, iz, bar);
+        tma_load_3d(sa + slot, &tm.m[1], kx, jy, iz, bar);
+        if (FACE) {
+            tma_load_3d(sy + slot, &tm.m[3], kx, jy, iz, bar);
+            tma_load_3d(sz + slot, &tm.m[4], kx, jy, iz, bar);
+        }
+        if (with_f) tma_load_3d(sf + slot, &tm.m[2], kx, jy, iz, bar);
+    };
+    auto tma_wait = [&](int x) {
+        const int r = x - (i0 - 2);
+        mbar_wait(mbar + r % SU, (unsigned)((r / SU) & 1), &g_sweep_wait_fail);
+    };
+    // the sweep from u = 0: this thread's chunk of a u slot (both paths)
+    auto zero_u = [&](int slot) {
+        if (ua_s >= 0) *reinterpret_cast<float4*>(su + slot + ua_s) = make_float4(0.f, 0.f, 0.f, 0.f);
+    };
     auto fetch_ua = [&](int q, int slot) {
         if (ua_s >= 0) {
             const int so = slot + ua_s, g = pbase(q) + ua_g;
@@ -292,25 +347,49 @@ __global__ void __launch_bounds__(NT, FACE ? 2 : (PRO ? 3 : 4)) k_rbgs_stream(Di
 
     // prologue: u, a of planes i0-2 .. i0 (waited for); with PD = 2 also
     // plane i0+1 (left in flight)
-    fetch_ua(i0 - 2, 0 * PL);
-    fetch_ua(i0 - 1, 1 * PL);
-    fetch_ua(i0, 2 * PL);
-    fetch_f(i0 - 1, 1 * PL);
-    fetch_f(i0, 2 * PL);
-    cp_commit();
+    if (tma) {
+        if (t == 0) {
+            for (int r = 0; r < SU; ++r) mbar_init(mbar + r, 1);
+            mbar_init_fence();
+        }
+        __syncthreads();
+        if (t == 0) {
+            tma_issue(i0 - 2, false);
+            tma_issue(i0 - 1, true);
+            tma_issue(i0, true);
+        }
+        if (!u_old) zero_u(0 * PL), zero_u(1 * PL), zero_u(2 * PL);
+    } else {
+        fetch_ua(i0 - 2, 0 * PL);
+        fetch_ua(i0 - 1, 1 * PL);
+        fetch_ua(i0, 2 * PL);
+        fetch_f(i0 - 1, 1 * PL);
+        fetch_f(i0, 2 * PL);
+        cp_commit();
+    }
+    auto wait_prologue = [&] {
+        if (tma) tma_wait(i0 - 2), tma_wait(i0 - 1), tma_wait(i0);
+        else cp_wait_all();
+    };
     if (PRO) {  // the three planes read first: their coarse values, then u + P(uc)
         const ProRaw r0 = pro_load(i0 - 2), r1 = pro_load(i0 - 1), r2 = pro_load(i0);
-        cp_wait_all();
+        wait_prologue();
         pro_apply(0 * PL, r0);
         pro_apply(1 * PL, r1);
         pro_apply(2 * PL, r2);
+    } else {
+        wait_prologue();
     }
-    cp_wait_all();
     __syncthreads();
     if (PD == 2) {
-        fetch_ua(i0 + 1, 3 * PL);
-        fetch_f(i0 + 1, 3 * PL);
-        cp_commit();
+        if (tma) {
+            if (t == 0) tma_issue(i0 + 1, true);
+            if (!u_old) zero_u(3 * PL);
+        } else {
+            fetch_ua(i0 + 1, 3 * PL);
+            fetch_f(i0 + 1, 3 * PL);
+            cp_commit();
+        }
     }
     U[0] = own(su, 0 * PL), U[1] = own(su, 1 * PL);
     A[0] = own(sa, 0 * PL), A[1] = own(sa, 1 * PL);
@@ -329,8 +408,18 @@ __global__ void __launch_bounds__(NT, FACE ? 2 : (PRO ? 3 : 4)) k_rbgs_stream(Di
         ProRaw pend;
         if (prolong) pend = pro_load(q + PD);
         if (fetch) {
-            fetch_ua(q + 1 + PD, ((it + 2 + PD) % SU) * PL);
-            if (it + PD <= CI) fetch_f(q + 1 + PD, ((it + 2 + PD) % SU) * PL);
+            if (tma) {
+                // the slot last held plane q - 4, read for the last time
+                // before the previous iteration's barrier
+                if (t == 0) {
+                    fence_async_smem();
+                    tma_issue(q + 1 + PD, it + PD <= CI);
+                }
+                if (!u_old) zero_u(((it + 2 + PD) % SU) * PL);
+            } else {
+                fetch_ua(q + 1 + PD, ((it + 2 + PD) % SU) * PL);
+                if (it + PD <= CI) fetch_f(q + 1 + PD, ((it + 2 + PD) % SU) * PL);
+            }
         }
         cp_commit();
         const double2 cor_now = cor;
@@ -402,10 +491,15 @@ __global__ void __launch_bounds__(NT, FACE ? 2 : (PRO ? 3 : 4)) k_rbgs_stream(Di
                 *reinterpret_cast<double2*>(u64 + g) =
                     make_double2(cor_now.x + (double)v.x, cor_now.y + (double)v.y);
         }
-        if (PD == 1) cp_wait_all();
-        else cp_wait_prior();
-        // this thread's copies of plane q + PD are complete; no one reads that
-        // slot before the barrier
+        if (tma) {
+            if (it <= CI + 2 - PD) tma_wait(q + PD);  // planes up to i0 + CI + 1 were fetched
+        } else if (PD == 1) {
+            cp_wait_all();
+        } else {
+            cp_wait_prior();
+        }
+        // this thread's copies of plane q + PD are complete (bulk copies: the
+        // whole plane); no one reads that slot before the barrier
         if (prolong) pro_apply(((it + 1 + PD) % SU) * PL, pend);
         __syncthreads();
     }
@@ -418,13 +512,47 @@ __global__ void __launch_bounds__(NT, FACE ? 2 : (PRO ? 3 : 4)) k_rbgs_stream(Di
 constexpr int kCIs[3] = {4, 8, 16};
 constexpr int kMaxDevices = 64;
 
+// The map of one grid array with the sweep's 72 x 12 x 1 box, from a cache
+// keyed by device, address and shape (the solver's buffers live as long as
+// their handle; a map only records an address and a shape).
+bool plane_map(CUtensorMap* out, const float* base, const Dims& d) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, const void*, int, int, int>, CUtensorMap> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const auto key = std::make_tuple(dev, (const void*)base, d.n0, d.n1, d.n2);
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it == cache.end()) {
+        CUtensorMap m;
+        if (!encode_grid_map(&m, base, d.n0, d.n1, d.n2, RK, RJ)) return false;
+        it = cache.emplace(key, m).first;
+    }
+    *out = it->second;
+    return true;
+}
+
+// Maps for a sweep of level L where some tile is clear of the seams
+// (n2 >= 4 TK, n1 >= 4 TJ) and the level allows bulk copies.
+template <bool FACE>
+void sweep_maps(SweepMaps& m, const Level& L, const float* u_old, const float* f, const float* a) {
+    std::memset(&m, 0, sizeof(m));
+    const Dims& d = L.d;
+    if (!L.tma || d.n2 < 4 * TK || d.n1 < 4 * TJ) return;
+    bool ok = (!u_old || plane_map(&m.m[0], u_old, d)) && plane_map(&m.m[1], a, d) && plane_map(&m.m[2], f, d);
+    if (FACE) ok = ok && plane_map(&m.m[3], a + d.cells, d) && plane_map(&m.m[4], a + 2 * (size_t)d.cells, d);
+    m.on = ok ? 1 : 0;
+}
+
 template <bool ISO, int CI, bool PRO, bool COR, bool FACE = false>
 void launch_ci(dim3 grid, const Level& L, float hx, float hy, float hz, const float* u_old, float* u_new,
                const float* f, const float* a, const float* uc, const Dims& dc, double* u64, cudaStream_t st) {
     constexpr int smem = FACE ? SMEM_FACE : SMEM;
+    SweepMaps maps;
+    sweep_maps<FACE>(maps, L, u_old, f, a);
     allow_smem((const void*)k_rbgs_stream<ISO, CI, PRO, COR, FACE>, smem);
     k_rbgs_stream<ISO, CI, PRO, COR, FACE><<<grid, NT, smem, st>>>(L.d, hx, hy, hz, u_old, u_new, f, a, uc,
-                                                                   dc, u64);
+                                                                   dc, u64, maps);
 }
 
 // Blocks of the PRO (or plain; FACE or nodal) variant resident at once on the
@@ -560,6 +688,39 @@ void tune_sweep_level(Level& L, const Level* coarse, const float* uc, float* u, 
             }
         L.tune[pro] = best;
     }
+}
+
+bool encode_grid_map(CUtensorMap* map, const float* base, int n0, int n1, int n2, int box_k, int box_j) {
+    using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static Encode fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (Encode)p;
+        cudaGetLastError();
+    });
+    if (!fn || ((uintptr_t)base & 15)) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)n2, (cuuint64_t)n1, (cuuint64_t)n0};
+    const cuuint64_t strides[2] = {(cuuint64_t)n2 * sizeof(float), (cuuint64_t)n2 * n1 * sizeof(float)};
+    const cuuint32_t box[3] = {(cuuint32_t)box_k, (cuuint32_t)box_j, 1u};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool sweep_wait_failed() {
+    int v = 0;
+    const int zero = 0;
+    if (cudaMemcpyFromSymbol(&v, g_sweep_wait_fail, sizeof(int)) != cudaSuccess) return false;
+    if (v) cudaMemcpyToSymbol(g_sweep_wait_fail, &zero, sizeof(int));
+    return v != 0;
 }
 
 // FP64 levels are bound by the FP64 issue rate, not by memory: the ring nodes

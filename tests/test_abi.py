@@ -123,6 +123,7 @@ def test_solve_runs_on_the_device_loop_by_default():
 
     assert default_params((16, 16, 16)).device_loop == 1
     assert default_params((16, 16, 16)).checkpoint == 0
+    assert default_params((16, 16, 16)).tma == 1  # bulk-copy staging on by default
     assert default_params((16, 16, 16), device_loop=0).device_loop == 0
 
 

@@ -242,6 +242,41 @@ def test_streaming_variants_give_the_same_bits_and_match_oracle():
         assert np.array_equal(phi, phis[0])
 
 
+def test_bulk_copy_staging_gives_the_same_bits_and_matches_oracle():
+    """Tiles of the streaming sweep clear of the periodic seams stage their
+    planes with bulk tensor copies (tma = 1, the default) where the level has
+    such tiles (n2 >= 256, n1 >= 32).  On 32 x 64 x 256 (the finest level has
+    them, on both sides of seam tiles) phi equals the per-thread-copy form
+    (tma = 0) bit for bit and matches the oracle; on the 512^3 workload's
+    first step (the 256^3 level runs the face-sum sweep with bulk copies too)
+    the two forms give the same bits."""
+    n = (32, 64, 256)
+    rng = np.random.default_rng(31)
+    k = np.arange(n[2])[None, None, :]
+    rho = np.exp(0.7 * rng.normal(size=n)) * (1 + 0.3 * np.sin(2 * np.pi * k / n[2]))
+    res = O.solve(O.OracleParams(n=n, k_max=2), rho)
+    phis = []
+    for tma in (1, 0):
+        R, st = _gpu_solve(n, rho, precision="mixed", k_max=2, replay_alpha=res.alpha, tma=tma)
+        assert R.params.tma == tma
+        phi = R.field("phi").cpu().numpy()
+        assert rel(phi, res.phi) <= 1e-4, tma
+        phis.append(phi)
+        R.close()
+    assert np.array_equal(phis[0], phis[1])
+    nn, box = 512, 800.0
+    pos_h, _ = lpt_particles(nn, box, 1002, order=2)
+    pos = torch.from_numpy(pos_h).cuda()
+    del pos_h
+    out = []
+    for tma in (1, 0):
+        with Recon((nn, nn, nn), box=box, precision="mixed", k_max=1, tma=tma) as R:
+            R.deposit_particles(pos)
+            R.solve()
+            out.append(R.field("phi").cpu().numpy())
+    assert np.array_equal(out[0], out[1])
+
+
 def test_per_face_coarse_levels_match_the_oracle_in_fewer_vcycles():
     """Mixed precision with per-face coarse coefficients (the default on cubic
     grids of at least 64^3) and with the re-discretised nodal hierarchy: both
