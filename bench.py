@@ -38,8 +38,8 @@ FALLBACK_HBM_GBS = 6800.0
 # + advance) x steps + V-cycle x cycles + one deposit, each pass timed on the
 # full grid by the oracle, with these counts.
 ORACLE_SOLVE_COUNTS = {
-    "lpt512": (27, 532),
-    "lpt256": (56, 1003),
+    "lpt512": (27, 379),
+    "lpt256": (56, 756),
 }
 
 
@@ -76,6 +76,12 @@ def _args():
                     help="precision of the --launch-list solve")
     ap.add_argument("--coarse-faces", type=int, default=None,
                     help="mixed precision's coarse-level coefficients (library default if unset)")
+    ap.add_argument("--warm-start", type=int, default=None,
+                    help="1: each step's linear solve starts from the last step's solution; "
+                         "0: from zero (library default if unset; both precisions)")
+    ap.add_argument("--tma", type=int, default=None,
+                    help="1: the streaming sweep stages planes by bulk tensor copies where it can; "
+                         "0: per-thread copies only (library default if unset)")
     ap.add_argument("--tune-inner", type=int, default=1,
                     help="1: each mixed-precision handle picks its FP32 V-cycles per FP64 defect "
                          "correction by timing on its first (untimed) solve")
@@ -245,9 +251,14 @@ def run_gb300(a):
         mg_kw["tune_inner"] = 1
     if a.group_max is not None:
         mg_kw["group_max"] = a.group_max
+    if a.tma is not None:
+        mg_kw["tma"] = a.tma
+    both_kw = {} if a.warm_start is None else {"warm_start": a.warm_start}
+    mg_kw.update(both_kw)
 
     def timed(precision, steps, warmup, profile=False, inner=None):
         kw = dict(mg_kw) if precision == "mixed" else {}
+        kw.update(both_kw)
         if inner:  # the count the timed solves' handle chose
             kw.pop("tune_inner", None)
             kw["inner_vcycles"] = inner
@@ -292,7 +303,7 @@ def run_gb300(a):
                 "timed_solves": a.fp64_steps, "warmup_solves": a.fp64_warmup,
                 "status": _status_name(f0.status), "steps_per_solve": f0.steps,
                 "vcycles_per_solve": f0.vcycles, "R_end": f0.R,
-                "multigrid": _mg_settings(resolved_params((n, n, n), precision="fp64")),
+                "multigrid": _mg_settings(resolved_params((n, n, n), precision="fp64", **both_kw)),
                 "same_steps_as_mixed": f0.steps == s0.steps,
                 "mixed_over_fp64_per_solve": value / value_fp64,
                 "mixed_over_fp64_per_step": per_step,
@@ -634,7 +645,8 @@ def _config(a, W):
 def _mg_settings(p):
     """The multigrid settings a solve resolved to."""
     return {"nu1": p.nu1, "nu2": p.nu2, "inner_vcycles": p.inner_vcycles if p.precision else None,
-            "max_vcycles": p.max_vcycles}
+            "max_vcycles": p.max_vcycles, "warm_start": p.warm_start,
+            "tma": p.tma if p.precision else None}
 
 
 def _status_name(code):

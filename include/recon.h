@@ -168,6 +168,10 @@ typedef struct {
                             copies.  Both compute the same bits.  A sweep whose
                             wait for a copy runs out (~1 s) makes recon_solve
                             return RECON_E_TIMEOUT.                            */
+    int warm_start;      /* 1 (default): each step's linear solve starts from the
+                            last step's phidot (the paper leaves the initial
+                            guess open; 0 before the first step) and stops at
+                            the same residual tol_in ||s||; 0: from phidot = 0. */
 } recon_params;
 
 /* Per-solve record.  The per-step arrays are optional caller-owned host

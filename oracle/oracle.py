@@ -34,6 +34,7 @@ class _Params(C.Structure):
         ("nu1", C.c_int), ("nu2", C.c_int), ("tol_in", C.c_double), ("max_vcycles", C.c_int),
         ("tol_out", C.c_double), ("k_max", C.c_int), ("d_max", C.c_double),
         ("alpha_min", C.c_double), ("lambda_floor", C.c_double), ("density_update", C.c_int),
+        ("warm_start", C.c_int),
     ]
 
 
@@ -63,13 +64,14 @@ class OracleParams:
     alpha_min: float = 2.0 ** -20
     lambda_floor: float = 0.01
     density_update: int = 0
+    warm_start: int = 1
 
     def _c(self) -> _Params:
         p = _Params()
         p.n[:] = [int(v) for v in self.n]
         for f in ("xi_m", "v_m", "a_min", "climiter", "s_side", "nu1", "nu2",
                   "tol_in", "max_vcycles", "tol_out", "k_max", "d_max", "alpha_min",
-                  "lambda_floor", "density_update"):
+                  "lambda_floor", "density_update", "warm_start"):
             setattr(p, f, getattr(self, f))
         return p
 

@@ -27,7 +27,9 @@
  *         4. R = rms(s); stop if R <= tol_out ("until the mass per volume
  *            element is approximately constant").
  *         5. with x ~ xi the operator is div(m grad .); a = max(m, a_min);
- *            solve L(a) phidot = s by multigrid V-cycles (App. A).
+ *            solve L(a) phidot = s by multigrid V-cycles (App. A), starting
+ *            from the last step's phidot (warm_start; the paper leaves the
+ *            initial guess open) or from 0.
  *         6. dphi = S phidot (App. A, Delta phi = S phidot), mean removed.
  *         7. step limiter: largest alpha = 2^-k >= alpha_min keeping the
  *            smallest eigenvalue of I + Hess(phi + alpha dphi) above
@@ -419,8 +421,14 @@ int orc_vcycle(const orc_params* p, const double* a, const double* f, double* u)
 int orc_mg_solve(const orc_params* p, const double* a, const double* s, double* u,
                  int* ncycles, double* relres) {
     if (!p || !a || !s || !u || !dims_ok(p->n, 4)) return ORC_E_INVALID;
+    memset(u, 0, ncells(p->n) * sizeof(double));
+    return orc_mg_solve_from(p, a, s, u, ncycles, relres);
+}
+
+int orc_mg_solve_from(const orc_params* p, const double* a, const double* s, double* u,
+                      int* ncycles, double* relres) {
+    if (!p || !a || !s || !u || !dims_ok(p->n, 4)) return ORC_E_INVALID;
     size_t len = ncells(p->n);
-    memset(u, 0, len * sizeof(double));
     double snorm = norm2(s, len);
     int cyc = 0;
     double rel = 0.0;
@@ -794,7 +802,8 @@ static int params_ok(const orc_params* p) {
            p->tol_in > 0.0 && p->max_vcycles > 0 && p->tol_out >= 0.0 && p->k_max >= 0 &&
            p->d_max > 0.0 && p->alpha_min > 0.0 && p->alpha_min <= 1.0 &&
            p->lambda_floor >= 0.0 && p->lambda_floor < 1.0 &&
-           (p->density_update == 0 || p->density_update == 1);
+           (p->density_update == 0 || p->density_update == 1) &&
+           (p->warm_start == 0 || p->warm_start == 1);
 }
 
 int orc_solve(const orc_params* p, const double* rho, const double* replay_alpha,
@@ -825,6 +834,7 @@ int orc_solve(const orc_params* p, const double* rho, const double* replay_alpha
         rc = ORC_E_NOMEM;
         goto out;
     }
+    memset(phidot, 0, len * sizeof(double));
     /* init: tracer c = node c with mass rho_c / rho_bar; phi = 0 */
     for (long i = 0; i < n[0]; ++i)
         for (long j = 0; j < n[1]; ++j)
@@ -874,7 +884,10 @@ int orc_solve(const orc_params* p, const double* rho, const double* replay_alpha
         for (size_t c = 0; c < len; ++c) a[c] = m[c] > p->a_min ? m[c] : p->a_min; /* 5 */
         int ncyc = 0;
         double rel = 0.0;
-        rc = orc_mg_solve(p, a, s, phidot, &ncyc, &rel);
+        /* the linear solve starts from the last step's phidot (warm_start;
+         * phidot = 0 before the first step) or from 0 */
+        rc = p->warm_start ? orc_mg_solve_from(p, a, s, phidot, &ncyc, &rel)
+                           : orc_mg_solve(p, a, s, phidot, &ncyc, &rel);
         if (rc) goto out;
         orc_apply_S(n, p->s_side, phidot, dphi);     /* 6 */
         double mu = mean(dphi, len);
@@ -1078,7 +1091,16 @@ int orc_adjoint(const orc_params* p, const double* rho, const double* alpha, int
         orc_cic_deposit(n, xi, w, (int64_t)len, m);
         if ((rc = orc_source(p, phi, m, s, NULL))) goto out;
         for (size_t c = 0; c < len; ++c) a[c] = m[c] > p->a_min ? m[c] : p->a_min;
-        if ((rc = orc_mg_solve(p, a, s, PD + (size_t)k * len, NULL, NULL))) goto out;
+        /* the forward solve's initial guess: the last step's phidot with
+         * warm_start (0 before the first step) */
+        if (p->warm_start) {
+            if (k == 0) memset(PD, 0, len * sizeof(double));
+            else memcpy(PD + (size_t)k * len, PD + (size_t)(k - 1) * len, len * sizeof(double));
+            rc = orc_mg_solve_from(p, a, s, PD + (size_t)k * len, NULL, NULL);
+        } else {
+            rc = orc_mg_solve(p, a, s, PD + (size_t)k * len, NULL, NULL);
+        }
+        if (rc) goto out;
         orc_apply_S(n, p->s_side, PD + (size_t)k * len, dphi);
         project_mean(dphi, len);
         memcpy(phi + len, phi, len * sizeof(double));

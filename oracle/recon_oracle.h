@@ -47,6 +47,9 @@ typedef struct {
     double lambda_floor;    /* step limiter: required lambda_min(I + Hess phi)   */
     int density_update;     /* 0: CIC re-deposit of tracers each step; 1: the
                                linear update m += alpha D(dphi) of App. A      */
+    int warm_start;         /* 1: each step's linear solve starts from the last
+                               step's phidot (the paper does not state the
+                               initial guess); 0: from phidot = 0              */
 } orc_params;
 
 /* Per-step record of orc_solve (arrays of length k_max, caller-owned; any may
@@ -95,6 +98,11 @@ int orc_vcycle(const orc_params* p, const double* a, const double* f, double* u)
  * *relres. */
 int orc_mg_solve(const orc_params* p, const double* a, const double* s, double* u,
                  int* ncycles, double* relres);
+/* The same solve from the initial guess held in u (a V-cycle is affine in u,
+ * so this equals u0 plus the solve of L e = s - L u0 from e = 0, stopped at
+ * the same absolute residual tol_in ||s||).  At least one cycle runs. */
+int orc_mg_solve_from(const orc_params* p, const double* a, const double* s, double* u,
+                      int* ncycles, double* relres);
 
 /* Geometry of the map x = xi + grad phi (Eq. mapping): per node the volume
  * element sqrt_g = det(I + Hess phi) and the minimum eigenvalue lambda0 of the

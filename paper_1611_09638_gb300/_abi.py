@@ -43,7 +43,7 @@ class recon_params(C.Structure):
         ("inner_vcycles", C.c_int), ("density_update", C.c_int), ("device_loop", C.c_int),
         ("checkpoint", C.c_int), ("stream_planes", C.c_int), ("restrict_planes", C.c_int),
         ("coarse_faces", C.c_int), ("tune_inner", C.c_int), ("group_max", C.c_int),
-        ("tma", C.c_int),
+        ("tma", C.c_int), ("warm_start", C.c_int),
     ]
 
 

@@ -318,6 +318,7 @@ int check_params(const recon_params* p) {
         return fail(RECON_E_INVALID, "coarse_faces = 1 needs RECON_MIXED on a cubic grid of at least 64^3");
     if (p->tune_inner != 0 && p->tune_inner != 1) return fail(RECON_E_INVALID, "tune_inner must be 0 or 1");
     if (p->tma != 0 && p->tma != 1) return fail(RECON_E_INVALID, "tma must be 0 or 1");
+    if (p->warm_start != 0 && p->warm_start != 1) return fail(RECON_E_INVALID, "warm_start must be 0 or 1");
     if (p->group_max < p->inner_vcycles || p->group_max > 64)
         return fail(RECON_E_INVALID, "need inner_vcycles <= group_max <= 64");
     return RECON_OK;
@@ -469,15 +470,21 @@ void step_head(Handle* H, const CtlHandles& h) {
     launch_ctl_step_begin(H->ctl, H->scal, H->arr, (double)H->cells, p.tol_out, h, H->st);
 }
 
-// Multigrid head: coefficient hierarchy, phidot = 0 and (mixed) the first
-// FP64 defect handed to the FP32 V-cycle.
-void mg_head(Handle* H, const CtlHandles& h) {
+// Multigrid head: coefficient hierarchy, the initial guess of phidot and
+// (mixed) the first FP64 defect handed to the FP32 V-cycle.  warm: phidot
+// keeps the last step's solution (0 before the first step, from solve_init)
+// and the first defect is the FP64 residual s - L phidot; otherwise
+// phidot = 0 and the defect is s itself (its FP32 copy).
+void mg_head(Handle* H, const CtlHandles& h, bool warm) {
     if (H->mixed) build_hierarchy<float>(H, H->c32);
     else build_hierarchy<double>(H, H->c64);
-    cudaMemsetAsync(H->phidot, 0, sizeof(double) * H->cells, H->st);
-    // with phidot = 0 the FP64 defect is s itself: its FP32 copy is the first
-    // right-hand side of the FP32 V-cycles
-    if (H->mixed) launch_to_f32(H->cells, H->s, H->f32[0], H->st);
+    if (warm) {
+        if (H->mixed)
+            launch_residual64_to32(H->lv[0], H->phidot, H->s, H->F64, H->D64, H->f32[0], H->part[0], H->st);
+    } else {
+        cudaMemsetAsync(H->phidot, 0, sizeof(double) * H->cells, H->st);
+        if (H->mixed) launch_to_f32(H->cells, H->s, H->f32[0], H->st);
+    }
     launch_ctl_mg_begin(H->ctl, H->arr, H->mixed ? 1 : 0, H->p.tol_in, H->p.max_vcycles,
                         h, H->st);
 }
@@ -572,6 +579,7 @@ void advance(Handle* H, const CtlHandles& h) {
 // init: tracer c = node c with mass rho_c / rho_bar, phi = 0
 void solve_init(Handle* H) {
     launch_ctl_init(H->ctl, H->st);
+    cudaMemsetAsync(H->phidot, 0, sizeof(double) * H->cells, H->st);  // the first step's initial guess
     launch_init_tracers(H->cells, H->rho, H->scal + SC_SUM_RHO, H->w, H->ox, H->oy, H->oz, H->phi,
                         H->phi32, H->st);
     if (H->p.density_update == 1)  // App. A: the mass per cell starts as rho / rho_bar
@@ -686,7 +694,7 @@ int tune_inner_vcycles(Handle* H) {
             if (H->chk_exec) cudaGraphExecDestroy(H->chk_exec);
             H->chk_exec = nullptr;
             CK(cudaEventRecord(H->ev0, H->st));
-            mg_head(H, none);
+            mg_head(H, none, false);  // step 0 starts from phidot = 0 either way
             if ((rc = read_ctl(H))) return rc;
             while (H->hctl->go_mg)
                 if ((rc = run_cycle(H))) return rc;
@@ -717,7 +725,7 @@ int solve_host(Handle* H) {
         if (!H->hctl->go_cont) break;
         {
             Range mg_range("recon multigrid");
-            mg_head(H, none);
+            mg_head(H, none, H->p.warm_start != 0);
             if ((rc = read_ctl(H))) return rc;
             while (H->hctl->go_mg)
                 if ((rc = run_cycle(H))) return rc;
@@ -818,7 +826,7 @@ int build_solve_graph(Handle* H) {
                     int r2 = new_handle(H->gst[2], 0, &h.mg);
                     if (!r2) r2 = new_handle(H->gst[2], 0, &h.adv);
                     if (r2) return r2;
-                    mg_head(H, h);
+                    mg_head(H, h, H->p.warm_start != 0);
                     cudaGraph_t b_mg = nullptr, b_adv = nullptr;
                     if ((r2 = add_conditional(H->gst[2], h.mg, cudaGraphCondTypeWhile, &b_mg))) return r2;
                     r2 = capture_into(H, H->gst[3], b_mg, &n.mg, [&]() -> int {
@@ -1019,7 +1027,7 @@ int adjoint_mg(Handle* H) {
     const CtlHandles none{};
     launch_ctl_init(H->ctl, H->st);
     launch_ctl_step_begin(H->ctl, H->scal, H->arr, (double)H->cells, -1.0, none, H->st);
-    mg_head(H, none);
+    mg_head(H, none, false);  // each adjoint solve starts from 0
     int rc = read_ctl(H);
     while (!rc && H->hctl->go_mg) {
         mg_iter(H, none);
@@ -1157,6 +1165,7 @@ int recon_default_params(recon_params* p, int n0, int n1, int n2) {
     p->tune_inner = 0;
     p->group_max = -1;
     p->tma = 1;
+    p->warm_start = 1;
     return RECON_OK;
 }
 

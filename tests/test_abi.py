@@ -38,7 +38,8 @@ def test_default_params_match_the_paper_and_the_oracle():
     q = O.OracleParams()
     assert list(p.n) == [32, 16, 8]
     for f in ("xi_m", "v_m", "a_min", "climiter", "s_side", "nu1", "nu2", "tol_in", "max_vcycles",
-              "tol_out", "k_max", "d_max", "alpha_min", "lambda_floor", "density_update"):
+              "tol_out", "k_max", "d_max", "alpha_min", "lambda_floor", "density_update",
+              "warm_start"):
         assert getattr(p, f) == getattr(q, f), f
 
 
