@@ -38,8 +38,8 @@ FALLBACK_HBM_GBS = 6800.0
 # + advance) x steps + V-cycle x cycles + one deposit, each pass timed on the
 # full grid by the oracle, with these counts.
 ORACLE_SOLVE_COUNTS = {
-    "lpt512": (27, 379),
-    "lpt256": (56, 756),
+    "lpt512": (27, 305),
+    "lpt256": (56, 705),
 }
 
 
@@ -82,6 +82,9 @@ def _args():
     ap.add_argument("--tma", type=int, default=None,
                     help="1: the streaming sweep stages planes by bulk tensor copies where it can; "
                          "0: per-thread copies only (library default if unset)")
+    ap.add_argument("--stream-planes", type=int, default=None,
+                    help="--launch-list: fix the planes per block of the streaming sweep and "
+                         "residual restriction (no timing launches at create)")
     ap.add_argument("--tune-inner", type=int, default=1,
                     help="1: each mixed-precision handle picks its FP32 V-cycles per FP64 defect "
                          "correction by timing on its first (untimed) solve")
@@ -803,6 +806,13 @@ def run_launch_list(a):
         kw["inner_vcycles"] = a.inner_vcycles
     if a.precision == "mixed" and a.coarse_faces is not None:
         kw["coarse_faces"] = a.coarse_faces
+    if a.precision == "mixed" and a.tma is not None:
+        kw["tma"] = a.tma
+    if a.warm_start is not None:
+        kw["warm_start"] = a.warm_start
+    if a.precision == "mixed" and a.stream_planes is not None:
+        kw["stream_planes"] = a.stream_planes
+        kw["restrict_planes"] = min(a.stream_planes, 8)
     with Recon((n, n, n), box=W.box, precision=a.precision, k_max=a.k_max, device_loop=0, **kw) as R:
         R.deposit_particles(torch.from_numpy(pos).cuda())
         st = R.solve()

@@ -168,10 +168,15 @@ typedef struct {
                             copies.  Both compute the same bits.  A sweep whose
                             wait for a copy runs out (~1 s) makes recon_solve
                             return RECON_E_TIMEOUT.                            */
-    int warm_start;      /* 1 (default): each step's linear solve starts from the
-                            last step's phidot (the paper leaves the initial
-                            guess open; 0 before the first step) and stops at
-                            the same residual tol_in ||s||; 0: from phidot = 0. */
+    int warm_start;      /* initial guess of each step's linear solve (the paper
+                            leaves it open; every choice stops at the same
+                            residual tol_in ||s||).  2 (default): extrapolated
+                            from the last two steps' phidot,
+                            phidot_{k-1} + (alpha_{k-1} / alpha_{k-2})
+                            (phidot_{k-1} - phidot_{k-2}) (one more FP64 array);
+                            1: the last step's phidot; 0: phidot = 0.  Before
+                            the first step phidot = 0, and step 1 takes
+                            phidot_0 under 2.                                  */
 } recon_params;
 
 /* Per-solve record.  The per-step arrays are optional caller-owned host

@@ -64,7 +64,7 @@ class OracleParams:
     alpha_min: float = 2.0 ** -20
     lambda_floor: float = 0.01
     density_update: int = 0
-    warm_start: int = 1
+    warm_start: int = 2
 
     def _c(self) -> _Params:
         p = _Params()

@@ -803,7 +803,22 @@ static int params_ok(const orc_params* p) {
            p->d_max > 0.0 && p->alpha_min > 0.0 && p->alpha_min <= 1.0 &&
            p->lambda_floor >= 0.0 && p->lambda_floor < 1.0 &&
            (p->density_update == 0 || p->density_update == 1) &&
-           (p->warm_start == 0 || p->warm_start == 1);
+           p->warm_start >= 0 && p->warm_start <= 2;
+}
+
+/* Initial guess of step k's linear solve under warm_start = 2: u holds
+ * phidot_{k-1}, prev phidot_{k-2}; u becomes phidot_{k-1} + (alpha_{k-1} /
+ * alpha_{k-2}) (phidot_{k-1} - phidot_{k-2}), a linear extrapolation along
+ * the step lengths that moved the mesh, and prev phidot_{k-1}.  Step 1 only
+ * keeps phidot_0 in prev. */
+static void warm_extrapolate(size_t len, int k, const double* alpha, double* u, double* prev) {
+    if (k < 1) return;
+    const double r = k >= 2 ? alpha[k - 1] / alpha[k - 2] : 0.0;
+    for (size_t c = 0; c < len; ++c) {
+        const double cur = u[c];
+        if (k >= 2) u[c] = cur + r * (cur - prev[c]);
+        prev[c] = cur;
+    }
 }
 
 int orc_solve(const orc_params* p, const double* rho, const double* replay_alpha,
@@ -829,12 +844,22 @@ int orc_solve(const orc_params* p, const double* rho, const double* replay_alpha
     double* g = (double*)malloc(len * sizeof(double));
     double* lam = (double*)malloc(len * sizeof(double));
     double* dm = NULL; /* mass change of the App. A update (density_update = 1) */
+    double* prev = NULL;   /* warm_start = 2: phidot of the step before the last */
+    double* alphas = NULL; /* warm_start = 2: the accepted step lengths */
     int rc = 0, k = 0, done = 0, stalled = 0;
     if (!w || !xi || !m || !s || !a || !phidot || !dphi || !g || !lam) {
         rc = ORC_E_NOMEM;
         goto out;
     }
     memset(phidot, 0, len * sizeof(double));
+    if (p->warm_start == 2) {
+        prev = (double*)malloc(len * sizeof(double));
+        alphas = (double*)malloc((size_t)(p->k_max > 0 ? p->k_max : 1) * sizeof(double));
+        if (!prev || !alphas) {
+            rc = ORC_E_NOMEM;
+            goto out;
+        }
+    }
     /* init: tracer c = node c with mass rho_c / rho_bar; phi = 0 */
     for (long i = 0; i < n[0]; ++i)
         for (long j = 0; j < n[1]; ++j)
@@ -884,8 +909,10 @@ int orc_solve(const orc_params* p, const double* rho, const double* replay_alpha
         for (size_t c = 0; c < len; ++c) a[c] = m[c] > p->a_min ? m[c] : p->a_min; /* 5 */
         int ncyc = 0;
         double rel = 0.0;
-        /* the linear solve starts from the last step's phidot (warm_start;
-         * phidot = 0 before the first step) or from 0 */
+        /* the linear solve starts from the last step's phidot (warm_start 1;
+         * phidot = 0 before the first step), its extrapolation from the last
+         * two (2) or from 0 */
+        if (p->warm_start == 2) warm_extrapolate(len, k, alphas, phidot, prev);
         rc = p->warm_start ? orc_mg_solve_from(p, a, s, phidot, &ncyc, &rel)
                            : orc_mg_solve(p, a, s, phidot, &ncyc, &rel);
         if (rc) goto out;
@@ -913,6 +940,7 @@ int orc_solve(const orc_params* p, const double* rho, const double* replay_alpha
         }
         rc = orc_advance(n, alpha, dphi, phi, xi, (int64_t)len); /* 8 */
         if (rc) goto out;
+        if (alphas) alphas[k] = alpha;
         if (tr) {
             if (tr->alpha) tr->alpha[k] = alpha;
             if (tr->ncycles) tr->ncycles[k] = ncyc;
@@ -926,7 +954,7 @@ int orc_solve(const orc_params* p, const double* rho, const double* replay_alpha
     if (xi_out) memcpy(xi_out, xi, 3 * len * sizeof(double));
 out:
     if (steps) *steps = k;
-    free(dm);
+    free(dm), free(prev), free(alphas);
     free(w), free(xi), free(m), free(s), free(a), free(phidot), free(dphi), free(g), free(lam);
     if (rc) return rc;
     return done ? 0 : (stalled ? 2 : 1);
@@ -1092,11 +1120,20 @@ int orc_adjoint(const orc_params* p, const double* rho, const double* alpha, int
         if ((rc = orc_source(p, phi, m, s, NULL))) goto out;
         for (size_t c = 0; c < len; ++c) a[c] = m[c] > p->a_min ? m[c] : p->a_min;
         /* the forward solve's initial guess: the last step's phidot with
-         * warm_start (0 before the first step) */
+         * warm_start 1, extrapolated from the last two with 2 (0 before the
+         * first step) */
         if (p->warm_start) {
-            if (k == 0) memset(PD, 0, len * sizeof(double));
-            else memcpy(PD + (size_t)k * len, PD + (size_t)(k - 1) * len, len * sizeof(double));
-            rc = orc_mg_solve_from(p, a, s, PD + (size_t)k * len, NULL, NULL);
+            double* u0 = PD + (size_t)k * len;
+            if (k == 0) {
+                memset(u0, 0, len * sizeof(double));
+            } else if (p->warm_start == 2 && k >= 2) {
+                const double r = alpha[k - 1] / alpha[k - 2];
+                const double *u1 = u0 - len, *u2 = u0 - 2 * len;
+                for (size_t c = 0; c < len; ++c) u0[c] = u1[c] + r * (u1[c] - u2[c]);
+            } else {
+                memcpy(u0, u0 - len, len * sizeof(double));
+            }
+            rc = orc_mg_solve_from(p, a, s, u0, NULL, NULL);
         } else {
             rc = orc_mg_solve(p, a, s, PD + (size_t)k * len, NULL, NULL);
         }

@@ -47,9 +47,12 @@ typedef struct {
     double lambda_floor;    /* step limiter: required lambda_min(I + Hess phi)   */
     int density_update;     /* 0: CIC re-deposit of tracers each step; 1: the
                                linear update m += alpha D(dphi) of App. A      */
-    int warm_start;         /* 1: each step's linear solve starts from the last
-                               step's phidot (the paper does not state the
-                               initial guess); 0: from phidot = 0              */
+    int warm_start;         /* initial guess of each step's linear solve (the
+                               paper does not state it): 0: phidot = 0; 1: the
+                               last step's phidot; 2: extrapolated from the
+                               last two, phidot_{k-1} + (alpha_{k-1} /
+                               alpha_{k-2}) (phidot_{k-1} - phidot_{k-2}) (step
+                               1 takes phidot_0)                               */
 } orc_params;
 
 /* Per-step record of orc_solve (arrays of length k_max, caller-owned; any may

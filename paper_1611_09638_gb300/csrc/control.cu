@@ -135,6 +135,22 @@ __global__ void k_zero_if_fresh(const Ctl* __restrict__ c, float* __restrict__ u
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < cells; e += gridDim.x * blockDim.x) u[e] = 0.f;
 }
 
+// Initial guess of step k's linear solve from the last two solutions (u holds
+// phidot_{k-1}, prev phidot_{k-2}): u += r (u - prev) with r = alpha_{k-1} /
+// alpha_{k-2}, the step lengths that moved the mesh between them; prev takes
+// phidot_{k-1}.  At k = 1 prev only takes phidot_0; at k = 0 nothing happens.
+__global__ void k_warm_extrapolate(const Ctl* __restrict__ c, const double* __restrict__ alpha,
+                                   double* __restrict__ u, double* __restrict__ prev, int cells) {
+    const int k = c->k;
+    if (k < 1) return;
+    const double r = k >= 2 ? alpha[k - 1] / alpha[k - 2] : 0.0;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < cells; e += gridDim.x * blockDim.x) {
+        const double cur = u[e];
+        if (k >= 2) u[e] = cur + r * (cur - prev[e]);
+        prev[e] = cur;
+    }
+}
+
 // Step length: the largest 2^-j the limiter certified, halved further while
 // max |alpha grad dphi| > d_max; below alpha_min the iteration stops with the
 // current map (RECON_STALLED).  With a replay array alpha_k is taken from it.
@@ -217,6 +233,12 @@ void launch_ctl_group_check(Ctl* c, const double* scal, const CtlArrays& a, int 
                             double tol_in, int max_vcycles, const CtlHandles& h, cudaStream_t st) {
     launch_counter()++;
     k_ctl_group_check<<<1, 1, 0, st>>>(c, scal, a, block, group_max, tol_in, max_vcycles, h);
+}
+
+void launch_warm_extrapolate(const Ctl* c, const double* alpha, double* u, double* prev, int cells,
+                             cudaStream_t st) {
+    launch_counter()++;
+    k_warm_extrapolate<<<kRedBlocks, kRedThreads, 0, st>>>(c, alpha, u, prev, cells);
 }
 
 void launch_zero_if_fresh(const Ctl* c, float* u, int cells, cudaStream_t st) {

@@ -66,6 +66,7 @@ struct Handle {
     double *rho = nullptr, *w = nullptr, *ox = nullptr, *oy = nullptr, *oz = nullptr;
     double *phi = nullptr, *m = nullptr, *a64 = nullptr, *t = nullptr, *s = nullptr;
     double *phidot = nullptr, *dphi = nullptr, *v3 = nullptr;  // v3: 3 x cells
+    double* phidot_prev = nullptr;  // warm_start = 2: phidot of the step before the last
     double* e6 = nullptr;  // triad I + Hess phi of the current step, 6 x cells
     double* inv64 = nullptr;  // FP64 mode: 1 / diagonal of the finest level
     double* F64 = nullptr;    // face coefficients (a_c + a_{c+e}) / 2 of the finest level, 3 x cells
@@ -318,7 +319,7 @@ int check_params(const recon_params* p) {
         return fail(RECON_E_INVALID, "coarse_faces = 1 needs RECON_MIXED on a cubic grid of at least 64^3");
     if (p->tune_inner != 0 && p->tune_inner != 1) return fail(RECON_E_INVALID, "tune_inner must be 0 or 1");
     if (p->tma != 0 && p->tma != 1) return fail(RECON_E_INVALID, "tma must be 0 or 1");
-    if (p->warm_start != 0 && p->warm_start != 1) return fail(RECON_E_INVALID, "warm_start must be 0 or 1");
+    if (p->warm_start < 0 || p->warm_start > 2) return fail(RECON_E_INVALID, "warm_start must be 0, 1 or 2");
     if (p->group_max < p->inner_vcycles || p->group_max > 64)
         return fail(RECON_E_INVALID, "need inner_vcycles <= group_max <= 64");
     return RECON_OK;
@@ -472,12 +473,15 @@ void step_head(Handle* H, const CtlHandles& h) {
 
 // Multigrid head: coefficient hierarchy, the initial guess of phidot and
 // (mixed) the first FP64 defect handed to the FP32 V-cycle.  warm: phidot
-// keeps the last step's solution (0 before the first step, from solve_init)
+// keeps the last step's solution (0 before the first step, from solve_init),
+// with warm_start = 2 extrapolated from the last two (k_warm_extrapolate),
 // and the first defect is the FP64 residual s - L phidot; otherwise
 // phidot = 0 and the defect is s itself (its FP32 copy).
 void mg_head(Handle* H, const CtlHandles& h, bool warm) {
     if (H->mixed) build_hierarchy<float>(H, H->c32);
     else build_hierarchy<double>(H, H->c64);
+    if (warm && H->p.warm_start == 2)
+        launch_warm_extrapolate(H->ctl, H->arr.alpha, H->phidot, H->phidot_prev, H->cells, H->st);
     if (warm) {
         if (H->mixed)
             launch_residual64_to32(H->lv[0], H->phidot, H->s, H->F64, H->D64, H->f32[0], H->part[0], H->st);
@@ -1165,7 +1169,7 @@ int recon_default_params(recon_params* p, int n0, int n1, int n2) {
     p->tune_inner = 0;
     p->group_max = -1;
     p->tma = 1;
-    p->warm_start = 1;
+    p->warm_start = 2;
     return RECON_OK;
 }
 
@@ -1231,6 +1235,7 @@ int recon_create(void** out, const recon_params* p_in, void* cuda_stream) {
     AL(H->phi, n); AL(H->m, n); AL(H->a64, n); AL(H->t, n); AL(H->s, n);
     AL(H->phidot, n); AL(H->dphi, n); AL(H->v3, 3 * n); AL(H->mfix, n); AL(H->e6, 6 * n);
     AL(H->F64, 3 * n); AL(H->D64, n); AL(H->phi32, n); AL(H->dphi32, n);
+    if (p->warm_start == 2) AL(H->phidot_prev, n);
     if (p->density_update == 1) AL(H->v3m, 6 * n);
     AL(H->minv, 65 * 130); AL(H->scal, SC_COUNT);
     const size_t km = (size_t)std::max(p->k_max, 1);

@@ -356,6 +356,10 @@ void launch_ctl_group_check(Ctl* c, const double* scal, const CtlArrays& a, int 
                             double tol_in, int max_vcycles, const CtlHandles& h, cudaStream_t st);
 // u = 0 where the control block says a new defect correction starts
 void launch_zero_if_fresh(const Ctl* c, float* u, int cells, cudaStream_t st);
+// The extrapolated initial guess of the step's linear solve (warm_start = 2):
+// u += (alpha_{k-1} / alpha_{k-2}) (u - prev) for k >= 2, prev = old u for k >= 1.
+void launch_warm_extrapolate(const Ctl* c, const double* alpha, double* u, double* prev, int cells,
+                             cudaStream_t st);
 void launch_ctl_mg_check(Ctl* c, const double* scal, const CtlArrays& a, int per_launch,
                          double tol_in, int max_vcycles, const CtlHandles& h, cudaStream_t st);
 void launch_ctl_select_alpha(Ctl* c, double* scal, const CtlArrays& a, const double* replay,

@@ -185,29 +185,34 @@ def test_replayed_alpha_reproduces_the_solve():
 
 
 def test_warm_start_reaches_the_same_solution_in_fewer_cycles():
-    """Each step's linear solve from the last step's phidot (warm_start = 1)
-    or from 0 stops at the same residual: converged to rounding (tol_in
-    1e-12) the two solves agree to rounding, at the default tolerance they
-    agree to the size of that tolerance and the warm start needs fewer
-    V-cycles; the first step, which has no earlier solution, is the same."""
+    """Each step's linear solve from 0 (warm_start = 0), from the last step's
+    phidot (1) or from its extrapolation along the step lengths (2) stops at
+    the same residual: converged to rounding (tol_in 1e-12) the solves agree
+    to rounding, at the default tolerance they agree to the size of that
+    tolerance and the warm starts need fewer V-cycles, the extrapolation
+    fewest; the first step, which has no earlier solution, is the same."""
     n = 32
     pos, _ = lpt_particles(n, 50.0, 6, order=2)
     rho = O.cic_deposit((n, n, n), pos / (50.0 / n))
     runs = {}
     for tol in (1e-12, 1e-8):
-        for ws in (0, 1):
+        for ws in (0, 1, 2):
             runs[tol, ws] = O.solve(O.OracleParams(n=(n, n, n), k_max=8, tol_in=tol, max_vcycles=200,
                                                    warm_start=ws), rho)
     for tol in (1e-12, 1e-8):
-        cold, warm = runs[tol, 0], runs[tol, 1]
-        assert cold.steps == warm.steps == 8 and np.array_equal(cold.alpha, warm.alpha)
-        assert cold.ncycles[0] == warm.ncycles[0]
-        assert np.all(warm.relres <= tol)
+        cold = runs[tol, 0]
+        for ws in (1, 2):
+            warm = runs[tol, ws]
+            assert cold.steps == warm.steps == 8 and np.array_equal(cold.alpha, warm.alpha)
+            assert cold.ncycles[0] == warm.ncycles[0]
+            assert np.all(warm.relres <= tol)
     conv = runs[1e-12, 0].phi
     rel = lambda r: np.linalg.norm(r.phi - conv) / np.linalg.norm(conv)
-    assert rel(runs[1e-12, 1]) < 1e-11
-    assert rel(runs[1e-8, 1]) < 1e-6 and rel(runs[1e-8, 0]) < 1e-6
-    assert runs[1e-8, 1].ncycles[1:].sum() < runs[1e-8, 0].ncycles[1:].sum()
+    assert rel(runs[1e-12, 1]) < 1e-11 and rel(runs[1e-12, 2]) < 1e-11
+    for ws in (0, 1, 2):
+        assert rel(runs[1e-8, ws]) < 1e-6
+    total = {ws: runs[1e-8, ws].ncycles[1:].sum() for ws in (0, 1, 2)}
+    assert total[2] <= total[1] < total[0], total
 
 
 @pytest.mark.parametrize("bad", ["dims", "negative", "zero", "nan"])

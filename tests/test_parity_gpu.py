@@ -94,6 +94,30 @@ def test_particle_deposit_matches_oracle(za32):
     assert np.abs(got - ref).max() <= 1e-10 * ref.max()
 
 
+def test_every_initial_guess_matches_the_oracle(za32):
+    """Each step's linear solve from 0, from the last step's phidot and from
+    its extrapolation along the step lengths (warm_start 0, 1, 2): with the
+    oracle's alpha replayed, the GPU takes the oracle's V-cycle counts (+- 1)
+    and phi matches the oracle run with the same initial guess (FP64 1e-6,
+    mixed 1e-4); the warm starts need fewer V-cycles."""
+    n, box = za32["n"], za32["box"]
+    h = box / n
+    total = {}
+    for ws in (0, 1, 2):
+        res = O.solve(O.OracleParams(n=(n, n, n), k_max=10, warm_start=ws), za32["rho"])
+        for prec, tol in (("fp64", 1e-6), ("mixed", 1e-4)):
+            R, st = _gpu_solve((n, n, n), za32["rho"], precision=prec, box=box, k_max=10,
+                               replay_alpha=res.alpha, warm_start=ws)
+            assert R.params.warm_start == ws and st.steps == res.steps
+            if prec == "fp64":
+                assert np.abs(st.ncycles - res.ncycles).max() <= 1
+                total[ws] = int(st.vcycles)
+            assert np.all(st.relres <= 1e-8)
+            assert rel(R.field("phi").cpu().numpy() / h ** 2, res.phi) <= tol, (ws, prec)
+            R.close()
+    assert total[2] <= total[1] < total[0], total
+
+
 def test_fp64_solve_matches_oracle(za32):
     n, box, res = za32["n"], za32["box"], za32["res"]
     R, st = _gpu_solve((n, n, n), za32["rho"], box=box, k_max=20)
