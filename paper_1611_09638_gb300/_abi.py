@@ -61,18 +61,25 @@ class recon_stats(C.Structure):
 _lib = None
 
 
+def _checked() -> bool:
+    """RECON_BUILD=checked selects the bounds-checked library."""
+    return os.environ.get("RECON_BUILD", "") == "checked"
+
+
 def lib_path():
-    return _build.LIB
+    return _build.lib_path(_checked())
 
 
 def load(build_if_missing: bool = True):
-    """Load librecon.so (building it first if it is missing or stale)."""
+    """Load librecon.so, or librecon_checked.so under RECON_BUILD=checked
+    (building it first if it is missing or stale)."""
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.build() if build_if_missing else _build.LIB
+    checked = _checked()
+    path = _build.build(checked=checked) if build_if_missing else _build.lib_path(checked)
     if not os.path.exists(path):
-        raise RuntimeError(f"librecon.so not built at {path}")
+        raise RuntimeError(f"{os.path.basename(path)} not built at {path}")
     lib = C.CDLL(path)
     lib.recon_default_params.restype = C.c_int
     lib.recon_default_params.argtypes = [C.POINTER(recon_params), C.c_int, C.c_int, C.c_int]

@@ -1,6 +1,12 @@
 """Build librecon.so (the CUDA solver behind include/recon.h) in-tree for
 sm_103a with nvcc: one object per translation unit, compiled in parallel,
-then linked into a shared library next to this file."""
+then linked into a shared library next to this file.
+
+build(checked=True) builds librecon_checked.so instead: the same library
+compiled with -DRECON_CHECKED, whose kernels check their computed shared- and
+global-memory offsets and report a failed check as a status (never a trap).
+The package loads it in place of librecon.so when RECON_BUILD=checked is set
+in the environment."""
 import os
 import subprocess
 import sys
@@ -9,6 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librecon.so")
+LIB_CHECKED = os.path.join(HERE, "librecon_checked.so")
 SOURCES = ["recon_api.cu", "mg_kernels.cu", "step_kernels.cu", "smoother.cu", "transfer.cu", "control.cu", "adjoint.cu", "noalloc.cu", "coarse_cluster.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
@@ -28,15 +35,24 @@ def _deps():
     return max(os.path.getmtime(f) for f in files)
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    """Compile and link librecon.so if any source is newer; return its path."""
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def lib_path(checked: bool = False) -> str:
+    return LIB_CHECKED if checked else LIB
+
+
+def build(force: bool = False, verbose: bool = False, extra=(), checked: bool = False) -> str:
+    """Compile and link librecon.so (librecon_checked.so with checked) if any
+    source is newer; return its path."""
+    lib = lib_path(checked)
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _deps():
+        return lib
+    build_dir = os.path.join(BUILD, "checked") if checked else BUILD
+    os.makedirs(build_dir, exist_ok=True)
+    if checked:
+        extra = tuple(extra) + ("-DRECON_CHECKED",)
     nvcc = _nvcc()
     procs, objs = [], []
     for src in SOURCES:
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        obj = os.path.join(build_dir, src.replace(".cu", ".o"))
         cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd))
@@ -51,10 +67,10 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
             print(out.decode(errors="replace"))
     if errs:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errs))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs], check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

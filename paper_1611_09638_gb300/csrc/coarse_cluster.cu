@@ -19,6 +19,7 @@
 // x face sums where they read a, and the y and z sums of their own planes.
 #include <cooperative_groups.h>
 
+#include "checked.cuh"
 #include "mg_stencil.cuh"
 #include "recon_internal.cuh"
 
@@ -48,7 +49,7 @@ struct CLev {
 template <typename T, int N, int P>
 __device__ inline T* plane_of(T* X, int gi, int self) {
     gi &= N - 1;
-    const int owner = gi / P;
+    const int owner = RC_OFF(gi / P, kCR, 301);  // a block of the cluster
     T* base = owner == self ? X : cg::this_cluster().map_shared_rank(X, owner);
     return base + (gi - owner * P) * (N * N);
 }
@@ -337,5 +338,7 @@ template bool launch_coarse_cluster<float>(const CoarseSet&, const float*, float
                                            cudaStream_t);
 template bool launch_coarse_cluster<double>(const CoarseSet&, const double*, double*, const double*, bool,
                                             cudaStream_t);
+
+int bounds_fail_cluster() { return bounds_fail_take(); }
 
 }  // namespace recon

@@ -1137,6 +1137,18 @@ int set_last_error(int code, const char* msg) {
 }
 }  // namespace recon
 
+// RECON_CHECKED build: the first failed index check (its id) of any
+// instrumented kernel since the last call, as a status; RECON_OK otherwise
+// (always in the normal build).  The device has finished the work by then.
+static int bounds_status() {
+    int id = bounds_fail_smoother();
+    if (!id) id = bounds_fail_transfer();
+    if (!id) id = bounds_fail_cluster();
+    if (!id) id = bounds_fail_steps();
+    if (id) return fail(RECON_E_CUDA, "index bounds check %d failed (RECON_CHECKED build)", id);
+    return RECON_OK;
+}
+
 extern "C" {
 
 int recon_default_params(recon_params* p, int n0, int n1, int n2) {
@@ -1437,6 +1449,10 @@ int recon_solve(void* hp, recon_stats* stats) {
     if (rc == RECON_OK) rc = solve(H, stats);
     if (rc >= 0 && H->mixed && sweep_wait_failed())
         rc = fail(RECON_E_TIMEOUT, "a streaming sweep gave up waiting for a bulk copy");
+    if (rc >= 0) {
+        const int b = bounds_status();
+        if (b) rc = b;
+    }
     if (rc < 0) {
         cudaStreamSynchronize(H->st);
         H->solved = false;
@@ -1484,6 +1500,10 @@ int recon_solve_batch(void* const* handles, int count, recon_stats* stats) {
     }
     if (worst >= 0 && sweep_wait_failed())
         worst = fail(RECON_E_TIMEOUT, "a streaming sweep gave up waiting for a bulk copy");
+    if (worst >= 0) {
+        const int b = bounds_status();
+        if (b) worst = b;
+    }
     return worst;
 }
 
@@ -1543,6 +1563,7 @@ int recon_adjoint(void* hp, const double* grad_delta_r, double* grad_rho) {
     if (!H->solved) return fail(RECON_E_STATE, "recon_adjoint needs a completed recon_solve");
     int rc = adjoint(H, grad_delta_r, grad_rho);
     if (rc) cudaStreamSynchronize(H->st);
+    if (!rc) rc = bounds_status();
     return rc;
 }
 

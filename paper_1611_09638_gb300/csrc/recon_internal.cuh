@@ -188,6 +188,13 @@ bool rbgs_prolong_fits(const Level& fine);
 // Whether a streaming sweep gave up waiting for a bulk copy since the last
 // call (on the current device); clears the record.
 bool sweep_wait_failed();
+// RECON_CHECKED build: the id of the first failed index check of each
+// instrumented translation unit since the last call (read and cleared;
+// always 0 in the normal build).
+int bounds_fail_smoother();
+int bounds_fail_transfer();
+int bounds_fail_cluster();
+int bounds_fail_steps();
 int launch_rbgs_prolong(const Level& fine, const Level& coarse, const float* uc, const float* u_old,
                         float* u_new, const float* f, const float* a, cudaStream_t st,
                         double* u64 = nullptr);

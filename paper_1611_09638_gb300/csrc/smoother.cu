@@ -49,6 +49,7 @@
 #include <tuple>
 
 #include "async_copy.cuh"
+#include "checked.cuh"
 #include "recon_internal.cuh"
 #include "tma.cuh"
 
@@ -172,17 +173,19 @@ __global__ void __launch_bounds__(NT, FACE ? 2 : (PRO ? 3 : 4)) k_rbgs_stream(Di
 
     // ---- offsets fixed for the whole block -------------------------------
     // fetch: this thread's 16-byte chunk of a u/a plane and of an f plane
+    // (RC_OFF: the RECON_CHECKED build checks each offset against the extent
+    // it addresses; otherwise it is the offset itself)
     int ua_s = -1, ua_g = 0;
     if (t < NUA) {
         const int r = t / CH, ch = t - r * CH;
-        ua_s = r * RK + ch * 4;
-        ua_g = (((j0 + r - H) & (d.n1 - 1)) << d.s2) + ((k0 - KO + ch * 4) & (d.n2 - 1));
+        ua_s = RC_OFF(r * RK + ch * 4, PL - 3, 101);
+        ua_g = RC_OFF((((j0 + r - H) & (d.n1 - 1)) << d.s2) + ((k0 - KO + ch * 4) & (d.n2 - 1)), plane - 3, 102);
     }
     int f_s = -1, f_g = 0;
     if (t < NF) {
         const int r = t / CH, ch = t - r * CH;
-        f_s = (r + 1) * RK + ch * 4;
-        f_g = (((j0 + r - 1) & (d.n1 - 1)) << d.s2) + ((k0 - KO + ch * 4) & (d.n2 - 1));
+        f_s = RC_OFF((r + 1) * RK + ch * 4, PL - 3, 103);
+        f_g = RC_OFF((((j0 + r - 1) & (d.n1 - 1)) << d.s2) + ((k0 - KO + ch * 4) & (d.n2 - 1)), plane - 3, 104);
     }
     // Columns: warp w takes rows 2 (w / 2) and 2 (w / 2) + 1 (one per half
     // warp) and column pairs 16 (w & 1) .. + 15.  The red column of a pair in
@@ -198,11 +201,12 @@ __global__ void __launch_bounds__(NT, FACE ? 2 : (PRO ? 3 : 4)) k_rbgs_stream(Di
 #pragma unroll
     for (int m = 0; m < 2; ++m) {
         z[m] = (m + 1 + jg) & 1;
-        ez[m] = (jj + H) * RK + KO + 2 * pr + z[m];
-        en[m] = ez[m] + (z[m] ? 1 : -1);  // the k neighbour in the adjacent pair
+        // the node and its rows j +- 1 lie in the plane buffer
+        ez[m] = RK + RC_OFF((jj + H) * RK + KO + 2 * pr + z[m] - RK, PL - 2 * RK, 105);
+        en[m] = RC_OFF(ez[m] + (z[m] ? 1 : -1), PL, 106);  // the k neighbour in the adjacent pair
     }
-    const int ep = (jj + H) * RK + KO + 2 * pr;  // the pair in a plane buffer (8-byte aligned)
-    const int gp = (jg << d.s2) + k0 + 2 * pr;   // the pair in a global plane
+    const int ep = RC_OFF((jj + H) * RK + KO + 2 * pr, PL - 1, 107);  // the pair in a plane buffer (8-byte aligned)
+    const int gp = RC_OFF((jg << d.s2) + k0 + 2 * pr, plane - 1, 108);   // the pair in a global plane
     // Ring tasks (threads t < NRING): the red node of row -1 or TJ (t < 66:
     // the 33 red nodes of each row) or of column -1 or TK of tile row t - 66.
     // ring_e: smem offset of the node in a plane of even and of odd q - i0.
@@ -222,7 +226,7 @@ __global__ void __launch_bounds__(NT, FACE ? 2 : (PRO ? 3 : 4)) k_rbgs_stream(Di
                 rj = t - 66;
                 kc = ((m + j0 + rj + k0 - 1) & 1) ? TK : -1;
             }
-            ring_e[m] = (rj + H) * RK + KO + kc;
+            ring_e[m] = RK + RC_OFF((rj + H) * RK + KO + kc - RK, PL - 2 * RK, 109);  // with rows +- 1
         }
     }
 
@@ -290,6 +294,10 @@ __global__ void __launch_bounds__(NT, FACE ? 2 : (PRO ? 3 : 4)) k_rbgs_stream(Di
         o0 = r0 + K0, o1 = r1 + K0, o02 = r0 + K2, o12 = r1 + K2;
     }
     const int cplane = dc.n1 * dc.n2;
+    if (PRO && ua_s >= 0) {  // pairs at o0, o1; single values at o02, o12
+        o0 = RC_OFF(o0, cplane - 1, 110), o1 = RC_OFF(o1, cplane - 1, 111);
+        o02 = RC_OFF(o02, cplane, 112), o12 = RC_OFF(o12, cplane, 113);
+    }
     // The coarse values one chunk's P(uc) needs: per coarse plane (one for an
     // even fine plane, two for an odd one), the pairs at (J0 | J1, K0..K0+1)
     // and the values at K0 + 2.  pro_load issues the loads; pro_value combines
@@ -714,6 +722,8 @@ bool encode_grid_map(CUtensorMap* map, const float* base, int n0, int n1, int n2
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
+
+int bounds_fail_smoother() { return bounds_fail_take(); }
 
 bool sweep_wait_failed() {
     int v = 0;

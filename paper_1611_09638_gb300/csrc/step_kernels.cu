@@ -2,6 +2,7 @@
 // than the multigrid solve: CIC deposits in 64-bit fixed point, geometry of
 // the map x = xi + grad phi, the limited source of Eq. (elliptic), the
 // smoothing operator S, the step limiter, the mesh advance and the outputs.
+#include "checked.cuh"
 #include "geometry.cuh"
 #include "recon_internal.cuh"
 #include "reduce.cuh"
@@ -197,7 +198,7 @@ __global__ void __launch_bounds__(256) k_deposit_tracers_tiled(Dims d, const dou
                 for (int dk = 0; dk < 2; ++dk) {
                     const unsigned long long qv = (unsigned long long)llrint(wxy * (dk ? fz : wz0));
                     if (local)
-                        atomicAdd(&acc[((bi + di) * DRJ + (bj + dj)) * DRK + (bk + dk)], qv);
+                        atomicAdd(&acc[RC_OFF(((bi + di) * DRJ + (bj + dj)) * DRK + (bk + dk), DCELLS, 401)], qv);
                     else
                         atomicAdd(&mfix[cell_index(d, i0 + di, j0 + dj, k0 + dk)], qv);
                 }
@@ -880,5 +881,7 @@ void launch_scale(int cells, const double* in, double s, double* out, cudaStream
     launch_counter()++;
     k_scale<<<nblocks(cells), kThreads, 0, st>>>(cells, in, s, out);
 }
+
+int bounds_fail_steps() { return bounds_fail_take(); }
 
 }  // namespace recon

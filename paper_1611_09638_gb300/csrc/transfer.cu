@@ -25,6 +25,7 @@
 // fetched), f for two; each plane is fetched with 16-byte cp.async copies.
 // DRAM traffic is one read of u, a, f and one write of the coarse plane.
 #include "async_copy.cuh"
+#include "checked.cuh"
 #include "recon_internal.cuh"
 
 namespace recon {
@@ -117,20 +118,24 @@ __global__ void __launch_bounds__(RT) k_resid_restrict_stream(Dims df, Dims dc, 
         const int e = t + m * RT;
         const int r = e / RCH, ch = e - r * RCH;
         const int gk = (k0 - RKO + ch * 4) & (df.n2 - 1);
-        ua_s[m] = e < NUA ? r * RRK + ch * 4 : -1;
-        ua_g[m] = (((j0 + r - RH) & (df.n1 - 1)) << df.s2) + gk;
-        f_s[m] = e < NFC ? (r + 1) * RRK + ch * 4 : -1;  // fine row r - 1
-        f_g[m] = (((j0 + r - 1) & (df.n1 - 1)) << df.s2) + gk;
+        // (RC_OFF: checked against the extent in the RECON_CHECKED build)
+        ua_s[m] = e < NUA ? RC_OFF(r * RRK + ch * 4, RPL - 3, 201) : -1;
+        ua_g[m] = RC_OFF((((j0 + r - RH) & (df.n1 - 1)) << df.s2) + gk, plane - 3, 202);
+        f_s[m] = e < NFC ? RC_OFF((r + 1) * RRK + ch * 4, RPL - 3, 203) : -1;  // fine row r - 1
+        f_g[m] = RC_OFF((((j0 + r - 1) & (df.n1 - 1)) << df.s2) + gk, plane - 3, 204);
     }
     // warp jc = coarse row, lane kc = coarse column: fine rows 2 jc, 2 jc + 1
     // (offsets e0, e1 of the column pair 2 kc, 2 kc + 1)
     const int jc = t >> 5, kc = t & 31;
-    const int e0 = (2 * jc + RH) * RRK + 2 * kc + RKO, e1 = e0 + RRK;
-    const int out_o = ((J0c + jc) << dc.s2) + K0c + kc;
+    // every read around the quad lies in [e0 - RRK - 1, e1 + RRK + 2)
+    const int e0 = RRK + 1 + RC_OFF((2 * jc + RH) * RRK + 2 * kc + RKO - RRK - 1, RPL - 3 * RRK - 2, 205);
+    const int e1 = e0 + RRK;
+    const int out_o = RC_OFF(((J0c + jc) << dc.s2) + K0c + kc, dc.n1 * dc.n2, 206);
     // ring residual of thread t < NRING: row -1 (columns -1 .. FK-1) or
     // column -1 (rows 0 .. FJ-1)
-    const int ring_e = t < FK + 1 ? (RH - 1) * RRK + RKO + t - 1
-                                  : (t < NRING ? (t - (FK + 1) + RH) * RRK + RKO - 1 : -1);
+    int ring_e = t < FK + 1 ? (RH - 1) * RRK + RKO + t - 1
+                            : (t < NRING ? (t - (FK + 1) + RH) * RRK + RKO - 1 : -1);
+    if (ring_e >= 0) ring_e = RRK + RC_OFF(ring_e - RRK, RPL - 2 * RRK, 207);  // with rows +- 1
 
     // Plane p is held in u / a slot (p - pS + 1) mod SUA and f slot
     // (p - pS) mod SFF; the plane loop is unrolled (p = pS + it), so every
@@ -204,7 +209,8 @@ __global__ void __launch_bounds__(RT) k_resid_restrict_stream(Dims df, Dims dc, 
                 acc += 0.5f * s;
             } else {  // p - 1 = 2I + 1 (odd) closes coarse plane I and opens I + 1
                 if (it > 1)
-                    out[((I0c - 1 + ((it - 1) >> 1)) << (dc.s1 + dc.s2)) + out_o] = acc + 0.25f * s;
+                    out[RC_OFF(((I0c - 1 + ((it - 1) >> 1)) << (dc.s1 + dc.s2)) + out_o, dc.cells, 208)] =
+                        acc + 0.25f * s;
                 acc = 0.25f * s;
             }
         }
@@ -396,5 +402,7 @@ void tune_resid_restrict_level(Level& fine, const Level& coarse, const float* u,
         }
     fine.tune[2] = best;
 }
+
+int bounds_fail_transfer() { return bounds_fail_take(); }
 
 }  // namespace recon

@@ -165,3 +165,19 @@ def test_resolve_params_touches_only_the_multigrid_settings():
     assert not p.replay_alpha  # still NULL
     assert lib.recon_resolve_params(None) == _abi.RECON_E_INVALID
     assert b"NULL" in lib.recon_last_error()
+
+
+def test_checked_library_builds_and_exports_the_same_entry_points():
+    """librecon_checked.so (the RECON_CHECKED build) compiles for sm_103a and
+    exports the entry points of librecon.so."""
+    import subprocess
+
+    from paper_1611_09638_gb300 import build as B
+
+    def exported(path):
+        out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True,
+                             check=True).stdout
+        return {ln.split()[-1] for ln in out.splitlines() if ln.split()[-1].startswith("recon_")}
+
+    plain, checked = exported(B.build()), exported(B.build(checked=True))
+    assert plain and plain == checked
