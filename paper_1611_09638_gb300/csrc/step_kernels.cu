@@ -35,6 +35,51 @@ __device__ inline void cic_abs(double x, int n, int& i0, double& f) {
     i0 = (int)fl;
 }
 
+// The eight CIC corner charges of one tracer in fixed point.  The offset of
+// the tracer from its home node is rounded on each axis to 2^-48 of a cell,
+// q = llrint(off 2^48): the lower node is home + (q >> 48) (floor) and the
+// fraction f = q mod 2^48.  The mass M = llrint(w scale) is split exactly,
+// first along x into M1 = floor(M f_x / 2^48) and M0 = M - M1, then each part
+// along y, then along z, so the charges are non-negative integers that sum to
+// M exactly (mass conservation per tracer).  The splits are 64 x 64-bit
+// integer multiplies (upper halves): the FP64 work per tracer is four
+// scalings and four conversions, against some 35 FP64 instructions for FP64
+// corner weights.  The rounding of a charge is below one unit (1 / scale) of
+// the fixed point, like llrint of an FP64 product, and the position's below
+// 2^-49 cells.
+struct CicCharges {
+    int i0, j0, k0;               // lower corner
+    unsigned long long c[2][2][2];  // charges at (i0 + di, j0 + dj, k0 + dk)
+};
+
+__device__ inline void split_fixed(unsigned long long m, unsigned long long f48, unsigned long long& lo,
+                                   unsigned long long& hi) {
+    hi = __umul64hi(m, f48 << 16);  // floor(m f / 2^48)
+    lo = m - hi;
+}
+
+__device__ inline CicCharges cic_charges(int i, int j, int k, double ox, double oy, double oz, double w,
+                                         double scale) {
+    constexpr double two48 = 281474976710656.0;  // 2^48
+    constexpr unsigned long long mask48 = (1ull << 48) - 1;
+    const long long qx = __double2ll_rn(ox * two48), qy = __double2ll_rn(oy * two48);
+    const long long qz = __double2ll_rn(oz * two48);
+    CicCharges r;
+    r.i0 = i + (int)(qx >> 48), r.j0 = j + (int)(qy >> 48), r.k0 = k + (int)(qz >> 48);
+    const unsigned long long fx = (unsigned long long)qx & mask48, fy = (unsigned long long)qy & mask48;
+    const unsigned long long fz = (unsigned long long)qz & mask48;
+    const unsigned long long M = (unsigned long long)__double2ll_rn(w * scale);
+    unsigned long long mx[2], mxy[2][2];
+    split_fixed(M, fx, mx[0], mx[1]);
+#pragma unroll
+    for (int di = 0; di < 2; ++di) {
+        split_fixed(mx[di], fy, mxy[di][0], mxy[di][1]);
+#pragma unroll
+        for (int dj = 0; dj < 2; ++dj) split_fixed(mxy[di][dj], fz, r.c[di][dj][0], r.c[di][dj][1]);
+    }
+    return r;
+}
+
 __device__ inline void atomic_add_fixed(unsigned long long* p, double v, double scale) {
     const long long q = llrint(v * scale);
     atomicAdd(p, (unsigned long long)q);
@@ -128,25 +173,11 @@ __global__ void k_deposit_tracers(Dims d, const double* __restrict__ ox,
     if (c >= d.cells) return;
     int i, j, k;
     cell_coords(d, c, i, j, k);
-    int i0, j0, k0;
-    double fx, fy, fz;
-    cic_offset(i, ox[c], i0, fx);
-    cic_offset(j, oy[c], j0, fy);
-    cic_offset(k, oz[c], k0, fz);
-    // the mass in fixed-point units folded into the x weights first:
-    // msc fx and msc (1 - fx) = msc - msc fx, then x-y pairs, then corners
-    const double msc = w[c] * scale;
-    const double mx1 = msc * fx, mx0 = msc - mx1;
-    const double wy0 = 1.0 - fy, wz0 = 1.0 - fz;
-    for (int di = 0; di < 2; ++di) {
-        const double wx = di ? mx1 : mx0;
-        for (int dj = 0; dj < 2; ++dj) {
-            const double wxy = wx * (dj ? fy : wy0);
+    const CicCharges q = cic_charges(i, j, k, ox[c], oy[c], oz[c], w[c], scale);
+    for (int di = 0; di < 2; ++di)
+        for (int dj = 0; dj < 2; ++dj)
             for (int dk = 0; dk < 2; ++dk)
-                atomicAdd(&mfix[cell_index(d, i0 + di, j0 + dj, k0 + dk)],
-                          (unsigned long long)llrint(wxy * (dk ? fz : wz0)));
-        }
-    }
+                atomicAdd(&mfix[cell_index(d, q.i0 + di, q.j0 + dj, q.k0 + dk)], q.c[di][dj][dk]);
 }
 
 // The same deposit (same fixed-point values) with shared-memory accumulation:
@@ -155,10 +186,8 @@ __global__ void k_deposit_tracers(Dims d, const double* __restrict__ ox,
 // held in shared memory, then adds the non-zero cells of that copy to the
 // grid.  A tracer whose stencil leaves the copy adds to the grid directly.
 // The fixed-point sums are integers, so the result is bit-identical to
-// k_deposit_tracers while the grid sees ~4x fewer atomics.  Per tracer the
-// eight corner charges cost 17 FP64 operations (the scaled mass w * 2^F
-// folded into the two x weights, then 4 x-y and 8 corner products) and one
-// conversion each.
+// k_deposit_tracers while the grid sees ~4x fewer atomics.  The corner
+// charges are cic_charges' exact integer split of the tracer's mass.
 constexpr int DTI = 8, DTJ = 16, DTK = 32, DH = 2;
 constexpr int DRI = DTI + 2 * DH, DRJ = DTJ + 2 * DH, DRK = DTK + 2 * DH;
 constexpr int DCELLS = DRI * DRJ * DRK;
@@ -179,24 +208,14 @@ __global__ void __launch_bounds__(256) k_deposit_tracers_tiled(Dims d, const dou
         const int li = q / (DTJ * DTK), lj = (q / DTK) % DTJ, lk = q % DTK;
         const int i = ti + li, j = tj + lj, k = tk + lk;
         const int c = cell_index(d, i, j, k);
-        int i0, j0, k0;
-        double fx, fy, fz;
-        cic_offset(i, ox[c], i0, fx);
-        cic_offset(j, oy[c], j0, fy);
-        cic_offset(k, oz[c], k0, fz);
-        // the mass in fixed-point units folded into the x weights first:
-        // msc fx and msc (1 - fx) = msc - msc fx, then x-y pairs, then corners
-        const double msc = w[c] * scale;
-        const double mx1 = msc * fx, mx0 = msc - mx1;
-        const double wy0 = 1.0 - fy, wz0 = 1.0 - fz;
+        const CicCharges ch = cic_charges(i, j, k, ox[c], oy[c], oz[c], w[c], scale);
+        const int i0 = ch.i0, j0 = ch.j0, k0 = ch.k0;
         const int bi = i0 - ti + DH, bj = j0 - tj + DH, bk = k0 - tk + DH;
         const bool local = bi >= 0 && bi + 1 < DRI && bj >= 0 && bj + 1 < DRJ && bk >= 0 && bk + 1 < DRK;
         for (int di = 0; di < 2; ++di) {
-            const double wx = di ? mx1 : mx0;
             for (int dj = 0; dj < 2; ++dj) {
-                const double wxy = wx * (dj ? fy : wy0);
                 for (int dk = 0; dk < 2; ++dk) {
-                    const unsigned long long qv = (unsigned long long)llrint(wxy * (dk ? fz : wz0));
+                    const unsigned long long qv = ch.c[di][dj][dk];
                     if (local)
                         atomicAdd(&acc[RC_OFF(((bi + di) * DRJ + (bj + dj)) * DRK + (bk + dk), DCELLS, 401)], qv);
                     else
