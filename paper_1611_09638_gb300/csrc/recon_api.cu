@@ -573,9 +573,11 @@ void advance(Handle* H, const CtlHandles& h) {
         launch_mass_literal(H->d, H->e6, H->dphi, alpha, H->m, H->v3m, H->st);
         launch_phi_advance(n, alpha, H->dphi, H->scal + SC_SUM_DPHI, H->phi, H->phi32, H->st);
     } else {
-        launch_node_velocity(H->d, H->e6, H->dphi, H->v3, H->v3 + n, H->v3 + 2 * (size_t)n, H->st);
-        launch_advance(H->d, H->v3, H->v3 + n, H->v3 + 2 * (size_t)n, alpha, H->dphi,
-                       H->scal + SC_SUM_DPHI, H->ox, H->oy, H->oz, H->phi, H->phi32, H->st);
+        // the node displacements alpha V in fixed point, in the v3 buffer
+        long long* d3 = reinterpret_cast<long long*>(H->v3);
+        launch_node_displacement(H->d, H->e6, H->dphi, alpha, d3, d3 + n, d3 + 2 * (size_t)n, H->st);
+        launch_advance(H->d, d3, d3 + n, d3 + 2 * (size_t)n, alpha, H->dphi, H->scal + SC_SUM_DPHI,
+                       H->ox, H->oy, H->oz, H->phi, H->phi32, H->st);
     }
     launch_ctl_step_end(H->ctl, H->p.k_max, h, H->st);
 }

@@ -292,9 +292,13 @@ void launch_limiter(const Dims& d, const LimiterParams& lp, const double* e6, co
                     cudaStream_t st);
 void launch_node_velocity(const Dims& d, const double* e6, const double* dphi, double* vx,
                           double* vy, double* vz, cudaStream_t st);
-// Tracers move by -alpha V(xi) (CIC-interpolated); phi += alpha (dphi - mean),
-// mean = *sum_dphi / cells.
-void launch_advance(const Dims& d, const double* vx, const double* vy, const double* vz,
+// The step's node displacements alpha V in fixed point (2^-51 cells), for
+// launch_advance.
+void launch_node_displacement(const Dims& d, const double* e6, const double* dphi, const double* alpha,
+                              long long* dx, long long* dy, long long* dz, cudaStream_t st);
+// Tracers move by -alpha V(xi) (the fixed-point displacements CIC-interpolated
+// in integer arithmetic); phi += alpha (dphi - mean), mean = *sum_dphi / cells.
+void launch_advance(const Dims& d, const long long* dx, const long long* dy, const long long* dz,
                     const double* alpha, const double* dphi, const double* sum_dphi, double* ox,
                     double* oy, double* oz, double* phi, float* phi32, cudaStream_t st);
 // App. A's linear density update: m += alpha d_mu(m (e^-1)^{mu nu} d_nu dphi)

@@ -36,38 +36,50 @@ __device__ inline void cic_abs(double x, int n, int& i0, double& f) {
 }
 
 // The eight CIC corner charges of one tracer in fixed point.  The offset of
-// the tracer from its home node is rounded on each axis to 2^-48 of a cell,
-// q = llrint(off 2^48): the lower node is home + (q >> 48) (floor) and the
-// fraction f = q mod 2^48.  The mass M = llrint(w scale) is split exactly,
-// first along x into M1 = floor(M f_x / 2^48) and M0 = M - M1, then each part
+// the tracer from its home node is rounded on each axis to 2^-52 of a cell
+// (fixed_axis): the lower node is home + floor and f the fraction in units of
+// 2^-52.  The mass M = llrint(w scale) is split exactly,
+// first along x into M1 = M f_x / 2^52 rounded to nearest and M0 = M - M1, then each part
 // along y, then along z, so the charges are non-negative integers that sum to
 // M exactly (mass conservation per tracer).  The splits are 64 x 64-bit
 // integer multiplies (upper halves): the FP64 work per tracer is four
 // scalings and four conversions, against some 35 FP64 instructions for FP64
 // corner weights.  The rounding of a charge is below one unit (1 / scale) of
 // the fixed point, like llrint of an FP64 product, and the position's below
-// 2^-49 cells.
+// 2^-53 cells, the rounding of an FP64 offset between 1/2 and 1 cell.
 struct CicCharges {
     int i0, j0, k0;               // lower corner
     unsigned long long c[2][2][2];  // charges at (i0 + di, j0 + dj, k0 + dk)
 };
 
-__device__ inline void split_fixed(unsigned long long m, unsigned long long f48, unsigned long long& lo,
+constexpr int kFracBits = 52;
+
+// The fixed-point position of a tracer along one axis: the offset from its
+// home node rounded to 2^-kFracBits of a cell (|off| < 2^11), as the lower
+// node and the fraction f in [0, 2^kFracBits).
+__device__ inline void fixed_axis(int home, double off, int& i0, unsigned long long& f) {
+    const long long q = __double2ll_rn(off * 4503599627370496.0);  // off 2^52
+    i0 = home + (int)(q >> kFracBits);                              // floor
+    f = (unsigned long long)q & ((1ull << kFracBits) - 1);
+}
+
+// m f / 2^52 rounded to nearest (the upper half of m (f 2^12), plus one where
+// the lower half is at least 2^63) and the rest m - that: an exact split
+// without a bias toward either side.
+__device__ inline void split_fixed(unsigned long long m, unsigned long long f, unsigned long long& lo,
                                    unsigned long long& hi) {
-    hi = __umul64hi(m, f48 << 16);  // floor(m f / 2^48)
+    const unsigned long long y = f << (64 - kFracBits);
+    hi = __umul64hi(m, y) + ((m * y) >> 63);
     lo = m - hi;
 }
 
 __device__ inline CicCharges cic_charges(int i, int j, int k, double ox, double oy, double oz, double w,
                                          double scale) {
-    constexpr double two48 = 281474976710656.0;  // 2^48
-    constexpr unsigned long long mask48 = (1ull << 48) - 1;
-    const long long qx = __double2ll_rn(ox * two48), qy = __double2ll_rn(oy * two48);
-    const long long qz = __double2ll_rn(oz * two48);
     CicCharges r;
-    r.i0 = i + (int)(qx >> 48), r.j0 = j + (int)(qy >> 48), r.k0 = k + (int)(qz >> 48);
-    const unsigned long long fx = (unsigned long long)qx & mask48, fy = (unsigned long long)qy & mask48;
-    const unsigned long long fz = (unsigned long long)qz & mask48;
+    unsigned long long fx, fy, fz;
+    fixed_axis(i, ox, r.i0, fx);
+    fixed_axis(j, oy, r.j0, fy);
+    fixed_axis(k, oz, r.k0, fz);
     const unsigned long long M = (unsigned long long)__double2ll_rn(w * scale);
     unsigned long long mx[2], mxy[2][2];
     split_fixed(M, fx, mx[0], mx[1]);
@@ -562,6 +574,42 @@ __global__ void k_node_velocity(Dims d, const double* __restrict__ e6,
     vz[c] = (Axz * gx + Ayz * gy + Azz * gz) * hinv;
 }
 
+// The step's node displacement alpha V = alpha e^-1 G (V as in
+// k_node_velocity) in fixed point with kDispBits fractional bits, for the
+// tracer advance's integer interpolation.  The step limiter bounds it by
+// d_max / lambda_floor (50 cells at the defaults); values beyond kDispMax
+// cells, which no valid step produces, are held at that bound.
+constexpr int kDispBits = 53;
+constexpr long long kDispMax = 1ll << (kDispBits + 7);  // 128 cells
+__global__ void k_node_displacement(Dims d, const double* __restrict__ e6,
+                                    const double* __restrict__ dphi, const double* __restrict__ alpha_p,
+                                    long long* __restrict__ dx, long long* __restrict__ dy,
+                                    long long* __restrict__ dz) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= d.cells) return;
+    int i, j, k;
+    cell_coords(d, c, i, j, k);
+    const size_t n = (size_t)d.cells;
+    Sym3 e;
+    e.xx = e6[c], e.yy = e6[n + c], e.zz = e6[2 * n + c];
+    e.xy = e6[3 * n + c], e.xz = e6[4 * n + c], e.yz = e6[5 * n + c];
+    const double gx = dphi[cell_index(d, i + 1, j, k)] - dphi[cell_index(d, i - 1, j, k)];
+    const double gy = dphi[cell_index(d, i, j + 1, k)] - dphi[cell_index(d, i, j - 1, k)];
+    const double gz = dphi[cell_index(d, i, j, k + 1)] - dphi[cell_index(d, i, j, k - 1)];
+    const double Axx = e.yy * e.zz - e.yz * e.yz, Ayy = e.xx * e.zz - e.xz * e.xz;
+    const double Azz = e.xx * e.yy - e.xy * e.xy, Axy = e.xz * e.yz - e.xy * e.zz;
+    const double Axz = e.xy * e.yz - e.yy * e.xz, Ayz = e.xy * e.xz - e.xx * e.yz;
+    // 1/2 of the central differences, alpha and 2^kDispBits in one factor
+    const double hinv = (0.5 * 9007199254740992.0) * *alpha_p / (e.xx * Axx + e.xy * Axy + e.xz * Axz);
+    auto fix = [](double v) {
+        const long long q = __double2ll_rn(v);  // saturates beyond the int64 range
+        return q > kDispMax ? kDispMax : (q < -kDispMax ? -kDispMax : q);
+    };
+    dx[c] = fix((Axx * gx + Axy * gy + Axz * gz) * hinv);
+    dy[c] = fix((Axy * gx + Ayy * gy + Ayz * gz) * hinv);
+    dz[c] = fix((Axz * gx + Ayz * gy + Azz * gz) * hinv);
+}
+
 // App. A's linear density update (the variant that carries m instead of
 // re-depositing tracers): K = m e^-1 at every node, e = I + Hess phi the
 // stored triad (symmetric, so K is too: xx, yy, zz, xy, xz, yz).
@@ -648,8 +696,25 @@ __global__ void k_phi_advance(int cells, const double* __restrict__ alpha_p,
     phi32[c] = (float)pn;
 }
 
-__global__ void k_advance(Dims d, const double* __restrict__ vx, const double* __restrict__ vy,
-                          const double* __restrict__ vz, const double* __restrict__ alpha_p,
+// (b - a) f / 2^52 rounded to nearest, added to a: one step of linear
+// interpolation of fixed-point values with a fraction f of fixed_axis
+// (|b - a| <= 2^61; the 128-bit product's upper half is the floor, its lower
+// half's top bit the rounding).
+__device__ inline long long lerp_fixed(long long a, long long b, unsigned long long f) {
+    const long long x = (b - a) * 2, y = (long long)(f << (63 - kFracBits));
+    const unsigned long long low = (unsigned long long)x * (unsigned long long)y;
+    return a + __mul64hi(x, y) + (long long)(low >> 63);
+}
+
+// Tracers move by -alpha V(xi), V CIC-interpolated from the nodes, in fixed
+// point: the offsets are rounded to 2^-52 cell as in cic_charges, and the
+// node displacements alpha V (k_node_displacement, 2^-kDispBits cells) are
+// interpolated by integer linear interpolation along k, then j, then i, each
+// step rounded to nearest (rounding down instead biases every move by about a
+// unit the same way, which the 40-step 32^3 trajectory amplified to 3e-6 in
+// R_k); the result leaves as one FP64 subtraction per axis.  phi += alpha (dphi - mean), mean = *sum_dphi / cells.
+__global__ void k_advance(Dims d, const long long* __restrict__ dx, const long long* __restrict__ dy,
+                          const long long* __restrict__ dz, const double* __restrict__ alpha_p,
                           const double* __restrict__ dphi, const double* __restrict__ sum_dphi,
                           double* __restrict__ ox, double* __restrict__ oy,
                           double* __restrict__ oz, double* __restrict__ phi,
@@ -661,23 +726,31 @@ __global__ void k_advance(Dims d, const double* __restrict__ vx, const double* _
     cell_coords(d, c, i, j, k);
     const double px = ox[c], py = oy[c], pz = oz[c];
     int i0, j0, k0;
-    double fx, fy, fz;
-    cic_offset(i, px, i0, fx);
-    cic_offset(j, py, j0, fy);
-    cic_offset(k, pz, k0, fz);
-    double ux = 0.0, uy = 0.0, uz = 0.0;
-    for (int di = 0; di < 2; ++di) {
-        const double wx = di ? fx : 1.0 - fx;
-        for (int dj = 0; dj < 2; ++dj) {
-            const double wy = dj ? fy : 1.0 - fy;
-            for (int dk = 0; dk < 2; ++dk) {
-                const double w = wx * wy * (dk ? fz : 1.0 - fz);
-                const int n = cell_index(d, i0 + di, j0 + dj, k0 + dk);
-                ux += w * vx[n], uy += w * vy[n], uz += w * vz[n];
-            }
+    unsigned long long fx, fy, fz;
+    fixed_axis(i, px, i0, fx);
+    fixed_axis(j, py, j0, fy);
+    fixed_axis(k, pz, k0, fz);
+    int nb[2][2][2];
+#pragma unroll
+    for (int di = 0; di < 2; ++di)
+#pragma unroll
+        for (int dj = 0; dj < 2; ++dj)
+#pragma unroll
+            for (int dk = 0; dk < 2; ++dk) nb[di][dj][dk] = cell_index(d, i0 + di, j0 + dj, k0 + dk);
+    auto interp = [&](const long long* __restrict__ D) {
+        long long cx[2];
+#pragma unroll
+        for (int di = 0; di < 2; ++di) {
+            const long long c0 = lerp_fixed(D[nb[di][0][0]], D[nb[di][0][1]], fz);
+            const long long c1 = lerp_fixed(D[nb[di][1][0]], D[nb[di][1][1]], fz);
+            cx[di] = lerp_fixed(c0, c1, fy);
         }
-    }
-    ox[c] = px - alpha * ux, oy[c] = py - alpha * uy, oz[c] = pz - alpha * uz;
+        return lerp_fixed(cx[0], cx[1], fx);
+    };
+    constexpr double unit = 1.0 / 9007199254740992.0;  // 2^-kDispBits
+    ox[c] = fma(-(double)interp(dx), unit, px);
+    oy[c] = fma(-(double)interp(dy), unit, py);
+    oz[c] = fma(-(double)interp(dz), unit, pz);
     const double mean = *sum_dphi * inv_pow2(d.cells);
     const double pn = phi[c] + alpha * (dphi[c] - mean);
     phi[c] = pn;
@@ -852,11 +925,17 @@ void launch_node_velocity(const Dims& d, const double* e6, const double* dphi, d
     k_node_velocity<<<nblocks(d.cells), kThreads, 0, st>>>(d, e6, dphi, vx, vy, vz);
 }
 
-void launch_advance(const Dims& d, const double* vx, const double* vy, const double* vz,
+void launch_node_displacement(const Dims& d, const double* e6, const double* dphi, const double* alpha,
+                              long long* dx, long long* dy, long long* dz, cudaStream_t st) {
+    launch_counter()++;
+    k_node_displacement<<<nblocks(d.cells), kThreads, 0, st>>>(d, e6, dphi, alpha, dx, dy, dz);
+}
+
+void launch_advance(const Dims& d, const long long* dx, const long long* dy, const long long* dz,
                     const double* alpha, const double* dphi, const double* sum_dphi, double* ox,
                     double* oy, double* oz, double* phi, float* phi32, cudaStream_t st) {
     launch_counter()++;
-    k_advance<<<nblocks(d.cells), kThreads, 0, st>>>(d, vx, vy, vz, alpha, dphi, sum_dphi, ox, oy,
+    k_advance<<<nblocks(d.cells), kThreads, 0, st>>>(d, dx, dy, dz, alpha, dphi, sum_dphi, ox, oy,
                                                      oz, phi, phi32);
 }
 
