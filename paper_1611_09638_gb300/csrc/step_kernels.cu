@@ -712,7 +712,8 @@ __device__ inline long long lerp_fixed(long long a, long long b, unsigned long l
 // interpolated by integer linear interpolation along k, then j, then i, each
 // step rounded to nearest (rounding down instead biases every move by about a
 // unit the same way, which the 40-step 32^3 trajectory amplified to 3e-6 in
-// R_k); the result leaves as one FP64 subtraction per axis.  phi += alpha (dphi - mean), mean = *sum_dphi / cells.
+// R_k); the result leaves as one FP64 subtraction per axis.
+// phi += alpha (dphi - mean), mean = *sum_dphi / cells.
 __global__ void k_advance(Dims d, const long long* __restrict__ dx, const long long* __restrict__ dy,
                           const long long* __restrict__ dz, const double* __restrict__ alpha_p,
                           const double* __restrict__ dphi, const double* __restrict__ sum_dphi,
