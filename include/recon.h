@@ -234,7 +234,10 @@ int recon_create(void** out, const recon_params* p, void* cuda_stream);
  * the CIC deposit accumulates in 64-bit fixed point, so the result does not
  * depend on the order of the particles.  RECON_GRID: data holds the density on
  * the grid (np must equal the cell count), mass must be NULL.  Rejects
- * NaN/Inf, negative masses or densities, and zero total mass. */
+ * NaN/Inf, negative masses or densities, and zero total mass.  Particle
+ * arrays in host memory (or on another device) are copied into a device
+ * staging buffer that the handle keeps, sized to the largest such input,
+ * until recon_destroy. */
 int recon_deposit(void* h, int mode, const double* data, const double* mass, int64_t np);
 
 /* Run the whole moving-mesh solve from phi = 0 on the deposited density

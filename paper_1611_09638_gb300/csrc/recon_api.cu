@@ -67,6 +67,9 @@ struct Handle {
     double *phi = nullptr, *m = nullptr, *a64 = nullptr, *t = nullptr, *s = nullptr;
     double *phidot = nullptr, *dphi = nullptr, *v3 = nullptr;  // v3: 3 x cells
     double* phidot_prev = nullptr;  // warm_start = 2: phidot of the step before the last
+    // staging of host particle inputs (grown to the largest, kept until destroy)
+    void* stage = nullptr;
+    size_t stage_bytes = 0;
     double* e6 = nullptr;  // triad I + Hess phi of the current step, 6 x cells
     double* inv64 = nullptr;  // FP64 mode: 1 / diagonal of the finest level
     double* F64 = nullptr;    // face coefficients (a_c + a_{c+e}) / 2 of the finest level, 3 x cells
@@ -152,6 +155,8 @@ int dalloc(Handle* H, T** p, size_t count) {
 void free_all(Handle* H) {
     for (void* q : H->allocs) cudaFree(q);
     H->allocs.clear();
+    if (H->stage) cudaFree(H->stage);
+    H->stage = nullptr, H->stage_bytes = 0;
     if (H->hscal) cudaFreeHost(H->hscal);
     if (H->ev0) cudaEventDestroy(H->ev0);
     if (H->ev1) cudaEventDestroy(H->ev1);
@@ -1384,21 +1389,29 @@ int recon_deposit(void* hp, int mode, const double* data, const double* mass, in
         launch_validate_grid(n, H->rho, H->part[0], H->part[1], H->st);
     } else if (mode == RECON_PARTICLES) {
         if (np <= 0) return fail(RECON_E_INVALID, "no particles");
-        // host inputs (and another device's) are staged through a temporary
-        // device buffer
+        // host inputs (and another device's) are staged through a device
+        // buffer the handle keeps (grown here when an input is larger; the
+        // old one is released once the stream has finished with it)
         const double* dpos = data;
         const double* dmass = mass;
-        void* stage = nullptr;
         bool host_pos = !is_local_device_ptr(data, H->device),
              host_mass = mass && !is_local_device_ptr(mass, H->device);
         size_t bytes = (host_pos ? 3 * sizeof(double) * np : 0) + (host_mass ? sizeof(double) * np : 0);
         if (bytes) {
-            cudaError_t e = cudaMallocAsync(&stage, bytes, H->st);
-            if (e != cudaSuccess) {
-                cudaGetLastError();
-                return fail(RECON_E_OOM, "staging buffer of %zu bytes failed", bytes);
+            if (bytes > H->stage_bytes) {
+                if (H->stage) {
+                    CK(cudaStreamSynchronize(H->st));
+                    cudaFree(H->stage);
+                    H->stage = nullptr, H->stage_bytes = 0;
+                }
+                if (cudaMalloc(&H->stage, bytes) != cudaSuccess) {
+                    cudaGetLastError();
+                    H->stage = nullptr;
+                    return fail(RECON_E_OOM, "staging buffer of %zu bytes failed", bytes);
+                }
+                H->stage_bytes = bytes;
             }
-            char* q = (char*)stage;
+            char* q = (char*)H->stage;
             if (host_pos) {
                 CK(cudaMemcpyAsync(q, data, 3 * sizeof(double) * np, cudaMemcpyDefault, H->st));
                 dpos = (const double*)q;
@@ -1423,7 +1436,6 @@ int recon_deposit(void* hp, int mode, const double* data, const double* mass, in
             launch_fix_to_double(n, H->mfix, 1.0 / scale, H->rho, H->st);
             launch_validate_grid(n, H->rho, H->part[0], H->part[1], H->st);
         }
-        if (stage) cudaFreeAsync(stage, H->st);
         if (rc) {
             cudaStreamSynchronize(H->st);
             return rc;

@@ -28,13 +28,6 @@ __device__ inline double inv_pow2(int n) {
     return __longlong_as_double((long long)(1023 - (__ffs(n) - 1)) << 52);
 }
 
-__device__ inline void cic_abs(double x, int n, int& i0, double& f) {
-    const double u = x - (double)n * floor(x / (double)n);
-    const double fl = floor(u);
-    f = u - fl;
-    i0 = (int)fl;
-}
-
 // The eight CIC corner charges of one tracer in fixed point.  The offset of
 // the tracer from its home node is rounded on each axis to 2^-52 of a cell
 // (fixed_axis): the lower node is home + floor and f the fraction in units of
@@ -73,14 +66,9 @@ __device__ inline void split_fixed(unsigned long long m, unsigned long long f, u
     lo = m - hi;
 }
 
-__device__ inline CicCharges cic_charges(int i, int j, int k, double ox, double oy, double oz, double w,
-                                         double scale) {
-    CicCharges r;
-    unsigned long long fx, fy, fz;
-    fixed_axis(i, ox, r.i0, fx);
-    fixed_axis(j, oy, r.j0, fy);
-    fixed_axis(k, oz, r.k0, fz);
-    const unsigned long long M = (unsigned long long)__double2ll_rn(w * scale);
+// The split of M over the corners for the fractions fx, fy, fz.
+__device__ inline void split_charges(unsigned long long M, unsigned long long fx, unsigned long long fy,
+                                     unsigned long long fz, CicCharges& r) {
     unsigned long long mx[2], mxy[2][2];
     split_fixed(M, fx, mx[0], mx[1]);
 #pragma unroll
@@ -89,13 +77,19 @@ __device__ inline CicCharges cic_charges(int i, int j, int k, double ox, double 
 #pragma unroll
         for (int dj = 0; dj < 2; ++dj) split_fixed(mxy[di][dj], fz, r.c[di][dj][0], r.c[di][dj][1]);
     }
+}
+
+__device__ inline CicCharges cic_charges(int i, int j, int k, double ox, double oy, double oz, double w,
+                                         double scale) {
+    CicCharges r;
+    unsigned long long fx, fy, fz;
+    fixed_axis(i, ox, r.i0, fx);
+    fixed_axis(j, oy, r.j0, fy);
+    fixed_axis(k, oz, r.k0, fz);
+    split_charges((unsigned long long)__double2ll_rn(w * scale), fx, fy, fz, r);
     return r;
 }
 
-__device__ inline void atomic_add_fixed(unsigned long long* p, double v, double scale) {
-    const long long q = llrint(v * scale);
-    atomicAdd(p, (unsigned long long)q);
-}
 
 // ---------------------------------------------------------------- kernels
 
@@ -134,23 +128,20 @@ __global__ void k_deposit_particles(Dims d, int64_t np, const double* __restrict
                                     unsigned long long* __restrict__ mfix) {
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= np) return;
-    int i0, j0, k0;
-    double fx, fy, fz;
-    cic_abs(pos[3 * p] * inv_h, d.n0, i0, fx);
-    cic_abs(pos[3 * p + 1] * inv_h, d.n1, j0, fy);
-    cic_abs(pos[3 * p + 2] * inv_h, d.n2, k0, fz);
+    // the position wrapped into [0, n) grid units, then as fixed_axis does
+    // for an offset from node 0 (the same integer charges as the tracers')
+    auto wrap = [](double x, int n) { return x - (double)n * floor(x / (double)n); };
+    CicCharges q;
+    unsigned long long fx, fy, fz;
+    fixed_axis(0, wrap(pos[3 * p] * inv_h, d.n0), q.i0, fx);
+    fixed_axis(0, wrap(pos[3 * p + 1] * inv_h, d.n1), q.j0, fy);
+    fixed_axis(0, wrap(pos[3 * p + 2] * inv_h, d.n2), q.k0, fz);
     const double m = mass ? mass[p] : 1.0;
-    for (int di = 0; di < 2; ++di) {
-        const double wx = di ? fx : 1.0 - fx;
-        for (int dj = 0; dj < 2; ++dj) {
-            const double wy = dj ? fy : 1.0 - fy;
-            for (int dk = 0; dk < 2; ++dk) {
-                const double wz = dk ? fz : 1.0 - fz;
-                atomic_add_fixed(&mfix[cell_index(d, i0 + di, j0 + dj, k0 + dk)], m * (wx * wy * wz),
-                                 scale);
-            }
-        }
-    }
+    split_charges((unsigned long long)__double2ll_rn(m * scale), fx, fy, fz, q);
+    for (int di = 0; di < 2; ++di)
+        for (int dj = 0; dj < 2; ++dj)
+            for (int dk = 0; dk < 2; ++dk)
+                atomicAdd(&mfix[cell_index(d, q.i0 + di, q.j0 + dj, q.k0 + dk)], q.c[di][dj][dk]);
 }
 
 __global__ void k_fix_to_double(int cells, unsigned long long* __restrict__ mfix, double inv_scale,
