@@ -330,7 +330,12 @@ def run_gb300(a):
 
     e2e = None
     if not a.no_e2e:
-        R = Recon((n, n, n), box=W.box, precision="mixed", k_max=a.k_max, **mg_kw)
+        # the same settings as the timed solves, with the V-cycles per defect
+        # correction their handle's tuner chose
+        kw_e2e = dict(mg_kw)
+        if kw_e2e.pop("tune_inner", None):
+            kw_e2e["inner_vcycles"] = s0.inner_vcycles
+        R = Recon((n, n, n), box=W.box, precision="mixed", k_max=a.k_max, **kw_e2e)
         pin_pos = torch.from_numpy(pos_host).pin_memory()
         out = torch.empty((n, n, n), dtype=torch.float64).pin_memory()
         for _ in range(1):
@@ -344,7 +349,7 @@ def run_gb300(a):
         k2 = max(1, min(a.steps, 3))
         for _ in range(k2):
             R.deposit_particles(pin_pos)
-            R.solve(record=False)
+            st_e2e = R.solve(record=False)
             R.field("delta_r", out=out)
         e1.record(stream)
         barrier()
@@ -354,6 +359,7 @@ def run_gb300(a):
         e2e = {"value": whole_job_mcells(cells, world, e2e_ms), "unit": "Mcells/s",
                "h2d_bytes_per_step": int(pos_host.nbytes), "d2h_bytes_per_step": int(out.numel() * 8),
                "ms_per_step": e2e_ms, "host_wall_ms_per_step": wall_ms,
+               "steps_per_solve": st_e2e.steps, "vcycles_per_solve": st_e2e.vcycles,
                "path": "recon_deposit(host pinned particles) + recon_solve + recon_field(delta_r -> host pinned)"}
 
     adj = None if a.no_adjoint else adjoint_timing(a, stream, barrier)
