@@ -259,7 +259,35 @@ def run_gb300(a):
     both_kw = {} if a.warm_start is None else {"warm_start": a.warm_start}
     mg_kw.update(both_kw)
 
-    def timed(precision, steps, warmup, profile=False, inner=None):
+    def run_e2e(R):
+        """The same solve end to end through the public calls, on the timed
+        handle: host pinned particles in, delta_r to host pinned memory out."""
+        pin_pos = torch.from_numpy(pos_host).pin_memory()
+        out = torch.empty((n, n, n), dtype=torch.float64).pin_memory()
+        R.deposit_particles(pin_pos)
+        R.solve(record=False)
+        R.field("delta_r", out=out)
+        barrier()
+        t0 = time.perf_counter()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        k2 = max(1, min(a.steps, 3))
+        for _ in range(k2):
+            R.deposit_particles(pin_pos)
+            st_e2e = R.solve(record=False)
+            R.field("delta_r", out=out)
+        e1.record(stream)
+        barrier()
+        e2e_ms = max_over_ranks(e0.elapsed_time(e1) / k2, world, "cuda")
+        wall_ms = (time.perf_counter() - t0) * 1e3 / k2
+        return {"value": whole_job_mcells(cells, world, e2e_ms), "unit": "Mcells/s",
+                "h2d_bytes_per_step": int(pos_host.nbytes), "d2h_bytes_per_step": int(out.numel() * 8),
+                "ms_per_step": e2e_ms, "host_wall_ms_per_step": wall_ms,
+                "steps_per_solve": st_e2e.steps, "vcycles_per_solve": st_e2e.vcycles,
+                "path": "recon_deposit(host pinned particles) + recon_solve + "
+                        "recon_field(delta_r -> host pinned), on the timed handle"}
+
+    def timed(precision, steps, warmup, profile=False, inner=None, then=None):
         kw = dict(mg_kw) if precision == "mixed" else {}
         kw.update(both_kw)
         if inner:  # the count the timed solves' handle chose
@@ -279,11 +307,15 @@ def run_gb300(a):
             e1.record(stream)
             barrier()
         ms = e0.elapsed_time(e1) / steps
+        extra = then(R) if then else None
         R.close()
+        if then:
+            return ms, stats, clk.summary(), extra
         return ms, stats, clk.summary()
 
     # the product path: each solve is one CUDA graph (device-side control)
-    ms_mixed, st_mixed, clocks = timed("mixed", a.steps, a.warmup)
+    ms_mixed, st_mixed, clocks, e2e = timed("mixed", a.steps, a.warmup,
+                                            then=None if a.no_e2e else run_e2e)
     # one more solve on the host-driven loop with CUDA events around every
     # finest-level sweep, for the roofline of the dominant kernel
     _, st_prof, _ = timed("mixed", 1, 0, profile=True, inner=st_mixed[0].inner_vcycles)
@@ -327,40 +359,6 @@ def run_gb300(a):
             "timed_in": "one extra solve with CUDA events around each finest-level sweep"}
     if traffic_note:
         roof["traffic_note"] = traffic_note
-
-    e2e = None
-    if not a.no_e2e:
-        # the same settings as the timed solves, with the V-cycles per defect
-        # correction their handle's tuner chose
-        kw_e2e = dict(mg_kw)
-        if kw_e2e.pop("tune_inner", None):
-            kw_e2e["inner_vcycles"] = s0.inner_vcycles
-        R = Recon((n, n, n), box=W.box, precision="mixed", k_max=a.k_max, **kw_e2e)
-        pin_pos = torch.from_numpy(pos_host).pin_memory()
-        out = torch.empty((n, n, n), dtype=torch.float64).pin_memory()
-        for _ in range(1):
-            R.deposit_particles(pin_pos)
-            R.solve(record=False)
-            R.field("delta_r", out=out)
-        barrier()
-        t0 = time.perf_counter()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        k2 = max(1, min(a.steps, 3))
-        for _ in range(k2):
-            R.deposit_particles(pin_pos)
-            st_e2e = R.solve(record=False)
-            R.field("delta_r", out=out)
-        e1.record(stream)
-        barrier()
-        e2e_ms = max_over_ranks(e0.elapsed_time(e1) / k2, world, "cuda")
-        wall_ms = (time.perf_counter() - t0) * 1e3 / k2
-        R.close()
-        e2e = {"value": whole_job_mcells(cells, world, e2e_ms), "unit": "Mcells/s",
-               "h2d_bytes_per_step": int(pos_host.nbytes), "d2h_bytes_per_step": int(out.numel() * 8),
-               "ms_per_step": e2e_ms, "host_wall_ms_per_step": wall_ms,
-               "steps_per_solve": st_e2e.steps, "vcycles_per_solve": st_e2e.vcycles,
-               "path": "recon_deposit(host pinned particles) + recon_solve + recon_field(delta_r -> host pinned)"}
 
     adj = None if a.no_adjoint else adjoint_timing(a, stream, barrier)
     mocks = None if a.no_mocks else mocks_timing(a, stream, barrier)
