@@ -150,8 +150,10 @@ typedef struct {
                             and 8 FP32 V-cycles per FP64 defect correction and
                             keeps the fastest for this and later solves (the
                             solution is the same to the stopping residual; the
-                            choice follows the timing).  Ignored with profile.
-                            0 (default): keep inner_vcycles.                    */
+                            choice follows the timing); 2: the same over every
+                            smoothing schedule (nu1, nu2) in (1,1), (1,2),
+                            (2,1), (2,2) as well.  Ignored with profile.
+                            0 (default): keep inner_vcycles, nu1 and nu2.       */
     int group_max;       /* RECON_MIXED: the most FP32 V-cycles one FP64 defect
                             correction may run (inner_vcycles .. 64).  Above
                             inner_vcycles the V-cycles run in blocks of
@@ -202,6 +204,7 @@ typedef struct {
                             write u), for the roofline                          */
     int inner_vcycles;   /* RECON_MIXED: FP32 V-cycles per FP64 defect correction
                             the solve used (params.tune_inner may have chosen it) */
+    int nu1, nu2;        /* pre / post sweeps per level the solve used           */
 } recon_stats;
 
 /* Fill *p with the defaults above for an n0 x n1 x n2 grid (grid units,

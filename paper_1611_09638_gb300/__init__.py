@@ -64,6 +64,8 @@ class SolveStats:
     smooth_sweeps: int = 0
     smooth_bytes: float = 0.0
     inner_vcycles: int = 0
+    nu1: int = 0
+    nu2: int = 0
     alpha: np.ndarray = field(default=None)
     Rk: np.ndarray = field(default=None)
     ncycles: np.ndarray = field(default=None)
@@ -135,7 +137,7 @@ class Recon:
         k = st.steps
         out = SolveStats(rc, k, st.vcycles, st.R0, st.R, st.min_det, st.min_lambda0,
                          st.max_delta_r, st.mass_error, st.ms, st.launches, st.smooth_ms,
-                         st.smooth_sweeps, st.smooth_bytes, st.inner_vcycles)
+                         st.smooth_sweeps, st.smooth_bytes, st.inner_vcycles, st.nu1, st.nu2)
         if record:
             out.alpha, out.ncycles, out.relres = arrs["alpha"][:k], arrs["ncycles"][:k], arrs["relres"][:k]
             stopped = rc in (RECON_OK, _abi.RECON_STALLED)

@@ -54,7 +54,7 @@ class recon_stats(C.Structure):
         ("max_delta_r", C.c_double), ("mass_error", C.c_double), ("ms", C.c_double),
         ("alpha", _D), ("Rk", _D), ("ncycles", _I), ("relres", _D),
         ("launches", C.c_longlong), ("smooth_ms", C.c_double), ("smooth_sweeps", C.c_int),
-        ("smooth_bytes", C.c_double), ("inner_vcycles", C.c_int),
+        ("smooth_bytes", C.c_double), ("inner_vcycles", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int),
     ]
 
 

@@ -322,7 +322,7 @@ int check_params(const recon_params* p) {
     if (p->coarse_faces != 0 && p->coarse_faces != 1) return fail(RECON_E_INVALID, "coarse_faces must be 0 or 1");
     if (p->coarse_faces == 1 && (p->precision != RECON_MIXED || !faces_apply(p)))
         return fail(RECON_E_INVALID, "coarse_faces = 1 needs RECON_MIXED on a cubic grid of at least 64^3");
-    if (p->tune_inner != 0 && p->tune_inner != 1) return fail(RECON_E_INVALID, "tune_inner must be 0 or 1");
+    if (p->tune_inner < 0 || p->tune_inner > 2) return fail(RECON_E_INVALID, "tune_inner must be 0, 1 or 2");
     if (p->tma != 0 && p->tma != 1) return fail(RECON_E_INVALID, "tma must be 0 or 1");
     if (p->warm_start < 0 || p->warm_start > 2) return fail(RECON_E_INVALID, "warm_start must be 0, 1 or 2");
     if (p->group_max < p->inner_vcycles || p->group_max > 64)
@@ -694,11 +694,23 @@ int tune_inner_vcycles(Handle* H) {
     if (rc) return rc;
     if (!H->hctl->go_cont) return RECON_OK;  // nothing to solve at step 0
     const int cand[5] = {3, 4, 5, 6, 8};
-    int best = H->p.inner_vcycles;
+    // tune_inner = 2 also tries every smoothing schedule (nu1, nu2) of the
+    // FP32 V-cycle (the same in the per-level, single-block and cluster parts)
+    const int sched2[4][2] = {{1, 1}, {1, 2}, {2, 1}, {2, 2}};
+    const int own[1][2] = {{H->p.nu1, H->p.nu2}};
+    const int (*sched)[2] = H->p.tune_inner == 2 ? sched2 : own;
+    const int nsched = H->p.tune_inner == 2 ? 4 : 1;
+    auto set_schedule = [&](int nu1, int nu2) {
+        H->p.nu1 = H->cc.nu1 = H->cs.nu1 = nu1;
+        H->p.nu2 = H->cc.nu2 = H->cs.nu2 = nu2;
+    };
+    int best = H->p.inner_vcycles, best_s = 0;
     float best_ms = 0.f;
     for (int round = 0; round < 2; ++round)
+        for (int si = 0; si < nsched; ++si)
         for (int n : cand) {
             if (H->adaptive && n > H->p.group_max) continue;
+            set_schedule(sched[si][0], sched[si][1]);
             H->p.inner_vcycles = n;
             if (H->cyc_exec) cudaGraphExecDestroy(H->cyc_exec);
             H->cyc_exec = nullptr;
@@ -713,8 +725,9 @@ int tune_inner_vcycles(Handle* H) {
             CK(cudaEventSynchronize(H->ev1));
             float ms = 0.f;
             CK(cudaEventElapsedTime(&ms, H->ev0, H->ev1));
-            if (round == 1 && (best_ms == 0.f || ms < best_ms)) best = n, best_ms = ms;
+            if (round == 1 && (best_ms == 0.f || ms < best_ms)) best = n, best_s = si, best_ms = ms;
         }
+    set_schedule(sched[best_s][0], sched[best_s][1]);
     H->p.inner_vcycles = best;
     if (H->cyc_exec) cudaGraphExecDestroy(H->cyc_exec);
     H->cyc_exec = nullptr;
@@ -937,6 +950,7 @@ void fill_stats(Handle* H, recon_stats* stats, float ms, long long launches, boo
     stats->mass_error = std::fabs(c.last_mass - (double)H->cells) / (double)H->cells;
     stats->launches = launches;
     stats->inner_vcycles = H->mixed ? H->p.inner_vcycles : 0;
+    stats->nu1 = H->p.nu1, stats->nu2 = H->p.nu2;
     const size_t km = (size_t)std::max(H->p.k_max, 1);
     const double* Rk = H->harr;
     const double* al = H->harr + km;

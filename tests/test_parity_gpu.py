@@ -325,9 +325,10 @@ def test_per_face_coarse_levels_match_the_oracle_in_fewer_vcycles():
 
 def test_schedule_autotuner_keeps_the_solution():
     """tune_inner: the first solve times the first step's linear solve with
-    3, 4, 5, 6 and 8 FP32 V-cycles per FP64 defect correction and keeps the
-    fastest; the result matches the oracle like any fixed count, and later
-    solves reuse the choice (the same bits)."""
+    3, 4, 5, 6 and 8 FP32 V-cycles per FP64 defect correction (and, with 2,
+    every smoothing schedule) and keeps the fastest; the result matches the
+    oracle like any fixed choice, and later solves reuse the choice (the same
+    bits)."""
     n, box = 64, 100.0
     pos, _ = lpt_particles(n, box, 23, order=2)
     rho = O.cic_deposit((n, n, n), pos / (box / n))
@@ -341,6 +342,15 @@ def test_schedule_autotuner_keeps_the_solution():
     st2 = R.solve()
     assert st2.inner_vcycles == st.inner_vcycles and st2.vcycles == st.vcycles
     assert np.array_equal(R.field("phi").cpu().numpy(), phi)
+    R.close()
+    # tune_inner = 2: the smoothing schedule (nu1, nu2) is timed as well
+    R, st = _gpu_solve((n, n, n), rho, precision="mixed", k_max=3, replay_alpha=res.alpha,
+                       tune_inner=2)
+    assert st.inner_vcycles in (3, 4, 5, 6, 8) and (st.nu1, st.nu2) in ((1, 1), (1, 2), (2, 1), (2, 2))
+    assert np.all(st.relres <= 1e-8)
+    assert rel(R.field("phi").cpu().numpy(), res.phi) <= 1e-4
+    st2 = R.solve()
+    assert (st2.nu1, st2.nu2, st2.inner_vcycles) == (st.nu1, st.nu2, st.inner_vcycles)
     R.close()
 
 
