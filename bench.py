@@ -85,9 +85,10 @@ def _args():
     ap.add_argument("--stream-planes", type=int, default=None,
                     help="--launch-list: fix the planes per block of the streaming sweep and "
                          "residual restriction (no timing launches at create)")
-    ap.add_argument("--tune-inner", type=int, default=1,
+    ap.add_argument("--tune-inner", type=int, default=2,
                     help="1: each mixed-precision handle picks its FP32 V-cycles per FP64 defect "
-                         "correction by timing on its first (untimed) solve")
+                         "correction by timing on its first (untimed) solve; 2: and its smoothing "
+                         "schedule (nu1, nu2)")
     return ap.parse_args()
 
 
@@ -251,7 +252,7 @@ def run_gb300(a):
     if a.coarse_faces is not None:
         mg_kw["coarse_faces"] = a.coarse_faces
     if a.tune_inner and a.inner_vcycles is None:
-        mg_kw["tune_inner"] = 1
+        mg_kw["tune_inner"] = a.tune_inner
     if a.group_max is not None:
         mg_kw["group_max"] = a.group_max
     if a.tma is not None:
@@ -290,9 +291,9 @@ def run_gb300(a):
     def timed(precision, steps, warmup, profile=False, inner=None, then=None):
         kw = dict(mg_kw) if precision == "mixed" else {}
         kw.update(both_kw)
-        if inner:  # the count the timed solves' handle chose
+        if inner:  # the schedule the timed solves' handle chose
             kw.pop("tune_inner", None)
-            kw["inner_vcycles"] = inner
+            kw.update(inner_vcycles=inner.inner_vcycles, nu1=inner.nu1, nu2=inner.nu2)
         R = Recon((n, n, n), box=W.box, precision=precision, profile=int(profile), k_max=a.k_max, **kw)
         R.deposit_particles(pos_dev)
         for _ in range(warmup):
@@ -321,7 +322,7 @@ def run_gb300(a):
         ms_mixed, st_mixed, clocks, e2e = timed("mixed", a.steps, a.warmup, then=run_e2e)
     # one more solve on the host-driven loop with CUDA events around every
     # finest-level sweep, for the roofline of the dominant kernel
-    _, st_prof, _ = timed("mixed", 1, 0, profile=True, inner=st_mixed[0].inner_vcycles)
+    _, st_prof, _ = timed("mixed", 1, 0, profile=True, inner=st_mixed[0])
     ms_fp64, st_fp64 = None, None
     if a.fp64_steps > 0:
         ms_fp64, st_fp64, _ = timed("fp64", a.fp64_steps, a.fp64_warmup)
@@ -380,7 +381,7 @@ def run_gb300(a):
         "config": _config(a, W),
         "solve": {"precision": "mixed", "status": _status_name(s0.status),
                   "steps_per_solve": s0.steps, "vcycles_per_solve": s0.vcycles,
-                  "inner_vcycles_used": s0.inner_vcycles,
+                  "inner_vcycles_used": s0.inner_vcycles, "nu_used": [s0.nu1, s0.nu2],
                   "coarse_levels": "per-face coefficients" if resolved_params(
                       (n, n, n), precision="mixed", **{k: v for k, v in mg_kw.items()
                                                         if k != "tune_inner"}).coarse_faces
