@@ -93,7 +93,7 @@ def delta_E(psi, box):
     div = np.zeros((n, n, n // 2 + 1), dtype=complex)
     for a in range(3):
         div += 1j * kv[a] * np.fft.rfftn(psi[a])
-    return -np.fft.irfftn(div, s=(n, n, n))
+    return -np.fft.irfftn(div, s=(n, n, n), axes=(0, 1, 2))
 
 
 def displacement_from_positions(pos, n, box):
