@@ -130,7 +130,8 @@ __global__ void k_deposit_particles(Dims d, int64_t np, const double* __restrict
     if (p >= np) return;
     // the position wrapped into [0, n) grid units, then as fixed_axis does
     // for an offset from node 0 (the same integer charges as the tracers')
-    auto wrap = [](double x, int n) { return x - (double)n * floor(x / (double)n); };
+    // (x * inv_pow2(n) is x / n exactly: n is a power of two)
+    auto wrap = [](double x, int n) { return x - (double)n * floor(x * inv_pow2(n)); };
     CicCharges q;
     unsigned long long fx, fy, fz;
     fixed_axis(0, wrap(pos[3 * p] * inv_h, d.n0), q.i0, fx);
