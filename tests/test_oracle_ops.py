@@ -301,6 +301,26 @@ def test_step_limiter_closed_form():
     assert al * gmax <= 0.3 < 2 * al * gmax
 
 
+def test_step_limiter_closed_form_with_cross_terms():
+    """dphi = A cos(2 pi (i + j + k) / N), phi = 0: every Hessian has equal
+    diagonal entries D cos(theta) and equal off-diagonal ones O cos(theta)
+    (D = -4 A sin^2(pi/N) from the 3-point second difference, O = -A
+    sin^2(2 pi/N) from the 4-point cross difference), so the eigenvalues of
+    I + alpha H are 1 + alpha cos(theta) (D - O) (twice) and 1 + alpha
+    cos(theta) (D + 2 O); the smallest, at theta = 0, is 1 - alpha c with
+    c = A (4 sin^2(pi/N) + 2 sin^2(2 pi/N)).  Sylvester's criterion must use
+    every off-diagonal entry to find it."""
+    N = 16
+    n = (N, N, N)
+    i, j, k = np.indices(n)
+    c1 = 4 * np.sin(np.pi / N) ** 2 + 2 * np.sin(2 * np.pi / N) ** 2
+    for target in (1.0, 0.25, 0.0625):
+        A = 0.75 * (1 - 0.01) / (c1 * target)
+        dphi = A * np.cos(2 * np.pi * (i + j + k) / N)
+        p = O.OracleParams(n=n, d_max=1e9)
+        assert O.step_limiter(p, np.zeros(n), dphi) == target
+
+
 # ----------------------------------------------------------------- advance
 
 def test_advance_closed_form():
